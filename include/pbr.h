@@ -1,0 +1,183 @@
+/*
+ * pbr.h -- C ABI of libpbr.so, the GB300 (sm_103a) point-splat renderer.
+ *
+ * The renderer implements the differentiable splatting of Zhang et al.,
+ * "Differentiable Point-Based Radiance Fields for Efficient View Synthesis"
+ * (SIGGRAPH Asia 2022):
+ *   Sec. 3.1, Eq. 1    projection p = (M (R P + t))v of every point;
+ *   Sec. 3.1, Eqs. 2-4 per-point SH colour c = sum_lm h_lm Y_lm(v), with the
+ *                      view direction v = (R P + t)/|R P + t| (Eq. 3);
+ *   Sec. 3.2, Eq. 5    image-space Gaussian kernel per point and pixel;
+ *   Sec. 3.2, Eqs. 6-7 depth sort and front-to-back alpha blending, limited
+ *                      to points within a cutoff distance of the pixel;
+ *   Sec. 3.3           gradients of the image w.r.t. positions and SH
+ *                      coefficients for end-to-end training.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an int status: PBR_OK (0) or a negative
+ *     PBR_ERR_* code; pbr_last_error() returns a message for the calling
+ *     thread.  No C++ exception crosses this boundary.
+ *   - Point arrays, images and gradient buffers are DEVICE pointers owned by
+ *     the caller (fp32, C-contiguous); cameras and options are HOST structs.
+ *     The caller keeps the point arrays alive and unchanged between a forward
+ *     call and the backward call that uses its state.
+ *   - The library owns the context, the forward state, graphs and resident
+ *     scenes; each has a matching destroy/free call.
+ *   - Work is enqueued on the given cudaStream_t (NULL = legacy default
+ *     stream).  Calls return when the work is enqueued, except where a
+ *     comment says the call synchronises.
+ *   - Images are packed per view in view order: view v occupies
+ *     [pix_base(v), pix_base(v) + H_v W_v) pixels of 3 floats (RGB),
+ *     row-major, pixel (0,0) at the top-left.
+ *
+ * Camera model (Sec. 3.1): X = R P + t (R row-major, world -> camera), the
+ * camera looks down +z, x right, y down; pixel centres at (x+0.5, y+0.5);
+ * p = (fx X.x/X.z + cx, fy X.y/X.z + cy).
+ */
+#ifndef PBR_H
+#define PBR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *pbr_stream_t; /* same type as cudaStream_t */
+
+enum {
+    PBR_OK = 0,
+    PBR_ERR_INVALID_ARG = -1,
+    PBR_ERR_OOM = -2,
+    PBR_ERR_CUDA = -3,
+    PBR_ERR_CAPACITY = -4,
+    PBR_ERR_TIMEOUT = -5,
+    PBR_ERR_DEVICE_STATUS = -6,
+    PBR_ERR_NOT_FOUND = -7,
+    PBR_ERR_BUSY = -8
+};
+
+typedef struct pbr_ctx pbr_ctx;
+typedef struct pbr_state pbr_state;
+typedef struct pbr_graph pbr_graph;
+
+/* One pinhole camera (Sec. 3.1, Eq. 1: intrinsics M = (fx, fy, cx, cy),
+ * extrinsics (R, t)) and the size of the image it renders. */
+typedef struct {
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    int32_t width, height;
+} pbr_camera;
+
+/* Renderer options.  pbr_default_opts() fills the defaults listed here. */
+typedef struct {
+    int32_t radius_mode;   /* 0 (default): kernel width s = fx * r / z pixels;
+                              1: s = r * min(W, H) / 2 (fixed image-space radius) */
+    int32_t dir_frame;     /* 0 (default): SH direction in the camera frame as in
+                              Sec. 3.1 Eq. 3; 1: world-frame direction R^T v */
+    float cutoff_k;        /* cutoff radius = cutoff_k * s (default 3) */
+    float alpha_max;       /* alpha = min(alpha_max, o * G), default 0.99, < 1 */
+    float t_eps;           /* stop once transmittance < t_eps (default 1e-5) */
+    int32_t max_per_pixel; /* composite at most this many points (0 = no cap) */
+    float bg[3];           /* background colour (default 0) */
+    float z_near;          /* points with z <= z_near are culled (default 0.01) */
+    int32_t tile_w, tile_h;/* tile size: 8x8, 16x16 (default) or 16x32 */
+    int32_t batch_depth;   /* points staged per block batch: 64..512 (default 256) */
+    int32_t reserved[4];
+} pbr_render_opts;
+
+/* One scene: n points with position [n,3], SH coefficients [n,K,3]
+ * (K = (sh_degree+1)^2, coefficient k = l*l + l + m, RGB innermost),
+ * kernel amplitude (opacity) [n] and radius [n].  Device pointers. */
+typedef struct {
+    const float *pos;
+    const float *sh;
+    const float *opacity;
+    const float *radius;
+    int64_t n;
+    int32_t sh_degree; /* 0..3 */
+    int32_t reserved;
+} pbr_points;
+
+/* Sizes of one forward pass (filled by pbr_state_info). */
+typedef struct {
+    int64_t n_point_views; /* sum over views of the scene's point count */
+    int64_t n_visible;     /* point-views that survive culling */
+    int64_t n_pairs;       /* (tile, point-view) pairs after binning */
+    int64_t n_tiles;       /* tiles over all views */
+    int64_t n_pixels;      /* pixels over all views */
+    /* device pointers into the state (valid until pbr_state_free) */
+    const uint32_t *tile_keys;  /* [n_pairs] global tile id, sorted */
+    const uint32_t *tile_vals;  /* [n_pairs] point-view id, (tile, depth, id) order */
+    const uint32_t *ranges;     /* [n_tiles][2] start, end into the lists */
+    const float *records;       /* [n_point_views][8] px, py, q', o, r, g, b, rc^2 */
+    const uint32_t *ntiles;     /* [n_point_views] tiles covered (0 = culled) */
+    const float *T_final;       /* [n_pixels] transmittance after compositing */
+    const uint32_t *n_contrib;  /* [n_pixels] list position after the last composited point */
+} pbr_state_info_t;
+
+/* ---------------------------------------------------------------- context */
+/* Creates a context on CUDA device `device`.  hbm_budget_bytes bounds the
+ * memory the serving loop may hold for in-flight requests (0 = 80% of free
+ * device memory at creation). */
+int pbr_create(pbr_ctx **out, int device, size_t hbm_budget_bytes);
+int pbr_destroy(pbr_ctx *ctx);
+/* Message for the last error on the calling thread ("" if none). */
+const char *pbr_last_error(void);
+void pbr_default_opts(pbr_render_opts *opts);
+/* Library version string and the compiled SM architecture. */
+const char *pbr_version(void);
+
+/* ---------------------------------------------------------------- render */
+/* Forward pass (Sec. 3.1 Eqs. 1-4, Sec. 3.2 Eqs. 5-7) of n_cams views in
+ * one batch.  Views may belong to different scenes: scene_of_view[v] (host
+ * array, NULL = all views of scene 0) picks scenes[]; a multi-frame video is
+ * n_scenes = frames.  out_rgb: device [sum_v H_v W_v, 3] fp32.
+ * state_out: when non-NULL receives the state the backward pass needs (owned
+ * by the library; free with pbr_state_free); when NULL the pass is
+ * forward-only and keeps nothing.  Synchronises the stream once (to size the
+ * tile lists).  Errors: INVALID_ARG (bad sizes, degree, options), OOM,
+ * CUDA, DEVICE_STATUS (a kernel flagged an inconsistent count). */
+int pbr_render_forward(pbr_ctx *ctx, const pbr_points *scenes, int32_t n_scenes,
+                       const int32_t *scene_of_view, const pbr_camera *cams, int32_t n_cams,
+                       const pbr_render_opts *opts, float *out_rgb, pbr_state **state_out,
+                       pbr_stream_t stream);
+
+/* Backward pass (Sec. 3.3) for L with dL/dI = grad_rgb (device, packed like
+ * out_rgb).  Gradients are OVERWRITTEN, packed over scenes in scene order:
+ * grad_pos [sum_s n_s, 3], grad_sh [sum_s n_s K_s 3], grad_opacity [sum_s n_s]
+ * (nullable).  Does not synchronise. */
+int pbr_render_backward(pbr_ctx *ctx, pbr_state *state, const float *grad_rgb, float *grad_pos,
+                        float *grad_sh, float *grad_opacity, pbr_stream_t stream);
+int pbr_state_free(pbr_ctx *ctx, pbr_state *state);
+/* Sizes and device pointers of a forward state (for inspection and tests).
+ * Synchronises the state's stream. */
+int pbr_state_info(pbr_state *state, pbr_state_info_t *info);
+
+/* Copies one array of a forward state into host memory (inspection and
+ * tests).  which: 0 tile keys, 1 tile values (point-view ids), 2 ranges,
+ * 3 records, 4 tile counts, 5 T_final, 6 n_contrib.  Copies
+ * min(cap_bytes, size) bytes; *size_bytes receives the full size.
+ * Synchronises the state's stream. */
+int pbr_state_read(pbr_state *state, int32_t which, void *host_dst, size_t cap_bytes,
+                   size_t *size_bytes);
+
+/* Image loss used by the training step: kind 0 = sum of squared errors
+ * (Sec. 3.3 Eq. 8, data term), kind 1 = sum of absolute errors.  Writes
+ * dL/dpred into grad (device, n floats) and adds the loss to *loss_dev
+ * (device double, caller zeroes it). */
+int pbr_image_loss(int32_t kind, const float *pred, const float *target, int64_t n, float *grad,
+                   double *loss_dev, pbr_stream_t stream);
+
+/* ------------------------------------------------------- microbenchmarks */
+/* Measures the device's FP32 FMA rate (flop/s, an FMA counted as 2) and
+ * MUFU ex2 rate (op/s) with the library's own kernels; used as the ALU
+ * roofline of the raster kernels.  Synchronises. */
+int pbr_measure_alu_peaks(int device, double *fp32_flops, double *ex2_ops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PBR_H */

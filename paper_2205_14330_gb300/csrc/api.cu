@@ -1,0 +1,464 @@
+// C ABI of libpbr (declared in include/pbr.h): argument checking, batch
+// layout, workspace management and the launch sequence of the forward and
+// backward passes of the point-splat renderer (Sec. 3.1-3.3).
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pbr.h"
+#include "pbr_internal.cuh"
+#include "api_internal.h"
+
+using namespace pbr;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+int pbr::set_error(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+extern "C" const char *pbr_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char *pbr_version(void) { return "pbr 0.1 (sm_103a)"; }
+
+extern "C" void pbr_default_opts(pbr_render_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->radius_mode = 0;
+    o->dir_frame = 0;
+    o->cutoff_k = 3.0f;
+    o->alpha_max = 0.99f;
+    o->t_eps = 1e-5f;
+    o->max_per_pixel = 0;
+    o->z_near = 0.01f;
+    o->tile_w = 16;
+    o->tile_h = 16;
+    o->batch_depth = 256;
+}
+
+// ---------------------------------------------------------------- context
+extern "C" int pbr_create(pbr_ctx **out, int device, size_t hbm_budget_bytes)
+{
+    if (!out) return set_error(PBR_ERR_INVALID_ARG, "pbr_create: out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return set_error(PBR_ERR_INVALID_ARG, "pbr_create: no CUDA device %d", device);
+    PBR_CUDA(cudaSetDevice(device));
+    pbr_ctx *c = new pbr_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    c->hbm_budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.8 * (double)free_b);
+    // keep freed stream-ordered allocations cached in the device pool
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    if (cudaMallocHost(&c->host_counters, 64) != cudaSuccess) {
+        delete c;
+        return set_error(PBR_ERR_OOM, "pbr_create: pinned host buffer");
+    }
+    *out = c;
+    return PBR_OK;
+}
+
+extern "C" int pbr_destroy(pbr_ctx *c)
+{
+    if (!c) return PBR_OK;
+    serve_shutdown(c);
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    if (c->host_counters) cudaFreeHost(c->host_counters);
+    delete c;
+    return PBR_OK;
+}
+
+// ----------------------------------------------------------- validation
+int pbr::check_opts(const pbr_render_opts *o)
+{
+    if (!o) return set_error(PBR_ERR_INVALID_ARG, "opts is NULL");
+    const bool tile_ok = (o->tile_w == 8 && o->tile_h == 8) || (o->tile_w == 16 && o->tile_h == 16) ||
+                         (o->tile_w == 16 && o->tile_h == 32);
+    if (!tile_ok) return set_error(PBR_ERR_INVALID_ARG, "tile must be 8x8, 16x16 or 16x32");
+    if (o->batch_depth < 32 || o->batch_depth > 1024 || (o->batch_depth & 31))
+        return set_error(PBR_ERR_INVALID_ARG, "batch_depth must be a multiple of 32 in [32,1024]");
+    if (!(o->alpha_max > 0.f && o->alpha_max < 1.f))
+        return set_error(PBR_ERR_INVALID_ARG, "alpha_max must be in (0,1)");
+    if (!(o->t_eps >= 0.f) || !(o->cutoff_k > 0.f) || o->max_per_pixel < 0)
+        return set_error(PBR_ERR_INVALID_ARG, "t_eps >= 0, cutoff_k > 0, max_per_pixel >= 0");
+    if (o->radius_mode < 0 || o->radius_mode > 1 || o->dir_frame < 0 || o->dir_frame > 1)
+        return set_error(PBR_ERR_INVALID_ARG, "radius_mode and dir_frame are 0 or 1");
+    return PBR_OK;
+}
+
+DevOpts pbr::dev_opts(const pbr_render_opts *o)
+{
+    DevOpts d;
+    d.radius_mode = o->radius_mode;
+    d.dir_frame = o->dir_frame;
+    d.cutoff_k = o->cutoff_k;
+    d.alpha_max = o->alpha_max;
+    d.t_eps = o->t_eps;
+    d.max_per_pixel = o->max_per_pixel;
+    for (int i = 0; i < 3; ++i) d.bg[i] = o->bg[i];
+    d.z_near = o->z_near;
+    d.tile_w = o->tile_w;
+    d.tile_h = o->tile_h;
+    return d;
+}
+
+int pbr::build_layout(const pbr_points *scenes, int32_t n_scenes, const int32_t *scene_of_view,
+                      const pbr_camera *cams, int32_t n_cams, const pbr_render_opts *o,
+                      HostLayout &L)
+{
+    if (n_scenes <= 0 || !scenes) return set_error(PBR_ERR_INVALID_ARG, "no scenes");
+    if (n_cams <= 0 || !cams) return set_error(PBR_ERR_INVALID_ARG, "no cameras");
+    L.views.resize(n_cams);
+    L.scenes.resize(n_scenes);
+    int64_t pbase = 0, shbase = 0, blk = 0;
+    for (int s = 0; s < n_scenes; ++s) {
+        const pbr_points &p = scenes[s];
+        if (p.n < 0 || p.sh_degree < 0 || p.sh_degree > 3)
+            return set_error(PBR_ERR_INVALID_ARG, "scene %d: n >= 0 and sh_degree in 0..3", s);
+        if (p.n > 0 && (!p.pos || !p.sh || !p.opacity || !p.radius))
+            return set_error(PBR_ERR_INVALID_ARG, "scene %d: NULL point array", s);
+        DevScene &d = L.scenes[s];
+        d.pos = p.pos;
+        d.sh = p.sh;
+        d.opacity = p.opacity;
+        d.radius = p.radius;
+        d.n = p.n;
+        d.deg = p.sh_degree;
+        d.K = (p.sh_degree + 1) * (p.sh_degree + 1);
+        d.point_base = pbase;
+        d.sh_base = shbase;
+        d.block_begin = blk;
+        d.view_begin = 0;
+        d.view_count = 0;
+        pbase += p.n;
+        shbase += p.n * d.K * 3;
+    }
+    std::vector<int32_t> sov(n_cams, 0);
+    for (int v = 0; v < n_cams; ++v) {
+        sov[v] = scene_of_view ? scene_of_view[v] : 0;
+        if (sov[v] < 0 || sov[v] >= n_scenes)
+            return set_error(PBR_ERR_INVALID_ARG, "scene_of_view[%d] out of range", v);
+    }
+    // view list grouped by scene (stable)
+    L.view_list.resize(n_cams);
+    for (int v = 0; v < n_cams; ++v) L.view_list[v] = v;
+    std::stable_sort(L.view_list.begin(), L.view_list.end(),
+                     [&](int a, int b) { return sov[a] < sov[b]; });
+    for (int j = 0; j < n_cams; ++j) {
+        DevScene &d = L.scenes[sov[L.view_list[j]]];
+        if (d.view_count == 0) d.view_begin = j;
+        d.view_count++;
+    }
+    // point-parallel grid: every scene with views gets ceil(n/PRE_THREADS) blocks
+    for (int s = 0; s < n_scenes; ++s) {
+        DevScene &d = L.scenes[s];
+        d.block_begin = blk;
+        if (d.view_count > 0) blk += (d.n + PRE_THREADS - 1) / PRE_THREADS;
+    }
+    L.n_point_blocks = blk;
+    int64_t pv = 0, pix = 0;
+    uint64_t tiles = 0;
+    for (int v = 0; v < n_cams; ++v) {
+        const pbr_camera &c = cams[v];
+        if (c.width <= 0 || c.height <= 0 || c.width > 32768 || c.height > 32768)
+            return set_error(PBR_ERR_INVALID_ARG, "camera %d: size %dx%d", v, c.width, c.height);
+        DevView &d = L.views[v];
+        d.fx = c.fx;
+        d.fy = c.fy;
+        d.cx = c.cx;
+        d.cy = c.cy;
+        std::memcpy(d.R, c.R, sizeof d.R);
+        std::memcpy(d.t, c.t, sizeof d.t);
+        d.W = c.width;
+        d.H = c.height;
+        d.tiles_x = (c.width + o->tile_w - 1) / o->tile_w;
+        d.tiles_y = (c.height + o->tile_h - 1) / o->tile_h;
+        d.tile_base = (uint32_t)tiles;
+        d.scene = sov[v];
+        d.pix_base = pix;
+        d.pv_base = pv;
+        tiles += (uint64_t)d.tiles_x * d.tiles_y;
+        pix += (int64_t)c.width * c.height;
+        pv += scenes[sov[v]].n;
+    }
+    if (pv >= (int64_t)UINT32_MAX || tiles >= UINT32_MAX)
+        return set_error(PBR_ERR_CAPACITY, "batch too large: %lld point-views, %llu tiles",
+                         (long long)pv, (unsigned long long)tiles);
+    L.n_pv = pv;
+    L.n_pix = pix;
+    L.n_tiles = (uint32_t)tiles;
+    L.n_points_total = pbase;
+    L.n_sh_total = shbase;
+    return PBR_OK;
+}
+
+// ------------------------------------------------------------ allocation
+int pbr::dalloc(void **p, size_t bytes, cudaStream_t s)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(PBR_ERR_OOM, "device allocation of %zu bytes failed: %s", bytes,
+                         cudaGetErrorString(e));
+    }
+    return PBR_OK;
+}
+
+void pbr::dfree(void *p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync(p, s);
+}
+
+static int key_bits_for(uint32_t n_keys)
+{
+    int b = 0;
+    while (b < 32 && (n_keys - 1) >> b) ++b;
+    return b < 1 ? 1 : b;
+}
+
+void pbr_state::release()
+{
+    void **all[] = {(void **)&d_views, (void **)&d_scenes, (void **)&d_view_list, (void **)&rec,
+                    (void **)&ntiles, (void **)&counters, (void **)&tile_keys,
+                    (void **)&tile_vals, (void **)&ranges, (void **)&T_final,
+                    (void **)&n_contrib};
+    for (void **p : all) {
+        dfree(*p, stream);
+        *p = nullptr;
+    }
+}
+
+// Runs the forward chain into the state's buffers.  Exact-size workspaces:
+// one host synchronisation after the per-point stage reads the pair count.
+int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s)
+{
+    HostLayout &L = st->layout;
+    const DevOpts &o = st->dopts;
+    // tables
+    PBR_TRY(dalloc((void **)&st->d_views, sizeof(DevView) * L.views.size(), s));
+    PBR_TRY(dalloc((void **)&st->d_scenes, sizeof(DevScene) * L.scenes.size(), s));
+    PBR_TRY(dalloc((void **)&st->d_view_list, sizeof(int32_t) * L.view_list.size(), s));
+    PBR_CUDA(cudaMemcpyAsync(st->d_views, L.views.data(), sizeof(DevView) * L.views.size(),
+                             cudaMemcpyHostToDevice, s));
+    PBR_CUDA(cudaMemcpyAsync(st->d_scenes, L.scenes.data(), sizeof(DevScene) * L.scenes.size(),
+                             cudaMemcpyHostToDevice, s));
+    PBR_CUDA(cudaMemcpyAsync(st->d_view_list, L.view_list.data(),
+                             sizeof(int32_t) * L.view_list.size(), cudaMemcpyHostToDevice, s));
+    Batch b = st->batch();
+    const int64_t npv = L.n_pv;
+    PBR_TRY(dalloc((void **)&st->rec, sizeof(float4) * 2 * npv, s));
+    PBR_TRY(dalloc((void **)&st->ntiles, sizeof(uint32_t) * npv, s));
+    PBR_TRY(dalloc((void **)&st->counters, 64, s));
+    TempBufs tmp(s);
+    uint32_t *zbits = nullptr;
+    uint2 *rect = nullptr;
+    PBR_TRY(tmp.alloc(&zbits, sizeof(uint32_t) * npv));
+    PBR_TRY(tmp.alloc(&rect, sizeof(uint2) * npv));
+    PBR_CUDA(cudaMemsetAsync(st->counters, 0, 64, s));
+    launch_preprocess_fwd(b, o, st->rec, zbits, st->ntiles, rect, st->counters, s);
+    PBR_CUDA(cudaGetLastError());
+    // size the lists
+    PBR_CUDA(cudaMemcpyAsync(c->host_counters, st->counters, 16, cudaMemcpyDeviceToHost, s));
+    PBR_CUDA(cudaStreamSynchronize(s));
+    const uint64_t n_pairs = c->host_counters[0], n_vis = c->host_counters[1];
+    if (n_pairs >= UINT32_MAX) {
+        return set_error(PBR_ERR_CAPACITY, "%llu (tile, point-view) pairs exceed 2^32-1",
+                         (unsigned long long)n_pairs);
+    }
+    st->n_vis = (int64_t)n_vis;
+    st->n_pairs = (int64_t)n_pairs;
+    uint32_t *vk = nullptr, *vv = nullptr, *vk2 = nullptr, *vv2 = nullptr;
+    uint32_t *pk2 = nullptr, *pv2 = nullptr;
+    void *temp = nullptr;
+    const int64_t cap_sort = std::max<int64_t>(n_vis, n_pairs);
+    const size_t temp_bytes = std::max(std::max(scan_temp_bytes(npv), radix_temp_bytes(cap_sort)),
+                                       scan_temp_bytes(n_vis));
+    PBR_TRY(tmp.alloc(&vk, sizeof(uint32_t) * n_vis));
+    PBR_TRY(tmp.alloc(&vv, sizeof(uint32_t) * n_vis));
+    PBR_TRY(tmp.alloc(&vk2, sizeof(uint32_t) * n_vis));
+    PBR_TRY(tmp.alloc(&vv2, sizeof(uint32_t) * n_vis));
+    PBR_TRY(dalloc((void **)&st->tile_keys, sizeof(uint32_t) * n_pairs, s));
+    PBR_TRY(dalloc((void **)&st->tile_vals, sizeof(uint32_t) * n_pairs, s));
+    PBR_TRY(tmp.alloc(&pk2, sizeof(uint32_t) * n_pairs));
+    PBR_TRY(tmp.alloc(&pv2, sizeof(uint32_t) * n_pairs));
+    PBR_TRY(dalloc((void **)&st->ranges, sizeof(uint2) * L.n_tiles, s));
+    PBR_TRY(dalloc((void **)&st->T_final, sizeof(float) * L.n_pix, s));
+    PBR_TRY(dalloc((void **)&st->n_contrib, sizeof(uint32_t) * L.n_pix, s));
+    PBR_TRY(tmp.alloc(&temp, temp_bytes));
+    uint32_t *status = (uint32_t *)((char *)st->counters + 32);
+    const uint32_t *n_vis_dev = (const uint32_t *)(st->counters + 1);  // low word (< 2^32)
+    const uint32_t *n_pairs_dev = (const uint32_t *)(st->counters + 0); // low word (< 2^32)
+    // 1. visible point-views with their depth keys, in point-view order
+    launch_compact_visible(st->ntiles, zbits, npv, vk, vv, nullptr, temp, s);
+    // 2. stable sort by fp32 depth bits
+    radix_sort_pairs(vk, vv, vk2, vv2, n_vis_dev, (int64_t)n_vis, 32, temp, s);
+    // 3. duplicate per covered tile, in depth order
+    uint32_t *tk = st->tile_keys, *tv = st->tile_vals;
+    launch_emit_pairs(b, o, vv, n_vis_dev, (int64_t)n_vis, st->ntiles, rect, tk, tv,
+                      (int64_t)n_pairs, status, temp, s);
+    // 4. stable sort by tile id
+    radix_sort_pairs(tk, tv, pk2, pv2, n_pairs_dev, (int64_t)n_pairs, key_bits_for(L.n_tiles),
+                     temp, s);
+    if (tk != st->tile_keys) { // result landed in the alternate buffers: swap ownership
+        for (void *&p : tmp.ptrs) {
+            if (p == (void *)tk) p = (void *)st->tile_keys;
+            else if (p == (void *)tv) p = (void *)st->tile_vals;
+        }
+        st->tile_keys = tk;
+        st->tile_vals = tv;
+    }
+    // 5. per-tile ranges
+    PBR_CUDA(cudaMemsetAsync(st->ranges, 0, sizeof(uint2) * L.n_tiles, s));
+    launch_tile_ranges(st->tile_keys, n_pairs_dev, (int64_t)n_pairs, st->ranges, L.n_tiles, s);
+    // 6. composite
+    launch_raster_fwd(b, o, st->batch_depth, st->ranges, st->tile_vals, st->rec, out_rgb,
+                      st->T_final, st->n_contrib, s);
+    PBR_CUDA(cudaGetLastError());
+    return PBR_OK;
+}
+
+extern "C" int pbr_render_forward(pbr_ctx *c, const pbr_points *scenes, int32_t n_scenes,
+                                  const int32_t *scene_of_view, const pbr_camera *cams,
+                                  int32_t n_cams, const pbr_render_opts *opts, float *out_rgb,
+                                  pbr_state **state_out, pbr_stream_t stream)
+{
+    if (state_out) *state_out = nullptr;
+    if (!c) return set_error(PBR_ERR_INVALID_ARG, "ctx is NULL");
+    PBR_TRY(check_opts(opts));
+    if (!out_rgb) return set_error(PBR_ERR_INVALID_ARG, "out_rgb is NULL");
+    PBR_CUDA(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    pbr_state *st = new pbr_state();
+    st->stream = s;
+    st->opts = *opts;
+    st->dopts = dev_opts(opts);
+    st->batch_depth = opts->batch_depth;
+    int rc = build_layout(scenes, n_scenes, scene_of_view, cams, n_cams, opts, st->layout);
+    if (rc == PBR_OK) rc = forward_eager(c, st, out_rgb, s);
+    if (rc != PBR_OK || !state_out) {
+        st->release();
+        delete st;
+        return rc;
+    }
+    *state_out = st;
+    return PBR_OK;
+}
+
+extern "C" int pbr_render_backward(pbr_ctx *c, pbr_state *st, const float *grad_rgb,
+                                   float *grad_pos, float *grad_sh, float *grad_opacity,
+                                   pbr_stream_t stream)
+{
+    if (!c || !st) return set_error(PBR_ERR_INVALID_ARG, "ctx or state is NULL");
+    if (!grad_rgb || !grad_pos || !grad_sh)
+        return set_error(PBR_ERR_INVALID_ARG, "grad_rgb, grad_pos and grad_sh are required");
+    PBR_CUDA(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const HostLayout &L = st->layout;
+    Batch b = st->batch();
+    float4 *g2d = nullptr;
+    PBR_TRY(dalloc((void **)&g2d, sizeof(float4) * 2 * L.n_pv, s));
+    PBR_CUDA(cudaMemsetAsync(g2d, 0, sizeof(float4) * 2 * L.n_pv, s));
+    launch_raster_bwd(b, st->dopts, st->batch_depth, st->ranges, st->tile_vals, st->rec,
+                      st->T_final, st->n_contrib, grad_rgb, g2d, s);
+    launch_preprocess_bwd(b, st->dopts, g2d, grad_pos, grad_sh, grad_opacity, s);
+    cudaError_t e = cudaGetLastError();
+    dfree(g2d, s);
+    if (e != cudaSuccess)
+        return set_error(PBR_ERR_CUDA, "backward launch: %s", cudaGetErrorString(e));
+    return PBR_OK;
+}
+
+extern "C" int pbr_state_free(pbr_ctx *c, pbr_state *st)
+{
+    (void)c;
+    if (!st) return PBR_OK;
+    st->release();
+    delete st;
+    return PBR_OK;
+}
+
+extern "C" int pbr_state_info(pbr_state *st, pbr_state_info_t *info)
+{
+    if (!st || !info) return set_error(PBR_ERR_INVALID_ARG, "state or info is NULL");
+    PBR_CUDA(cudaStreamSynchronize(st->stream));
+    uint32_t status = 0;
+    PBR_CUDA(cudaMemcpy(&status, (char *)st->counters + 32, 4, cudaMemcpyDeviceToHost));
+    std::memset(info, 0, sizeof *info);
+    info->n_point_views = st->layout.n_pv;
+    info->n_visible = st->n_vis;
+    info->n_pairs = st->n_pairs;
+    info->n_tiles = st->layout.n_tiles;
+    info->n_pixels = st->layout.n_pix;
+    info->tile_keys = st->tile_keys;
+    info->tile_vals = st->tile_vals;
+    info->ranges = (const uint32_t *)st->ranges;
+    info->records = (const float *)st->rec;
+    info->ntiles = st->ntiles;
+    info->T_final = st->T_final;
+    info->n_contrib = st->n_contrib;
+    if (status) return set_error(PBR_ERR_DEVICE_STATUS, "device status 0x%x", status);
+    return PBR_OK;
+}
+
+extern "C" int pbr_state_read(pbr_state *st, int32_t which, void *host_dst, size_t cap_bytes,
+                              size_t *size_bytes)
+{
+    if (!st) return set_error(PBR_ERR_INVALID_ARG, "state is NULL");
+    const void *src = nullptr;
+    size_t n = 0;
+    const HostLayout &L = st->layout;
+    switch (which) {
+    case 0: src = st->tile_keys; n = 4 * (size_t)st->n_pairs; break;
+    case 1: src = st->tile_vals; n = 4 * (size_t)st->n_pairs; break;
+    case 2: src = st->ranges; n = 8 * (size_t)L.n_tiles; break;
+    case 3: src = st->rec; n = 32 * (size_t)L.n_pv; break;
+    case 4: src = st->ntiles; n = 4 * (size_t)L.n_pv; break;
+    case 5: src = st->T_final; n = 4 * (size_t)L.n_pix; break;
+    case 6: src = st->n_contrib; n = 4 * (size_t)L.n_pix; break;
+    default: return set_error(PBR_ERR_INVALID_ARG, "pbr_state_read: unknown array %d", which);
+    }
+    if (size_bytes) *size_bytes = n;
+    PBR_CUDA(cudaStreamSynchronize(st->stream));
+    const size_t m = n < cap_bytes ? n : cap_bytes;
+    if (m && host_dst && src) PBR_CUDA(cudaMemcpy(host_dst, src, m, cudaMemcpyDeviceToHost));
+    return PBR_OK;
+}
+
+extern "C" int pbr_image_loss(int32_t kind, const float *pred, const float *target, int64_t n,
+                              float *grad, double *loss_dev, pbr_stream_t stream)
+{
+    if ((kind != 0 && kind != 1) || n < 0 || (n > 0 && (!pred || !target || !grad || !loss_dev)))
+        return set_error(PBR_ERR_INVALID_ARG, "pbr_image_loss: bad arguments");
+    launch_image_loss(kind, pred, target, n, grad, loss_dev, (cudaStream_t)stream);
+    PBR_CUDA(cudaGetLastError());
+    return PBR_OK;
+}
+
+extern "C" int pbr_measure_alu_peaks(int device, double *fp32_flops, double *ex2_ops)
+{
+    if (measure_alu_peaks(device, fp32_flops, ex2_ops) != 0)
+        return set_error(PBR_ERR_CUDA, "microbenchmark failed");
+    return PBR_OK;
+}

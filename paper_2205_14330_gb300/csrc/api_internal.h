@@ -1,0 +1,116 @@
+// Host-side objects behind the opaque handles of pbr.h.
+#pragma once
+
+#include <cstdarg>
+#include <cstdint>
+#include <vector>
+
+#include "pbr.h"
+#include "pbr_internal.cuh"
+
+struct ServeState; // serving loop (serve.cu)
+
+struct pbr_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t hbm_budget = 0;
+    unsigned long long *host_counters = nullptr; // pinned
+    ServeState *serve = nullptr;
+};
+
+namespace pbr {
+
+struct HostLayout {
+    std::vector<DevView> views;
+    std::vector<DevScene> scenes;
+    std::vector<int32_t> view_list;
+    int64_t n_pv = 0, n_pix = 0, n_point_blocks = 0;
+    int64_t n_points_total = 0, n_sh_total = 0;
+    uint32_t n_tiles = 0;
+};
+
+int set_error(int code, const char *fmt, ...);
+int check_opts(const pbr_render_opts *o);
+DevOpts dev_opts(const pbr_render_opts *o);
+int build_layout(const pbr_points *scenes, int32_t n_scenes, const int32_t *scene_of_view,
+                 const pbr_camera *cams, int32_t n_cams, const pbr_render_opts *o, HostLayout &L);
+int dalloc(void **p, size_t bytes, cudaStream_t s);
+void dfree(void *p, cudaStream_t s);
+void serve_shutdown(pbr_ctx *c);
+
+} // namespace pbr
+
+struct pbr_state {
+    cudaStream_t stream = nullptr;
+    pbr_render_opts opts{};
+    pbr::DevOpts dopts{};
+    int batch_depth = 256;
+    pbr::HostLayout layout;
+    int64_t n_vis = 0, n_pairs = 0;
+    // device buffers kept for the backward pass (all freed by release())
+    pbr::DevView *d_views = nullptr;
+    pbr::DevScene *d_scenes = nullptr;
+    int32_t *d_view_list = nullptr;
+    float4 *rec = nullptr;
+    uint32_t *ntiles = nullptr;
+    unsigned long long *counters = nullptr; // [0] pairs, [1] visible, byte 32: status
+    uint32_t *tile_keys = nullptr, *tile_vals = nullptr;
+    uint2 *ranges = nullptr;
+    float *T_final = nullptr;
+    uint32_t *n_contrib = nullptr;
+
+    pbr::Batch batch() const
+    {
+        pbr::Batch b;
+        b.views = d_views;
+        b.scenes = d_scenes;
+        b.view_list = d_view_list;
+        b.n_views = (int32_t)layout.views.size();
+        b.n_scenes = (int32_t)layout.scenes.size();
+        b.n_pv = layout.n_pv;
+        b.n_tiles = layout.n_tiles;
+        b.n_pix = layout.n_pix;
+        b.n_point_blocks = layout.n_point_blocks;
+        return b;
+    }
+    void release();
+};
+
+namespace pbr {
+// Temporaries of one call, freed (stream-ordered) when the call returns.
+struct TempBufs {
+    cudaStream_t s;
+    std::vector<void *> ptrs;
+    explicit TempBufs(cudaStream_t st) : s(st) {}
+    ~TempBufs()
+    {
+        for (void *p : ptrs) dfree(p, s);
+    }
+    template <class T> int alloc(T **p, size_t bytes)
+    {
+        int rc = dalloc((void **)p, bytes, s);
+        if (rc == PBR_OK) ptrs.push_back((void *)*p);
+        return rc;
+    }
+};
+} // namespace pbr
+
+namespace pbr {
+int forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s);
+}
+
+#define PBR_CUDA(x)                                                                             \
+    do {                                                                                        \
+        cudaError_t e_ = (x);                                                                   \
+        if (e_ != cudaSuccess) {                                                                \
+            cudaGetLastError();                                                                 \
+            return pbr::set_error(PBR_ERR_CUDA, "%s:%d %s: %s", __FILE__, __LINE__, #x,         \
+                                  cudaGetErrorString(e_));                                      \
+        }                                                                                       \
+    } while (0)
+
+#define PBR_TRY(x)                                                                              \
+    do {                                                                                        \
+        int r_ = (x);                                                                           \
+        if (r_ != PBR_OK) return r_;                                                            \
+    } while (0)

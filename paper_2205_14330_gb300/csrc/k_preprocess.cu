@@ -1,0 +1,313 @@
+// Per-point stages of the renderer.
+//
+// preprocess_fwd (Sec. 3.1 Eqs. 1-4, Sec. 3.2 cutoff): one thread per point,
+// looping over every view of the point's scene, so position, radius,
+// opacity and the [K,3] SH block are read from HBM once per batch.  For each
+// (view, point) it writes a 32-byte record {px, py, q', o, r, g, b, rc^2},
+// the fp32 depth bits, the covered tile rectangle and the tile count.
+//
+// The discrete decisions (cull, cutoff radius, pixel box, tile rectangle,
+// depth key) use IEEE fp32 round-to-nearest operations with no
+// contraction, in a fixed order, so they can be reproduced exactly:
+//   X_a = ((R_a0 P0 + R_a1 P1) + R_a2 P2) + t_a
+//   px = fx (X0 / X2) + cx,   py = fy (X1 / X2) + cy
+//   s  = (fx r) / X2  (radius_mode 0)  or  (r min(W,H)) 0.5  (mode 1)
+//   rc = cutoff_k s,  rc2 = rc rc
+//   pixel box: [floor(px - rc) - 1, ceil(px + rc)] clamped to the image.
+//
+// preprocess_bwd (Sec. 3.3): one thread per point; per view it chains the
+// screen-space adjoint {dpx, dpy, dq, do, dr, dg, db} (q = 1/s^2) through the
+// kernel width, the projection, the direction normalisation and the SH basis
+// back to the point position, SH coefficients and opacity.  Views are
+// visited in a fixed order, so the result does not depend on scheduling.
+#include "pbr_internal.cuh"
+#include "sh.cuh"
+
+namespace pbr {
+
+namespace {
+
+__device__ __forceinline__ int find_scene(const Batch &b, int64_t block)
+{
+    int s = 0;
+    for (int j = 1; j < b.n_scenes; ++j)
+        if (b.scenes[j].block_begin <= block) s = j;
+    return s;
+}
+
+// Cooperative, coalesced copy of the block's SH coefficients into shared
+// memory (the per-thread slice is then read with a stride of K*3 floats).
+__device__ __forceinline__ void stage_sh(const float *__restrict__ sh, int64_t first, int count,
+                                         int K3, float *s_sh)
+{
+    const int64_t base = first * K3;
+    const int total = count * K3;
+    for (int j = threadIdx.x; j < total; j += blockDim.x) s_sh[j] = __ldg(sh + base + j);
+}
+
+template <int DEG>
+__device__ void pre_fwd_point(const Batch &b, const DevOpts &o, const DevScene &sc, int64_t i,
+                              const float *hs, float4 *__restrict__ rec,
+                              uint32_t *__restrict__ zbits, uint32_t *__restrict__ ntiles,
+                              uint2 *__restrict__ rect, uint32_t &vis_cnt, uint32_t &pair_cnt)
+{
+    constexpr int K = SH<DEG>::K;
+    float h[K * 3];
+#pragma unroll
+    for (int j = 0; j < K * 3; ++j) h[j] = hs[j];
+    const float P0 = __ldg(sc.pos + 3 * i), P1 = __ldg(sc.pos + 3 * i + 1),
+                P2 = __ldg(sc.pos + 3 * i + 2);
+    const float r = __ldg(sc.radius + i);
+    const float op = __ldg(sc.opacity + i);
+
+    for (int vv = 0; vv < sc.view_count; ++vv) {
+        const int v = b.view_list[sc.view_begin + vv];
+        const DevView &V = b.views[v];
+        const int64_t pv = V.pv_base + i;
+        float X[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float s = __fmul_rn(V.R[3 * a], P0);
+            s = __fadd_rn(s, __fmul_rn(V.R[3 * a + 1], P1));
+            s = __fadd_rn(s, __fmul_rn(V.R[3 * a + 2], P2));
+            X[a] = __fadd_rn(s, V.t[a]);
+        }
+        const float z = X[2];
+        uint32_t nt = 0;
+        if (z > o.z_near) {
+            const float px = __fadd_rn(__fmul_rn(V.fx, __fdiv_rn(X[0], z)), V.cx);
+            const float py = __fadd_rn(__fmul_rn(V.fy, __fdiv_rn(X[1], z)), V.cy);
+            float sg;
+            if (o.radius_mode == 0)
+                sg = __fdiv_rn(__fmul_rn(V.fx, r), z);
+            else
+                sg = __fmul_rn(__fmul_rn(r, (float)min(V.W, V.H)), 0.5f);
+            const float rc = __fmul_rn(o.cutoff_k, sg);
+            const float rc2 = __fmul_rn(rc, rc);
+            float xlo = __fsub_rn(floorf(__fsub_rn(px, rc)), 1.0f);
+            float xhi = ceilf(__fadd_rn(px, rc));
+            float ylo = __fsub_rn(floorf(__fsub_rn(py, rc)), 1.0f);
+            float yhi = ceilf(__fadd_rn(py, rc));
+            const float W1 = (float)(V.W - 1), H1 = (float)(V.H - 1);
+            if (sg > 0.0f && xhi >= 0.0f && xlo <= W1 && yhi >= 0.0f && ylo <= H1) {
+                xlo = xlo < 0.0f ? 0.0f : xlo;
+                ylo = ylo < 0.0f ? 0.0f : ylo;
+                xhi = xhi > W1 ? W1 : xhi;
+                yhi = yhi > H1 ? H1 : yhi;
+                const int tx0 = (int)xlo / o.tile_w, tx1 = (int)xhi / o.tile_w;
+                const int ty0 = (int)ylo / o.tile_h, ty1 = (int)yhi / o.tile_h;
+                nt = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+                // view direction (Eq. 3) and colour (Eq. 4)
+                const float inv = rsqrtf(X[0] * X[0] + X[1] * X[1] + z * z);
+                float dx = X[0] * inv, dy = X[1] * inv, dz = z * inv;
+                if (o.dir_frame == 1) {
+                    const float wx = V.R[0] * dx + V.R[3] * dy + V.R[6] * dz;
+                    const float wy = V.R[1] * dx + V.R[4] * dy + V.R[7] * dz;
+                    const float wz = V.R[2] * dx + V.R[5] * dy + V.R[8] * dz;
+                    dx = wx;
+                    dy = wy;
+                    dz = wz;
+                }
+                float Y[K];
+                sh_basis<DEG>(dx, dy, dz, Y);
+                float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    c0 = fmaf(h[3 * k], Y[k], c0);
+                    c1 = fmaf(h[3 * k + 1], Y[k], c1);
+                    c2 = fmaf(h[3 * k + 2], Y[k], c2);
+                }
+                const float qp = -0.5f * LOG2E / (sg * sg);
+                rec[2 * pv] = make_float4(px, py, qp, op);
+                rec[2 * pv + 1] = make_float4(c0, c1, c2, rc2);
+                zbits[pv] = __float_as_uint(z);
+                rect[pv] = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16),
+                                      (uint32_t)tx1 | ((uint32_t)ty1 << 16));
+                ++vis_cnt;
+                pair_cnt += nt;
+            }
+        }
+        ntiles[pv] = nt;
+    }
+}
+
+__global__ void __launch_bounds__(PRE_THREADS)
+preprocess_fwd_kernel(Batch b, DevOpts o, float4 *__restrict__ rec, uint32_t *__restrict__ zbits,
+                      uint32_t *__restrict__ ntiles, uint2 *__restrict__ rect,
+                      unsigned long long *__restrict__ counters)
+{
+    __shared__ float s_sh[PRE_THREADS * 48];
+    const int s = find_scene(b, blockIdx.x);
+    const DevScene sc = b.scenes[s];
+    const int64_t first = (int64_t)(blockIdx.x - sc.block_begin) * PRE_THREADS;
+    const int count = (int)(sc.n - first < PRE_THREADS ? sc.n - first : PRE_THREADS);
+    if (count <= 0) return; // whole block past the scene (uniform)
+    const int K3 = sc.K * 3;
+    stage_sh(sc.sh, first, count, K3, s_sh);
+    __syncthreads();
+    uint32_t vis = 0, pairs = 0;
+    if ((int)threadIdx.x < count) {
+        const int64_t i = first + threadIdx.x;
+        const float *hs = s_sh + threadIdx.x * K3;
+        switch (sc.deg) {
+        case 0: pre_fwd_point<0>(b, o, sc, i, hs, rec, zbits, ntiles, rect, vis, pairs); break;
+        case 1: pre_fwd_point<1>(b, o, sc, i, hs, rec, zbits, ntiles, rect, vis, pairs); break;
+        case 2: pre_fwd_point<2>(b, o, sc, i, hs, rec, zbits, ntiles, rect, vis, pairs); break;
+        default: pre_fwd_point<3>(b, o, sc, i, hs, rec, zbits, ntiles, rect, vis, pairs); break;
+        }
+    }
+    // per-warp totals, one atomic per warp: counters[0] pairs, [1] visible
+    vis = __reduce_add_sync(0xffffffffu, vis);
+    pairs = __reduce_add_sync(0xffffffffu, pairs);
+    if ((threadIdx.x & 31) == 0) {
+        if (pairs) atomicAdd(counters, (unsigned long long)pairs);
+        if (vis) atomicAdd(counters + 1, (unsigned long long)vis);
+    }
+}
+
+// ------------------------------------------------------------- backward
+template <int DEG>
+__device__ void pre_bwd_point(const Batch &b, const DevOpts &o, const DevScene &sc, int64_t i,
+                              float *hs, const float4 *__restrict__ g2d,
+                              float *__restrict__ grad_pos, float *__restrict__ grad_opacity)
+{
+    constexpr int K = SH<DEG>::K;
+    float h[K * 3], dh[K * 3];
+#pragma unroll
+    for (int j = 0; j < K * 3; ++j) {
+        h[j] = hs[j];
+        dh[j] = 0.0f;
+    }
+    const float P0 = __ldg(sc.pos + 3 * i), P1 = __ldg(sc.pos + 3 * i + 1),
+                P2 = __ldg(sc.pos + 3 * i + 2);
+    const float r = __ldg(sc.radius + i);
+    float dP0 = 0.f, dP1 = 0.f, dP2 = 0.f, dop = 0.f;
+
+    for (int vv = 0; vv < sc.view_count; ++vv) {
+        const int v = b.view_list[sc.view_begin + vv];
+        const DevView &V = b.views[v];
+        const int64_t pv = V.pv_base + i;
+        const float4 ga = g2d[2 * pv];     // dpx, dpy, dq, do
+        const float4 gb = g2d[2 * pv + 1]; // dr, dg, db, -
+        if (ga.x == 0.f && ga.y == 0.f && ga.z == 0.f && ga.w == 0.f && gb.x == 0.f &&
+            gb.y == 0.f && gb.z == 0.f)
+            continue; // culled or never composited
+        float X[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            X[a] = V.R[3 * a] * P0 + V.R[3 * a + 1] * P1 + V.R[3 * a + 2] * P2 + V.t[a];
+        const float z = X[2];
+        const float iz = 1.0f / z;
+        float dX0 = 0.f, dX1 = 0.f, dX2 = 0.f;
+        // p = (fx X0/z + cx, fy X1/z + cy)
+        dX0 += ga.x * V.fx * iz;
+        dX2 -= ga.x * V.fx * X[0] * iz * iz;
+        dX1 += ga.y * V.fy * iz;
+        dX2 -= ga.y * V.fy * X[1] * iz * iz;
+        // q = 1/s^2 = z^2 / (fx r)^2  =>  dq/dz = 2 q / z  (radius_mode 0)
+        if (o.radius_mode == 0) {
+            const float s = V.fx * r * iz;
+            dX2 += ga.z * 2.0f * iz / (s * s);
+        }
+        dop += ga.w;
+        // colour: c = sum_k h_k Y_k(v)
+        const float nrm2 = X[0] * X[0] + X[1] * X[1] + z * z;
+        const float inv = rsqrtf(nrm2);
+        const float vx = X[0] * inv, vy = X[1] * inv, vz = z * inv;
+        float ux = vx, uy = vy, uz = vz;
+        if (o.dir_frame == 1) {
+            ux = V.R[0] * vx + V.R[3] * vy + V.R[6] * vz;
+            uy = V.R[1] * vx + V.R[4] * vy + V.R[7] * vz;
+            uz = V.R[2] * vx + V.R[5] * vy + V.R[8] * vz;
+        }
+        float Y[K], w[K];
+        sh_basis<DEG>(ux, uy, uz, Y);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            dh[3 * k] = fmaf(Y[k], gb.x, dh[3 * k]);
+            dh[3 * k + 1] = fmaf(Y[k], gb.y, dh[3 * k + 1]);
+            dh[3 * k + 2] = fmaf(Y[k], gb.z, dh[3 * k + 2]);
+            w[k] = h[3 * k] * gb.x + h[3 * k + 1] * gb.y + h[3 * k + 2] * gb.z;
+        }
+        if (DEG > 0) {
+            float gx = 0.f, gy = 0.f, gz = 0.f;
+            sh_grad_accum<DEG>(ux, uy, uz, w, gx, gy, gz);
+            if (o.dir_frame == 1) { // u = R^T v  =>  dv = R du
+                const float ax = V.R[0] * gx + V.R[1] * gy + V.R[2] * gz;
+                const float ay = V.R[3] * gx + V.R[4] * gy + V.R[5] * gz;
+                const float az = V.R[6] * gx + V.R[7] * gy + V.R[8] * gz;
+                gx = ax;
+                gy = ay;
+                gz = az;
+            }
+            // v = X/|X|  =>  dX = (dv - v (v . dv)) / |X|
+            const float vd = vx * gx + vy * gy + vz * gz;
+            dX0 += (gx - vx * vd) * inv;
+            dX1 += (gy - vy * vd) * inv;
+            dX2 += (gz - vz * vd) * inv;
+        }
+        // X = R P + t  =>  dP = R^T dX
+        dP0 += V.R[0] * dX0 + V.R[3] * dX1 + V.R[6] * dX2;
+        dP1 += V.R[1] * dX0 + V.R[4] * dX1 + V.R[7] * dX2;
+        dP2 += V.R[2] * dX0 + V.R[5] * dX1 + V.R[8] * dX2;
+    }
+    const int64_t gi = sc.point_base + i;
+    grad_pos[3 * gi] = dP0;
+    grad_pos[3 * gi + 1] = dP1;
+    grad_pos[3 * gi + 2] = dP2;
+    if (grad_opacity) grad_opacity[gi] = dop;
+#pragma unroll
+    for (int j = 0; j < K * 3; ++j) hs[j] = dh[j];
+}
+
+__global__ void __launch_bounds__(PRE_THREADS)
+preprocess_bwd_kernel(Batch b, DevOpts o, const float4 *__restrict__ g2d,
+                      float *__restrict__ grad_pos, float *__restrict__ grad_sh,
+                      float *__restrict__ grad_opacity)
+{
+    __shared__ float s_sh[PRE_THREADS * 48];
+    const int s = find_scene(b, blockIdx.x);
+    const DevScene sc = b.scenes[s];
+    const int64_t first = (int64_t)(blockIdx.x - sc.block_begin) * PRE_THREADS;
+    const int count = (int)(sc.n - first < PRE_THREADS ? sc.n - first : PRE_THREADS);
+    if (count <= 0) return;
+    const int K3 = sc.K * 3;
+    stage_sh(sc.sh, first, count, K3, s_sh);
+    __syncthreads();
+    if ((int)threadIdx.x < count) {
+        const int64_t i = first + threadIdx.x;
+        float *hs = s_sh + threadIdx.x * K3;
+        switch (sc.deg) {
+        case 0: pre_bwd_point<0>(b, o, sc, i, hs, g2d, grad_pos, grad_opacity); break;
+        case 1: pre_bwd_point<1>(b, o, sc, i, hs, g2d, grad_pos, grad_opacity); break;
+        case 2: pre_bwd_point<2>(b, o, sc, i, hs, g2d, grad_pos, grad_opacity); break;
+        default: pre_bwd_point<3>(b, o, sc, i, hs, g2d, grad_pos, grad_opacity); break;
+        }
+    }
+    __syncthreads();
+    // coalesced write-back of the SH gradient slice
+    float *dst = grad_sh + sc.sh_base + first * K3;
+    const int total = count * K3;
+    for (int j = threadIdx.x; j < total; j += blockDim.x) dst[j] = s_sh[j];
+}
+
+} // namespace
+
+void launch_preprocess_fwd(const Batch &b, const DevOpts &o, float4 *rec, uint32_t *zbits,
+                           uint32_t *ntiles, uint2 *rect, unsigned long long *counters,
+                           cudaStream_t s)
+{
+    if (b.n_point_blocks <= 0) return;
+    preprocess_fwd_kernel<<<(unsigned)b.n_point_blocks, PRE_THREADS, 0, s>>>(
+        b, o, rec, zbits, ntiles, rect, counters);
+}
+
+void launch_preprocess_bwd(const Batch &b, const DevOpts &o, const float4 *g2d, float *grad_pos,
+                           float *grad_sh, float *grad_opacity, cudaStream_t s)
+{
+    if (b.n_point_blocks <= 0) return;
+    preprocess_bwd_kernel<<<(unsigned)b.n_point_blocks, PRE_THREADS, 0, s>>>(
+        b, o, g2d, grad_pos, grad_sh, grad_opacity);
+}
+
+} // namespace pbr

@@ -1,0 +1,116 @@
+// Internal declarations shared by the CUDA translation units of libpbr.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pbr {
+
+// Status bits raised by kernels (device word, read by the host after a pass).
+enum : uint32_t {
+    ST_PAIR_OVERFLOW = 1u << 0,  // more (tile, point-view) pairs than capacity
+    ST_COUNT_OVERFLOW = 1u << 1, // a 32-bit count or index would overflow
+    ST_BAD_RANGE = 1u << 2,      // inconsistent tile range
+};
+
+// One view of the batch: camera of Sec. 3.1 Eq. 1 plus its place in the
+// packed pixel, tile and point-view numbering.
+struct DevView {
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    int32_t W, H;
+    int32_t tiles_x, tiles_y;
+    uint32_t tile_base;  // first global tile id of the view
+    int32_t scene;       // index into the scene table
+    int64_t pix_base;    // first pixel of the view in the packed image
+    int64_t pv_base;     // first point-view id: pv = pv_base + point index
+};
+
+// One scene (point set) of the batch.
+struct DevScene {
+    const float *pos;     // [n,3]
+    const float *sh;      // [n,K,3]
+    const float *opacity; // [n]
+    const float *radius;  // [n]
+    int64_t n;
+    int32_t K, deg;
+    int32_t view_begin, view_count; // slice of the scene-sorted view list
+    int64_t point_base;             // offset of the scene in packed gradients
+    int64_t sh_base;                // offset (floats) in the packed SH gradient
+    int64_t block_begin;            // first block of the point-parallel grids
+};
+
+// Renderer constants in device form.
+struct DevOpts {
+    int32_t radius_mode, dir_frame;
+    float cutoff_k, alpha_max, t_eps;
+    int32_t max_per_pixel;
+    float bg[3];
+    float z_near;
+    int32_t tile_w, tile_h;
+};
+
+// Everything a launch needs about the batch layout (passed by value).
+struct Batch {
+    const DevView *views;       // [n_views]
+    const DevScene *scenes;     // [n_scenes]
+    const int32_t *view_list;   // views sorted by scene
+    int32_t n_views, n_scenes;
+    int64_t n_pv;               // point-views
+    uint32_t n_tiles;
+    int64_t n_pix;
+    int64_t n_point_blocks;     // blocks of the point-parallel grids
+};
+
+constexpr int PRE_THREADS = 128;
+
+// log2(e) and the factor that turns q' = -log2(e) / (2 s^2) into q = 1 / s^2
+constexpr float LOG2E = 1.4426950408889634f;
+constexpr float QP_TO_Q = -2.0f / 1.4426950408889634f;
+
+// ---- preprocess (k_preprocess.cu)
+// counters[0] += (tile, point-view) pairs, counters[1] += visible point-views
+void launch_preprocess_fwd(const Batch &b, const DevOpts &o, float4 *rec, uint32_t *zbits,
+                           uint32_t *ntiles, uint2 *rect, unsigned long long *counters,
+                           cudaStream_t s);
+void launch_preprocess_bwd(const Batch &b, const DevOpts &o, const float4 *g2d, float *grad_pos,
+                           float *grad_sh, float *grad_opacity, cudaStream_t s);
+
+// ---- scans, sorts and binning (k_sort.cu)
+size_t scan_temp_bytes(int64_t n);
+// Compacts visible point-views (ntiles > 0): keys_out = z bits, vals_out = pv.
+// Writes the visible count to *n_vis (device).
+void launch_compact_visible(const uint32_t *ntiles, const uint32_t *zbits, int64_t n_pv,
+                            uint32_t *keys_out, uint32_t *vals_out, uint32_t *n_vis, void *temp,
+                            cudaStream_t s);
+// Radix sort of (key, value) pairs, stable; n read from device *n_dev,
+// capacity cap.  key_bits: number of low key bits that can be non-zero.
+// Sorted result ends in (keys, vals) (buffers are ping-ponged internally).
+size_t radix_temp_bytes(int64_t cap);
+void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *&keys_alt, uint32_t *&vals_alt,
+                      const uint32_t *n_dev, int64_t cap, int key_bits, void *temp,
+                      cudaStream_t s);
+// Emits (tile, pv) pairs in depth order (same scan as count, with output).
+void launch_emit_pairs(const Batch &b, const DevOpts &o, const uint32_t *sorted_pv,
+                       const uint32_t *n_vis, int64_t cap_vis, const uint32_t *ntiles,
+                       const uint2 *rect, uint32_t *keys, uint32_t *vals, int64_t cap_pairs,
+                       uint32_t *status, void *temp, cudaStream_t s);
+void launch_tile_ranges(const uint32_t *keys, const uint32_t *n_pairs, int64_t cap_pairs,
+                        uint2 *ranges, uint32_t n_tiles, cudaStream_t s);
+
+// ---- raster (k_raster.cu)
+void launch_raster_fwd(const Batch &b, const DevOpts &o, int batch_depth, const uint2 *ranges,
+                       const uint32_t *pv_list, const float4 *rec, float *out_rgb,
+                       float *T_final, uint32_t *n_contrib, cudaStream_t s);
+void launch_raster_bwd(const Batch &b, const DevOpts &o, int batch_depth, const uint2 *ranges,
+                       const uint32_t *pv_list, const float4 *rec, const float *T_final,
+                       const uint32_t *n_contrib, const float *grad_rgb, float4 *g2d,
+                       cudaStream_t s);
+
+// ---- misc (k_misc.cu)
+void launch_image_loss(int kind, const float *pred, const float *target, int64_t n, float *grad,
+                       double *loss, cudaStream_t s);
+int measure_alu_peaks(int device, double *fp32_flops, double *ex2_ops);
+
+} // namespace pbr

@@ -1,0 +1,305 @@
+"""ctypes binding of libpbr.so (declared in include/pbr.h).
+
+Argument marshalling only: every stage of the renderer runs in the library's
+CUDA kernels.  PyTorch provides device memory (tensors) and the current
+stream.  There is no CPU fallback: if the library cannot be loaded, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+try:
+    import torch
+except ImportError:  # pragma: no cover - torch is required for device memory
+    torch = None
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpbr.so")
+
+PBR_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "CAPACITY", -5: "TIMEOUT",
+          -6: "DEVICE_STATUS", -7: "NOT_FOUND", -8: "BUSY"}
+
+
+class PBRError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pbr error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class Camera(C.Structure):
+    _fields_ = [("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("R", C.c_float * 9), ("t", C.c_float * 3),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("radius_mode", C.c_int32), ("dir_frame", C.c_int32), ("cutoff_k", C.c_float),
+                ("alpha_max", C.c_float), ("t_eps", C.c_float), ("max_per_pixel", C.c_int32),
+                ("bg", C.c_float * 3), ("z_near", C.c_float), ("tile_w", C.c_int32),
+                ("tile_h", C.c_int32), ("batch_depth", C.c_int32), ("reserved", C.c_int32 * 4)]
+
+
+class Points(C.Structure):
+    _fields_ = [("pos", C.c_void_p), ("sh", C.c_void_p), ("opacity", C.c_void_p),
+                ("radius", C.c_void_p), ("n", C.c_int64), ("sh_degree", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class StateInfo(C.Structure):
+    _fields_ = [("n_point_views", C.c_int64), ("n_visible", C.c_int64), ("n_pairs", C.c_int64),
+                ("n_tiles", C.c_int64), ("n_pixels", C.c_int64),
+                ("tile_keys", C.c_void_p), ("tile_vals", C.c_void_p), ("ranges", C.c_void_p),
+                ("records", C.c_void_p), ("ntiles", C.c_void_p), ("T_final", C.c_void_p),
+                ("n_contrib", C.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Loads libpbr.so (raising if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libpbr.so is missing ({LIB_PATH}); run "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = C.CDLL(LIB_PATH)
+            vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+            L.pbr_create.argtypes = [C.POINTER(vp), C.c_int, C.c_size_t]
+            L.pbr_destroy.argtypes = [vp]
+            L.pbr_last_error.restype = C.c_char_p
+            L.pbr_version.restype = C.c_char_p
+            L.pbr_default_opts.argtypes = [C.POINTER(Opts)]
+            L.pbr_default_opts.restype = None
+            L.pbr_render_forward.argtypes = [vp, C.POINTER(Points), i32, vp, C.POINTER(Camera),
+                                             i32, C.POINTER(Opts), vp, C.POINTER(vp), vp]
+            L.pbr_render_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+            L.pbr_state_free.argtypes = [vp, vp]
+            L.pbr_state_info.argtypes = [vp, C.POINTER(StateInfo)]
+            L.pbr_state_read.argtypes = [vp, i32, vp, C.c_size_t, C.POINTER(C.c_size_t)]
+            L.pbr_image_loss.argtypes = [i32, vp, vp, i64, vp, vp, vp]
+            L.pbr_measure_alu_peaks.argtypes = [C.c_int, C.POINTER(C.c_double),
+                                                C.POINTER(C.c_double)]
+            _lib = L
+    return _lib
+
+
+def check(rc):
+    if rc != PBR_OK:
+        raise PBRError(rc, lib().pbr_last_error().decode(errors="replace"))
+    return rc
+
+
+# ------------------------------------------------------------ marshalling
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().pbr_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if k == "bg":
+            for j in range(3):
+                o.bg[j] = float(v[j])
+        elif k == "tile":
+            o.tile_w, o.tile_h = int(v[0]), int(v[1])
+        else:
+            cur = getattr(o, k)
+            setattr(o, k, float(v) if isinstance(cur, float) else int(v))
+    return o
+
+
+def make_cameras(cams):
+    arr = (Camera * max(1, len(cams)))()
+    for i, c in enumerate(cams):
+        a = arr[i]
+        a.fx, a.fy, a.cx, a.cy = float(c["fx"]), float(c["fy"]), float(c["cx"]), float(c["cy"])
+        R = np.asarray(c["R"], np.float32).reshape(9)
+        t = np.asarray(c["t"], np.float32).reshape(3)
+        for j in range(9):
+            a.R[j] = float(R[j])
+        for j in range(3):
+            a.t[j] = float(t[j])
+        a.width, a.height = int(c["width"]), int(c["height"])
+    return arr
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else C.c_void_p(0)
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Scene:
+    """Device-resident point set: pos [n,3], sh [n,K,3], opacity [n], radius [n]."""
+
+    def __init__(self, pos, sh, opacity, radius, deg, device="cuda"):
+        def dev(a):
+            t = a if torch.is_tensor(a) else torch.from_numpy(np.ascontiguousarray(a))
+            return t.to(device=device, dtype=torch.float32).contiguous()
+        self.pos, self.sh, self.opacity, self.radius = dev(pos), dev(sh), dev(opacity), dev(radius)
+        self.deg = int(deg)
+        self.n = int(self.pos.shape[0])
+        assert self.sh.shape == (self.n, (self.deg + 1) ** 2, 3)
+
+    def points(self) -> Points:
+        return Points(_ptr(self.pos), _ptr(self.sh), _ptr(self.opacity), _ptr(self.radius),
+                      self.n, self.deg, 0)
+
+
+def n_pixels(cams):
+    return sum(int(c["width"]) * int(c["height"]) for c in cams)
+
+
+class State:
+    """Forward state needed by the backward pass (freed on close/GC)."""
+
+    def __init__(self, renderer, handle, scenes):
+        self.renderer, self.handle, self.scenes = renderer, handle, scenes
+
+    def info(self) -> dict:
+        inf = StateInfo()
+        check(lib().pbr_state_info(self.handle, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in StateInfo._fields_}
+
+    ARRAYS = {"tile_keys": (0, np.uint32), "tile_vals": (1, np.uint32), "ranges": (2, np.uint32),
+              "records": (3, np.float32), "ntiles": (4, np.uint32), "T_final": (5, np.float32),
+              "n_contrib": (6, np.uint32)}
+
+    def read(self, name: str) -> np.ndarray:
+        """Host copy of one state array (see pbr_state_read)."""
+        which, dt = self.ARRAYS[name]
+        size = C.c_size_t()
+        check(lib().pbr_state_read(self.handle, which, None, 0, C.byref(size)))
+        out = np.empty(size.value // np.dtype(dt).itemsize, dt)
+        check(lib().pbr_state_read(self.handle, which, out.ctypes.data, size.value,
+                                   C.byref(size)))
+        if name == "ranges":
+            out = out.reshape(-1, 2)
+        elif name == "records":
+            out = out.reshape(-1, 8)
+        return out
+
+    def close(self):
+        if self.handle:
+            lib().pbr_state_free(self.renderer.ctx, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Renderer:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0):
+        self.ctx = C.c_void_p()
+        check(lib().pbr_create(C.byref(self.ctx), int(device), int(hbm_budget)))
+        self.device = int(device)
+
+    def close(self):
+        if self.ctx:
+            lib().pbr_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, scenes, cams, opts=None, scene_of_view=None, keep_state=True, out=None):
+        """Renders every camera; returns (image [sum H W, 3] fp32 on device, State|None)."""
+        scenes = scenes if isinstance(scenes, (list, tuple)) else [scenes]
+        opts = opts or default_opts()
+        pts = (Points * len(scenes))(*[s.points() for s in scenes])
+        cam_arr = make_cameras(cams)
+        sov = None
+        if scene_of_view is not None:
+            sov = (C.c_int32 * len(cams))(*[int(x) for x in scene_of_view])
+        npix = n_pixels(cams)
+        if out is None:
+            out = torch.empty((npix, 3), dtype=torch.float32, device=f"cuda:{self.device}")
+        h = C.c_void_p()
+        check(lib().pbr_render_forward(self.ctx, pts, len(scenes), sov, cam_arr, len(cams),
+                                       C.byref(opts), _ptr(out), C.byref(h) if keep_state else None,
+                                       _stream()))
+        return out, (State(self, h, scenes) if keep_state else None)
+
+    def backward(self, state: State, grad_rgb, want_opacity=True):
+        """Gradients (packed over the state's scenes) for dL/dimage = grad_rgb."""
+        scenes = state.scenes
+        dev = f"cuda:{self.device}"
+        n_tot = sum(s.n for s in scenes)
+        n_sh = sum(s.n * (s.deg + 1) ** 2 * 3 for s in scenes)
+        gpos = torch.empty((n_tot, 3), dtype=torch.float32, device=dev)
+        gsh = torch.empty((n_sh,), dtype=torch.float32, device=dev)
+        gop = torch.empty((n_tot,), dtype=torch.float32, device=dev) if want_opacity else None
+        g = grad_rgb.to(dtype=torch.float32).contiguous()
+        check(lib().pbr_render_backward(self.ctx, state.handle, _ptr(g), _ptr(gpos), _ptr(gsh),
+                                        _ptr(gop) if gop is not None else None, _stream()))
+        return gpos, gsh, gop
+
+
+def image_loss(pred, target, kind="l2"):
+    """(loss, dL/dpred) of a sum-of-squares (kind l2) or sum-of-abs (l1) loss."""
+    grad = torch.empty_like(pred)
+    loss = torch.zeros(1, dtype=torch.float64, device=pred.device)
+    check(lib().pbr_image_loss(0 if kind == "l2" else 1, _ptr(pred), _ptr(target), pred.numel(),
+                               _ptr(grad), _ptr(loss), _stream()))
+    return loss, grad
+
+
+def measure_alu_peaks(device: int = 0):
+    f, e = C.c_double(), C.c_double()
+    check(lib().pbr_measure_alu_peaks(device, C.byref(f), C.byref(e)))
+    return f.value, e.value
+
+
+# ------------------------------------------------------- autograd wrapper
+_default_renderer = {}
+
+
+def renderer(device: int = 0) -> Renderer:
+    r = _default_renderer.get(device)
+    if r is None:
+        r = _default_renderer[device] = Renderer(device)
+    return r
+
+
+if torch is not None:
+    class PBRRenderFn(torch.autograd.Function):
+        """Differentiable render of one scene through the library's hand-written
+        backward pass (positions, SH coefficients, opacity)."""
+
+        @staticmethod
+        def forward(ctx, pos, sh, opacity, radius, deg, cams, opts):
+            r = renderer(pos.device.index or 0)
+            scene = Scene(pos.detach(), sh.detach(), opacity.detach(), radius.detach(), deg,
+                          device=pos.device)
+            img, st = r.forward([scene], cams, opts)
+            ctx.state = st
+            ctx.shapes = (pos.shape, sh.shape, opacity.shape)
+            return img
+
+        @staticmethod
+        def backward(ctx, grad_img):
+            st = ctx.state
+            r = st.renderer
+            gpos, gsh, gop = r.backward(st, grad_img)
+            st.close()
+            ps, ss, os_ = ctx.shapes
+            return gpos.view(ps), gsh.view(ss), gop.view(os_), None, None, None, None
+
+    def render(pos, sh, opacity, radius, deg, cams, opts=None):
+        return PBRRenderFn.apply(pos, sh, opacity, radius, deg, cams, opts or default_opts())

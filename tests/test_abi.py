@@ -1,0 +1,51 @@
+"""The C ABI library builds for sm_103a, loads without a GPU and exports
+every function that include/pbr.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(pbr_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2205_14330_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("pbr_render_forward", "pbr_render_backward", "pbr_create", "pbr_destroy",
+                     "pbr_state_free", "pbr_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r"\b(pbr_\w+)\b", out))
+    assert set(_declared()) <= exported
+
+
+def test_host_only_calls_work_without_a_gpu(libpath):
+    from paper_2205_14330_gb300 import pbr
+    o = pbr.default_opts()
+    assert (o.tile_w, o.tile_h, o.batch_depth) == (16, 16, 256)
+    assert abs(o.alpha_max - 0.99) < 1e-7 and abs(o.cutoff_k - 3.0) < 1e-7
+    assert b"sm_103a" in pbr.lib().pbr_version()

@@ -1,0 +1,277 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: tile lists, ranges, tile counts and the fp32 screen positions and
+cutoff radii are compared bit for bit; images to max abs 1e-4 on colours of
+order 1; gradients to relative L2 1e-3.  Every case also prints its error
+against the oracle.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2205_14330_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-4
+GRAD_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def R():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2205_14330_gb300 import pbr
+    r = pbr.Renderer(0)
+    yield r
+    r.close()
+
+
+def _pbr():
+    from paper_2205_14330_gb300 import pbr
+    return pbr
+
+
+def _oracle_kw(kw):
+    kw = dict(kw)
+    if "tile" in kw:
+        kw["tile_w"], kw["tile_h"] = kw.pop("tile")
+    kw.pop("batch_depth", None)
+    return kw
+
+
+def _gpu_render(R, sc, cams, **kw):
+    pbr = _pbr()
+    scene = pbr.Scene(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"])
+    img, st = R.forward([scene], cams, pbr.default_opts(**kw))
+    return img, st, scene
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def _small_scene(seed, n=300, deg=2, spread=0.8, r=(0.02, 0.06)):
+    rng = np.random.default_rng(seed)
+    return dict(pos=rng.uniform(-spread, spread, (n, 3)).astype(np.float32),
+                sh=scenes.sh_coeffs(rng, n, deg, std=0.3),
+                opacity=rng.uniform(0.2, 0.95, n).astype(np.float32),
+                radius=rng.uniform(r[0], r[1], n).astype(np.float32), deg=deg)
+
+
+# ------------------------------------------------------------------ forward
+def test_tiny_config_image(R):
+    sc = scenes.tiny()
+    img, st, _ = _gpu_render(R, sc, sc["cams"])
+    ref, T, _ = O.render(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], sc["cams"])
+    got = img.cpu().numpy()
+    err = np.abs(got - ref).max()
+    print(f"tiny: image max abs err vs FP64 oracle {err:.3e}")
+    assert err <= IMG_TOL
+    assert np.abs(st.read("T_final") - T).max() <= IMG_TOL
+    full, _, _ = O.render(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], sc["cams"],
+                          screen_fp32=0)
+    print(f"tiny: image max abs err vs all-double oracle {np.abs(got - full).max():.3e}")
+    st.close()
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (16, 32)])
+def test_bins_and_records_bit_exact(R, tile):
+    sc = _small_scene(1, n=400)
+    cams = [scenes.camera((0.3, 0.2, 2.2), 70, 45), scenes.camera((-1.8, 0.4, 1.5), 33, 57),
+            scenes.camera((0.0, 2.0, 0.3), 16, 16)]
+    img, st, _ = _gpu_render(R, sc, cams, tile=tile)
+    keys, vals, ranges, recs = O.bin_tiles(sc["pos"], sc["sh"], sc["radius"], sc["deg"], cams,
+                                           tile_w=tile[0], tile_h=tile[1])
+    assert np.array_equal(st.read("tile_keys"), keys)
+    assert np.array_equal(st.read("tile_vals"), vals)
+    assert np.array_equal(st.read("ranges"), ranges)
+    flat = recs.reshape(-1)
+    vis = flat["visible"] == 1
+    nt = st.read("ntiles")
+    assert np.array_equal(nt > 0, vis)
+    assert np.array_equal(nt[vis], flat["ntiles"][vis].astype(np.uint32))
+    rec = st.read("records")
+    assert np.array_equal(rec[vis, 0].view(np.uint32), flat["px32"][vis].view(np.uint32))
+    assert np.array_equal(rec[vis, 1].view(np.uint32), flat["py32"][vis].view(np.uint32))
+    assert np.array_equal(rec[vis, 7].view(np.uint32), flat["rc2_32"][vis].view(np.uint32))
+    col_err = np.abs(rec[vis, 4:7] - flat["rgb"][vis]).max()
+    assert col_err <= 1e-5, col_err
+    ref, _, _ = O.render(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], cams)
+    err = np.abs(img.cpu().numpy() - ref).max()
+    print(f"tile {tile}: {len(keys)} pairs bit-exact; image max abs err {err:.3e}")
+    assert err <= IMG_TOL
+    st.close()
+
+
+def test_image_independent_of_tile_size_and_batch_depth(R):
+    sc = _small_scene(2, n=500)
+    cams = [scenes.camera((0.5, -0.3, 2.4), 97, 61)]
+    imgs = []
+    for tile, depth in (((16, 16), 256), ((8, 8), 32), ((16, 32), 512), ((16, 16), 64)):
+        img, st, _ = _gpu_render(R, sc, cams, tile=tile, batch_depth=depth)
+        imgs.append(img.cpu().numpy())
+        st.close()
+    for im in imgs[1:]:
+        assert np.array_equal(im, imgs[0])
+
+
+def test_forward_is_deterministic(R):
+    sc = _small_scene(3, n=2000, r=(0.01, 0.05))
+    cams = [scenes.camera((0.1, 0.1, 2.5), 128, 96)]
+    a, sa, _ = _gpu_render(R, sc, cams)
+    b, sb, _ = _gpu_render(R, sc, cams)
+    assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+    sa.close()
+    sb.close()
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(dir_frame=1), dict(radius_mode=1),
+                                dict(max_per_pixel=15), dict(bg=(0.2, 0.5, 0.9)),
+                                dict(t_eps=0.0, cutoff_k=4.0), dict(alpha_max=0.5)],
+                         ids=["default", "world-dir", "ndc-radius", "n15", "bg", "no-stop",
+                              "amax"])
+def test_option_variants(R, kw):
+    sc = _small_scene(4, n=600)
+    if kw.get("radius_mode") == 1:
+        sc["radius"] = (sc["radius"] * 0.1).astype(np.float32)
+    cams = [scenes.camera((1.0, 0.5, 2.0), 80, 64)]
+    img, st, _ = _gpu_render(R, sc, cams, **kw)
+    ref, _, _ = O.render(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], cams,
+                         **_oracle_kw(kw))
+    err = np.abs(img.cpu().numpy() - ref).max()
+    print(f"{kw}: image max abs err {err:.3e}")
+    assert err <= IMG_TOL
+    st.close()
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2, 3])
+def test_sh_degrees(R, deg):
+    sc = _small_scene(5 + deg, n=300, deg=deg)
+    cams = [scenes.camera((0.0, -1.0, 2.0), 48, 48)]
+    img, st, _ = _gpu_render(R, sc, cams)
+    ref, _, _ = O.render(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], deg, cams)
+    assert np.abs(img.cpu().numpy() - ref).max() <= IMG_TOL
+    st.close()
+
+
+def test_edge_cases(R):
+    pbr = _pbr()
+    cam = scenes.camera((0.0, 0.0, 2.5), 20, 12)
+    # empty scene -> background everywhere
+    empty = dict(pos=np.zeros((0, 3), np.float32), sh=np.zeros((0, 1, 3), np.float32),
+                 opacity=np.zeros(0, np.float32), radius=np.zeros(0, np.float32), deg=0)
+    img, st, _ = _gpu_render(R, empty, [cam], bg=(0.1, 0.2, 0.3))
+    assert np.allclose(img.cpu().numpy(), [0.1, 0.2, 0.3])
+    st.close()
+    # every point behind the camera or at the near plane -> culled
+    sc = _small_scene(9, n=50)
+    sc["pos"][:, 2] = np.float32(2.5)  # z = 0 in the camera frame
+    img, st, _ = _gpu_render(R, sc, [cam])
+    assert np.all(img.cpu().numpy() == 0) and st.info()["n_pairs"] == 0
+    st.close()
+    # a 1x1 image and a one-row image
+    sc = _small_scene(10, n=200, spread=0.2, r=(0.05, 0.2))
+    for W, H in ((1, 1), (37, 1), (1, 29)):
+        c = scenes.camera((0.0, 0.0, 2.0), W, H)
+        img, st, _ = _gpu_render(R, sc, [c])
+        ref, _, _ = O.render(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], [c])
+        assert np.abs(img.cpu().numpy() - ref).max() <= IMG_TOL
+        st.close()
+    # equal depths: ties broken by point index
+    sc = _small_scene(11, n=40)
+    sc["pos"][:, 2] = np.float32(0.25)
+    img, st, _ = _gpu_render(R, sc, [cam])
+    ref, _, _ = O.render(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], [cam])
+    assert np.abs(img.cpu().numpy() - ref).max() <= IMG_TOL
+    st.close()
+    # invalid arguments are rejected, not run
+    with pytest.raises(pbr.PBRError):
+        _gpu_render(R, sc, [cam], tile=(32, 32))
+    with pytest.raises(pbr.PBRError):
+        _gpu_render(R, sc, [scenes.camera((0, 0, 2), 0, 10)])
+
+
+def test_multi_scene_multi_view(R):
+    pbr = _pbr()
+    a = _small_scene(12, n=300, deg=1)
+    b = _small_scene(13, n=500, deg=3)
+    cams = [scenes.camera((0.2, 0.1, 2.3), 50, 40), scenes.camera((-1.5, 0.3, 1.6), 41, 33),
+            scenes.camera((0.0, 1.9, 0.6), 64, 64)]
+    sov = [1, 0, 1]
+    sa = pbr.Scene(a["pos"], a["sh"], a["opacity"], a["radius"], a["deg"])
+    sb = pbr.Scene(b["pos"], b["sh"], b["opacity"], b["radius"], b["deg"])
+    img, st = R.forward([sa, sb], cams, pbr.default_opts(), scene_of_view=sov)
+    got = img.cpu().numpy()
+    off = 0
+    for v, c in enumerate(cams):
+        sc = (a, b)[sov[v]]
+        ref, _, _ = O.render(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], [c])
+        n = c["width"] * c["height"]
+        assert np.abs(got[off:off + n] - ref).max() <= IMG_TOL
+        off += n
+    # gradients are packed per scene
+    g = np.random.default_rng(0).normal(size=got.shape).astype(np.float32)
+    import torch
+    gpos, gsh, gop = R.backward(st, torch.from_numpy(g).cuda())
+    gpos, gsh, gop = gpos.cpu().numpy(), gsh.cpu().numpy(), gop.cpu().numpy()
+    pbase, shbase = 0, 0
+    for si, sc in enumerate((a, b)):
+        views = [v for v in range(3) if sov[v] == si]
+        pix = []
+        offs = np.cumsum([0] + [c["width"] * c["height"] for c in cams])
+        gsel = np.concatenate([g[offs[v]:offs[v + 1]] for v in views])
+        dpos, dsh, dop = O.backward(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"],
+                                    [cams[v] for v in views], gsel)
+        n, K = len(sc["pos"]), (sc["deg"] + 1) ** 2
+        assert _rel(gpos[pbase:pbase + n], dpos) <= GRAD_TOL
+        assert _rel(gsh[shbase:shbase + n * K * 3].reshape(n, K, 3), dsh) <= GRAD_TOL
+        assert _rel(gop[pbase:pbase + n], dop) <= GRAD_TOL
+        pbase += n
+        shbase += n * K * 3
+    st.close()
+
+
+# ----------------------------------------------------------------- backward
+def test_tiny_config_gradients(R):
+    """Config: L2 loss against the image of positions jittered by N(0, 0.01)."""
+    import torch
+    pbr = _pbr()
+    sc = scenes.tiny()
+    img, st, _ = _gpu_render(R, sc, sc["cams"])
+    tgt_sc = dict(sc, pos=sc["target_pos"])
+    target, tst, _ = _gpu_render(R, tgt_sc, sc["cams"])
+    tst.close()
+    loss, g = pbr.image_loss(img, target, "l2")
+    gpos, gsh, gop = R.backward(st, g)
+    gn = g.cpu().numpy().astype(np.float64)
+    dpos, dsh, dop = O.backward(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"],
+                                sc["cams"], gn)
+    e = (_rel(gpos.cpu().numpy(), dpos), _rel(gsh.cpu().numpy().reshape(dsh.shape), dsh),
+         _rel(gop.cpu().numpy(), dop))
+    print(f"tiny grads rel L2 vs FP64 oracle: pos {e[0]:.2e} sh {e[1]:.2e} opacity {e[2]:.2e}")
+    assert max(e) <= GRAD_TOL
+    ref_loss = float(((img.cpu().numpy().astype(np.float64) - target.cpu().numpy()) ** 2).sum())
+    assert abs(float(loss.item()) - ref_loss) <= 1e-6 * max(1.0, ref_loss)
+    st.close()
+
+
+@pytest.mark.parametrize("kw", [dict(dir_frame=1), dict(radius_mode=1), dict(max_per_pixel=15),
+                                dict(bg=(0.3, 0.1, 0.7)), dict(tile=(8, 8)), dict(tile=(16, 32))],
+                         ids=["world-dir", "ndc", "n15", "bg", "8x8", "16x32"])
+def test_gradient_variants(R, kw):
+    import torch
+    sc = _small_scene(20, n=400, deg=3)
+    if kw.get("radius_mode") == 1:
+        sc["radius"] = (sc["radius"] * 0.1).astype(np.float32)
+    cams = [scenes.camera((0.4, 0.6, 2.1), 72, 56), scenes.camera((-1.2, -0.2, 1.9), 40, 48)]
+    img, st, _ = _gpu_render(R, sc, cams, **kw)
+    g = np.random.default_rng(1).normal(size=img.shape).astype(np.float32)
+    gpos, gsh, gop = R.backward(st, torch.from_numpy(g).cuda())
+    dpos, dsh, dop = O.backward(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], cams,
+                                g.astype(np.float64), **_oracle_kw(kw))
+    e = (_rel(gpos.cpu().numpy(), dpos), _rel(gsh.cpu().numpy().reshape(dsh.shape), dsh),
+         _rel(gop.cpu().numpy(), dop))
+    print(f"{kw}: grads rel L2 pos {e[0]:.2e} sh {e[1]:.2e} opacity {e[2]:.2e}")
+    assert max(e) <= GRAD_TOL
+    st.close()
