@@ -1,0 +1,418 @@
+"""Benchmark of the differentiable point-splat renderer on one GB300.
+
+A step is one training pass over a batch of views of a synthetic scene:
+forward render of every view (projection, SH colour, binning, depth and tile
+sort, compositing), the image loss, and the hand-written backward pass to
+position / SH / opacity gradients.  The default workload is 1M surface
+points with SH degree 3 seen by 64 cameras of mixed resolution (60.7 MP per
+step).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload batched|static|tiny|dynamic]
+
+`--impl reference` times the FP64 CPU oracle (the only other implementation
+of the method here) on a bounded pixel sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2205_14330_gb300 import scenes  # noqa: E402
+
+METRIC = "megapixels/s fwd and fwd+bwd at 1M pts vs plain renderer; serving p50/p99 ms"
+FALLBACK_HBM_GBS = 6800.0
+
+# FP32 operations per pair (FMA counted as 2), read off the compositing loops:
+#   cutoff test: 2 sub, 2 mul, 1 add, 1 compare                       = 6
+#   forward composite: 2 mul, 1 min, 1 mul, 3 FMA (6), 1 sub          = 11 (+1 ex2)
+#   backward contribution: alpha (3), 1-alpha, 2 divides (4),
+#     weight, c.g (5), dc (3), dalpha (3), S (2), q, grads (8)        = 31 (+1 ex2)
+FLOP_TEST, FLOP_FWD, FLOP_BWD = 6, 11, 31
+
+
+def workload(name, seed=0):
+    if name == "batched":
+        sc = scenes.batched_multiview(seed)
+        desc = ("batched multi-view: 1M surface points (40 shapes), SH degree 3, 64 cameras on "
+                "a hemisphere at 400^2/800^2/1280x720/1920x1080, forward + L2 loss + backward")
+    elif name == "static":
+        sc = scenes.static_train(seed)
+        desc = ("static training step: 500k surface points, SH degree 2, 4 cameras at 800^2, "
+                "forward + L1 loss + backward")
+    elif name == "tiny":
+        sc = scenes.tiny(seed)
+        desc = "tiny: 4096 points, SH degree 2, one 128^2 camera, forward + L2 loss + backward"
+    elif name == "dynamic":
+        d = scenes.dynamic_video(seed)
+        desc = ("dynamic video: 30 frames x 200k points, SH degree 2, 16 cameras at 1024x768 "
+                "(480 views), forward + L2 loss + backward with per-frame gradients")
+        return d, desc
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return sc, desc
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            with open(p) as f:
+                d = json.load(f)
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured", d
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback", {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device, self.proc, self.path = device, None, None
+
+    def start(self):
+        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- oracle arm
+def oracle_sample(sc, n_pix, seed=0, view=0):
+    """Forward + backward of the FP64 oracle on n_pix random pixels of one
+    view; returns (seconds, pixels, threads)."""
+    from oracle import oracle as O
+    pos, sh, op, rad, deg = (sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"])
+    cam = sc["cams"][view]
+    rng = np.random.default_rng(seed)
+    pix = np.stack([np.zeros(n_pix, np.int32), rng.integers(0, cam["width"], n_pix),
+                    rng.integers(0, cam["height"], n_pix)], 1).astype(np.int32)
+    t0 = time.perf_counter()
+    rgb, _, _ = O.render(pos, sh, op, rad, deg, [cam], pix=pix)
+    g = 2.0 * (rgb - 0.5)
+    O.backward(pos, sh, op, rad, deg, [cam], g, pix=pix)
+    return time.perf_counter() - t0, n_pix, O.num_threads()
+
+
+def run_reference(args, sc, desc):
+    from oracle import oracle as O
+    O.build()
+    if "frames" in sc:
+        sc = dict(pos=sc["frames"][0], sh=sc["sh"], opacity=sc["opacity"],
+                  radius=sc["radius"], deg=sc["deg"], cams=sc["cams"])
+    n_pix = args.ref_pixels
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle_sample(sc, 64, seed=99)
+    secs, px = 0.0, 0
+    for k in range(args.steps):
+        s, p, threads = oracle_sample(sc, n_pix, seed=k)
+        secs += s
+        px += p
+    v = px / secs / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "oracle_sample_pixels": n_pix},
+            "cpu_baseline": {"value": v, "unit": "MP/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{n_pix} random pixels of view 0 per step, forward + "
+                                       "backward, FP64 brute force over every point"},
+            "e2e": {"value": v, "unit": "MP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched",
+                    choices=["batched", "static", "tiny", "dynamic"])
+    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--batch-depth", type=int, default=256)
+    ap.add_argument("--ref-pixels", type=int, default=2048)
+    ap.add_argument("--cpu-pixels", type=int, default=2048)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    sc, desc = workload(args.workload)
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, sc, desc)
+        return
+
+    import torch
+    from paper_2205_14330_gb300 import pbr
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:  # independent replicas: every rank renders its own copy of the batch
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    tw, th = (int(x) for x in args.tile.split("x"))
+    opts = pbr.default_opts(tile=(tw, th), batch_depth=args.batch_depth)
+    R = pbr.Renderer(local)
+    dev = f"cuda:{local}"
+
+    if "frames" in sc:
+        scene_list = [pbr.Scene(p, sc["sh"], sc["opacity"], sc["radius"], sc["deg"], dev)
+                      for p in sc["frames"]]
+        cams = [c for _ in sc["frames"] for c in sc["cams"]]
+        sov = [f for f in range(len(sc["frames"])) for _ in sc["cams"]]
+        n_points = sum(s.n for s in scene_list)
+    else:
+        scene_list = [pbr.Scene(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], dev)]
+        cams, sov = sc["cams"], None
+        n_points = scene_list[0].n
+    npix = pbr.n_pixels(cams)
+    mp = npix / 1e6
+    loss_kind = "l1" if sc.get("loss") == "l1" else "l2"
+
+    # target image: the same cameras with perturbed SH coefficients
+    rng = np.random.default_rng(1)
+    tgt_scenes = [pbr.Scene(s.pos, s.sh + torch.from_numpy(
+        rng.normal(0, 0.1, tuple(s.sh.shape)).astype(np.float32)).to(dev), s.opacity, s.radius,
+        s.deg, dev) for s in scene_list]
+    target, _ = R.forward(tgt_scenes, cams, opts, scene_of_view=sov, keep_state=False)
+    del tgt_scenes
+    img = torch.empty((npix, 3), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(scs=scene_list, tgt=target):
+        _, st = R.forward(scs, cams, opts, scene_of_view=sov, out=img)
+        loss, g = pbr.image_loss(img, tgt, loss_kind)
+        grads = R.backward(st, g)
+        return st, loss, grads
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    def timed(fn, k):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1) / k
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # warm-up (also sizes the stream-ordered memory pool)
+    for _ in range(max(args.warmup, 0)):
+        st, _, _ = step()
+        st.close()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K training steps, stage timing on, clocks sampled
+    clocks = ClockSampler(local)
+    R.set_stage_timing(True)
+    R.stage_times()  # reset
+    launches0 = pbr.kernel_launches()
+    states = []
+
+    def train_step():
+        st, _, _ = step()
+        states.append(st)
+
+    clocks.start()
+    ms = timed(train_step, args.steps)
+    clk = clocks.stop()
+    launches = pbr.kernel_launches() - launches0
+    stage = R.stage_times()
+    R.set_stage_timing(False)
+    pair_stats = states[-1].stats()
+    for s_ in states:
+        s_.close()
+    states.clear()
+    value = world * mp / (ms * 1e-3)
+
+    # ---- forward only
+    def fwd():
+        R.forward(scene_list, cams, opts, scene_of_view=sov, out=img, keep_state=False)
+    fwd_ms = timed(fwd, max(1, args.steps // 2))
+
+    # ---- plain single-view renderer: same kernels, one view per launch chain
+    plain = None
+    if not args.no_plain and sov is None:
+        def plain_step():
+            for v in range(len(cams)):
+                out_v = torch.empty((pbr.n_pixels([cams[v]]), 3), dtype=torch.float32, device=dev)
+                _, st = R.forward(scene_list, [cams[v]], opts, out=out_v)
+                tgt_v = target[sum(pbr.n_pixels([c]) for c in cams[:v]):][:out_v.shape[0]]
+                _, g = pbr.image_loss(out_v, tgt_v, loss_kind)
+                R.backward(st, g)
+                st.close()
+        def plain_fwd():
+            for v in range(len(cams)):
+                out_v = torch.empty((pbr.n_pixels([cams[v]]), 3), dtype=torch.float32, device=dev)
+                R.forward(scene_list, [cams[v]], opts, out=out_v, keep_state=False)
+        plain_step()
+        k = max(1, min(3, args.steps // 3))
+        p_ms = timed(plain_step, k)
+        pf_ms = timed(plain_fwd, k)
+        plain = {"fwd_bwd_mp_s": mp / (p_ms * 1e-3), "fwd_mp_s": mp / (pf_ms * 1e-3),
+                 "ms_per_step": p_ms, "speedup_fwd_bwd": p_ms / ms, "speedup_fwd": pf_ms / fwd_ms}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = []
+        for s in scene_list:
+            host.append([t.detach().cpu().pin_memory() for t in (s.pos, s.sh, s.opacity, s.radius)])
+        host_tgt = target.cpu().pin_memory()
+        dev_scenes = [pbr.Scene(torch.empty_like(s.pos), torch.empty_like(s.sh),
+                                torch.empty_like(s.opacity), torch.empty_like(s.radius), s.deg, dev)
+                      for s in scene_list]
+        dev_tgt = torch.empty_like(target)
+        n_tot = sum(s.n for s in scene_list)
+        n_sh = sum(s.sh.numel() for s in scene_list)
+        out_h = [torch.empty((n_tot, 3)).pin_memory(), torch.empty(n_sh).pin_memory(),
+                 torch.empty(n_tot).pin_memory(), torch.empty(1, dtype=torch.float64).pin_memory()]
+        h2d = sum(t.numel() * t.element_size() for ts in host for t in ts) + \
+            host_tgt.numel() * host_tgt.element_size()
+        d2h = sum(t.numel() * t.element_size() for t in out_h)
+
+        def e2e_step():
+            for hs, ds in zip(host, dev_scenes):
+                for h, d in zip(hs, (ds.pos, ds.sh, ds.opacity, ds.radius)):
+                    d.copy_(h, non_blocking=True)
+            dev_tgt.copy_(host_tgt, non_blocking=True)
+            st, loss, (gpos, gsh, gop) = step(dev_scenes, dev_tgt)
+            out_h[0].copy_(gpos, non_blocking=True)
+            out_h[1].copy_(gsh, non_blocking=True)
+            out_h[2].copy_(gop, non_blocking=True)
+            out_h[3].copy_(loss, non_blocking=True)
+            states.append(st)
+        e2e_step()
+        torch.cuda.synchronize()
+        states.clear()
+        e_ms = timed(e2e_step, max(1, args.steps // 2))
+        for s_ in states:
+            s_.close()
+        states.clear()
+        e2e = {"value": world * mp / (e_ms * 1e-3), "unit": "MP/s", "ms_per_step": e_ms,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # ---- roofline of the dominant kernel
+    hbm_peak, hbm_src, peaks = measured_peaks()
+    stage_ms = {k: v[0] / max(1, args.steps) for k, v in stage.items() if v[1]}
+    dom = max(stage_ms, key=stage_ms.get)
+    sm_mhz = (clk or {}).get("sm_mhz") or 1500.0
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
+    if dom in ("raster_fwd", "raster_bwd"):
+        if dom == "raster_fwd":
+            flops = (pair_stats["fwd_examined"] * FLOP_TEST
+                     + pair_stats["fwd_composited"] * FLOP_FWD)
+        else:
+            flops = (pair_stats["bwd_examined"] * FLOP_TEST
+                     + pair_stats["bwd_contributing"] * FLOP_BWD)
+        achieved = flops / (stage_ms[dom] * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (sampled)",
+                "work": {k: int(v) for k, v in pair_stats.items()}}
+    else:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm_peak, "unit": "GB/s",
+                "frac": None, "traffic": None, "peak_source": hbm_src}
+
+    # ---- CPU oracle on a bounded sample
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        osc = sc if "frames" not in sc else dict(pos=sc["frames"][0], sh=sc["sh"],
+                                                 opacity=sc["opacity"], radius=sc["radius"],
+                                                 deg=sc["deg"], cams=sc["cams"])
+        secs, px, threads = oracle_sample(osc, args.cpu_pixels)
+        cpu = {"value": px / secs / 1e6, "unit": "MP/s", "cores": threads, "kind": "oracle",
+               "sample": f"{px} random pixels of view 0, forward + backward, FP64 brute force "
+                         f"over all {osc['pos'].shape[0]} points ({secs:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "MP/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": desc, "points": n_points, "views": len(cams),
+                           "megapixels_per_step": mp, "tile": args.tile,
+                           "batch_depth": args.batch_depth, "loss": loss_kind,
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "l2_policy": "inputs larger than L2 (params "
+                                        f"{sum(s.pos.numel()+s.sh.numel()+2*s.n for s in scene_list)*4/1e6:.0f} MB, "
+                                        f"images {npix*12/1e6:.0f} MB per step)"},
+                "fwd_mp_s": world * mp / (fwd_ms * 1e-3), "fwd_ms": fwd_ms,
+                "plain": plain, "stage_ms": stage_ms, "roofline": roof,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches // max(1, args.steps)),
+                "gpu_launches_timed_region": int(launches), "clocks": clk,
+                "pairs": {k: int(v) for k, v in pair_stats.items()},
+                "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    R.close()
+
+
+if __name__ == "__main__":
+    main()

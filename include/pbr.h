@@ -171,6 +171,24 @@ int pbr_state_read(pbr_state *state, int32_t which, void *host_dst, size_t cap_b
 int pbr_image_loss(int32_t kind, const float *pred, const float *target, int64_t n, float *grad,
                    double *loss_dev, pbr_stream_t stream);
 
+/* Raster pair counts of a forward state (and of the backward passes run on
+ * it): out4 = {forward pairs examined, forward pairs composited, backward
+ * pairs examined, backward pairs contributing}.  These are the work units of
+ * the compositing kernels' ALU roofline.  Synchronises the state's stream. */
+int pbr_state_stats(pbr_state *state, unsigned long long *out4);
+
+/* --------------------------------------------------- measurement support */
+/* Number of CUDA kernels this library has launched in this process. */
+unsigned long long pbr_kernel_launches(void);
+/* Switches per-stage CUDA-event timing on (enable = 1) or off for the
+ * context's forward and backward calls.  Stages: 0 preprocess, 1 compact,
+ * 2 depth sort, 3 emit pairs, 4 tile sort, 5 tile ranges, 6 raster forward,
+ * 7 raster backward (with its zeroing), 8 preprocess backward, 9 other. */
+int pbr_set_stage_timing(pbr_ctx *ctx, int enable);
+/* Accumulated milliseconds and call counts per stage since the last query
+ * (arrays of n entries); resets the accumulators.  Synchronises. */
+int pbr_stage_times(pbr_ctx *ctx, double *ms, long long *calls, int n);
+
 /* ------------------------------------------------------- microbenchmarks */
 /* Measures the device's FP32 FMA rate (flop/s, an FMA counted as 2) and
  * MUFU ex2 rate (op/s) with the library's own kernels; used as the ALU

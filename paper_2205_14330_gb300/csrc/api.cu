@@ -2,6 +2,7 @@
 // layout, workspace management and the launch sequence of the forward and
 // backward passes of the point-splat renderer (Sec. 3.1-3.3).
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -13,6 +14,76 @@
 #include "api_internal.h"
 
 using namespace pbr;
+
+// --------------------------------------------------- launches and timing
+static std::atomic<unsigned long long> g_launches{0};
+void pbr::count_launches(int n) { g_launches.fetch_add((unsigned long long)n); }
+unsigned long long pbr::launches_total() { return g_launches.load(); }
+extern "C" unsigned long long pbr_kernel_launches(void) { return g_launches.load(); }
+
+static cudaEvent_t take_event(pbr_ctx *c)
+{
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+pbr::StageScope::StageScope(pbr_ctx *c, int stage, cudaStream_t s) : c_(c), stage_(stage), s_(s)
+{
+    if (!c_ || !c_->timing) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s_, &cs);
+    if (cs != cudaStreamCaptureStatusNone) return;
+    std::lock_guard<std::mutex> g(c_->timing_mu);
+    a_ = take_event(c_);
+    cudaEventRecord(a_, s_);
+}
+
+pbr::StageScope::~StageScope()
+{
+    if (!a_) return;
+    std::lock_guard<std::mutex> g(c_->timing_mu);
+    cudaEvent_t b = take_event(c_);
+    cudaEventRecord(b, s_);
+    c_->pending.push_back({stage_, a_, b});
+}
+
+extern "C" int pbr_set_stage_timing(pbr_ctx *c, int enable)
+{
+    if (!c) return PBR_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(c->timing_mu);
+    c->timing = enable != 0;
+    return PBR_OK;
+}
+
+extern "C" int pbr_stage_times(pbr_ctx *c, double *ms, long long *calls, int n)
+{
+    if (!c) return PBR_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(c->timing_mu);
+    for (auto &r : c->pending) {
+        cudaEventSynchronize(r.b);
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+            c->stage_ms[r.stage] += t;
+            c->stage_calls[r.stage] += 1;
+        }
+        c->event_pool.push_back(r.a);
+        c->event_pool.push_back(r.b);
+    }
+    c->pending.clear();
+    for (int i = 0; i < n && i < STG_COUNT; ++i) {
+        if (ms) ms[i] = c->stage_ms[i];
+        if (calls) calls[i] = c->stage_calls[i];
+        c->stage_ms[i] = 0.0;
+        c->stage_calls[i] = 0;
+    }
+    return PBR_OK;
+}
 
 // ------------------------------------------------------------------ errors
 static thread_local std::string g_err;
@@ -84,6 +155,11 @@ extern "C" int pbr_destroy(pbr_ctx *c)
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     if (c->host_counters) cudaFreeHost(c->host_counters);
+    for (auto &r : c->pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
     delete c;
     return PBR_OK;
 }
@@ -270,14 +346,17 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
     const int64_t npv = L.n_pv;
     PBR_TRY(dalloc((void **)&st->rec, sizeof(float4) * 2 * npv, s));
     PBR_TRY(dalloc((void **)&st->ntiles, sizeof(uint32_t) * npv, s));
-    PBR_TRY(dalloc((void **)&st->counters, 64, s));
+    PBR_TRY(dalloc((void **)&st->counters, 128, s));
     TempBufs tmp(s);
     uint32_t *zbits = nullptr;
     uint2 *rect = nullptr;
     PBR_TRY(tmp.alloc(&zbits, sizeof(uint32_t) * npv));
     PBR_TRY(tmp.alloc(&rect, sizeof(uint2) * npv));
-    PBR_CUDA(cudaMemsetAsync(st->counters, 0, 64, s));
-    launch_preprocess_fwd(b, o, st->rec, zbits, st->ntiles, rect, st->counters, s);
+    PBR_CUDA(cudaMemsetAsync(st->counters, 0, 128, s));
+    {
+        StageScope t(c, STG_PREPROCESS_FWD, s);
+        launch_preprocess_fwd(b, o, st->rec, zbits, st->ntiles, rect, st->counters, s);
+    }
     PBR_CUDA(cudaGetLastError());
     // size the lists
     PBR_CUDA(cudaMemcpyAsync(c->host_counters, st->counters, 16, cudaMemcpyDeviceToHost, s));
@@ -307,20 +386,32 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
     PBR_TRY(dalloc((void **)&st->T_final, sizeof(float) * L.n_pix, s));
     PBR_TRY(dalloc((void **)&st->n_contrib, sizeof(uint32_t) * L.n_pix, s));
     PBR_TRY(tmp.alloc(&temp, temp_bytes));
-    uint32_t *status = (uint32_t *)((char *)st->counters + 32);
+    uint32_t *status = (uint32_t *)((char *)st->counters + 64);
     const uint32_t *n_vis_dev = (const uint32_t *)(st->counters + 1);  // low word (< 2^32)
     const uint32_t *n_pairs_dev = (const uint32_t *)(st->counters + 0); // low word (< 2^32)
     // 1. visible point-views with their depth keys, in point-view order
-    launch_compact_visible(st->ntiles, zbits, npv, vk, vv, nullptr, temp, s);
+    {
+        StageScope t(c, STG_COMPACT, s);
+        launch_compact_visible(st->ntiles, zbits, npv, vk, vv, nullptr, temp, s);
+    }
     // 2. stable sort by fp32 depth bits
-    radix_sort_pairs(vk, vv, vk2, vv2, n_vis_dev, (int64_t)n_vis, 32, temp, s);
+    {
+        StageScope t(c, STG_DEPTH_SORT, s);
+        radix_sort_pairs(vk, vv, vk2, vv2, n_vis_dev, (int64_t)n_vis, 32, temp, s);
+    }
     // 3. duplicate per covered tile, in depth order
     uint32_t *tk = st->tile_keys, *tv = st->tile_vals;
-    launch_emit_pairs(b, o, vv, n_vis_dev, (int64_t)n_vis, st->ntiles, rect, tk, tv,
-                      (int64_t)n_pairs, status, temp, s);
+    {
+        StageScope t(c, STG_EMIT, s);
+        launch_emit_pairs(b, o, vv, n_vis_dev, (int64_t)n_vis, st->ntiles, rect, tk, tv,
+                          (int64_t)n_pairs, status, temp, s);
+    }
     // 4. stable sort by tile id
-    radix_sort_pairs(tk, tv, pk2, pv2, n_pairs_dev, (int64_t)n_pairs, key_bits_for(L.n_tiles),
-                     temp, s);
+    {
+        StageScope t(c, STG_TILE_SORT, s);
+        radix_sort_pairs(tk, tv, pk2, pv2, n_pairs_dev, (int64_t)n_pairs,
+                         key_bits_for(L.n_tiles), temp, s);
+    }
     if (tk != st->tile_keys) { // result landed in the alternate buffers: swap ownership
         for (void *&p : tmp.ptrs) {
             if (p == (void *)tk) p = (void *)st->tile_keys;
@@ -330,11 +421,18 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
         st->tile_vals = tv;
     }
     // 5. per-tile ranges
-    PBR_CUDA(cudaMemsetAsync(st->ranges, 0, sizeof(uint2) * L.n_tiles, s));
-    launch_tile_ranges(st->tile_keys, n_pairs_dev, (int64_t)n_pairs, st->ranges, L.n_tiles, s);
+    {
+        StageScope t(c, STG_RANGES, s);
+        PBR_CUDA(cudaMemsetAsync(st->ranges, 0, sizeof(uint2) * L.n_tiles, s));
+        launch_tile_ranges(st->tile_keys, n_pairs_dev, (int64_t)n_pairs, st->ranges, L.n_tiles,
+                           s);
+    }
     // 6. composite
-    launch_raster_fwd(b, o, st->batch_depth, st->ranges, st->tile_vals, st->rec, out_rgb,
-                      st->T_final, st->n_contrib, s);
+    {
+        StageScope t(c, STG_RASTER_FWD, s);
+        launch_raster_fwd(b, o, st->batch_depth, st->ranges, st->tile_vals, st->rec, out_rgb,
+                          st->T_final, st->n_contrib, st->counters + 2, s);
+    }
     PBR_CUDA(cudaGetLastError());
     return PBR_OK;
 }
@@ -379,10 +477,16 @@ extern "C" int pbr_render_backward(pbr_ctx *c, pbr_state *st, const float *grad_
     Batch b = st->batch();
     float4 *g2d = nullptr;
     PBR_TRY(dalloc((void **)&g2d, sizeof(float4) * 2 * L.n_pv, s));
-    PBR_CUDA(cudaMemsetAsync(g2d, 0, sizeof(float4) * 2 * L.n_pv, s));
-    launch_raster_bwd(b, st->dopts, st->batch_depth, st->ranges, st->tile_vals, st->rec,
-                      st->T_final, st->n_contrib, grad_rgb, g2d, s);
-    launch_preprocess_bwd(b, st->dopts, g2d, grad_pos, grad_sh, grad_opacity, s);
+    {
+        StageScope t(c, STG_RASTER_BWD, s);
+        PBR_CUDA(cudaMemsetAsync(g2d, 0, sizeof(float4) * 2 * L.n_pv, s));
+        launch_raster_bwd(b, st->dopts, st->batch_depth, st->ranges, st->tile_vals, st->rec,
+                          st->T_final, st->n_contrib, grad_rgb, g2d, st->counters + 2, s);
+    }
+    {
+        StageScope t(c, STG_PREPROCESS_BWD, s);
+        launch_preprocess_bwd(b, st->dopts, g2d, grad_pos, grad_sh, grad_opacity, s);
+    }
     cudaError_t e = cudaGetLastError();
     dfree(g2d, s);
     if (e != cudaSuccess)
@@ -404,7 +508,7 @@ extern "C" int pbr_state_info(pbr_state *st, pbr_state_info_t *info)
     if (!st || !info) return set_error(PBR_ERR_INVALID_ARG, "state or info is NULL");
     PBR_CUDA(cudaStreamSynchronize(st->stream));
     uint32_t status = 0;
-    PBR_CUDA(cudaMemcpy(&status, (char *)st->counters + 32, 4, cudaMemcpyDeviceToHost));
+    PBR_CUDA(cudaMemcpy(&status, (char *)st->counters + 64, 4, cudaMemcpyDeviceToHost));
     std::memset(info, 0, sizeof *info);
     info->n_point_views = st->layout.n_pv;
     info->n_visible = st->n_vis;
@@ -443,6 +547,15 @@ extern "C" int pbr_state_read(pbr_state *st, int32_t which, void *host_dst, size
     PBR_CUDA(cudaStreamSynchronize(st->stream));
     const size_t m = n < cap_bytes ? n : cap_bytes;
     if (m && host_dst && src) PBR_CUDA(cudaMemcpy(host_dst, src, m, cudaMemcpyDeviceToHost));
+    return PBR_OK;
+}
+
+extern "C" int pbr_state_stats(pbr_state *st, unsigned long long *out4)
+{
+    if (!st || !out4) return set_error(PBR_ERR_INVALID_ARG, "state or out is NULL");
+    PBR_CUDA(cudaStreamSynchronize(st->stream));
+    PBR_CUDA(cudaMemcpy(out4, st->counters + 2, 4 * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost));
     return PBR_OK;
 }
 

@@ -3,6 +3,7 @@
 
 #include <cstdarg>
 #include <cstdint>
+#include <mutex>
 #include <vector>
 
 #include "pbr.h"
@@ -16,6 +17,17 @@ struct pbr_ctx {
     size_t hbm_budget = 0;
     unsigned long long *host_counters = nullptr; // pinned
     ServeState *serve = nullptr;
+    // optional per-stage CUDA-event timing
+    std::mutex timing_mu;
+    bool timing = false;
+    struct StageRec {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<StageRec> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double stage_ms[pbr::STG_COUNT] = {};
+    long long stage_calls[pbr::STG_COUNT] = {};
 };
 
 namespace pbr {
@@ -53,7 +65,9 @@ struct pbr_state {
     int32_t *d_view_list = nullptr;
     float4 *rec = nullptr;
     uint32_t *ntiles = nullptr;
-    unsigned long long *counters = nullptr; // [0] pairs, [1] visible, byte 32: status
+    // [0] pairs, [1] visible, [2..3] raster-fwd examined/composited pairs,
+    // [4..5] raster-bwd examined/contributing pairs; byte 64: status word
+    unsigned long long *counters = nullptr;
     uint32_t *tile_keys = nullptr, *tile_vals = nullptr;
     uint2 *ranges = nullptr;
     float *T_final = nullptr;
@@ -97,7 +111,21 @@ struct TempBufs {
 
 namespace pbr {
 int forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s);
-}
+
+// Records CUDA events around one stage on stream s when the context has
+// stage timing switched on (pbr_set_stage_timing); otherwise does nothing.
+class StageScope {
+  public:
+    StageScope(pbr_ctx *c, int stage, cudaStream_t s);
+    ~StageScope();
+
+  private:
+    pbr_ctx *c_;
+    int stage_;
+    cudaStream_t s_;
+    cudaEvent_t a_ = nullptr;
+};
+} // namespace pbr
 
 #define PBR_CUDA(x)                                                                             \
     do {                                                                                        \

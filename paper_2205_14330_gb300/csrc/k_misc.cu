@@ -78,6 +78,7 @@ void launch_image_loss(int kind, const float *pred, const float *target, int64_t
     int64_t blocks = (n + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     image_loss_kernel<<<(unsigned)blocks, 256, 0, s>>>(kind, pred, target, n, grad, loss);
+    count_launches(1);
 }
 
 int measure_alu_peaks(int device, double *fp32_flops, double *ex2_ops)

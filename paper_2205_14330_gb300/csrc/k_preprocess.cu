@@ -300,6 +300,7 @@ void launch_preprocess_fwd(const Batch &b, const DevOpts &o, float4 *rec, uint32
     if (b.n_point_blocks <= 0) return;
     preprocess_fwd_kernel<<<(unsigned)b.n_point_blocks, PRE_THREADS, 0, s>>>(
         b, o, rec, zbits, ntiles, rect, counters);
+    count_launches(1);
 }
 
 void launch_preprocess_bwd(const Batch &b, const DevOpts &o, const float4 *g2d, float *grad_pos,
@@ -308,6 +309,7 @@ void launch_preprocess_bwd(const Batch &b, const DevOpts &o, const float4 *g2d, 
     if (b.n_point_blocks <= 0) return;
     preprocess_bwd_kernel<<<(unsigned)b.n_point_blocks, PRE_THREADS, 0, s>>>(
         b, o, g2d, grad_pos, grad_sh, grad_opacity);
+    count_launches(1);
 }
 
 } // namespace pbr

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(TW * TH)
 raster_fwd_kernel(Batch b, DevOpts o, int depth, const uint2 *__restrict__ ranges,
                   const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
                   float *__restrict__ out_rgb, float *__restrict__ T_final,
-                  uint32_t *__restrict__ n_contrib)
+                  uint32_t *__restrict__ n_contrib, unsigned long long *__restrict__ stats)
 {
     extern __shared__ float4 s_rec[]; // [depth] a-part, then [depth] b-part
     float4 *s_a = s_rec, *s_b = s_rec + depth;
@@ -65,7 +65,7 @@ raster_fwd_kernel(Batch b, DevOpts o, int depth, const uint2 *__restrict__ range
     const uint32_t s = rg.x, e = rg.y > rg.x ? rg.y : rg.x;
 
     float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    uint32_t cnt = 0, last = 0;
+    uint32_t cnt = 0, last = 0, examined = 0;
     bool done = !inside;
     const uint32_t maxpp = (uint32_t)o.max_per_pixel;
     for (uint32_t base = s; base < e; base += depth) {
@@ -78,7 +78,8 @@ raster_fwd_kernel(Batch b, DevOpts o, int depth, const uint2 *__restrict__ range
         }
         __syncthreads();
         if (!done) {
-            for (int k = 0; k < nb; ++k) {
+            int k = 0;
+            for (; k < nb; ++k) {
                 const float4 a = s_a[k];
                 const float dx = __fsub_rn(ux, a.x), dy = __fsub_rn(uy, a.y);
                 const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
@@ -94,10 +95,20 @@ raster_fwd_kernel(Batch b, DevOpts o, int depth, const uint2 *__restrict__ range
                     last = base + k - s + 1;
                     if (T < o.t_eps || cnt == maxpp) {
                         done = true;
+                        ++k;
                         break;
                     }
                 }
             }
+            examined += k;
+        }
+    }
+    if (stats) { // pair counts for the ALU roofline: [0] examined, [1] composited
+        const uint32_t we = __reduce_add_sync(0xffffffffu, examined);
+        const uint32_t wc = __reduce_add_sync(0xffffffffu, cnt);
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(stats, (unsigned long long)we);
+            atomicAdd(stats + 1, (unsigned long long)wc);
         }
     }
     if (inside) {
@@ -147,7 +158,8 @@ __global__ void __launch_bounds__(TW * TH)
 raster_bwd_kernel(Batch b, DevOpts o, int depth, const uint2 *__restrict__ ranges,
                   const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
                   const float *__restrict__ T_final, const uint32_t *__restrict__ n_contrib,
-                  const float *__restrict__ grad_rgb, float *__restrict__ g2d)
+                  const float *__restrict__ grad_rgb, float *__restrict__ g2d,
+                  unsigned long long *__restrict__ stats)
 {
     extern __shared__ float4 s_rec[];
     float4 *s_a = s_rec, *s_b = s_rec + depth;
@@ -183,6 +195,7 @@ raster_bwd_kernel(Batch b, DevOpts o, int depth, const uint2 *__restrict__ range
 #pragma unroll
     for (int j = 0; j < TW * TH / 32; ++j) maxL = max(maxL, s_max[j]);
 
+    uint32_t examined = 0, used = 0;
     for (int64_t bend = maxL; bend > 0; bend -= depth) {
         const uint32_t bstart = (uint32_t)(bend > depth ? bend - depth : 0);
         const int nb = (int)(bend - bstart);
@@ -199,12 +212,14 @@ raster_bwd_kernel(Batch b, DevOpts o, int depth, const uint2 *__restrict__ range
             float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool contrib = false;
             if (idx < L) {
+                ++examined;
                 const float4 a = s_a[k];
                 const float dx = __fsub_rn(ux, a.x), dy = __fsub_rn(uy, a.y);
                 const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
                 const float4 c = s_b[k];
                 if (d2 <= c.w) {
                     contrib = true;
+                    ++used;
                     const float G = ex2_approx(d2 * a.z);
                     const float raw = a.w * G;
                     const float alpha = fminf(o.alpha_max, raw);
@@ -235,55 +250,70 @@ raster_bwd_kernel(Batch b, DevOpts o, int depth, const uint2 *__restrict__ range
             }
         }
     }
+    if (stats) { // [2] examined, [3] contributing
+        const uint32_t we = __reduce_add_sync(0xffffffffu, examined);
+        const uint32_t wu = __reduce_add_sync(0xffffffffu, used);
+        if (lane == 0) {
+            atomicAdd(stats + 2, (unsigned long long)we);
+            atomicAdd(stats + 3, (unsigned long long)wu);
+        }
+    }
 }
 
 template <int TW, int TH>
 void fwd_dispatch(const Batch &b, const DevOpts &o, int depth, const uint2 *ranges,
                   const uint32_t *pv_list, const float4 *rec, float *out_rgb, float *T_final,
-                  uint32_t *n_contrib, cudaStream_t s)
+                  uint32_t *n_contrib, unsigned long long *stats, cudaStream_t s)
 {
     const size_t smem = (size_t)depth * 2 * sizeof(float4);
     raster_fwd_kernel<TW, TH><<<b.n_tiles, TW * TH, smem, s>>>(b, o, depth, ranges, pv_list, rec,
-                                                              out_rgb, T_final, n_contrib);
+                                                              out_rgb, T_final, n_contrib, stats);
+    count_launches(1);
 }
 
 template <int TW, int TH>
 void bwd_dispatch(const Batch &b, const DevOpts &o, int depth, const uint2 *ranges,
                   const uint32_t *pv_list, const float4 *rec, const float *T_final,
-                  const uint32_t *n_contrib, const float *grad_rgb, float4 *g2d, cudaStream_t s)
+                  const uint32_t *n_contrib, const float *grad_rgb, float4 *g2d,
+                  unsigned long long *stats, cudaStream_t s)
 {
     const size_t smem = (size_t)depth * (2 * sizeof(float4) + sizeof(uint32_t));
     raster_bwd_kernel<TW, TH><<<b.n_tiles, TW * TH, smem, s>>>(
-        b, o, depth, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d);
+        b, o, depth, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d, stats);
+    count_launches(1);
 }
 
 } // namespace
 
 void launch_raster_fwd(const Batch &b, const DevOpts &o, int depth, const uint2 *ranges,
                        const uint32_t *pv_list, const float4 *rec, float *out_rgb,
-                       float *T_final, uint32_t *n_contrib, cudaStream_t s)
+                       float *T_final, uint32_t *n_contrib, unsigned long long *stats,
+                       cudaStream_t s)
 {
     if (b.n_tiles == 0) return;
     if (o.tile_w == 8 && o.tile_h == 8)
-        fwd_dispatch<8, 8>(b, o, depth, ranges, pv_list, rec, out_rgb, T_final, n_contrib, s);
+        fwd_dispatch<8, 8>(b, o, depth, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats, s);
     else if (o.tile_w == 16 && o.tile_h == 32)
-        fwd_dispatch<16, 32>(b, o, depth, ranges, pv_list, rec, out_rgb, T_final, n_contrib, s);
+        fwd_dispatch<16, 32>(b, o, depth, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats, s);
     else
-        fwd_dispatch<16, 16>(b, o, depth, ranges, pv_list, rec, out_rgb, T_final, n_contrib, s);
+        fwd_dispatch<16, 16>(b, o, depth, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats, s);
 }
 
 void launch_raster_bwd(const Batch &b, const DevOpts &o, int depth, const uint2 *ranges,
                        const uint32_t *pv_list, const float4 *rec, const float *T_final,
                        const uint32_t *n_contrib, const float *grad_rgb, float4 *g2d,
-                       cudaStream_t s)
+                       unsigned long long *stats, cudaStream_t s)
 {
     if (b.n_tiles == 0) return;
     if (o.tile_w == 8 && o.tile_h == 8)
-        bwd_dispatch<8, 8>(b, o, depth, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, g2d, s);
+        bwd_dispatch<8, 8>(b, o, depth, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, g2d,
+                           stats, s);
     else if (o.tile_w == 16 && o.tile_h == 32)
-        bwd_dispatch<16, 32>(b, o, depth, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, g2d, s);
+        bwd_dispatch<16, 32>(b, o, depth, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, g2d,
+                             stats, s);
     else
-        bwd_dispatch<16, 16>(b, o, depth, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, g2d, s);
+        bwd_dispatch<16, 16>(b, o, depth, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, g2d,
+                             stats, s);
 }
 
 } // namespace pbr

@@ -176,6 +176,7 @@ void run_scan(Load ld, Act act, const uint32_t *n_dev, int64_t cap, void *temp,
     scan_reduce_kernel<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(ld, n_dev, cap, sums);
     scan_top_kernel<<<1, 1024, 0, s>>>(sums, nb, total, status);
     scan_down_kernel<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(ld, act, n_dev, cap, sums);
+    count_launches(3);
 }
 
 // ----------------------------------------------------------- functors
@@ -395,6 +396,7 @@ void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *&keys_alt, uin
         run_scan(LoadU32{hist}, ActStore{hist}, nullptr, nb * RADIX, scan_tmp, nullptr, nullptr, s);
         radix_scatter_kernel<<<(unsigned)nb, SORT_THREADS, 0, s>>>(keys, vals, keys_alt, vals_alt,
                                                                    n_dev, cap, shift, hist, nb);
+        count_launches(2);
         uint32_t *tk = keys, *tv = vals;
         keys = keys_alt;
         vals = vals_alt;
@@ -421,6 +423,7 @@ void launch_tile_ranges(const uint32_t *keys, const uint32_t *n_pairs, int64_t c
     const int th = 256;
     const int64_t nb = (cap_pairs + th - 1) / th;
     tile_ranges_kernel<<<(unsigned)nb, th, 0, s>>>(keys, n_pairs, cap_pairs, ranges, n_tiles);
+    count_launches(1);
 }
 
 } // namespace pbr

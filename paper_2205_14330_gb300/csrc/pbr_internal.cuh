@@ -65,6 +65,25 @@ struct Batch {
 
 constexpr int PRE_THREADS = 128;
 
+// Stages of a pass, for the optional per-stage CUDA-event timing.
+enum Stage : int {
+    STG_PREPROCESS_FWD = 0,
+    STG_COMPACT,
+    STG_DEPTH_SORT,
+    STG_EMIT,
+    STG_TILE_SORT,
+    STG_RANGES,
+    STG_RASTER_FWD,
+    STG_RASTER_BWD,
+    STG_PREPROCESS_BWD,
+    STG_OTHER,
+    STG_COUNT
+};
+
+// Number of kernels this library has launched (process-wide).
+void count_launches(int n);
+unsigned long long launches_total();
+
 // log2(e) and the factor that turns q' = -log2(e) / (2 s^2) into q = 1 / s^2
 constexpr float LOG2E = 1.4426950408889634f;
 constexpr float QP_TO_Q = -2.0f / 1.4426950408889634f;
@@ -102,11 +121,12 @@ void launch_tile_ranges(const uint32_t *keys, const uint32_t *n_pairs, int64_t c
 // ---- raster (k_raster.cu)
 void launch_raster_fwd(const Batch &b, const DevOpts &o, int batch_depth, const uint2 *ranges,
                        const uint32_t *pv_list, const float4 *rec, float *out_rgb,
-                       float *T_final, uint32_t *n_contrib, cudaStream_t s);
+                       float *T_final, uint32_t *n_contrib, unsigned long long *stats,
+                       cudaStream_t s);
 void launch_raster_bwd(const Batch &b, const DevOpts &o, int batch_depth, const uint2 *ranges,
                        const uint32_t *pv_list, const float4 *rec, const float *T_final,
                        const uint32_t *n_contrib, const float *grad_rgb, float4 *g2d,
-                       cudaStream_t s);
+                       unsigned long long *stats, cudaStream_t s);
 
 // ---- misc (k_misc.cu)
 void launch_image_loss(int kind, const float *pred, const float *target, int64_t n, float *grad,

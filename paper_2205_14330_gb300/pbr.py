@@ -59,6 +59,9 @@ class StateInfo(C.Structure):
                 ("n_contrib", C.c_void_p)]
 
 
+STAGES = ["preprocess_fwd", "compact", "depth_sort", "emit_pairs", "tile_sort", "tile_ranges",
+          "raster_fwd", "raster_bwd", "preprocess_bwd", "other"]
+
 _lib = None
 _lock = threading.Lock()
 
@@ -86,6 +89,12 @@ def lib():
             L.pbr_state_info.argtypes = [vp, C.POINTER(StateInfo)]
             L.pbr_state_read.argtypes = [vp, i32, vp, C.c_size_t, C.POINTER(C.c_size_t)]
             L.pbr_image_loss.argtypes = [i32, vp, vp, i64, vp, vp, vp]
+            L.pbr_state_stats.argtypes = [vp, C.POINTER(C.c_ulonglong)]
+            L.pbr_kernel_launches.restype = C.c_ulonglong
+            L.pbr_kernel_launches.argtypes = []
+            L.pbr_set_stage_timing.argtypes = [vp, C.c_int]
+            L.pbr_stage_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                                          C.c_int]
             L.pbr_measure_alu_peaks.argtypes = [C.c_int, C.POINTER(C.c_double),
                                                 C.POINTER(C.c_double)]
             _lib = L
@@ -187,6 +196,13 @@ class State:
             out = out.reshape(-1, 8)
         return out
 
+    def stats(self) -> dict:
+        """Raster pair counts (the compositing kernels' work units)."""
+        out = (C.c_ulonglong * 4)()
+        check(lib().pbr_state_stats(self.handle, out))
+        return dict(fwd_examined=out[0], fwd_composited=out[1], bwd_examined=out[2],
+                    bwd_contributing=out[3])
+
     def close(self):
         if self.handle:
             lib().pbr_state_free(self.renderer.ctx, self.handle)
@@ -217,6 +233,16 @@ class Renderer:
             self.close()
         except Exception:
             pass
+
+    def set_stage_timing(self, enable: bool):
+        check(lib().pbr_set_stage_timing(self.ctx, 1 if enable else 0))
+
+    def stage_times(self) -> dict:
+        """{stage: (ms, calls)} accumulated since the last call (synchronises)."""
+        ms = (C.c_double * len(STAGES))()
+        calls = (C.c_longlong * len(STAGES))()
+        check(lib().pbr_stage_times(self.ctx, ms, calls, len(STAGES)))
+        return {name: (ms[i], calls[i]) for i, name in enumerate(STAGES)}
 
     def forward(self, scenes, cams, opts=None, scene_of_view=None, keep_state=True, out=None):
         """Renders every camera; returns (image [sum H W, 3] fp32 on device, State|None)."""
@@ -258,6 +284,10 @@ def image_loss(pred, target, kind="l2"):
     check(lib().pbr_image_loss(0 if kind == "l2" else 1, _ptr(pred), _ptr(target), pred.numel(),
                                _ptr(grad), _ptr(loss), _stream()))
     return loss, grad
+
+
+def kernel_launches() -> int:
+    return int(lib().pbr_kernel_launches())
 
 
 def measure_alu_peaks(device: int = 0):
