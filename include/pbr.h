@@ -189,6 +189,31 @@ int pbr_set_stage_timing(pbr_ctx *ctx, int enable);
  * (arrays of n entries); resets the accumulators.  Synchronises. */
 int pbr_stage_times(pbr_ctx *ctx, double *ms, long long *calls, int n);
 
+/* ------------------------------------------------ allocation-free forward */
+/* The paper has no counterpart: this is a deployment variant of
+ * pbr_render_forward (forward only, no state) for callers that cannot
+ * allocate device memory -- e.g. plug-ins running under a host
+ * application's allocator, or real-time loops that must not call the
+ * allocator after start-up.  All intermediate buffers live in one static
+ * device array of 16 MiB inside the library (held by every GPU that loads
+ * it, until exit); scenes, cameras and out_rgb are as for
+ * pbr_render_forward.  Calls no cudaMalloc/cudaFree/cudaMallocAsync.
+ *   - A pass that needs more than the 16 MiB (roughly: 48 B per point-view,
+ *     8 B per pixel, 16 B per (tile, point-view) pair, plus sort scratch) is
+ *     rejected with PBR_ERR_CAPACITY and a message giving the size needed;
+ *     the check on pair counts happens after the per-point stage.
+ *   - The first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress (with that device current); make that first call
+ *     before any stream capture.
+ *   - Every call shares the array and it keeps the last call's contents
+ *     (counters and tile ranges are cleared on each call); calls whose GPU
+ *     work overlaps -- other streams or other host threads -- race on it.
+ *   - Synchronises the stream once, like pbr_render_forward. */
+int pbr_render_forward_noalloc(const pbr_points *scenes, int32_t n_scenes,
+                               const int32_t *scene_of_view, const pbr_camera *cams,
+                               int32_t n_cams, const pbr_render_opts *opts, float *out_rgb,
+                               pbr_stream_t stream);
+
 /* ------------------------------------------------------- microbenchmarks */
 /* Measures the device's FP32 FMA rate (flop/s, an FMA counted as 2) and
  * MUFU ex2 rate (op/s) with the library's own kernels; used as the ALU

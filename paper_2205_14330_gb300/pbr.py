@@ -89,6 +89,9 @@ def lib():
             L.pbr_state_info.argtypes = [vp, C.POINTER(StateInfo)]
             L.pbr_state_read.argtypes = [vp, i32, vp, C.c_size_t, C.POINTER(C.c_size_t)]
             L.pbr_image_loss.argtypes = [i32, vp, vp, i64, vp, vp, vp]
+            L.pbr_render_forward_noalloc.argtypes = [C.POINTER(Points), i32, vp,
+                                                     C.POINTER(Camera), i32, C.POINTER(Opts),
+                                                     vp, vp]
             L.pbr_state_stats.argtypes = [vp, C.POINTER(C.c_ulonglong)]
             L.pbr_kernel_launches.restype = C.c_ulonglong
             L.pbr_kernel_launches.argtypes = []
@@ -275,6 +278,24 @@ class Renderer:
         check(lib().pbr_render_backward(self.ctx, state.handle, _ptr(g), _ptr(gpos), _ptr(gsh),
                                         _ptr(gop) if gop is not None else None, _stream()))
         return gpos, gsh, gop
+
+
+def render_forward_noalloc(scenes, cams, opts=None, scene_of_view=None, out=None):
+    """Forward render through pbr_render_forward_noalloc (the library keeps
+    all intermediate buffers in a fixed 16 MiB device array and allocates
+    nothing; sizes beyond it raise PBRError CAPACITY)."""
+    scenes = scenes if isinstance(scenes, (list, tuple)) else [scenes]
+    opts = opts or default_opts()
+    pts = (Points * len(scenes))(*[s.points() for s in scenes])
+    cam_arr = make_cameras(cams)
+    sov = None
+    if scene_of_view is not None:
+        sov = (C.c_int32 * len(cams))(*[int(x) for x in scene_of_view])
+    if out is None:
+        out = torch.empty((n_pixels(cams), 3), dtype=torch.float32, device=scenes[0].pos.device)
+    check(lib().pbr_render_forward_noalloc(pts, len(scenes), sov, cam_arr, len(cams),
+                                           C.byref(opts), _ptr(out), _stream()))
+    return out
 
 
 def image_loss(pred, target, kind="l2"):
