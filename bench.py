@@ -176,7 +176,8 @@ def main():
     ap.add_argument("--workload", default="batched",
                     choices=["batched", "static", "tiny", "dynamic"])
     ap.add_argument("--tile", default="16x16")
-    ap.add_argument("--batch-depth", type=int, default=256)
+    ap.add_argument("--batch-depth", type=int, default=0,
+                    help="0 = warp-streamed compositing, else block-staged batch size")
     ap.add_argument("--ref-pixels", type=int, default=2048)
     ap.add_argument("--cpu-pixels", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -284,6 +285,8 @@ def main():
     stage = R.stage_times()
     R.set_stage_timing(False)
     pair_stats = states[-1].stats()
+    sizes = {k: int(v) for k, v in states[-1].info().items()
+             if k in ("n_point_views", "n_visible", "n_pairs", "n_tiles", "n_pixels")}
     for s_ in states:
         s_.close()
     states.clear()
@@ -406,7 +409,7 @@ def main():
                 "plain": plain, "stage_ms": stage_ms, "roofline": roof,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches // max(1, args.steps)),
                 "gpu_launches_timed_region": int(launches), "clocks": clk,
-                "pairs": {k: int(v) for k, v in pair_stats.items()},
+                "pairs": {k: int(v) for k, v in pair_stats.items()}, "sizes": sizes,
                 "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src}
         print(json.dumps(line))
     if dist is not None:

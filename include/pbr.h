@@ -84,7 +84,10 @@ typedef struct {
     float bg[3];           /* background colour (default 0) */
     float z_near;          /* points with z <= z_near are culled (default 0.01) */
     int32_t tile_w, tile_h;/* tile size: 8x8, 16x16 (default) or 16x32 */
-    int32_t batch_depth;   /* points staged per block batch: 64..512 (default 256) */
+    int32_t batch_depth;   /* compositing schedule: 0 (default) = warp-streamed (each
+                              warp walks its tile list alone, no block barriers);
+                              32..1024 (multiple of 32) = block-staged batches of
+                              that many points in shared memory */
     int32_t reserved[4];
 } pbr_render_opts;
 
@@ -112,7 +115,7 @@ typedef struct {
     const uint32_t *tile_keys;  /* [n_pairs] global tile id, sorted */
     const uint32_t *tile_vals;  /* [n_pairs] point-view id, (tile, depth, id) order */
     const uint32_t *ranges;     /* [n_tiles][2] start, end into the lists */
-    const float *records;       /* [n_point_views][8] px, py, q', o, r, g, b, rc^2 */
+    const float *records;       /* [n_point_views][8] px, py, rc^2, q', o, r, g, b */
     const uint32_t *ntiles;     /* [n_point_views] tiles covered (0 = culled) */
     const float *T_final;       /* [n_pixels] transmittance after compositing */
     const uint32_t *n_contrib;  /* [n_pixels] list position after the last composited point */

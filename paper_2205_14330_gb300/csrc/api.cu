@@ -116,7 +116,7 @@ extern "C" void pbr_default_opts(pbr_render_opts *o)
     o->z_near = 0.01f;
     o->tile_w = 16;
     o->tile_h = 16;
-    o->batch_depth = 256;
+    o->batch_depth = 0;
 }
 
 // ---------------------------------------------------------------- context
@@ -171,8 +171,9 @@ int pbr::check_opts(const pbr_render_opts *o)
     const bool tile_ok = (o->tile_w == 8 && o->tile_h == 8) || (o->tile_w == 16 && o->tile_h == 16) ||
                          (o->tile_w == 16 && o->tile_h == 32);
     if (!tile_ok) return set_error(PBR_ERR_INVALID_ARG, "tile must be 8x8, 16x16 or 16x32");
-    if (o->batch_depth < 32 || o->batch_depth > 1024 || (o->batch_depth & 31))
-        return set_error(PBR_ERR_INVALID_ARG, "batch_depth must be a multiple of 32 in [32,1024]");
+    if (o->batch_depth != 0 && (o->batch_depth < 32 || o->batch_depth > 1024 || (o->batch_depth & 31)))
+        return set_error(PBR_ERR_INVALID_ARG,
+                         "batch_depth must be 0 (warp-streamed) or a multiple of 32 in [32,1024]");
     if (!(o->alpha_max > 0.f && o->alpha_max < 1.f))
         return set_error(PBR_ERR_INVALID_ARG, "alpha_max must be in (0,1)");
     if (!(o->t_eps >= 0.f) || !(o->cutoff_k > 0.f) || o->max_per_pixel < 0)
@@ -353,15 +354,19 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
     PBR_TRY(tmp.alloc(&zbits, sizeof(uint32_t) * npv));
     PBR_TRY(tmp.alloc(&rect, sizeof(uint2) * npv));
     PBR_CUDA(cudaMemsetAsync(st->counters, 0, 128, s));
+    PBR_CUDA(cudaMemsetAsync((char *)st->counters + 48, 0xff, 4, s)); // depth-bits minimum
     {
         StageScope t(c, STG_PREPROCESS_FWD, s);
         launch_preprocess_fwd(b, o, st->rec, zbits, st->ntiles, rect, st->counters, s);
     }
     PBR_CUDA(cudaGetLastError());
     // size the lists
-    PBR_CUDA(cudaMemcpyAsync(c->host_counters, st->counters, 16, cudaMemcpyDeviceToHost, s));
+    PBR_CUDA(cudaMemcpyAsync(c->host_counters, st->counters, 64, cudaMemcpyDeviceToHost, s));
     PBR_CUDA(cudaStreamSynchronize(s));
     const uint64_t n_pairs = c->host_counters[0], n_vis = c->host_counters[1];
+    const uint32_t zlo = ((const uint32_t *)c->host_counters)[12];
+    const uint32_t zhi = ((const uint32_t *)c->host_counters)[13];
+    const int depth_bits = (n_vis > 0 && zhi > zlo) ? 32 - __builtin_clz(zhi - zlo) : 0;
     if (n_pairs >= UINT32_MAX) {
         return set_error(PBR_ERR_CAPACITY, "%llu (tile, point-view) pairs exceed 2^32-1",
                          (unsigned long long)n_pairs);
@@ -373,7 +378,7 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
     void *temp = nullptr;
     const int64_t cap_sort = std::max<int64_t>(n_vis, n_pairs);
     const size_t temp_bytes = std::max(std::max(scan_temp_bytes(npv), radix_temp_bytes(cap_sort)),
-                                       scan_temp_bytes(n_vis));
+                                       emit_temp_bytes((int64_t)n_vis));
     PBR_TRY(tmp.alloc(&vk, sizeof(uint32_t) * n_vis));
     PBR_TRY(tmp.alloc(&vv, sizeof(uint32_t) * n_vis));
     PBR_TRY(tmp.alloc(&vk2, sizeof(uint32_t) * n_vis));
@@ -397,7 +402,7 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
     // 2. stable sort by fp32 depth bits
     {
         StageScope t(c, STG_DEPTH_SORT, s);
-        radix_sort_pairs(vk, vv, vk2, vv2, n_vis_dev, (int64_t)n_vis, 32, temp, s);
+        radix_sort_pairs(vk, vv, vk2, vv2, n_vis_dev, (int64_t)n_vis, depth_bits, temp, s, zlo);
     }
     // 3. duplicate per covered tile, in depth order
     uint32_t *tk = st->tile_keys, *tv = st->tile_vals;

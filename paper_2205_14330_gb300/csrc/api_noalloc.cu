@@ -135,6 +135,7 @@ extern "C" int pbr_render_forward_noalloc(const pbr_points *scenes, int32_t n_sc
     const int64_t cap_sort = n_vis > n_pairs ? (int64_t)n_vis : (int64_t)n_pairs;
     size_t temp_bytes = scan_temp_bytes(npv);
     if (radix_temp_bytes(cap_sort) > temp_bytes) temp_bytes = radix_temp_bytes(cap_sort);
+    if (emit_temp_bytes((int64_t)n_vis) > temp_bytes) temp_bytes = emit_temp_bytes((int64_t)n_vis);
     uint32_t *vk = cv.take<uint32_t>(4 * n_vis), *vv = cv.take<uint32_t>(4 * n_vis);
     uint32_t *vk2 = cv.take<uint32_t>(4 * n_vis), *vv2 = cv.take<uint32_t>(4 * n_vis);
     uint32_t *tk = cv.take<uint32_t>(4 * n_pairs), *tv = cv.take<uint32_t>(4 * n_pairs);

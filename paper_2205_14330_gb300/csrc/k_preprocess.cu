@@ -3,7 +3,7 @@
 // preprocess_fwd (Sec. 3.1 Eqs. 1-4, Sec. 3.2 cutoff): one thread per point,
 // looping over every view of the point's scene, so position, radius,
 // opacity and the [K,3] SH block are read from HBM once per batch.  For each
-// (view, point) it writes a 32-byte record {px, py, q', o, r, g, b, rc^2},
+// (view, point) it writes a 32-byte record {px, py, rc^2, q'} {o, r, g, b},
 // the fp32 depth bits, the covered tile rectangle and the tile count.
 //
 // The discrete decisions (cull, cutoff radius, pixel box, tile rectangle,
@@ -49,7 +49,8 @@ template <int DEG>
 __device__ void pre_fwd_point(const Batch &b, const DevOpts &o, const DevScene &sc, int64_t i,
                               const float *hs, float4 *__restrict__ rec,
                               uint32_t *__restrict__ zbits, uint32_t *__restrict__ ntiles,
-                              uint2 *__restrict__ rect, uint32_t &vis_cnt, uint32_t &pair_cnt)
+                              uint2 *__restrict__ rect, uint32_t &vis_cnt, uint32_t &pair_cnt,
+                              uint32_t &zlo, uint32_t &zhi)
 {
     constexpr int K = SH<DEG>::K;
     float h[K * 3];
@@ -118,13 +119,15 @@ __device__ void pre_fwd_point(const Batch &b, const DevOpts &o, const DevScene &
                     c2 = fmaf(h[3 * k + 2], Y[k], c2);
                 }
                 const float qp = -0.5f * LOG2E / (sg * sg);
-                rec[2 * pv] = make_float4(px, py, qp, op);
-                rec[2 * pv + 1] = make_float4(c0, c1, c2, rc2);
+                rec[2 * pv] = make_float4(px, py, rc2, qp);
+                rec[2 * pv + 1] = make_float4(op, c0, c1, c2);
                 zbits[pv] = __float_as_uint(z);
                 rect[pv] = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16),
                                       (uint32_t)tx1 | ((uint32_t)ty1 << 16));
                 ++vis_cnt;
                 pair_cnt += nt;
+                zlo = min(zlo, __float_as_uint(z));
+                zhi = max(zhi, __float_as_uint(z));
             }
         }
         ntiles[pv] = nt;
@@ -145,23 +148,30 @@ preprocess_fwd_kernel(Batch b, DevOpts o, float4 *__restrict__ rec, uint32_t *__
     const int K3 = sc.K * 3;
     stage_sh(sc.sh, first, count, K3, s_sh);
     __syncthreads();
-    uint32_t vis = 0, pairs = 0;
+    uint32_t vis = 0, pairs = 0, zlo = 0xffffffffu, zhi = 0u;
     if ((int)threadIdx.x < count) {
         const int64_t i = first + threadIdx.x;
         const float *hs = s_sh + threadIdx.x * K3;
         switch (sc.deg) {
-        case 0: pre_fwd_point<0>(b, o, sc, i, hs, rec, zbits, ntiles, rect, vis, pairs); break;
-        case 1: pre_fwd_point<1>(b, o, sc, i, hs, rec, zbits, ntiles, rect, vis, pairs); break;
-        case 2: pre_fwd_point<2>(b, o, sc, i, hs, rec, zbits, ntiles, rect, vis, pairs); break;
-        default: pre_fwd_point<3>(b, o, sc, i, hs, rec, zbits, ntiles, rect, vis, pairs); break;
+        case 0: pre_fwd_point<0>(b, o, sc, i, hs, rec, zbits, ntiles, rect, vis, pairs, zlo, zhi); break;
+        case 1: pre_fwd_point<1>(b, o, sc, i, hs, rec, zbits, ntiles, rect, vis, pairs, zlo, zhi); break;
+        case 2: pre_fwd_point<2>(b, o, sc, i, hs, rec, zbits, ntiles, rect, vis, pairs, zlo, zhi); break;
+        default: pre_fwd_point<3>(b, o, sc, i, hs, rec, zbits, ntiles, rect, vis, pairs, zlo, zhi); break;
         }
     }
-    // per-warp totals, one atomic per warp: counters[0] pairs, [1] visible
+    // per-warp totals, one atomic per warp: counters[0] pairs, [1] visible,
+    // 32-bit words 12 / 13: smallest / largest depth bits of a visible pv
     vis = __reduce_add_sync(0xffffffffu, vis);
     pairs = __reduce_add_sync(0xffffffffu, pairs);
+    zlo = __reduce_min_sync(0xffffffffu, zlo);
+    zhi = __reduce_max_sync(0xffffffffu, zhi);
     if ((threadIdx.x & 31) == 0) {
         if (pairs) atomicAdd(counters, (unsigned long long)pairs);
-        if (vis) atomicAdd(counters + 1, (unsigned long long)vis);
+        if (vis) {
+            atomicAdd(counters + 1, (unsigned long long)vis);
+            atomicMin((unsigned int *)counters + 12, zlo);
+            atomicMax((unsigned int *)counters + 13, zhi);
+        }
     }
 }
 

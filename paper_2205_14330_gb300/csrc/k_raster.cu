@@ -1,27 +1,36 @@
 // Per-tile compositing of Sec. 3.2 and its adjoint.
 //
-// raster_fwd: one block per screen tile, one thread per pixel.  The tile's
-// list (already ordered by depth, then point id) is staged through shared
-// memory in batches of `depth` records.  Per pixel centre u and listed point
+// Per pixel centre u and listed point (records {px, py, rc^2, q'} {o, rgb}):
 //   d2 = (ux - px)^2 + (uy - py)^2            (fp32, round-to-nearest, no FMA)
 //   if d2 <= rc^2:                             (the cutoff of Sec. 3.2)
 //     alpha = min(alpha_max, o * 2^(q' d2))    (Eq. 5, q' = -log2(e)/(2 s^2))
 //     C += T alpha c ;  T *= (1 - alpha)       (Eqs. 6-7, front to back)
 // stopping after the point that takes T below t_eps or reaches the count
-// cap.  A block leaves the list as soon as every pixel in it has stopped
-// (__syncthreads_count).  Writes C + T bg, T and the list position just
-// after the last composited point.
+// cap.  Outputs C + T bg, T and the list position just after the last
+// composited point.
 //
-// raster_bwd: same tiling, walking each pixel's list back to front from its
-// last composited point.  T before a point is recovered as T_after/(1-alpha);
-// S accumulates the colour behind the point, so
+// The adjoint walks each pixel's list back to front from that position.  T
+// before a point is recovered as T_after/(1-alpha); S accumulates the colour
+// behind the point, so
 //   dL/dc     = alpha T g
 //   dL/dalpha = T (c.g) - S / (1 - alpha)
 // and, below the alpha_max clamp,
 //   dL/do = dL/dalpha G,  dL/dp = dL/dalpha alpha q (u - p),
 //   dL/dq = -dL/dalpha alpha d2 / 2          (q = 1/s^2).
 // The 7 per-point terms of a warp are summed with a transposed shuffle
-// reduction (9 shuffles) and added with one atomic per term per warp.
+// reduction (9 shuffles) before they are added to the per-(view, point)
+// buffer.
+//
+// A block covers one TW x TH screen tile; each warp owns an 8 x 4 sub-block
+// of it and skips list entries whose cutoff disc misses its sub-block.  Two
+// schedules:
+//   - warp-streamed (batch depth 0, default): every warp walks the tile list
+//     by itself, 32 entries per step (loads shared through L1), culls them
+//     with one ballot and stops as soon as its own pixels have saturated.
+//     No block barriers.
+//   - block-staged (batch depth > 0): the block stages `depth` records in
+//     shared memory and each warp culls the batch into its own list; block
+//     barriers between batches, per-block shared-memory gradient sums.
 #include "pbr_internal.cuh"
 
 namespace pbr {
@@ -35,6 +44,13 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
+__device__ __forceinline__ uint32_t lanemask_lt_r()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
 __device__ __forceinline__ int find_view_by_tile(const Batch &b, uint32_t tile)
 {
     int lo = 0, hi = b.n_views - 1;
@@ -45,80 +61,44 @@ __device__ __forceinline__ int find_view_by_tile(const Batch &b, uint32_t tile)
     return lo;
 }
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH)
-raster_fwd_kernel(Batch b, DevOpts o, int depth, const uint2 *__restrict__ ranges,
-                  const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
-                  float *__restrict__ out_rgb, float *__restrict__ T_final,
-                  uint32_t *__restrict__ n_contrib, unsigned long long *__restrict__ stats)
-{
-    extern __shared__ float4 s_rec[]; // [depth] a-part, then [depth] b-part
-    float4 *s_a = s_rec, *s_b = s_rec + depth;
-    const uint32_t tile = blockIdx.x;
-    const DevView &V = b.views[find_view_by_tile(b, tile)];
-    const uint32_t local = tile - V.tile_base;
-    const int tx = (int)(local % (uint32_t)V.tiles_x), ty = (int)(local / (uint32_t)V.tiles_x);
-    const int x = tx * TW + (int)(threadIdx.x % TW), y = ty * TH + (int)(threadIdx.x / TW);
-    const bool inside = x < V.W && y < V.H;
-    const float ux = (float)x + 0.5f, uy = (float)y + 0.5f;
-    const uint2 rg = ranges[tile];
-    const uint32_t s = rg.x, e = rg.y > rg.x ? rg.y : rg.x;
+// The calling thread's pixel and its warp's 8 x 4 rectangle of pixel
+// centres [xl, xh] x [yl, yh] inside tile `tile`.
+struct PixelGeom {
+    const DevView *V;
+    int x, y;
+    bool inside;
+    float ux, uy, xl, xh, yl, yh;
+};
 
-    float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    uint32_t cnt = 0, last = 0, examined = 0;
-    bool done = !inside;
-    const uint32_t maxpp = (uint32_t)o.max_per_pixel;
-    for (uint32_t base = s; base < e; base += depth) {
-        if (__syncthreads_count(!done) == 0) break;
-        const int nb = (int)min((uint32_t)depth, e - base);
-        for (int k = threadIdx.x; k < nb; k += TW * TH) {
-            const uint32_t pv = pv_list[base + k];
-            s_a[k] = rec[2 * (size_t)pv];
-            s_b[k] = rec[2 * (size_t)pv + 1];
-        }
-        __syncthreads();
-        if (!done) {
-            int k = 0;
-            for (; k < nb; ++k) {
-                const float4 a = s_a[k];
-                const float dx = __fsub_rn(ux, a.x), dy = __fsub_rn(uy, a.y);
-                const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-                const float4 c = s_b[k];
-                if (d2 <= c.w) {
-                    const float alpha = fminf(o.alpha_max, a.w * ex2_approx(d2 * a.z));
-                    const float w = alpha * T;
-                    C0 = fmaf(w, c.x, C0);
-                    C1 = fmaf(w, c.y, C1);
-                    C2 = fmaf(w, c.z, C2);
-                    T = T - w;
-                    ++cnt;
-                    last = base + k - s + 1;
-                    if (T < o.t_eps || cnt == maxpp) {
-                        done = true;
-                        ++k;
-                        break;
-                    }
-                }
-            }
-            examined += k;
-        }
-    }
-    if (stats) { // pair counts for the ALU roofline: [0] examined, [1] composited
-        const uint32_t we = __reduce_add_sync(0xffffffffu, examined);
-        const uint32_t wc = __reduce_add_sync(0xffffffffu, cnt);
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(stats, (unsigned long long)we);
-            atomicAdd(stats + 1, (unsigned long long)wc);
-        }
-    }
-    if (inside) {
-        const int64_t pix = V.pix_base + (int64_t)y * V.W + x;
-        out_rgb[3 * pix] = C0 + T * o.bg[0];
-        out_rgb[3 * pix + 1] = C1 + T * o.bg[1];
-        out_rgb[3 * pix + 2] = C2 + T * o.bg[2];
-        T_final[pix] = T;
-        n_contrib[pix] = last;
-    }
+template <int TW, int TH>
+__device__ __forceinline__ PixelGeom pixel_geom(const Batch &b, uint32_t tile, int w, int lane)
+{
+    PixelGeom g;
+    g.V = &b.views[find_view_by_tile(b, tile)];
+    const uint32_t local = tile - g.V->tile_base;
+    const int tx = (int)(local % (uint32_t)g.V->tiles_x), ty = (int)(local / (uint32_t)g.V->tiles_x);
+    const int sx0 = tx * TW + (w % (TW / 8)) * 8, sy0 = ty * TH + (w / (TW / 8)) * 4;
+    g.x = sx0 + (lane & 7);
+    g.y = sy0 + (lane >> 3);
+    g.inside = g.x < g.V->W && g.y < g.V->H;
+    g.ux = (float)g.x + 0.5f;
+    g.uy = (float)g.y + 0.5f;
+    g.xl = (float)sx0 + 0.5f;
+    g.xh = (float)sx0 + 7.5f;
+    g.yl = (float)sy0 + 0.5f;
+    g.yh = (float)sy0 + 3.5f;
+    return g;
+}
+
+// Culling test of one record against a rectangle of pixel centres: the same
+// fp32 round-to-nearest operations as the per-pixel cutoff test, applied to
+// the rectangle point nearest the splat centre, so it never drops a point
+// that some pixel of the rectangle would include.
+__device__ __forceinline__ bool disc_meets_rect(const float4 a, const PixelGeom &g)
+{
+    const float cx = fminf(fmaxf(a.x, g.xl), g.xh), cy = fminf(fmaxf(a.y, g.yl), g.yh);
+    const float ex = __fsub_rn(cx, a.x), ey = __fsub_rn(cy, a.y);
+    return __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)) <= a.z;
 }
 
 // Sum of 8 per-lane values over the warp; lane l returns the total of value
@@ -153,33 +133,170 @@ __device__ __forceinline__ float warp_sum8_transposed(const float v[8], int lane
     return r;
 }
 
+// One composited point, front to back.  Returns true when the pixel stops.
+__device__ __forceinline__ bool pixel_blend(float d2, const float4 a, const float4 c,
+                                            const DevOpts &o, float &T, float &C0, float &C1,
+                                            float &C2, uint32_t &cnt)
+{
+    const float alpha = fminf(o.alpha_max, c.x * ex2_approx(d2 * a.w));
+    const float wgt = alpha * T;
+    C0 = fmaf(wgt, c.y, C0);
+    C1 = fmaf(wgt, c.z, C1);
+    C2 = fmaf(wgt, c.w, C2);
+    T = T - wgt;
+    ++cnt;
+    return T < o.t_eps || cnt == (uint32_t)o.max_per_pixel;
+}
+
+// Per-pixel adjoint of one composited point (see the file comment).  On
+// return v[0..6] = {dpx, dpy, dq, do, dr, dg, db}; T and S are updated.
+__device__ __forceinline__ void pixel_adjoint(float d2, float dx, float dy, const float4 a,
+                                              const float4 c, float amax, float g0, float g1,
+                                              float g2, float &T, float &S, float v[8])
+{
+    const float G = ex2_approx(d2 * a.w);
+    const float raw = c.x * G;
+    const float alpha = fminf(amax, raw);
+    const float om = 1.0f - alpha;
+    const float Tb = __fdividef(T, om);
+    const float wgt = alpha * Tb;
+    const float cg = c.y * g0 + c.z * g1 + c.w * g2;
+    v[4] = wgt * g0;
+    v[5] = wgt * g1;
+    v[6] = wgt * g2;
+    const float dalpha = Tb * cg - __fdividef(S, om);
+    S = fmaf(wgt, cg, S);
+    T = Tb;
+    if (raw < amax) {
+        const float q = a.w * QP_TO_Q;
+        const float ca = dalpha * alpha;
+        v[0] = ca * q * dx;
+        v[1] = ca * q * dy;
+        v[2] = -0.5f * ca * d2;
+        v[3] = dalpha * G;
+    }
+}
+
+__device__ __forceinline__ float pixel_d2(float ux, float uy, float px, float py, float &dx,
+                                          float &dy)
+{
+    dx = __fsub_rn(ux, px);
+    dy = __fsub_rn(uy, py);
+    return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+}
+
+__device__ __forceinline__ float4 shfl4(const float4 v, int j)
+{
+    return make_float4(__shfl_sync(0xffffffffu, v.x, j), __shfl_sync(0xffffffffu, v.y, j),
+                       __shfl_sync(0xffffffffu, v.z, j), __shfl_sync(0xffffffffu, v.w, j));
+}
+
+__device__ __forceinline__ void write_pixel(const PixelGeom &g, const DevOpts &o, float T,
+                                            float C0, float C1, float C2, uint32_t last,
+                                            float *out_rgb, float *T_final, uint32_t *n_contrib)
+{
+    if (!g.inside) return;
+    const int64_t pix = g.V->pix_base + (int64_t)g.y * g.V->W + g.x;
+    out_rgb[3 * pix] = C0 + T * o.bg[0];
+    out_rgb[3 * pix + 1] = C1 + T * o.bg[1];
+    out_rgb[3 * pix + 2] = C2 + T * o.bg[2];
+    T_final[pix] = T;
+    n_contrib[pix] = last;
+}
+
+__device__ __forceinline__ void add_stats(unsigned long long *stats, uint32_t a, uint32_t b,
+                                          int lane)
+{
+    if (!stats) return;
+    const uint32_t wa = __reduce_add_sync(0xffffffffu, a);
+    const uint32_t wb = __reduce_add_sync(0xffffffffu, b);
+    if (lane == 0) {
+        atomicAdd(stats, (unsigned long long)wa);
+        atomicAdd(stats + 1, (unsigned long long)wb);
+    }
+}
+
+// ======================================================= warp-streamed
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW * TH)
-raster_bwd_kernel(Batch b, DevOpts o, int depth, const uint2 *__restrict__ ranges,
-                  const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
-                  const float *__restrict__ T_final, const uint32_t *__restrict__ n_contrib,
-                  const float *__restrict__ grad_rgb, float *__restrict__ g2d,
-                  unsigned long long *__restrict__ stats)
+raster_fwd_stream_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
+                         const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
+                         float *__restrict__ out_rgb, float *__restrict__ T_final,
+                         uint32_t *__restrict__ n_contrib, unsigned long long *__restrict__ stats)
 {
-    extern __shared__ float4 s_rec[];
-    float4 *s_a = s_rec, *s_b = s_rec + depth;
-    uint32_t *s_pv = (uint32_t *)(s_rec + 2 * depth);
-    __shared__ uint32_t s_max[TW * TH / 32];
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t tile = blockIdx.x;
-    const DevView &V = b.views[find_view_by_tile(b, tile)];
-    const uint32_t local = tile - V.tile_base;
-    const int tx = (int)(local % (uint32_t)V.tiles_x), ty = (int)(local / (uint32_t)V.tiles_x);
-    const int x = tx * TW + (int)(threadIdx.x % TW), y = ty * TH + (int)(threadIdx.x / TW);
-    const bool inside = x < V.W && y < V.H;
-    const float ux = (float)x + 0.5f, uy = (float)y + 0.5f;
+    const PixelGeom g = pixel_geom<TW, TH>(b, tile, w, lane);
     const uint2 rg = ranges[tile];
-    const uint32_t s = rg.x;
+    const uint32_t s = rg.x, e = rg.y > rg.x ? rg.y : rg.x;
+
+    float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    uint32_t cnt = 0, last = 0, examined = 0;
+    bool done = !g.inside;
+    if (!__all_sync(0xffffffffu, done)) {
+        // software pipeline: the next step's entry is loaded one step early
+        uint32_t pv_n = 0;
+        float4 a_n = make_float4(0.f, 0.f, -1.f, 0.f);
+        if (s + lane < e) {
+            pv_n = __ldg(pv_list + s + lane);
+            a_n = __ldg(rec + 2 * (size_t)pv_n);
+        }
+        for (uint32_t c = s; c < e; c += 32) {
+            const uint32_t pv = pv_n;
+            const float4 a = a_n;
+            const bool valid = c + lane < e;
+            if (c + 32 + lane < e) {
+                pv_n = __ldg(pv_list + c + 32 + lane);
+                a_n = __ldg(rec + 2 * (size_t)pv_n);
+            }
+            const bool hit = valid && disc_meets_rect(a, g);
+            uint32_t m = __ballot_sync(0xffffffffu, hit);
+            float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (hit) bb = __ldg(rec + 2 * (size_t)pv + 1);
+            bool stop = false;
+            while (m) {
+                const int j = __ffs(m) - 1;
+                m &= m - 1;
+                const float4 aj = shfl4(a, j);
+                const float4 cj = shfl4(bb, j);
+                if (!done) {
+                    ++examined;
+                    float dx, dy;
+                    const float d2 = pixel_d2(g.ux, g.uy, aj.x, aj.y, dx, dy);
+                    if (d2 <= aj.z) {
+                        last = c + j - s + 1;
+                        done = pixel_blend(d2, aj, cj, o, T, C0, C1, C2, cnt);
+                    }
+                }
+                if (__all_sync(0xffffffffu, done)) {
+                    stop = true;
+                    break;
+                }
+            }
+            if (stop) break;
+        }
+    }
+    add_stats(stats, examined, cnt, lane);
+    write_pixel(g, o, T, C0, C1, C2, last, out_rgb, T_final, n_contrib);
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH)
+raster_bwd_stream_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
+                         const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
+                         const float *__restrict__ T_final, const uint32_t *__restrict__ n_contrib,
+                         const float *__restrict__ grad_rgb, float *__restrict__ g2d,
+                         unsigned long long *__restrict__ stats)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t tile = blockIdx.x;
+    const PixelGeom g = pixel_geom<TW, TH>(b, tile, w, lane);
+    const uint32_t s = ranges[tile].x;
 
     float T = 1.0f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
     uint32_t L = 0;
-    if (inside) {
-        const int64_t pix = V.pix_base + (int64_t)y * V.W + x;
+    if (g.inside) {
+        const int64_t pix = g.V->pix_base + (int64_t)g.y * g.V->W + g.x;
         T = T_final[pix];
         L = n_contrib[pix];
         g0 = grad_rgb[3 * pix];
@@ -187,87 +304,235 @@ raster_bwd_kernel(Batch b, DevOpts o, int depth, const uint2 *__restrict__ range
         g2 = grad_rgb[3 * pix + 2];
     }
     float S = T * (o.bg[0] * g0 + o.bg[1] * g1 + o.bg[2] * g2);
-    // longest list prefix any pixel of the block needs
     const uint32_t wmax = __reduce_max_sync(0xffffffffu, L);
-    if (lane == 0) s_max[threadIdx.x >> 5] = wmax;
+    uint32_t examined = 0, used = 0;
+    if (wmax > 0) {
+        int64_t c = (int64_t)((wmax - 1) & ~31u);
+        uint32_t pv_n = 0;
+        float4 a_n = make_float4(0.f, 0.f, -1.f, 0.f);
+        if ((uint32_t)c + lane < wmax) {
+            pv_n = __ldg(pv_list + s + (uint32_t)c + lane);
+            a_n = __ldg(rec + 2 * (size_t)pv_n);
+        }
+        for (; c >= 0; c -= 32) {
+            const uint32_t pv = pv_n;
+            const float4 a = a_n;
+            const bool valid = (uint32_t)c + lane < wmax;
+            if (c >= 32) {
+                pv_n = __ldg(pv_list + s + (uint32_t)c - 32 + lane);
+                a_n = __ldg(rec + 2 * (size_t)pv_n);
+            }
+            const bool hit = valid && disc_meets_rect(a, g);
+            uint32_t m = __ballot_sync(0xffffffffu, hit);
+            float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (hit) bb = __ldg(rec + 2 * (size_t)pv + 1);
+            while (m) {
+                const int j = 31 - __clz(m); // back to front
+                m &= ~(1u << j);
+                const float4 aj = shfl4(a, j);
+                const float4 cj = shfl4(bb, j);
+                const uint32_t pvj = __shfl_sync(0xffffffffu, pv, j);
+                float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                bool contrib = false;
+                if ((uint32_t)c + j < L) {
+                    ++examined;
+                    float dx, dy;
+                    const float d2 = pixel_d2(g.ux, g.uy, aj.x, aj.y, dx, dy);
+                    if (d2 <= aj.z) {
+                        contrib = true;
+                        ++used;
+                        pixel_adjoint(d2, dx, dy, aj, cj, o.alpha_max, g0, g1, g2, T, S, v);
+                    }
+                }
+                if (__any_sync(0xffffffffu, contrib)) {
+                    const float tot = warp_sum8_transposed(v, lane);
+                    const int which = (lane >> 2) & 7;
+                    if ((lane & 3) == 0 && which < 7) atomicAdd(g2d + 8 * (size_t)pvj + which, tot);
+                }
+            }
+        }
+    }
+    add_stats(stats ? stats + 2 : nullptr, examined, used, lane);
+}
+
+// ========================================================= block-staged
+// Builds, in shared memory, the ascending list of batch entries whose cutoff
+// disc reaches the warp's rectangle.  Returns the count.
+__device__ __forceinline__ int warp_cull(const float4 *s_a, int nb, const PixelGeom &g,
+                                         uint16_t *list, int lane)
+{
+    int cnt = 0;
+    const uint32_t lt = lanemask_lt_r();
+    for (int k0 = 0; k0 < nb; k0 += 32) {
+        const int k = k0 + lane;
+        const bool hit = k < nb && disc_meets_rect(s_a[k], g);
+        const uint32_t m = __ballot_sync(0xffffffffu, hit);
+        if (hit) list[cnt + __popc(m & lt)] = (uint16_t)k;
+        cnt += __popc(m);
+    }
+    __syncwarp();
+    return cnt;
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH)
+raster_fwd_staged_kernel(Batch b, DevOpts o, int depth, const uint2 *__restrict__ ranges,
+                         const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
+                         float *__restrict__ out_rgb, float *__restrict__ T_final,
+                         uint32_t *__restrict__ n_contrib, unsigned long long *__restrict__ stats)
+{
+    constexpr int NT = TW * TH;
+    extern __shared__ float4 s_rec[]; // [depth] a-part, [depth] b-part, per-warp lists
+    float4 *s_a = s_rec, *s_b = s_rec + depth;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint16_t *s_list = (uint16_t *)(s_rec + 2 * depth) + w * depth;
+    const uint32_t tile = blockIdx.x;
+    const PixelGeom g = pixel_geom<TW, TH>(b, tile, w, lane);
+    const uint2 rg = ranges[tile];
+    const uint32_t s = rg.x, e = rg.y > rg.x ? rg.y : rg.x;
+
+    float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    uint32_t cnt = 0, last = 0, examined = 0;
+    bool done = !g.inside;
+    for (uint32_t base = s; base < e; base += depth) {
+        if (__syncthreads_count(!done) == 0) break;
+        const int nb = (int)min((uint32_t)depth, e - base);
+        for (int k = threadIdx.x; k < nb; k += NT) {
+            const uint32_t pv = pv_list[base + k];
+            s_a[k] = rec[2 * (size_t)pv];
+            s_b[k] = rec[2 * (size_t)pv + 1];
+        }
+        __syncthreads();
+        if (!__any_sync(0xffffffffu, !done)) continue;
+        const int nl = warp_cull(s_a, nb, g, s_list, lane);
+        if (done) continue;
+        int j = 0;
+        for (; j < nl; ++j) {
+            const int k = s_list[j];
+            const float4 a = s_a[k];
+            float dx, dy;
+            const float d2 = pixel_d2(g.ux, g.uy, a.x, a.y, dx, dy);
+            if (d2 <= a.z) {
+                last = base + k - s + 1;
+                if (pixel_blend(d2, a, s_b[k], o, T, C0, C1, C2, cnt)) {
+                    done = true;
+                    ++j;
+                    break;
+                }
+            }
+        }
+        examined += j;
+    }
+    add_stats(stats, examined, cnt, lane);
+    write_pixel(g, o, T, C0, C1, C2, last, out_rgb, T_final, n_contrib);
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH)
+raster_bwd_staged_kernel(Batch b, DevOpts o, int depth, const uint2 *__restrict__ ranges,
+                         const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
+                         const float *__restrict__ T_final, const uint32_t *__restrict__ n_contrib,
+                         const float *__restrict__ grad_rgb, float *__restrict__ g2d,
+                         unsigned long long *__restrict__ stats)
+{
+    constexpr int NT = TW * TH;
+    extern __shared__ float4 s_rec[];
+    float4 *s_a = s_rec, *s_b = s_rec + depth;
+    float *s_acc = (float *)(s_rec + 2 * depth); // [depth][8] block sums of the terms
+    uint32_t *s_pv = (uint32_t *)(s_acc + 8 * depth);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint16_t *s_list = (uint16_t *)(s_pv + depth) + w * depth;
+    __shared__ uint32_t s_max[NT / 32];
+    const uint32_t tile = blockIdx.x;
+    const PixelGeom g = pixel_geom<TW, TH>(b, tile, w, lane);
+    const uint32_t s = ranges[tile].x;
+
+    float T = 1.0f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    uint32_t L = 0;
+    if (g.inside) {
+        const int64_t pix = g.V->pix_base + (int64_t)g.y * g.V->W + g.x;
+        T = T_final[pix];
+        L = n_contrib[pix];
+        g0 = grad_rgb[3 * pix];
+        g1 = grad_rgb[3 * pix + 1];
+        g2 = grad_rgb[3 * pix + 2];
+    }
+    float S = T * (o.bg[0] * g0 + o.bg[1] * g1 + o.bg[2] * g2);
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, L);
+    if (lane == 0) s_max[w] = wmax;
     __syncthreads();
     uint32_t maxL = 0;
 #pragma unroll
-    for (int j = 0; j < TW * TH / 32; ++j) maxL = max(maxL, s_max[j]);
+    for (int j = 0; j < NT / 32; ++j) maxL = max(maxL, s_max[j]);
 
     uint32_t examined = 0, used = 0;
     for (int64_t bend = maxL; bend > 0; bend -= depth) {
         const uint32_t bstart = (uint32_t)(bend > depth ? bend - depth : 0);
         const int nb = (int)(bend - bstart);
         __syncthreads(); // previous batch fully consumed
-        for (int k = threadIdx.x; k < nb; k += TW * TH) {
+        for (int k = threadIdx.x; k < nb; k += NT) {
             const uint32_t pv = pv_list[s + bstart + k];
             s_pv[k] = pv;
             s_a[k] = rec[2 * (size_t)pv];
             s_b[k] = rec[2 * (size_t)pv + 1];
+            reinterpret_cast<float4 *>(s_acc)[2 * k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            reinterpret_cast<float4 *>(s_acc)[2 * k + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncthreads();
-        for (int k = nb - 1; k >= 0; --k) {
-            const uint32_t idx = bstart + k;
+        // warps whose pixels all stop before this batch skip it
+        const int nwb = bstart < wmax ? (int)min((uint32_t)nb, wmax - bstart) : 0;
+        const int nl = nwb > 0 ? warp_cull(s_a, nwb, g, s_list, lane) : 0;
+        for (int j = nl - 1; j >= 0; --j) {
+            const int k = s_list[j];
             float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool contrib = false;
-            if (idx < L) {
+            if (bstart + k < L) {
                 ++examined;
                 const float4 a = s_a[k];
-                const float dx = __fsub_rn(ux, a.x), dy = __fsub_rn(uy, a.y);
-                const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-                const float4 c = s_b[k];
-                if (d2 <= c.w) {
+                float dx, dy;
+                const float d2 = pixel_d2(g.ux, g.uy, a.x, a.y, dx, dy);
+                if (d2 <= a.z) {
                     contrib = true;
                     ++used;
-                    const float G = ex2_approx(d2 * a.z);
-                    const float raw = a.w * G;
-                    const float alpha = fminf(o.alpha_max, raw);
-                    const float om = 1.0f - alpha;
-                    const float Tb = __fdividef(T, om);
-                    const float wgt = alpha * Tb;
-                    const float cg = c.x * g0 + c.y * g1 + c.z * g2;
-                    v[4] = wgt * g0;
-                    v[5] = wgt * g1;
-                    v[6] = wgt * g2;
-                    const float dalpha = Tb * cg - __fdividef(S, om);
-                    S = fmaf(wgt, cg, S);
-                    T = Tb;
-                    if (raw < o.alpha_max) {
-                        const float q = a.z * QP_TO_Q;
-                        const float ca = dalpha * alpha;
-                        v[0] = ca * q * dx;
-                        v[1] = ca * q * dy;
-                        v[2] = -0.5f * ca * d2;
-                        v[3] = dalpha * G;
-                    }
+                    pixel_adjoint(d2, dx, dy, a, s_b[k], o.alpha_max, g0, g1, g2, T, S, v);
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
                 const float tot = warp_sum8_transposed(v, lane);
                 const int which = (lane >> 2) & 7;
-                if ((lane & 3) == 0 && which < 7) atomicAdd(g2d + 8 * (size_t)s_pv[k] + which, tot);
+                if ((lane & 3) == 0 && which < 7) atomicAdd(s_acc + 8 * k + which, tot);
             }
         }
-    }
-    if (stats) { // [2] examined, [3] contributing
-        const uint32_t we = __reduce_add_sync(0xffffffffu, examined);
-        const uint32_t wu = __reduce_add_sync(0xffffffffu, used);
-        if (lane == 0) {
-            atomicAdd(stats + 2, (unsigned long long)we);
-            atomicAdd(stats + 3, (unsigned long long)wu);
+        __syncthreads();
+        // one global atomic per (block, point, term)
+        for (int t = threadIdx.x; t < nb * 7; t += NT) {
+            const int k = t / 7, cc = t - 7 * k;
+            const float val = s_acc[8 * k + cc];
+            if (val != 0.f) atomicAdd(g2d + 8 * (size_t)s_pv[k] + cc, val);
         }
     }
+    add_stats(stats ? stats + 2 : nullptr, examined, used, lane);
 }
 
+// ------------------------------------------------------------ dispatch
 template <int TW, int TH>
 void fwd_dispatch(const Batch &b, const DevOpts &o, int depth, const uint2 *ranges,
                   const uint32_t *pv_list, const float4 *rec, float *out_rgb, float *T_final,
                   uint32_t *n_contrib, unsigned long long *stats, cudaStream_t s)
 {
-    const size_t smem = (size_t)depth * 2 * sizeof(float4);
-    raster_fwd_kernel<TW, TH><<<b.n_tiles, TW * TH, smem, s>>>(b, o, depth, ranges, pv_list, rec,
-                                                              out_rgb, T_final, n_contrib, stats);
+    if (depth == 0) {
+        raster_fwd_stream_kernel<TW, TH><<<b.n_tiles, TW * TH, 0, s>>>(
+            b, o, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats);
+    } else {
+        const size_t smem =
+            (size_t)depth * (2 * sizeof(float4) + (TW * TH / 32) * sizeof(uint16_t));
+        static const bool attr = cudaFuncSetAttribute(raster_fwd_staged_kernel<TW, TH>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      160 * 1024) == cudaSuccess;
+        (void)attr;
+        raster_fwd_staged_kernel<TW, TH><<<b.n_tiles, TW * TH, smem, s>>>(
+            b, o, depth, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats);
+    }
     count_launches(1);
 }
 
@@ -277,9 +542,19 @@ void bwd_dispatch(const Batch &b, const DevOpts &o, int depth, const uint2 *rang
                   const uint32_t *n_contrib, const float *grad_rgb, float4 *g2d,
                   unsigned long long *stats, cudaStream_t s)
 {
-    const size_t smem = (size_t)depth * (2 * sizeof(float4) + sizeof(uint32_t));
-    raster_bwd_kernel<TW, TH><<<b.n_tiles, TW * TH, smem, s>>>(
-        b, o, depth, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d, stats);
+    if (depth == 0) {
+        raster_bwd_stream_kernel<TW, TH><<<b.n_tiles, TW * TH, 0, s>>>(
+            b, o, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d, stats);
+    } else {
+        const size_t smem = (size_t)depth * (4 * sizeof(float4) + sizeof(uint32_t) +
+                                             (TW * TH / 32) * sizeof(uint16_t));
+        static const bool attr = cudaFuncSetAttribute(raster_bwd_staged_kernel<TW, TH>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      160 * 1024) == cudaSuccess;
+        (void)attr;
+        raster_bwd_staged_kernel<TW, TH><<<b.n_tiles, TW * TH, smem, s>>>(
+            b, o, depth, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d, stats);
+    }
     count_launches(1);
 }
 

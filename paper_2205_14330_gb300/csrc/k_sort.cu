@@ -28,8 +28,6 @@ constexpr int SCAN_ITEMS = 16;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS; // 4096
 constexpr int SCAN_WARPS = SCAN_THREADS / 32;
 
-constexpr int RADIX_BITS = 8;
-constexpr int RADIX = 1 << RADIX_BITS;
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_ITEMS = 16;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS; // 4096
@@ -203,145 +201,222 @@ struct ActStore {
     uint32_t *p;
     __device__ void operator()(int64_t i, uint32_t pos, uint32_t) const { p[i] = pos; }
 };
-struct LoadTileCount {
-    const uint32_t *sorted_pv, *ntiles;
-    __device__ uint32_t operator()(int64_t j) const { return ntiles[sorted_pv[j]]; }
-};
-struct ActEmit {
-    const uint32_t *sorted_pv;
-    const uint2 *rect;
-    const DevView *views;
-    int32_t n_views;
-    uint32_t *keys, *vals;
-    int64_t cap;
-    uint32_t *status;
-    __device__ void operator()(int64_t j, uint32_t pos, uint32_t nt) const
-    {
-        const uint32_t pv = sorted_pv[j];
-        // view of this point-view: last view with pv_base <= pv
-        int lo = 0, hi = n_views - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (views[mid].pv_base <= (int64_t)pv) lo = mid; else hi = mid - 1;
-        }
-        const DevView &V = views[lo];
-        const uint2 rc = rect[pv];
-        const int tx0 = rc.x & 0xffff, ty0 = rc.x >> 16, tx1 = rc.y & 0xffff, ty1 = rc.y >> 16;
-        if ((int64_t)pos + nt > cap) {
-            atomicOr(status, ST_PAIR_OVERFLOW);
-            return;
-        }
-        uint32_t q = pos;
-        for (int ty = ty0; ty <= ty1; ++ty)
-            for (int tx = tx0; tx <= tx1; ++tx) {
-                keys[q] = V.tile_base + (uint32_t)(ty * V.tiles_x + tx);
-                vals[q] = pv;
-                ++q;
-            }
-    }
-};
-
 // ----------------------------------------------------------- radix sort
+// One LSD pass over a digit of `width` <= RB bits of (key - key_lo) at
+// `shift`.  Keys are loaded before any warp-synchronous work so that all of a
+// thread's loads are in flight together.
+constexpr int RB = 9;
+constexpr int RBINS = 1 << RB;
+
+__device__ __forceinline__ uint32_t digit_of(uint32_t key, uint32_t key_lo, int shift, uint32_t mask)
+{
+    return ((key - key_lo) >> shift) & mask;
+}
+
 __global__ void __launch_bounds__(SORT_THREADS)
 radix_hist_kernel(const uint32_t *__restrict__ keys, const uint32_t *n_dev, int64_t cap,
-                  int shift, uint32_t *__restrict__ hist, int64_t nb)
+                  uint32_t key_lo, int shift, int width, uint32_t *__restrict__ hist, int64_t nb)
 {
-    __shared__ uint32_t s_h[SORT_WARPS][RADIX];
+    __shared__ uint32_t s_h[SORT_WARPS][RBINS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int j = threadIdx.x; j < SORT_WARPS * RADIX; j += SORT_THREADS) (&s_h[0][0])[j] = 0;
-    __syncthreads();
+    for (int j = threadIdx.x; j < SORT_WARPS * RBINS; j += SORT_THREADS) (&s_h[0][0])[j] = 0;
     const int64_t n = dev_count(n_dev, cap);
     const int64_t base = (int64_t)blockIdx.x * SORT_TILE + (int64_t)w * 32 * SORT_ITEMS;
+    const uint32_t mask = (1u << width) - 1u;
+    uint32_t d[SORT_ITEMS];
+#pragma unroll
     for (int r = 0; r < SORT_ITEMS; ++r) {
         const int64_t i = base + r * 32 + lane;
-        const uint32_t d = i < n ? (keys[i] >> shift) & (RADIX - 1) : RADIX;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (d < RADIX && (peers & lanemask_lt()) == 0) s_h[w][d] += __popc(peers);
+        d[r] = i < n ? digit_of(keys[i], key_lo, shift, mask) : (uint32_t)RBINS;
+    }
+    __syncthreads();
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+        const uint32_t peers = __match_any_sync(0xffffffffu, d[r]);
+        if (d[r] < RBINS && (peers & lt) == 0) s_h[w][d[r]] += __popc(peers);
         __syncwarp();
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < RADIX; d += SORT_THREADS) {
+    const int bins = 1 << width;
+    for (int dd = threadIdx.x; dd < bins; dd += SORT_THREADS) {
         uint32_t t = 0;
-        for (int j = 0; j < SORT_WARPS; ++j) t += s_h[j][d];
-        hist[(int64_t)d * nb + blockIdx.x] = t;
+#pragma unroll
+        for (int j = 0; j < SORT_WARPS; ++j) t += s_h[j][dd];
+        hist[(int64_t)dd * nb + blockIdx.x] = t;
     }
 }
+
+constexpr size_t SCATTER_SMEM = sizeof(uint32_t) * (2 * SORT_TILE + SORT_WARPS * RBINS + 3 * RBINS +
+                                                    SORT_WARPS);
 
 __global__ void __launch_bounds__(SORT_THREADS)
 radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                      uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
-                     const uint32_t *n_dev, int64_t cap, int shift,
+                     const uint32_t *n_dev, int64_t cap, uint32_t key_lo, int shift, int width,
                      const uint32_t *__restrict__ hist, int64_t nb)
 {
-    __shared__ uint32_t s_k[SORT_TILE];
-    __shared__ uint32_t s_v[SORT_TILE];
-    __shared__ uint32_t s_wh[SORT_WARPS][RADIX];
-    __shared__ uint32_t s_dbase[RADIX];
-    __shared__ uint32_t s_gbase[RADIX];
-    __shared__ uint32_t s_scan[SORT_WARPS];
+    extern __shared__ uint32_t s_mem[];
+    uint32_t *s_k = s_mem;                               // [SORT_TILE]
+    uint32_t *s_v = s_k + SORT_TILE;                     // [SORT_TILE]
+    uint32_t(*s_wh)[RBINS] = (uint32_t(*)[RBINS])(s_v + SORT_TILE); // [warps][RBINS]
+    uint32_t *s_tot = s_v + SORT_TILE + SORT_WARPS * RBINS;
+    uint32_t *s_dbase = s_tot + RBINS;
+    uint32_t *s_gbase = s_dbase + RBINS;
+    uint32_t *s_scan = s_gbase + RBINS;
     const int64_t n = dev_count(n_dev, cap);
     const int64_t blk = (int64_t)blockIdx.x * SORT_TILE;
     if (blk >= n) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int j = threadIdx.x; j < SORT_WARPS * RADIX; j += SORT_THREADS) (&s_wh[0][0])[j] = 0;
-    __syncthreads();
+    const uint32_t mask = (1u << width) - 1u;
+    const int bins = 1 << width;
+    for (int j = threadIdx.x; j < SORT_WARPS * RBINS; j += SORT_THREADS) (&s_wh[0][0])[j] = 0;
     const int64_t base = blk + (int64_t)w * 32 * SORT_ITEMS;
     uint32_t key[SORT_ITEMS], val[SORT_ITEMS], rank[SORT_ITEMS];
-    const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int r = 0; r < SORT_ITEMS; ++r) {
         const int64_t i = base + r * 32 + lane;
         const bool ok = i < n;
         key[r] = ok ? keys_in[i] : 0u;
         val[r] = ok ? vals_in[i] : 0u;
-        const uint32_t d = ok ? (key[r] >> shift) & (RADIX - 1) : RADIX;
+    }
+    __syncthreads();
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+        const bool ok = base + r * 32 + lane < n;
+        const uint32_t d = ok ? digit_of(key[r], key_lo, shift, mask) : (uint32_t)RBINS;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t before = d < RADIX ? s_wh[w][d] : 0u;
+        const uint32_t before = d < RBINS ? s_wh[w][d] : 0u;
         __syncwarp();
-        if (d < RADIX && (peers & lt) == 0) s_wh[w][d] = before + __popc(peers);
+        if (d < RBINS && (peers & lt) == 0) s_wh[w][d] = before + __popc(peers);
         __syncwarp();
         rank[r] = before + __popc(peers & lt);
     }
     __syncthreads();
     // per digit: exclusive prefix over warps, digit total, global base
-    uint32_t dtot = 0;
-    {
-        const int d = threadIdx.x; // SORT_THREADS == RADIX
-        for (int j = 0; j < SORT_WARPS; ++j) {
-            const uint32_t t = s_wh[j][d];
-            s_wh[j][d] = dtot;
-            dtot += t;
+    for (int dd = threadIdx.x; dd < RBINS; dd += SORT_THREADS) {
+        uint32_t t = 0;
+        if (dd < bins) {
+#pragma unroll
+            for (int j = 0; j < SORT_WARPS; ++j) {
+                const uint32_t x = s_wh[j][dd];
+                s_wh[j][dd] = t;
+                t += x;
+            }
+            s_gbase[dd] = hist[(int64_t)dd * nb + blockIdx.x];
         }
-        s_gbase[d] = hist[(int64_t)d * nb + blockIdx.x];
+        s_tot[dd] = t;
     }
-    // block exclusive scan of dtot over the 256 digits
+    __syncthreads();
+    // block exclusive scan of the digit totals (RBINS / SORT_THREADS per thread)
     {
-        const uint32_t inc = warp_incl_scan(dtot);
+        constexpr int PER = RBINS / SORT_THREADS;
+        uint32_t loc[PER], sum = 0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            loc[q] = s_tot[threadIdx.x * PER + q];
+            sum += loc[q];
+        }
+        const uint32_t inc = warp_incl_scan(sum);
         if (lane == 31) s_scan[w] = inc;
         __syncthreads();
-        uint32_t off = 0;
+        uint32_t off = inc - sum;
         for (int j = 0; j < w; ++j) off += s_scan[j];
-        s_dbase[threadIdx.x] = off + inc - dtot;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            s_dbase[threadIdx.x * PER + q] = off;
+            off += loc[q];
+        }
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < SORT_ITEMS; ++r) {
-        const int64_t i = base + r * 32 + lane;
-        if (i < n) {
-            const uint32_t d = (key[r] >> shift) & (RADIX - 1);
-            const uint32_t loc = s_dbase[d] + s_wh[w][d] + rank[r];
-            s_k[loc] = key[r];
-            s_v[loc] = val[r];
+        if (base + r * 32 + lane < n) {
+            const uint32_t d = digit_of(key[r], key_lo, shift, mask);
+            const uint32_t l = s_dbase[d] + s_wh[w][d] + rank[r];
+            s_k[l] = key[r];
+            s_v[l] = val[r];
         }
     }
     __syncthreads();
     const int cnt = (int)(n - blk < SORT_TILE ? n - blk : SORT_TILE);
     for (int j = threadIdx.x; j < cnt; j += SORT_THREADS) {
         const uint32_t k = s_k[j];
-        const uint32_t d = (k >> shift) & (RADIX - 1);
+        const uint32_t d = digit_of(k, key_lo, shift, mask);
         const uint32_t g = s_gbase[d] + (uint32_t)j - s_dbase[d];
         keys_out[g] = k;
         vals_out[g] = s_v[j];
+    }
+}
+
+// ------------------------------------------------------------ emission
+__global__ void gather_counts_kernel(const uint32_t *__restrict__ sorted_pv,
+                                     const uint32_t *__restrict__ ntiles, const uint32_t *n_dev,
+                                     int64_t cap, uint32_t *__restrict__ nt_sorted)
+{
+    const int64_t n = dev_count(n_dev, cap);
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) nt_sorted[j] = ntiles[sorted_pv[j]];
+}
+
+// Each warp owns 32 consecutive depth-sorted point-views; their pair runs
+// are contiguous in the output, so the warp writes them together: output q
+// belongs to the last lane whose run starts at or before q.
+__global__ void __launch_bounds__(256)
+emit_pairs_kernel(const DevView *__restrict__ views, int32_t n_views,
+                  const uint32_t *__restrict__ sorted_pv, const uint32_t *__restrict__ nt_sorted,
+                  const uint32_t *__restrict__ offs, const uint2 *__restrict__ rect,
+                  const uint32_t *n_dev, int64_t cap_vis, uint32_t *__restrict__ keys,
+                  uint32_t *__restrict__ vals, int64_t cap_pairs, uint32_t *status)
+{
+    const int64_t n = dev_count(n_dev, cap_vis);
+    const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31;
+    if (j0 >= n) return; // whole warp past the end
+    const int lane = threadIdx.x & 31;
+    const int64_t j = j0 + lane;
+    const bool ok = j < n;
+    uint32_t pre = 0, nt = 0, pv = 0, tb = 0, wx = 1, tpx = 1;
+    if (ok) {
+        pre = offs[j];
+        nt = nt_sorted[j];
+        pv = sorted_pv[j];
+        int lo = 0, hi = n_views - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (views[mid].pv_base <= (int64_t)pv) lo = mid; else hi = mid - 1;
+        }
+        const uint2 rc = rect[pv];
+        const uint32_t tx0 = rc.x & 0xffff, ty0 = rc.x >> 16, tx1 = rc.y & 0xffff;
+        tpx = (uint32_t)views[lo].tiles_x;
+        tb = views[lo].tile_base + ty0 * tpx + tx0;
+        wx = tx1 - tx0 + 1;
+    } else {
+        pre = 0xffffffffu; // never owns an output
+    }
+    const uint32_t start = __shfl_sync(0xffffffffu, pre, 0);
+    const uint32_t last_lane = (uint32_t)(n - 1 - j0 < 31 ? n - 1 - j0 : 31);
+    const uint32_t end = __shfl_sync(0xffffffffu, pre + nt, last_lane);
+    if (lane == 0 && (int64_t)end > cap_pairs) atomicOr(status, ST_PAIR_OVERFLOW);
+    for (uint32_t q0 = start; q0 < end; q0 += 32) {
+        const uint32_t q = q0 + lane;
+        // owner: largest lane with pre <= q
+        int o = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t p = __shfl_sync(0xffffffffu, pre, o + step);
+            if (p <= q) o += step;
+        }
+        const uint32_t opre = __shfl_sync(0xffffffffu, pre, o);
+        const uint32_t otb = __shfl_sync(0xffffffffu, tb, o);
+        const uint32_t owx = __shfl_sync(0xffffffffu, wx, o);
+        const uint32_t otpx = __shfl_sync(0xffffffffu, tpx, o);
+        const uint32_t opv = __shfl_sync(0xffffffffu, pv, o);
+        if (q < end && (int64_t)q < cap_pairs) {
+            const uint32_t t = q - opre;
+            keys[q] = otb + (t / owx) * otpx + (t % owx);
+            vals[q] = opv;
+        }
     }
 }
 
@@ -379,23 +454,36 @@ void launch_compact_visible(const uint32_t *ntiles, const uint32_t *zbits, int64
 size_t radix_temp_bytes(int64_t cap)
 {
     const int64_t nb = (cap + SORT_TILE - 1) / SORT_TILE;
-    const int64_t hist = (nb > 0 ? nb : 1) * RADIX;
+    const int64_t hist = (nb > 0 ? nb : 1) * RBINS;
     return (size_t)hist * sizeof(uint32_t) + scan_temp_bytes(hist);
+}
+
+int radix_passes(int key_bits)
+{
+    return key_bits <= 0 ? 0 : (key_bits + RB - 1) / RB;
 }
 
 void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *&keys_alt, uint32_t *&vals_alt,
                       const uint32_t *n_dev, int64_t cap, int key_bits, void *temp,
-                      cudaStream_t s)
+                      cudaStream_t s, uint32_t key_lo)
 {
-    if (cap <= 0) return;
+    if (cap <= 0 || key_bits <= 0) return; // all keys equal: already in stable order
+    static const bool attr = cudaFuncSetAttribute(radix_scatter_kernel,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)SCATTER_SMEM) == cudaSuccess;
+    (void)attr;
     const int64_t nb = (cap + SORT_TILE - 1) / SORT_TILE;
     uint32_t *hist = (uint32_t *)temp;
-    void *scan_tmp = hist + nb * RADIX;
-    for (int shift = 0; shift < key_bits; shift += RADIX_BITS) {
-        radix_hist_kernel<<<(unsigned)nb, SORT_THREADS, 0, s>>>(keys, n_dev, cap, shift, hist, nb);
-        run_scan(LoadU32{hist}, ActStore{hist}, nullptr, nb * RADIX, scan_tmp, nullptr, nullptr, s);
-        radix_scatter_kernel<<<(unsigned)nb, SORT_THREADS, 0, s>>>(keys, vals, keys_alt, vals_alt,
-                                                                   n_dev, cap, shift, hist, nb);
+    void *scan_tmp = hist + nb * RBINS;
+    const int passes = radix_passes(key_bits);
+    const int width = (key_bits + passes - 1) / passes;
+    for (int shift = 0; shift < key_bits; shift += width) {
+        const int wd = key_bits - shift < width ? key_bits - shift : width;
+        radix_hist_kernel<<<(unsigned)nb, SORT_THREADS, 0, s>>>(keys, n_dev, cap, key_lo, shift, wd,
+                                                                hist, nb);
+        run_scan(LoadU32{hist}, ActStore{hist}, nullptr, nb << wd, scan_tmp, nullptr, nullptr, s);
+        radix_scatter_kernel<<<(unsigned)nb, SORT_THREADS, SCATTER_SMEM, s>>>(
+            keys, vals, keys_alt, vals_alt, n_dev, cap, key_lo, shift, wd, hist, nb);
         count_launches(2);
         uint32_t *tk = keys, *tv = vals;
         keys = keys_alt;
@@ -405,15 +493,27 @@ void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *&keys_alt, uin
     }
 }
 
+size_t emit_temp_bytes(int64_t cap_vis)
+{
+    return (size_t)(cap_vis > 0 ? cap_vis : 1) * 2 * sizeof(uint32_t) + scan_temp_bytes(cap_vis);
+}
+
 void launch_emit_pairs(const Batch &b, const DevOpts &o, const uint32_t *sorted_pv,
                        const uint32_t *n_vis, int64_t cap_vis, const uint32_t *ntiles,
                        const uint2 *rect, uint32_t *keys, uint32_t *vals, int64_t cap_pairs,
                        uint32_t *status, void *temp, cudaStream_t s)
 {
     (void)o;
-    run_scan(LoadTileCount{sorted_pv, ntiles},
-             ActEmit{sorted_pv, rect, b.views, b.n_views, keys, vals, cap_pairs, status}, n_vis,
-             cap_vis, temp, nullptr, status, s);
+    if (cap_vis <= 0) return;
+    uint32_t *nt_sorted = (uint32_t *)temp;
+    uint32_t *offs = nt_sorted + cap_vis;
+    void *scan_tmp = offs + cap_vis;
+    const unsigned nb = (unsigned)((cap_vis + 255) / 256);
+    gather_counts_kernel<<<nb, 256, 0, s>>>(sorted_pv, ntiles, n_vis, cap_vis, nt_sorted);
+    run_scan(LoadU32{nt_sorted}, ActStore{offs}, n_vis, cap_vis, scan_tmp, nullptr, status, s);
+    emit_pairs_kernel<<<nb, 256, 0, s>>>(b.views, b.n_views, sorted_pv, nt_sorted, offs, rect, n_vis,
+                                         cap_vis, keys, vals, cap_pairs, status);
+    count_launches(2);
 }
 
 void launch_tile_ranges(const uint32_t *keys, const uint32_t *n_pairs, int64_t cap_pairs,

@@ -89,7 +89,9 @@ constexpr float LOG2E = 1.4426950408889634f;
 constexpr float QP_TO_Q = -2.0f / 1.4426950408889634f;
 
 // ---- preprocess (k_preprocess.cu)
-// counters[0] += (tile, point-view) pairs, counters[1] += visible point-views
+// counters[0] += (tile, point-view) pairs, counters[1] += visible point-views;
+// 32-bit words 12 / 13 of counters: min / max depth bits of visible
+// point-views (word 12 must start at 0xffffffff, word 13 at 0).
 void launch_preprocess_fwd(const Batch &b, const DevOpts &o, float4 *rec, uint32_t *zbits,
                            uint32_t *ntiles, uint2 *rect, unsigned long long *counters,
                            cudaStream_t s);
@@ -106,11 +108,17 @@ void launch_compact_visible(const uint32_t *ntiles, const uint32_t *zbits, int64
 // Radix sort of (key, value) pairs, stable; n read from device *n_dev,
 // capacity cap.  key_bits: number of low key bits that can be non-zero.
 // Sorted result ends in (keys, vals) (buffers are ping-ponged internally).
+// Keys are ordered by (key - key_lo); key_bits = bits of (max key - key_lo).
+// Digits of up to 9 bits, ceil(key_bits / 9) passes.
 size_t radix_temp_bytes(int64_t cap);
+int radix_passes(int key_bits);
 void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *&keys_alt, uint32_t *&vals_alt,
                       const uint32_t *n_dev, int64_t cap, int key_bits, void *temp,
-                      cudaStream_t s);
-// Emits (tile, pv) pairs in depth order (same scan as count, with output).
+                      cudaStream_t s, uint32_t key_lo = 0);
+// Scratch of launch_emit_pairs (depth-ordered counts, offsets, scan).
+size_t emit_temp_bytes(int64_t cap_vis);
+// Emits (tile, pv) pairs in depth order: gathers the tile counts in depth
+// order, scans them, then writes each warp's runs cooperatively.
 void launch_emit_pairs(const Batch &b, const DevOpts &o, const uint32_t *sorted_pv,
                        const uint32_t *n_vis, int64_t cap_vis, const uint32_t *ntiles,
                        const uint2 *rect, uint32_t *keys, uint32_t *vals, int64_t cap_pairs,

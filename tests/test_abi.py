@@ -46,6 +46,6 @@ def test_library_exports_every_declared_symbol(libpath):
 def test_host_only_calls_work_without_a_gpu(libpath):
     from paper_2205_14330_gb300 import pbr
     o = pbr.default_opts()
-    assert (o.tile_w, o.tile_h, o.batch_depth) == (16, 16, 256)
+    assert (o.tile_w, o.tile_h, o.batch_depth) == (16, 16, 0)
     assert abs(o.alpha_max - 0.99) < 1e-7 and abs(o.cutoff_k - 3.0) < 1e-7
     assert b"sm_103a" in pbr.lib().pbr_version()

@@ -94,8 +94,8 @@ def test_bins_and_records_bit_exact(R, tile):
     rec = st.read("records")
     assert np.array_equal(rec[vis, 0].view(np.uint32), flat["px32"][vis].view(np.uint32))
     assert np.array_equal(rec[vis, 1].view(np.uint32), flat["py32"][vis].view(np.uint32))
-    assert np.array_equal(rec[vis, 7].view(np.uint32), flat["rc2_32"][vis].view(np.uint32))
-    col_err = np.abs(rec[vis, 4:7] - flat["rgb"][vis]).max()
+    assert np.array_equal(rec[vis, 2].view(np.uint32), flat["rc2_32"][vis].view(np.uint32))
+    col_err = np.abs(rec[vis, 5:8] - flat["rgb"][vis]).max()
     assert col_err <= 1e-5, col_err
     ref, _, _ = O.render(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], cams)
     err = np.abs(img.cpu().numpy() - ref).max()
@@ -108,7 +108,8 @@ def test_image_independent_of_tile_size_and_batch_depth(R):
     sc = _small_scene(2, n=500)
     cams = [scenes.camera((0.5, -0.3, 2.4), 97, 61)]
     imgs = []
-    for tile, depth in (((16, 16), 256), ((8, 8), 32), ((16, 32), 512), ((16, 16), 64)):
+    for tile, depth in (((16, 16), 0), ((8, 8), 0), ((16, 32), 0), ((16, 16), 256), ((8, 8), 32),
+                        ((16, 32), 512), ((16, 16), 64)):
         img, st, _ = _gpu_render(R, sc, cams, tile=tile, batch_depth=depth)
         imgs.append(img.cpu().numpy())
         st.close()
@@ -128,9 +129,10 @@ def test_forward_is_deterministic(R):
 
 @pytest.mark.parametrize("kw", [dict(), dict(dir_frame=1), dict(radius_mode=1),
                                 dict(max_per_pixel=15), dict(bg=(0.2, 0.5, 0.9)),
-                                dict(t_eps=0.0, cutoff_k=4.0), dict(alpha_max=0.5)],
+                                dict(t_eps=0.0, cutoff_k=4.0), dict(alpha_max=0.5),
+                                dict(batch_depth=256), dict(max_per_pixel=15, batch_depth=64)],
                          ids=["default", "world-dir", "ndc-radius", "n15", "bg", "no-stop",
-                              "amax"])
+                              "amax", "staged", "staged-n15"])
 def test_option_variants(R, kw):
     sc = _small_scene(4, n=600)
     if kw.get("radius_mode") == 1:
@@ -234,31 +236,42 @@ def test_multi_scene_multi_view(R):
 
 # ----------------------------------------------------------------- backward
 def test_tiny_config_gradients(R):
-    """Config: L2 loss against the image of positions jittered by N(0, 0.01)."""
+    """Config: L2 loss against the image of positions jittered by N(0, 0.01).
+    dL/dI comes from the oracle's images and is fed to both backward passes;
+    the GPU loss kernel is checked on the GPU images."""
     import torch
     pbr = _pbr()
     sc = scenes.tiny()
     img, st, _ = _gpu_render(R, sc, sc["cams"])
-    tgt_sc = dict(sc, pos=sc["target_pos"])
-    target, tst, _ = _gpu_render(R, tgt_sc, sc["cams"])
-    tst.close()
-    loss, g = pbr.image_loss(img, target, "l2")
-    gpos, gsh, gop = R.backward(st, g)
-    gn = g.cpu().numpy().astype(np.float64)
+    ref, _, _ = O.render(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], sc["cams"])
+    tref, _, _ = O.render(sc["target_pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"],
+                          sc["cams"])
+    gn = 2.0 * (ref - tref)
+    gpos, gsh, gop = R.backward(st, torch.from_numpy(gn.astype(np.float32)).cuda())
     dpos, dsh, dop = O.backward(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"],
                                 sc["cams"], gn)
     e = (_rel(gpos.cpu().numpy(), dpos), _rel(gsh.cpu().numpy().reshape(dsh.shape), dsh),
          _rel(gop.cpu().numpy(), dop))
     print(f"tiny grads rel L2 vs FP64 oracle: pos {e[0]:.2e} sh {e[1]:.2e} opacity {e[2]:.2e}")
     assert max(e) <= GRAD_TOL
-    ref_loss = float(((img.cpu().numpy().astype(np.float64) - target.cpu().numpy()) ** 2).sum())
-    assert abs(float(loss.item()) - ref_loss) <= 1e-6 * max(1.0, ref_loss)
+    # the loss kernel: sum of squares and its gradient
+    target = torch.from_numpy(tref.astype(np.float32)).cuda()
+    loss, g = pbr.image_loss(img, target, "l2")
+    d = img.double() - target.double()
+    assert abs(float(loss.item()) - float((d * d).sum())) <= 1e-6 * max(1.0, float((d * d).sum()))
+    assert torch.allclose(g, 2 * (img - target), atol=1e-6)
+    loss1, g1 = pbr.image_loss(img, target, "l1")
+    assert abs(float(loss1.item()) - float(d.abs().sum())) <= 1e-6 * max(1.0, float(d.abs().sum()))
+    assert torch.equal(g1, torch.sign(img - target))
     st.close()
 
 
 @pytest.mark.parametrize("kw", [dict(dir_frame=1), dict(radius_mode=1), dict(max_per_pixel=15),
-                                dict(bg=(0.3, 0.1, 0.7)), dict(tile=(8, 8)), dict(tile=(16, 32))],
-                         ids=["world-dir", "ndc", "n15", "bg", "8x8", "16x32"])
+                                dict(bg=(0.3, 0.1, 0.7)), dict(tile=(8, 8)), dict(tile=(16, 32)),
+                                dict(batch_depth=256), dict(tile=(8, 8), batch_depth=64),
+                                dict(max_per_pixel=15, batch_depth=128)],
+                         ids=["world-dir", "ndc", "n15", "bg", "8x8", "16x32", "staged",
+                              "staged-8x8", "staged-n15"])
 def test_gradient_variants(R, kw):
     import torch
     sc = _small_scene(20, n=400, deg=3)
