@@ -183,6 +183,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -261,27 +262,48 @@ def main():
             ms = float(t.item())
         return ms
 
-    # warm-up (also sizes the stream-ordered memory pool)
+    # ---- schedule: autotuned over tile size x compositing schedule
+    tune = None
+    if args.autotune:
+        opts, table = pbr.autotune(R, scene_list, cams, opts, scene_of_view=sov, backward=True,
+                                   reps=2)
+        tune = {f"{t[0]}x{t[1]}/{'staged-' + str(d) if d else ('persistent' if p else 'streamed')}":
+                round(v, 3) for (t, d, p), v in table.items()}
+    sched = {"tile": f"{opts.tile_w}x{opts.tile_h}", "batch_depth": int(opts.batch_depth),
+             "persistent": int(opts.persistent)}
+
+    # ---- timed region A: training steps as one CUDA-graph replay each
+    G = pbr.Graph(R, scene_list, cams, opts, scene_of_view=sov, target=target, loss=loss_kind)
     for _ in range(max(args.warmup, 0)):
+        G.launch(pbr.Graph.STEP)
+    ok, n_pairs_replay, cap_pairs = G.check()
+    if not ok:
+        G.replan()
+    clocks = ClockSampler(local)
+    launches0 = pbr.kernel_launches()
+    clocks.start()
+    ms = timed(lambda: G.launch(pbr.Graph.STEP), args.steps)
+    clk = clocks.stop()
+    launches = pbr.kernel_launches() - launches0
+    ok, _, _ = G.check()
+    assert ok, "graph replay outgrew its plan during the timed region"
+    value = world * mp / (ms * 1e-3)
+    fwd_ms = timed(lambda: G.launch(pbr.Graph.FORWARD), max(1, args.steps // 2))
+
+    # ---- timed region B: the same steps eagerly, with per-stage CUDA events
+    for _ in range(2):
         st, _, _ = step()
         st.close()
-    torch.cuda.synchronize()
-
-    # ---- timed region: K training steps, stage timing on, clocks sampled
-    clocks = ClockSampler(local)
     R.set_stage_timing(True)
     R.stage_times()  # reset
-    launches0 = pbr.kernel_launches()
     states = []
 
     def train_step():
         st, _, _ = step()
         states.append(st)
 
-    clocks.start()
-    ms = timed(train_step, args.steps)
-    clk = clocks.stop()
-    launches = pbr.kernel_launches() - launches0
+    k_eager = max(2, args.steps // 2)
+    eager_ms = timed(train_step, k_eager)
     stage = R.stage_times()
     R.set_stage_timing(False)
     pair_stats = states[-1].stats()
@@ -290,12 +312,6 @@ def main():
     for s_ in states:
         s_.close()
     states.clear()
-    value = world * mp / (ms * 1e-3)
-
-    # ---- forward only
-    def fwd():
-        R.forward(scene_list, cams, opts, scene_of_view=sov, out=img, keep_state=False)
-    fwd_ms = timed(fwd, max(1, args.steps // 2))
 
     # ---- plain single-view renderer: same kernels, one view per launch chain
     plain = None
@@ -319,49 +335,41 @@ def main():
         plain = {"fwd_bwd_mp_s": mp / (p_ms * 1e-3), "fwd_mp_s": mp / (pf_ms * 1e-3),
                  "ms_per_step": p_ms, "speedup_fwd_bwd": p_ms / ms, "speedup_fwd": pf_ms / fwd_ms}
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers (graph step)
     e2e = None
     if not args.no_e2e:
-        host = []
-        for s in scene_list:
-            host.append([t.detach().cpu().pin_memory() for t in (s.pos, s.sh, s.opacity, s.radius)])
+        host = [[t.detach().cpu().pin_memory() for t in (s.pos, s.sh, s.opacity, s.radius)]
+                for s in scene_list]
         host_tgt = target.cpu().pin_memory()
-        dev_scenes = [pbr.Scene(torch.empty_like(s.pos), torch.empty_like(s.sh),
-                                torch.empty_like(s.opacity), torch.empty_like(s.radius), s.deg, dev)
-                      for s in scene_list]
-        dev_tgt = torch.empty_like(target)
-        n_tot = sum(s.n for s in scene_list)
-        n_sh = sum(s.sh.numel() for s in scene_list)
-        out_h = [torch.empty((n_tot, 3)).pin_memory(), torch.empty(n_sh).pin_memory(),
-                 torch.empty(n_tot).pin_memory(), torch.empty(1, dtype=torch.float64).pin_memory()]
+        out_h = [torch.empty(tuple(G.grad_pos.shape)).pin_memory(),
+                 torch.empty(tuple(G.grad_sh.shape)).pin_memory(),
+                 torch.empty(tuple(G.grad_opacity.shape)).pin_memory(),
+                 torch.empty(1, dtype=torch.float64).pin_memory()]
         h2d = sum(t.numel() * t.element_size() for ts in host for t in ts) + \
             host_tgt.numel() * host_tgt.element_size()
         d2h = sum(t.numel() * t.element_size() for t in out_h)
 
         def e2e_step():
-            for hs, ds in zip(host, dev_scenes):
+            for hs, ds in zip(host, scene_list):
                 for h, d in zip(hs, (ds.pos, ds.sh, ds.opacity, ds.radius)):
                     d.copy_(h, non_blocking=True)
-            dev_tgt.copy_(host_tgt, non_blocking=True)
-            st, loss, (gpos, gsh, gop) = step(dev_scenes, dev_tgt)
-            out_h[0].copy_(gpos, non_blocking=True)
-            out_h[1].copy_(gsh, non_blocking=True)
-            out_h[2].copy_(gop, non_blocking=True)
-            out_h[3].copy_(loss, non_blocking=True)
-            states.append(st)
+            target.copy_(host_tgt, non_blocking=True)
+            G.launch(pbr.Graph.STEP)
+            out_h[0].copy_(G.grad_pos, non_blocking=True)
+            out_h[1].copy_(G.grad_sh, non_blocking=True)
+            out_h[2].copy_(G.grad_opacity, non_blocking=True)
+            out_h[3].copy_(G.loss, non_blocking=True)
         e2e_step()
-        torch.cuda.synchronize()
-        states.clear()
         e_ms = timed(e2e_step, max(1, args.steps // 2))
-        for s_ in states:
-            s_.close()
-        states.clear()
         e2e = {"value": world * mp / (e_ms * 1e-3), "unit": "MP/s", "ms_per_step": e_ms,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "path": "pinned host -> device copies, graph training step, gradients and loss "
+                       "-> pinned host"}
+    G.close()
 
     # ---- roofline of the dominant kernel
     hbm_peak, hbm_src, peaks = measured_peaks()
-    stage_ms = {k: v[0] / max(1, args.steps) for k, v in stage.items() if v[1]}
+    stage_ms = {k: v[0] / k_eager for k, v in stage.items() if v[1]}
     dom = max(stage_ms, key=stage_ms.get)
     sm_mhz = (clk or {}).get("sm_mhz") or 1500.0
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
@@ -399,15 +407,19 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": desc, "points": n_points, "views": len(cams),
-                           "megapixels_per_step": mp, "tile": args.tile,
-                           "batch_depth": args.batch_depth, "loss": loss_kind,
+                           "megapixels_per_step": mp, "schedule": sched, "loss": loss_kind,
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2_policy": "inputs larger than L2 (params "
                                         f"{sum(s.pos.numel()+s.sh.numel()+2*s.n for s in scene_list)*4/1e6:.0f} MB, "
                                         f"images {npix*12/1e6:.0f} MB per step)"},
                 "fwd_mp_s": world * mp / (fwd_ms * 1e-3), "fwd_ms": fwd_ms,
+                "eager_ms_per_step": eager_ms, "eager_mp_s": world * mp / (eager_ms * 1e-3),
+                "schedule": sched, "autotune_ms": tune,
+                "timing": "value/fwd: CUDA-graph replays of the whole step; stage_ms and the "
+                          "roofline: the same steps launched eagerly with per-stage CUDA events",
                 "plain": plain, "stage_ms": stage_ms, "roofline": roof,
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches // max(1, args.steps)),
+                "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches // max(1, args.steps)),
                 "gpu_launches_timed_region": int(launches), "clocks": clk,
                 "pairs": {k: int(v) for k, v in pair_stats.items()}, "sizes": sizes,
                 "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src}

@@ -88,7 +88,11 @@ typedef struct {
                               warp walks its tile list alone, no block barriers);
                               32..1024 (multiple of 32) = block-staged batches of
                               that many points in shared memory */
-    int32_t reserved[4];
+    int32_t persistent;    /* 1: warp-streamed compositing as one persistent launch
+                              (SM-count grid, warps pull (tile, 8x4 sub-block)
+                              items longest tile first); 0 (default): one block
+                              per tile.  Ignored by the block-staged schedule. */
+    int32_t reserved[3];
 } pbr_render_opts;
 
 /* One scene: n points with position [n,3], SH coefficients [n,K,3]
@@ -179,6 +183,56 @@ int pbr_image_loss(int32_t kind, const float *pred, const float *target, int64_t
  * pairs examined, backward pairs contributing}.  These are the work units of
  * the compositing kernels' ALU roofline.  Synchronises the state's stream. */
 int pbr_state_stats(pbr_state *state, unsigned long long *out4);
+
+/* ------------------------------------------------------- batched graphs */
+/* Plans one batch of views (the same arguments as pbr_render_forward) and
+ * captures it as CUDA graphs that replay without any host synchronisation:
+ * an eager planning pass measures the pair count and depth range, buffers
+ * are allocated once (pairs x (1 + headroom)), and the forward chain -- and,
+ * when gradient buffers are given, the backward pass and a whole training
+ * step (forward, image loss against `target`, backward) -- are captured.
+ * Graph phases for pbr_graph_launch: 0 forward (writes out_rgb), 1 backward
+ * (reads grad_rgb, needs grad_rgb non-NULL), 2 training step (needs target;
+ * writes the loss to loss_out when non-NULL and gradients to grad_*).
+ * The point arrays and output buffers are bound at capture: update their
+ * contents in place between launches (e.g. after an optimiser step).
+ * loss_kind: 0 sum of squares, 1 sum of absolute values.  Synchronises the
+ * stream during planning.  Errors: INVALID_ARG, OOM, CUDA. */
+int pbr_graph_create(pbr_ctx *ctx, const pbr_points *scenes, int32_t n_scenes,
+                     const int32_t *scene_of_view, const pbr_camera *cams, int32_t n_cams,
+                     const pbr_render_opts *opts, float *out_rgb, const float *target,
+                     int32_t loss_kind, double *loss_out, const float *grad_rgb, float *grad_pos,
+                     float *grad_sh, float *grad_opacity, double headroom, pbr_stream_t stream,
+                     pbr_graph **out);
+/* Enqueues one replay of a phase on `stream`. */
+int pbr_graph_launch(pbr_graph *graph, int32_t phase, pbr_stream_t stream);
+/* Synchronises `stream` and reads the device status word: PBR_ERR_CAPACITY
+ * when the last replay had more pairs than planned or depths outside the
+ * planned key range (its output is then invalid: call pbr_graph_replan and
+ * launch again).  Optional outputs: pair count of the last replay and the
+ * planned capacity. */
+int pbr_graph_check(pbr_graph *graph, pbr_stream_t stream, int64_t *n_pairs, int64_t *cap_pairs);
+/* Re-plans on the current point data and re-captures (synchronises). */
+int pbr_graph_replan(pbr_graph *graph, pbr_stream_t stream);
+/* Replaces the cameras' intrinsics and extrinsics (image sizes must be
+ * unchanged) for the following launches.  Synchronises the stream. */
+int pbr_graph_set_cameras(pbr_graph *graph, const pbr_camera *cams, int32_t n_cams,
+                          pbr_stream_t stream);
+int pbr_graph_destroy(pbr_graph *graph);
+
+/* Autotuner: times every schedule candidate (tile 8x8 / 16x16 / 16x32 x
+ * {warp-streamed, persistent warp-streamed, block-staged 128 / 256 / 512})
+ * on this batch -- forward only (mode 0) or forward + backward (mode 1),
+ * `reps` timed runs each -- and writes the fastest into *opts (tile_w,
+ * tile_h, batch_depth, persistent).  The choice is cached in the context
+ * per shape class (views, log2 pixels, log2 point-views, SH degrees, mode);
+ * a cached class returns at once unless ms_out is given.  ms_out (nullable,
+ * 15 entries) receives the mean milliseconds per candidate in the order
+ * above, *n_candidates the number timed.  Synchronises. */
+int pbr_autotune(pbr_ctx *ctx, const pbr_points *scenes, int32_t n_scenes,
+                 const int32_t *scene_of_view, const pbr_camera *cams, int32_t n_cams,
+                 pbr_render_opts *opts, int32_t mode, int32_t reps, double *ms_out,
+                 int32_t *n_candidates, pbr_stream_t stream);
 
 /* --------------------------------------------------- measurement support */
 /* Number of CUDA kernels this library has launched in this process. */

@@ -320,7 +320,7 @@ void pbr_state::release()
     void **all[] = {(void **)&d_views, (void **)&d_scenes, (void **)&d_view_list, (void **)&rec,
                     (void **)&ntiles, (void **)&counters, (void **)&tile_keys,
                     (void **)&tile_vals, (void **)&ranges, (void **)&T_final,
-                    (void **)&n_contrib};
+                    (void **)&n_contrib, (void **)&tile_order, (void **)&work};
     for (void **p : all) {
         dfree(*p, stream);
         *p = nullptr;
@@ -432,11 +432,18 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
         launch_tile_ranges(st->tile_keys, n_pairs_dev, (int64_t)n_pairs, st->ranges, L.n_tiles,
                            s);
     }
-    // 6. composite
+    // 6. composite (optionally as one persistent launch over a longest-first tile order)
+    const bool persist = st->opts.persistent && st->batch_depth == 0;
+    if (persist) {
+        PBR_TRY(dalloc((void **)&st->tile_order, sizeof(uint32_t) * L.n_tiles, s));
+        PBR_TRY(dalloc((void **)&st->work, 64 * sizeof(uint32_t), s));
+    }
     {
         StageScope t(c, STG_RASTER_FWD, s);
+        if (persist) launch_tile_order(st->ranges, L.n_tiles, st->tile_order, st->work, s);
         launch_raster_fwd(b, o, st->batch_depth, st->ranges, st->tile_vals, st->rec, out_rgb,
-                          st->T_final, st->n_contrib, st->counters + 2, s);
+                          st->T_final, st->n_contrib, st->counters + 2, s, st->tile_order,
+                          st->work);
     }
     PBR_CUDA(cudaGetLastError());
     return PBR_OK;
@@ -485,8 +492,10 @@ extern "C" int pbr_render_backward(pbr_ctx *c, pbr_state *st, const float *grad_
     {
         StageScope t(c, STG_RASTER_BWD, s);
         PBR_CUDA(cudaMemsetAsync(g2d, 0, sizeof(float4) * 2 * L.n_pv, s));
+        if (st->work) reset_work_counters(st->work, s);
         launch_raster_bwd(b, st->dopts, st->batch_depth, st->ranges, st->tile_vals, st->rec,
-                          st->T_final, st->n_contrib, grad_rgb, g2d, st->counters + 2, s);
+                          st->T_final, st->n_contrib, grad_rgb, g2d, st->counters + 2, s,
+                          st->tile_order, st->work);
     }
     {
         StageScope t(c, STG_PREPROCESS_BWD, s);

@@ -1,9 +1,12 @@
 // Host-side objects behind the opaque handles of pbr.h.
 #pragma once
 
+#include <array>
 #include <cstdarg>
 #include <cstdint>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "pbr.h"
@@ -28,6 +31,8 @@ struct pbr_ctx {
     std::vector<cudaEvent_t> event_pool;
     double stage_ms[pbr::STG_COUNT] = {};
     long long stage_calls[pbr::STG_COUNT] = {};
+    // autotuner cache: shape class -> {tile_w, tile_h, batch_depth, persistent}
+    std::map<std::tuple<int64_t, int64_t, int64_t, int64_t, int64_t>, std::array<int, 4>> tuned;
 };
 
 namespace pbr {
@@ -72,6 +77,8 @@ struct pbr_state {
     uint2 *ranges = nullptr;
     float *T_final = nullptr;
     uint32_t *n_contrib = nullptr;
+    uint32_t *tile_order = nullptr; // persistent raster: tiles, longest list first
+    uint32_t *work = nullptr;       // persistent raster: item counters + buckets
 
     pbr::Batch batch() const
     {

@@ -70,6 +70,7 @@ struct PixelGeom {
     float ux, uy, xl, xh, yl, yh;
 };
 
+// Sub-block `w` of tile `tile` (sub-blocks numbered row-major, TW/8 per row).
 template <int TW, int TH>
 __device__ __forceinline__ PixelGeom pixel_geom(const Batch &b, uint32_t tile, int w, int lane)
 {
@@ -217,16 +218,18 @@ __device__ __forceinline__ void add_stats(unsigned long long *stats, uint32_t a,
 }
 
 // ======================================================= warp-streamed
+// One warp composites sub-block `sub` of tile `tile`.
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH)
-raster_fwd_stream_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
-                         const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
-                         float *__restrict__ out_rgb, float *__restrict__ T_final,
-                         uint32_t *__restrict__ n_contrib, unsigned long long *__restrict__ stats)
+__device__ __forceinline__ void fwd_stream_item(const Batch &b, const DevOpts &o, uint32_t tile,
+                                                int sub, int lane, const uint2 *__restrict__ ranges,
+                                                const uint32_t *__restrict__ pv_list,
+                                                const float4 *__restrict__ rec,
+                                                float *__restrict__ out_rgb,
+                                                float *__restrict__ T_final,
+                                                uint32_t *__restrict__ n_contrib,
+                                                uint32_t &examined_acc, uint32_t &composited_acc)
 {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const uint32_t tile = blockIdx.x;
-    const PixelGeom g = pixel_geom<TW, TH>(b, tile, w, lane);
+    const PixelGeom g = pixel_geom<TW, TH>(b, tile, sub, lane);
     const uint2 rg = ranges[tile];
     const uint32_t s = rg.x, e = rg.y > rg.x ? rg.y : rg.x;
 
@@ -276,23 +279,25 @@ raster_fwd_stream_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
             if (stop) break;
         }
     }
-    add_stats(stats, examined, cnt, lane);
+    examined_acc += examined;
+    composited_acc += cnt;
     write_pixel(g, o, T, C0, C1, C2, last, out_rgb, T_final, n_contrib);
 }
 
+// One warp back-propagates through sub-block `sub` of tile `tile`.
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH)
-raster_bwd_stream_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
-                         const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
-                         const float *__restrict__ T_final, const uint32_t *__restrict__ n_contrib,
-                         const float *__restrict__ grad_rgb, float *__restrict__ g2d,
-                         unsigned long long *__restrict__ stats)
+__device__ __forceinline__ void bwd_stream_item(const Batch &b, const DevOpts &o, uint32_t tile,
+                                                int sub, int lane, const uint2 *__restrict__ ranges,
+                                                const uint32_t *__restrict__ pv_list,
+                                                const float4 *__restrict__ rec,
+                                                const float *__restrict__ T_final,
+                                                const uint32_t *__restrict__ n_contrib,
+                                                const float *__restrict__ grad_rgb,
+                                                float *__restrict__ g2d, uint32_t &examined,
+                                                uint32_t &used)
 {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const uint32_t tile = blockIdx.x;
-    const PixelGeom g = pixel_geom<TW, TH>(b, tile, w, lane);
+    const PixelGeom g = pixel_geom<TW, TH>(b, tile, sub, lane);
     const uint32_t s = ranges[tile].x;
-
     float T = 1.0f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
     uint32_t L = 0;
     if (g.inside) {
@@ -305,54 +310,175 @@ raster_bwd_stream_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
     }
     float S = T * (o.bg[0] * g0 + o.bg[1] * g1 + o.bg[2] * g2);
     const uint32_t wmax = __reduce_max_sync(0xffffffffu, L);
-    uint32_t examined = 0, used = 0;
-    if (wmax > 0) {
-        int64_t c = (int64_t)((wmax - 1) & ~31u);
-        uint32_t pv_n = 0;
-        float4 a_n = make_float4(0.f, 0.f, -1.f, 0.f);
-        if ((uint32_t)c + lane < wmax) {
-            pv_n = __ldg(pv_list + s + (uint32_t)c + lane);
+    if (wmax == 0) return;
+    int64_t c = (int64_t)((wmax - 1) & ~31u);
+    uint32_t pv_n = 0;
+    float4 a_n = make_float4(0.f, 0.f, -1.f, 0.f);
+    if ((uint32_t)c + lane < wmax) {
+        pv_n = __ldg(pv_list + s + (uint32_t)c + lane);
+        a_n = __ldg(rec + 2 * (size_t)pv_n);
+    }
+    for (; c >= 0; c -= 32) {
+        const uint32_t pv = pv_n;
+        const float4 a = a_n;
+        const bool valid = (uint32_t)c + lane < wmax;
+        if (c >= 32) {
+            pv_n = __ldg(pv_list + s + (uint32_t)c - 32 + lane);
             a_n = __ldg(rec + 2 * (size_t)pv_n);
         }
-        for (; c >= 0; c -= 32) {
-            const uint32_t pv = pv_n;
-            const float4 a = a_n;
-            const bool valid = (uint32_t)c + lane < wmax;
-            if (c >= 32) {
-                pv_n = __ldg(pv_list + s + (uint32_t)c - 32 + lane);
-                a_n = __ldg(rec + 2 * (size_t)pv_n);
+        const bool hit = valid && disc_meets_rect(a, g);
+        uint32_t m = __ballot_sync(0xffffffffu, hit);
+        float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (hit) bb = __ldg(rec + 2 * (size_t)pv + 1);
+        while (m) {
+            const int j = 31 - __clz(m); // back to front
+            m &= ~(1u << j);
+            const float4 aj = shfl4(a, j);
+            const float4 cj = shfl4(bb, j);
+            const uint32_t pvj = __shfl_sync(0xffffffffu, pv, j);
+            float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            bool contrib = false;
+            if ((uint32_t)c + j < L) {
+                ++examined;
+                float dx, dy;
+                const float d2 = pixel_d2(g.ux, g.uy, aj.x, aj.y, dx, dy);
+                if (d2 <= aj.z) {
+                    contrib = true;
+                    ++used;
+                    pixel_adjoint(d2, dx, dy, aj, cj, o.alpha_max, g0, g1, g2, T, S, v);
+                }
             }
-            const bool hit = valid && disc_meets_rect(a, g);
-            uint32_t m = __ballot_sync(0xffffffffu, hit);
-            float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (hit) bb = __ldg(rec + 2 * (size_t)pv + 1);
-            while (m) {
-                const int j = 31 - __clz(m); // back to front
-                m &= ~(1u << j);
-                const float4 aj = shfl4(a, j);
-                const float4 cj = shfl4(bb, j);
-                const uint32_t pvj = __shfl_sync(0xffffffffu, pv, j);
-                float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                bool contrib = false;
-                if ((uint32_t)c + j < L) {
-                    ++examined;
-                    float dx, dy;
-                    const float d2 = pixel_d2(g.ux, g.uy, aj.x, aj.y, dx, dy);
-                    if (d2 <= aj.z) {
-                        contrib = true;
-                        ++used;
-                        pixel_adjoint(d2, dx, dy, aj, cj, o.alpha_max, g0, g1, g2, T, S, v);
-                    }
-                }
-                if (__any_sync(0xffffffffu, contrib)) {
-                    const float tot = warp_sum8_transposed(v, lane);
-                    const int which = (lane >> 2) & 7;
-                    if ((lane & 3) == 0 && which < 7) atomicAdd(g2d + 8 * (size_t)pvj + which, tot);
-                }
+            if (__any_sync(0xffffffffu, contrib)) {
+                const float tot = warp_sum8_transposed(v, lane);
+                const int which = (lane >> 2) & 7;
+                if ((lane & 3) == 0 && which < 7) atomicAdd(g2d + 8 * (size_t)pvj + which, tot);
             }
         }
     }
-    add_stats(stats ? stats + 2 : nullptr, examined, used, lane);
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH)
+raster_fwd_stream_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
+                         const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
+                         float *__restrict__ out_rgb, float *__restrict__ T_final,
+                         uint32_t *__restrict__ n_contrib, unsigned long long *__restrict__ stats)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t ex = 0, co = 0;
+    fwd_stream_item<TW, TH>(b, o, blockIdx.x, threadIdx.x >> 5, lane, ranges, pv_list, rec,
+                            out_rgb, T_final, n_contrib, ex, co);
+    add_stats(stats, ex, co, lane);
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH)
+raster_bwd_stream_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
+                         const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
+                         const float *__restrict__ T_final, const uint32_t *__restrict__ n_contrib,
+                         const float *__restrict__ grad_rgb, float *__restrict__ g2d,
+                         unsigned long long *__restrict__ stats)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t ex = 0, us = 0;
+    bwd_stream_item<TW, TH>(b, o, blockIdx.x, threadIdx.x >> 5, lane, ranges, pv_list, rec,
+                            T_final, n_contrib, grad_rgb, g2d, ex, us);
+    add_stats(stats ? stats + 2 : nullptr, ex, us, lane);
+}
+
+// ------------------------------------------------------------ persistent
+// Persistent warps: each warp takes (tile, sub-block) items from an atomic
+// counter over `order` (tiles sorted longest list first), so long tiles
+// start early and no warp idles while work remains.
+constexpr int PERSIST_THREADS = 256;
+
+__device__ __forceinline__ uint32_t next_item(uint32_t *work, int lane)
+{
+    uint32_t it = 0;
+    if (lane == 0) it = atomicAdd(work, 1u);
+    return __shfl_sync(0xffffffffu, it, 0);
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(PERSIST_THREADS)
+raster_fwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
+                          const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
+                          float *__restrict__ out_rgb, float *__restrict__ T_final,
+                          uint32_t *__restrict__ n_contrib, unsigned long long *__restrict__ stats,
+                          const uint32_t *__restrict__ order, uint32_t *work)
+{
+    constexpr uint32_t SUBS = (TW / 8) * (TH / 4);
+    const int lane = threadIdx.x & 31;
+    const uint32_t n_items = b.n_tiles * SUBS;
+    uint32_t ex = 0, co = 0;
+    for (uint32_t it = next_item(work, lane); it < n_items; it = next_item(work, lane))
+        fwd_stream_item<TW, TH>(b, o, order[it / SUBS], (int)(it % SUBS), lane, ranges, pv_list,
+                                rec, out_rgb, T_final, n_contrib, ex, co);
+    add_stats(stats, ex, co, lane);
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(PERSIST_THREADS)
+raster_bwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
+                          const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
+                          const float *__restrict__ T_final, const uint32_t *__restrict__ n_contrib,
+                          const float *__restrict__ grad_rgb, float *__restrict__ g2d,
+                          unsigned long long *__restrict__ stats, const uint32_t *__restrict__ order,
+                          uint32_t *work)
+{
+    constexpr uint32_t SUBS = (TW / 8) * (TH / 4);
+    const int lane = threadIdx.x & 31;
+    const uint32_t n_items = b.n_tiles * SUBS;
+    uint32_t ex = 0, us = 0;
+    for (uint32_t it = next_item(work, lane); it < n_items; it = next_item(work, lane))
+        bwd_stream_item<TW, TH>(b, o, order[it / SUBS], (int)(it % SUBS), lane, ranges, pv_list,
+                                rec, T_final, n_contrib, grad_rgb, g2d, ex, us);
+    add_stats(stats ? stats + 2 : nullptr, ex, us, lane);
+}
+
+// Tile order, longest list first: bucket = floor(log2(length)), buckets in
+// descending order (order inside a bucket is arbitrary; it only affects
+// scheduling).  work[0] = forward item counter, work[1] = backward item
+// counter, work[2..34) = bucket counts / offsets.
+__global__ void tile_bucket_count_kernel(const uint2 *__restrict__ ranges, uint32_t n_tiles,
+                                         uint32_t *work)
+{
+    __shared__ uint32_t s_c[32];
+    if (threadIdx.x < 32) s_c[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n_tiles) {
+        const uint2 r = ranges[t];
+        const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
+        atomicAdd(&s_c[31 - (len ? __clz(len) : 31)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && s_c[threadIdx.x]) atomicAdd(work + 2 + threadIdx.x, s_c[threadIdx.x]);
+}
+
+__global__ void tile_bucket_scan_kernel(uint32_t *work)
+{
+    if (threadIdx.x == 0) {
+        work[0] = 0;
+        work[1] = 0;
+        uint32_t run = 0;
+        for (int bkt = 31; bkt >= 0; --bkt) { // longest first
+            const uint32_t c = work[2 + bkt];
+            work[2 + bkt] = run;
+            run += c;
+        }
+    }
+}
+
+__global__ void tile_bucket_scatter_kernel(const uint2 *__restrict__ ranges, uint32_t n_tiles,
+                                           uint32_t *work, uint32_t *__restrict__ order)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    const uint2 r = ranges[t];
+    const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
+    const uint32_t pos = atomicAdd(work + 2 + (31 - (len ? __clz(len) : 31)), 1u);
+    order[pos] = t;
 }
 
 // ========================================================= block-staged
@@ -515,12 +641,26 @@ raster_bwd_staged_kernel(Batch b, DevOpts o, int depth, const uint2 *__restrict_
 }
 
 // ------------------------------------------------------------ dispatch
+int persist_grid(const void *kernel)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, PERSIST_THREADS, 0);
+    return sms * (per_sm > 0 ? per_sm : 1);
+}
+
 template <int TW, int TH>
 void fwd_dispatch(const Batch &b, const DevOpts &o, int depth, const uint2 *ranges,
                   const uint32_t *pv_list, const float4 *rec, float *out_rgb, float *T_final,
-                  uint32_t *n_contrib, unsigned long long *stats, cudaStream_t s)
+                  uint32_t *n_contrib, unsigned long long *stats, const uint32_t *order,
+                  uint32_t *work, cudaStream_t s)
 {
-    if (depth == 0) {
+    if (depth == 0 && order) {
+        static const int grid = persist_grid((const void *)raster_fwd_persist_kernel<TW, TH>);
+        raster_fwd_persist_kernel<TW, TH><<<grid, PERSIST_THREADS, 0, s>>>(
+            b, o, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats, order, work);
+    } else if (depth == 0) {
         raster_fwd_stream_kernel<TW, TH><<<b.n_tiles, TW * TH, 0, s>>>(
             b, o, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats);
     } else {
@@ -540,9 +680,15 @@ template <int TW, int TH>
 void bwd_dispatch(const Batch &b, const DevOpts &o, int depth, const uint2 *ranges,
                   const uint32_t *pv_list, const float4 *rec, const float *T_final,
                   const uint32_t *n_contrib, const float *grad_rgb, float4 *g2d,
-                  unsigned long long *stats, cudaStream_t s)
+                  unsigned long long *stats, const uint32_t *order, uint32_t *work,
+                  cudaStream_t s)
 {
-    if (depth == 0) {
+    if (depth == 0 && order) {
+        static const int grid = persist_grid((const void *)raster_bwd_persist_kernel<TW, TH>);
+        raster_bwd_persist_kernel<TW, TH><<<grid, PERSIST_THREADS, 0, s>>>(
+            b, o, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d, stats, order,
+            work + 1);
+    } else if (depth == 0) {
         raster_bwd_stream_kernel<TW, TH><<<b.n_tiles, TW * TH, 0, s>>>(
             b, o, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d, stats);
     } else {
@@ -560,35 +706,56 @@ void bwd_dispatch(const Batch &b, const DevOpts &o, int depth, const uint2 *rang
 
 } // namespace
 
+void launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, uint32_t *work,
+                       cudaStream_t s)
+{
+    cudaMemsetAsync(work, 0, 34 * sizeof(uint32_t), s);
+    if (n_tiles == 0) return;
+    const unsigned nb = (n_tiles + 255) / 256;
+    tile_bucket_count_kernel<<<nb, 256, 0, s>>>(ranges, n_tiles, work);
+    tile_bucket_scan_kernel<<<1, 32, 0, s>>>(work);
+    tile_bucket_scatter_kernel<<<nb, 256, 0, s>>>(ranges, n_tiles, work, order);
+    count_launches(3);
+}
+
+void reset_work_counters(uint32_t *work, cudaStream_t s)
+{
+    cudaMemsetAsync(work, 0, 2 * sizeof(uint32_t), s);
+}
+
 void launch_raster_fwd(const Batch &b, const DevOpts &o, int depth, const uint2 *ranges,
                        const uint32_t *pv_list, const float4 *rec, float *out_rgb,
                        float *T_final, uint32_t *n_contrib, unsigned long long *stats,
-                       cudaStream_t s)
+                       cudaStream_t s, const uint32_t *order, uint32_t *work)
 {
     if (b.n_tiles == 0) return;
     if (o.tile_w == 8 && o.tile_h == 8)
-        fwd_dispatch<8, 8>(b, o, depth, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats, s);
+        fwd_dispatch<8, 8>(b, o, depth, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats,
+                           order, work, s);
     else if (o.tile_w == 16 && o.tile_h == 32)
-        fwd_dispatch<16, 32>(b, o, depth, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats, s);
+        fwd_dispatch<16, 32>(b, o, depth, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats,
+                             order, work, s);
     else
-        fwd_dispatch<16, 16>(b, o, depth, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats, s);
+        fwd_dispatch<16, 16>(b, o, depth, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats,
+                             order, work, s);
 }
 
 void launch_raster_bwd(const Batch &b, const DevOpts &o, int depth, const uint2 *ranges,
                        const uint32_t *pv_list, const float4 *rec, const float *T_final,
                        const uint32_t *n_contrib, const float *grad_rgb, float4 *g2d,
-                       unsigned long long *stats, cudaStream_t s)
+                       unsigned long long *stats, cudaStream_t s, const uint32_t *order,
+                       uint32_t *work)
 {
     if (b.n_tiles == 0) return;
     if (o.tile_w == 8 && o.tile_h == 8)
         bwd_dispatch<8, 8>(b, o, depth, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, g2d,
-                           stats, s);
+                           stats, order, work, s);
     else if (o.tile_w == 16 && o.tile_h == 32)
         bwd_dispatch<16, 32>(b, o, depth, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, g2d,
-                             stats, s);
+                             stats, order, work, s);
     else
         bwd_dispatch<16, 16>(b, o, depth, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, g2d,
-                             stats, s);
+                             stats, order, work, s);
 }
 
 } // namespace pbr

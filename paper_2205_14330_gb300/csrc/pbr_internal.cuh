@@ -127,14 +127,22 @@ void launch_tile_ranges(const uint32_t *keys, const uint32_t *n_pairs, int64_t c
                         uint2 *ranges, uint32_t n_tiles, cudaStream_t s);
 
 // ---- raster (k_raster.cu)
+// batch_depth 0 = warp-streamed, > 0 = block-staged.  With order/work set
+// (warp-streamed only) the launch is persistent: warps pull (tile,
+// sub-block) items from work[0] (forward) / work[1] (backward) over `order`.
 void launch_raster_fwd(const Batch &b, const DevOpts &o, int batch_depth, const uint2 *ranges,
                        const uint32_t *pv_list, const float4 *rec, float *out_rgb,
                        float *T_final, uint32_t *n_contrib, unsigned long long *stats,
-                       cudaStream_t s);
+                       cudaStream_t s, const uint32_t *order = nullptr, uint32_t *work = nullptr);
 void launch_raster_bwd(const Batch &b, const DevOpts &o, int batch_depth, const uint2 *ranges,
                        const uint32_t *pv_list, const float4 *rec, const float *T_final,
                        const uint32_t *n_contrib, const float *grad_rgb, float4 *g2d,
-                       unsigned long long *stats, cudaStream_t s);
+                       unsigned long long *stats, cudaStream_t s,
+                       const uint32_t *order = nullptr, uint32_t *work = nullptr);
+// Longest-first tile order for the persistent raster; work: 34 u32 words.
+void launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, uint32_t *work,
+                       cudaStream_t s);
+void reset_work_counters(uint32_t *work, cudaStream_t s);
 
 // ---- misc (k_misc.cu)
 void launch_image_loss(int kind, const float *pred, const float *target, int64_t n, float *grad,

@@ -42,7 +42,8 @@ class Opts(C.Structure):
     _fields_ = [("radius_mode", C.c_int32), ("dir_frame", C.c_int32), ("cutoff_k", C.c_float),
                 ("alpha_max", C.c_float), ("t_eps", C.c_float), ("max_per_pixel", C.c_int32),
                 ("bg", C.c_float * 3), ("z_near", C.c_float), ("tile_w", C.c_int32),
-                ("tile_h", C.c_int32), ("batch_depth", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("tile_h", C.c_int32), ("batch_depth", C.c_int32), ("persistent", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class Points(C.Structure):
@@ -92,6 +93,17 @@ def lib():
             L.pbr_render_forward_noalloc.argtypes = [C.POINTER(Points), i32, vp,
                                                      C.POINTER(Camera), i32, C.POINTER(Opts),
                                                      vp, vp]
+            L.pbr_graph_create.argtypes = [vp, C.POINTER(Points), i32, vp, C.POINTER(Camera), i32,
+                                           C.POINTER(Opts), vp, vp, i32, vp, vp, vp, vp, vp,
+                                           C.c_double, vp, C.POINTER(vp)]
+            L.pbr_graph_launch.argtypes = [vp, i32, vp]
+            L.pbr_graph_check.argtypes = [vp, vp, C.POINTER(i64), C.POINTER(i64)]
+            L.pbr_graph_replan.argtypes = [vp, vp]
+            L.pbr_graph_set_cameras.argtypes = [vp, C.POINTER(Camera), i32, vp]
+            L.pbr_graph_destroy.argtypes = [vp]
+            L.pbr_autotune.argtypes = [vp, C.POINTER(Points), i32, vp, C.POINTER(Camera), i32,
+                                       C.POINTER(Opts), i32, i32, C.POINTER(C.c_double),
+                                       C.POINTER(i32), vp]
             L.pbr_state_stats.argtypes = [vp, C.POINTER(C.c_ulonglong)]
             L.pbr_kernel_launches.restype = C.c_ulonglong
             L.pbr_kernel_launches.argtypes = []
@@ -296,6 +308,98 @@ def render_forward_noalloc(scenes, cams, opts=None, scene_of_view=None, out=None
     check(lib().pbr_render_forward_noalloc(pts, len(scenes), sov, cam_arr, len(cams),
                                            C.byref(opts), _ptr(out), _stream()))
     return out
+
+
+class Graph:
+    """A batch of views captured as CUDA graphs (see pbr_graph_create).
+
+    Phases: FORWARD (0) writes `out`; BACKWARD (1) reads `grad_rgb`; STEP (2)
+    runs forward, the image loss against `target` and backward.  Tensors
+    passed here are bound to the graph: update them in place."""
+
+    FORWARD, BACKWARD, STEP = 0, 1, 2
+
+    def __init__(self, renderer, scenes, cams, opts=None, scene_of_view=None, target=None,
+                 loss="l2", backward=True, grad_rgb=None, headroom=0.25):
+        self.renderer = renderer
+        self.scenes = scenes if isinstance(scenes, (list, tuple)) else [scenes]
+        self.cams = list(cams)
+        self.opts = opts or default_opts()
+        dev = self.scenes[0].pos.device
+        self.out = torch.empty((n_pixels(cams), 3), dtype=torch.float32, device=dev)
+        self.target = target
+        self.grad_rgb = grad_rgb
+        self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
+        n_tot = sum(s.n for s in self.scenes)
+        n_sh = sum(s.sh.numel() for s in self.scenes)
+        self.grad_pos = self.grad_sh = self.grad_opacity = None
+        if backward:
+            self.grad_pos = torch.zeros((n_tot, 3), dtype=torch.float32, device=dev)
+            self.grad_sh = torch.zeros((n_sh,), dtype=torch.float32, device=dev)
+            self.grad_opacity = torch.zeros((n_tot,), dtype=torch.float32, device=dev)
+        pts = (Points * len(self.scenes))(*[s.points() for s in self.scenes])
+        sov = None
+        if scene_of_view is not None:
+            sov = (C.c_int32 * len(cams))(*[int(x) for x in scene_of_view])
+        self._keep = (pts, sov)
+        self.handle = C.c_void_p()
+        check(lib().pbr_graph_create(
+            renderer.ctx, pts, len(self.scenes), sov, make_cameras(cams), len(cams),
+            C.byref(self.opts), _ptr(self.out), _ptr(target), 0 if loss == "l2" else 1,
+            _ptr(self.loss), _ptr(grad_rgb), _ptr(self.grad_pos), _ptr(self.grad_sh),
+            _ptr(self.grad_opacity), float(headroom), _stream(), C.byref(self.handle)))
+
+    def launch(self, phase=0):
+        check(lib().pbr_graph_launch(self.handle, int(phase), _stream()))
+
+    def check(self):
+        """(ok, pairs of the last replay, planned capacity); synchronises."""
+        n, cap = C.c_int64(), C.c_int64()
+        rc = lib().pbr_graph_check(self.handle, _stream(), C.byref(n), C.byref(cap))
+        if rc not in (PBR_OK, -4):
+            check(rc)
+        return rc == PBR_OK, n.value, cap.value
+
+    def replan(self):
+        check(lib().pbr_graph_replan(self.handle, _stream()))
+
+    def set_cameras(self, cams):
+        check(lib().pbr_graph_set_cameras(self.handle, make_cameras(cams), len(cams), _stream()))
+
+    def close(self):
+        if self.handle:
+            lib().pbr_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+N_TUNE_CANDIDATES = 15
+TUNE_CANDIDATES = [(t, d, p) for t in ((16, 16), (8, 8), (16, 32))
+                   for (d, p) in ((0, 0), (0, 1), (128, 0), (256, 0), (512, 0))]
+
+
+def autotune(renderer, scenes, cams, opts=None, scene_of_view=None, backward=True, reps=2,
+             report=True):
+    """Times every schedule candidate on this batch and returns (best opts,
+    {(tile, batch_depth, persistent): ms})."""
+    scenes = scenes if isinstance(scenes, (list, tuple)) else [scenes]
+    opts = opts or default_opts()
+    pts = (Points * len(scenes))(*[s.points() for s in scenes])
+    sov = None
+    if scene_of_view is not None:
+        sov = (C.c_int32 * len(cams))(*[int(x) for x in scene_of_view])
+    ms = (C.c_double * N_TUNE_CANDIDATES)()
+    n = C.c_int32()
+    check(lib().pbr_autotune(renderer.ctx, pts, len(scenes), sov, make_cameras(cams), len(cams),
+                             C.byref(opts), 1 if backward else 0, int(reps), ms if report else None,
+                             C.byref(n), _stream()))
+    table = {TUNE_CANDIDATES[i]: ms[i] for i in range(n.value)} if report else {}
+    return opts, table
 
 
 def image_loss(pred, target, kind="l2"):

@@ -37,6 +37,7 @@ def _oracle_kw(kw):
     if "tile" in kw:
         kw["tile_w"], kw["tile_h"] = kw.pop("tile")
     kw.pop("batch_depth", None)
+    kw.pop("persistent", None)
     return kw
 
 
@@ -108,9 +109,10 @@ def test_image_independent_of_tile_size_and_batch_depth(R):
     sc = _small_scene(2, n=500)
     cams = [scenes.camera((0.5, -0.3, 2.4), 97, 61)]
     imgs = []
-    for tile, depth in (((16, 16), 0), ((8, 8), 0), ((16, 32), 0), ((16, 16), 256), ((8, 8), 32),
-                        ((16, 32), 512), ((16, 16), 64)):
-        img, st, _ = _gpu_render(R, sc, cams, tile=tile, batch_depth=depth)
+    for tile, depth, per in (((16, 16), 0, 0), ((8, 8), 0, 0), ((16, 32), 0, 0), ((16, 16), 0, 1),
+                             ((8, 8), 0, 1), ((16, 32), 0, 1), ((16, 16), 256, 0),
+                             ((8, 8), 32, 0), ((16, 32), 512, 0), ((16, 16), 64, 0)):
+        img, st, _ = _gpu_render(R, sc, cams, tile=tile, batch_depth=depth, persistent=per)
         imgs.append(img.cpu().numpy())
         st.close()
     for im in imgs[1:]:
@@ -269,9 +271,10 @@ def test_tiny_config_gradients(R):
 @pytest.mark.parametrize("kw", [dict(dir_frame=1), dict(radius_mode=1), dict(max_per_pixel=15),
                                 dict(bg=(0.3, 0.1, 0.7)), dict(tile=(8, 8)), dict(tile=(16, 32)),
                                 dict(batch_depth=256), dict(tile=(8, 8), batch_depth=64),
-                                dict(max_per_pixel=15, batch_depth=128)],
+                                dict(max_per_pixel=15, batch_depth=128), dict(persistent=1),
+                                dict(persistent=1, tile=(16, 32), max_per_pixel=15)],
                          ids=["world-dir", "ndc", "n15", "bg", "8x8", "16x32", "staged",
-                              "staged-8x8", "staged-n15"])
+                              "staged-8x8", "staged-n15", "persistent", "persistent-16x32-n15"])
 def test_gradient_variants(R, kw):
     import torch
     sc = _small_scene(20, n=400, deg=3)
