@@ -166,6 +166,60 @@ def run_reference(args, sc, desc):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------- serving
+def run_serving(pbr, R, data, opts, rate, duration, max_batch, n_streams, seed=0, pool=192):
+    """Poisson request stream against the serving loop; returns its stats."""
+    import collections
+    import torch
+    sv = pbr.Server(R, opts, max_batch_views=max_batch, n_streams=n_streams)
+    ids = [sv.upload(d) for d in data]
+    reqs = scenes.serving_requests(seed, rate, duration, n_scenes=len(data))
+    dev = f"cuda:{R.device}"
+    bufs = [torch.empty(1920 * 1088 * 3, dtype=torch.float32, device=dev) for _ in range(pool)]
+    free = collections.deque(range(pool))
+    outstanding = collections.deque()
+    t0 = pbr.now() + 0.05
+    for r in reqs:
+        target = t0 + r["t"]
+        while True:
+            d = target - pbr.now()
+            if d <= 0:
+                break
+            time.sleep(min(d, 2e-4))
+        if not free:
+            rid, b = outstanding.popleft()
+            sv.wait(rid)
+            free.append(b)
+        b = free.popleft()
+        W, H = int(r["cam"]["width"]), int(r["cam"]["height"])
+        rid, _ = sv.submit(ids[r["scene"]], r["cam"], out=bufs[b][:W * H * 3].view(W * H, 3),
+                           arrival=target)
+        outstanding.append((rid, b))
+    bad = 0
+    for rid, _ in outstanding:
+        bad += sv.wait(rid) != 0
+    st = sv.stats()
+    sv.stop()
+    return {"rate_req_s": rate, "requests": len(reqs), "completed": st["completed"],
+            "rejected": st["rejected"] + bad, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "mean_ms": st["mean_ms"], "mp_s": st["megapixels"] / max(st["span_s"], 1e-9),
+            "batches": st["batches"], "mean_batch_views": st["mean_batch_views"],
+            "max_batch_views": st["max_batch_views"]}
+
+
+def serving_report(pbr, R, rates, seconds):
+    data = scenes.serving_scenes(0)
+    opts = pbr.default_opts()
+    out = {"workload": "8 resident scenes of 100k-2M points, SH degree 0-3; Poisson arrivals; "
+                       "random cameras on a sphere of radius 3-5 at 256x256..1920x1080 "
+                       "(multiples of 16); forward only",
+           "seconds_per_rate": seconds, "batched": [], "plain": []}
+    for rate in rates:
+        out["batched"].append(run_serving(pbr, R, data, opts, rate, seconds, 64, 2))
+        out["plain"].append(run_serving(pbr, R, data, opts, rate, seconds, 1, 1))
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -184,6 +238,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--serve-rates", default="500",
+                    help="comma-separated Poisson arrival rates (req/s); empty = no serving run")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -401,6 +458,11 @@ def main():
                "sample": f"{px} random pixels of view 0, forward + backward, FP64 brute force "
                          f"over all {osc['pos'].shape[0]} points ({secs:.1f} s)"}
 
+    serving = None
+    if rank == 0 and args.serve_rates:
+        serving = serving_report(pbr, R, [float(x) for x in args.serve_rates.split(",")],
+                                 args.serve_seconds)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MP/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -417,7 +479,7 @@ def main():
                 "schedule": sched, "autotune_ms": tune,
                 "timing": "value/fwd: CUDA-graph replays of the whole step; stage_ms and the "
                           "roofline: the same steps launched eagerly with per-stage CUDA events",
-                "plain": plain, "stage_ms": stage_ms, "roofline": roof,
+                "plain": plain, "serving": serving, "stage_ms": stage_ms, "roofline": roof,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches // max(1, args.steps)),
                 "gpu_launches_timed_region": int(launches), "clocks": clk,

@@ -234,6 +234,52 @@ int pbr_autotune(pbr_ctx *ctx, const pbr_points *scenes, int32_t n_scenes,
                  pbr_render_opts *opts, int32_t mode, int32_t reps, double *ms_out,
                  int32_t *n_candidates, pbr_stream_t stream);
 
+/* ---------------------------------------------------------------- serving */
+/* Statistics of the serving loop (pbr_serve_stats). */
+typedef struct {
+    int64_t submitted, completed, rejected, queued, in_flight_batches, batches,
+        max_batch_views;
+    double mean_batch_views;
+    double megapixels;  /* pixels of completed requests / 1e6 */
+    double span_s;      /* first arrival to last completion */
+    double p50_ms, p99_ms, mean_ms, max_ms; /* arrival -> completion latency */
+    size_t hbm_in_use, hbm_budget;
+} pbr_serve_stats_t;
+
+/* Starts the context's serving thread.  Requests are rendered with `opts`
+ * in batches of up to max_batch_views views (any mix of scenes and image
+ * sizes), with up to n_streams batches in flight on separate streams.  A
+ * batch is admitted when a stream is free and its estimated workspace fits
+ * in the HBM budget (pbr_create / pbr_serve_set_budget) minus what the
+ * batches in flight hold; a request that cannot fit even alone is rejected
+ * with PBR_ERR_OOM.  Not in the paper: the serving form of the renderer. */
+int pbr_serve_start(pbr_ctx *ctx, const pbr_render_opts *opts, int32_t max_batch_views,
+                    int32_t n_streams);
+/* Finishes queued and in-flight requests, stops the thread, frees scenes. */
+int pbr_serve_stop(pbr_ctx *ctx);
+int pbr_serve_set_budget(pbr_ctx *ctx, size_t hbm_budget_bytes);
+/* Copies a scene (host or device arrays, detected by unified addressing)
+ * into library-owned HBM and returns its id.  Synchronous. */
+int pbr_upload_scene(pbr_ctx *ctx, const pbr_points *points, int32_t *scene_id);
+/* Frees a resident scene; PBR_ERR_BUSY while requests on it are pending. */
+int pbr_evict_scene(pbr_ctx *ctx, int32_t scene_id);
+/* Queues a forward render of scene `scene_id` from `cam` into
+ * out_rgb_device ([H, W, 3] fp32, caller-owned, untouched until the request
+ * completes).  arrival_time: the request's arrival on the steady clock in
+ * seconds (<= 0: now), used for latency.  Returns at once with *req_id. */
+int pbr_submit_request(pbr_ctx *ctx, int32_t scene_id, const pbr_camera *cam,
+                       float *out_rgb_device, double arrival_time, uint64_t *req_id);
+/* *done = 1 once the request has completed (its output is then final);
+ * *status is its result code.  A completed request is forgotten after the
+ * call that reports it done. */
+int pbr_poll(pbr_ctx *ctx, uint64_t req_id, int32_t *done, int32_t *status);
+/* Waits up to timeout_ms for a request; PBR_ERR_TIMEOUT if not done. */
+int pbr_wait(pbr_ctx *ctx, uint64_t req_id, int32_t timeout_ms, int32_t *status);
+/* Current statistics; reset != 0 clears them afterwards. */
+int pbr_serve_stats(pbr_ctx *ctx, pbr_serve_stats_t *stats, int32_t reset);
+/* The serving loop's steady clock (seconds), for arrival times. */
+double pbr_now(void);
+
 /* --------------------------------------------------- measurement support */
 /* Number of CUDA kernels this library has launched in this process. */
 unsigned long long pbr_kernel_launches(void);

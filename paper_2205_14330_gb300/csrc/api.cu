@@ -274,6 +274,7 @@ int pbr::build_layout(const pbr_points *scenes, int32_t n_scenes, const int32_t 
         d.scene = sov[v];
         d.pix_base = pix;
         d.pv_base = pv;
+        d.out = nullptr;
         tiles += (uint64_t)d.tiles_x * d.tiles_y;
         pix += (int64_t)c.width * c.height;
         pv += scenes[sov[v]].n;
@@ -360,12 +361,15 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
         launch_preprocess_fwd(b, o, st->rec, zbits, st->ntiles, rect, st->counters, s);
     }
     PBR_CUDA(cudaGetLastError());
-    // size the lists
-    PBR_CUDA(cudaMemcpyAsync(c->host_counters, st->counters, 64, cudaMemcpyDeviceToHost, s));
+    // size the lists (pinned read-back buffer per host thread: the serving
+    // thread and callers may run forward passes concurrently)
+    static thread_local unsigned long long *host = nullptr;
+    if (!host) PBR_CUDA(cudaMallocHost((void **)&host, 64));
+    PBR_CUDA(cudaMemcpyAsync(host, st->counters, 64, cudaMemcpyDeviceToHost, s));
     PBR_CUDA(cudaStreamSynchronize(s));
-    const uint64_t n_pairs = c->host_counters[0], n_vis = c->host_counters[1];
-    const uint32_t zlo = ((const uint32_t *)c->host_counters)[12];
-    const uint32_t zhi = ((const uint32_t *)c->host_counters)[13];
+    const uint64_t n_pairs = host[0], n_vis = host[1];
+    const uint32_t zlo = ((const uint32_t *)host)[12];
+    const uint32_t zhi = ((const uint32_t *)host)[13];
     const int depth_bits = (n_vis > 0 && zhi > zlo) ? 32 - __builtin_clz(zhi - zlo) : 0;
     if (n_pairs >= UINT32_MAX) {
         return set_error(PBR_ERR_CAPACITY, "%llu (tile, point-view) pairs exceed 2^32-1",

@@ -197,10 +197,12 @@ __device__ __forceinline__ void write_pixel(const PixelGeom &g, const DevOpts &o
                                             float *out_rgb, float *T_final, uint32_t *n_contrib)
 {
     if (!g.inside) return;
-    const int64_t pix = g.V->pix_base + (int64_t)g.y * g.V->W + g.x;
-    out_rgb[3 * pix] = C0 + T * o.bg[0];
-    out_rgb[3 * pix + 1] = C1 + T * o.bg[1];
-    out_rgb[3 * pix + 2] = C2 + T * o.bg[2];
+    const int64_t local = (int64_t)g.y * g.V->W + g.x;
+    const int64_t pix = g.V->pix_base + local;
+    float *dst = g.V->out ? g.V->out + 3 * local : out_rgb + 3 * pix;
+    dst[0] = C0 + T * o.bg[0];
+    dst[1] = C1 + T * o.bg[1];
+    dst[2] = C2 + T * o.bg[2];
     T_final[pix] = T;
     n_contrib[pix] = last;
 }

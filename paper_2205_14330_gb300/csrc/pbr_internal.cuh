@@ -25,6 +25,8 @@ struct DevView {
     int32_t scene;       // index into the scene table
     int64_t pix_base;    // first pixel of the view in the packed image
     int64_t pv_base;     // first point-view id: pv = pv_base + point index
+    float *out;          // when set, the view's RGB goes here ([H,W,3]) instead of the
+                         // packed image (serving: one output buffer per request)
 };
 
 // One scene (point set) of the batch.

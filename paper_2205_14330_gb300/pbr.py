@@ -60,6 +60,15 @@ class StateInfo(C.Structure):
                 ("n_contrib", C.c_void_p)]
 
 
+class ServeStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rejected", C.c_int64),
+                ("queued", C.c_int64), ("in_flight_batches", C.c_int64), ("batches", C.c_int64),
+                ("max_batch_views", C.c_int64), ("mean_batch_views", C.c_double),
+                ("megapixels", C.c_double), ("span_s", C.c_double), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("max_ms", C.c_double),
+                ("hbm_in_use", C.c_size_t), ("hbm_budget", C.c_size_t)]
+
+
 STAGES = ["preprocess_fwd", "compact", "depth_sort", "emit_pairs", "tile_sort", "tile_ranges",
           "raster_fwd", "raster_bwd", "preprocess_bwd", "other"]
 
@@ -104,6 +113,18 @@ def lib():
             L.pbr_autotune.argtypes = [vp, C.POINTER(Points), i32, vp, C.POINTER(Camera), i32,
                                        C.POINTER(Opts), i32, i32, C.POINTER(C.c_double),
                                        C.POINTER(i32), vp]
+            L.pbr_serve_start.argtypes = [vp, C.POINTER(Opts), i32, i32]
+            L.pbr_serve_stop.argtypes = [vp]
+            L.pbr_serve_set_budget.argtypes = [vp, C.c_size_t]
+            L.pbr_upload_scene.argtypes = [vp, C.POINTER(Points), C.POINTER(i32)]
+            L.pbr_evict_scene.argtypes = [vp, i32]
+            L.pbr_submit_request.argtypes = [vp, i32, C.POINTER(Camera), vp, C.c_double,
+                                             C.POINTER(C.c_uint64)]
+            L.pbr_poll.argtypes = [vp, C.c_uint64, C.POINTER(i32), C.POINTER(i32)]
+            L.pbr_wait.argtypes = [vp, C.c_uint64, i32, C.POINTER(i32)]
+            L.pbr_serve_stats.argtypes = [vp, C.POINTER(ServeStats), i32]
+            L.pbr_now.restype = C.c_double
+            L.pbr_now.argtypes = []
             L.pbr_state_stats.argtypes = [vp, C.POINTER(C.c_ulonglong)]
             L.pbr_kernel_launches.restype = C.c_ulonglong
             L.pbr_kernel_launches.argtypes = []
@@ -376,6 +397,78 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Continuous-batching request loop over resident scenes (pbr_serve_*)."""
+
+    def __init__(self, renderer, opts=None, max_batch_views=64, n_streams=2, hbm_budget=None):
+        self.renderer = renderer
+        self.ctx = renderer.ctx
+        if hbm_budget is not None:
+            check(lib().pbr_serve_set_budget(self.ctx, int(hbm_budget)))
+        check(lib().pbr_serve_start(self.ctx, C.byref(opts or default_opts()),
+                                    int(max_batch_views), int(n_streams)))
+        self.running = True
+        self._outs = {}
+
+    def set_budget(self, nbytes):
+        check(lib().pbr_serve_set_budget(self.ctx, int(nbytes)))
+
+    def upload(self, scene) -> int:
+        """Copies a Scene (or dict of numpy arrays with 'deg') into library HBM."""
+        if not isinstance(scene, Scene):
+            keep = [np.ascontiguousarray(scene[k], np.float32)
+                    for k in ("pos", "sh", "opacity", "radius")]
+            pts = Points(*[C.c_void_p(a.ctypes.data) for a in keep], len(keep[0]),
+                         int(scene["deg"]), 0)
+        else:
+            pts = scene.points()
+        sid = C.c_int32()
+        check(lib().pbr_upload_scene(self.ctx, C.byref(pts), C.byref(sid)))
+        return sid.value
+
+    def evict(self, scene_id):
+        check(lib().pbr_evict_scene(self.ctx, int(scene_id)))
+
+    def submit(self, scene_id, cam, out=None, arrival=0.0):
+        """Queues a render; returns (request id, output tensor [H*W, 3])."""
+        if out is None:
+            out = torch.empty((int(cam["width"]) * int(cam["height"]), 3), dtype=torch.float32,
+                              device=f"cuda:{self.renderer.device}")
+        rid = C.c_uint64()
+        check(lib().pbr_submit_request(self.ctx, int(scene_id), make_cameras([cam]), _ptr(out),
+                                       float(arrival), C.byref(rid)))
+        self._outs[rid.value] = out
+        return rid.value, out
+
+    def poll(self, rid):
+        done, st = C.c_int32(), C.c_int32()
+        check(lib().pbr_poll(self.ctx, C.c_uint64(rid), C.byref(done), C.byref(st)))
+        if done.value:
+            self._outs.pop(rid, None)
+        return bool(done.value), st.value
+
+    def wait(self, rid, timeout_ms=60000):
+        st = C.c_int32()
+        check(lib().pbr_wait(self.ctx, C.c_uint64(rid), int(timeout_ms), C.byref(st)))
+        self._outs.pop(rid, None)
+        return st.value
+
+    def stats(self, reset=False) -> dict:
+        s = ServeStats()
+        check(lib().pbr_serve_stats(self.ctx, C.byref(s), 1 if reset else 0))
+        return {k: getattr(s, k) for k, _ in ServeStats._fields_}
+
+    def stop(self):
+        if self.running:
+            check(lib().pbr_serve_stop(self.ctx))
+            self.running = False
+
+
+def now() -> float:
+    """The serving loop's clock (seconds), for request arrival times."""
+    return float(lib().pbr_now())
 
 
 N_TUNE_CANDIDATES = 15

@@ -1,0 +1,124 @@
+"""Serving form: resident scenes, continuous batching of mixed-size views,
+admission by HBM budget.  Every request's image must be the same whether it
+is rendered alone (pbr_render_forward) or inside a mixed batch."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2205_14330_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def env():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2205_14330_gb300 import pbr
+    yield pbr
+
+
+def _scenes(seed=0):
+    rng = np.random.default_rng(seed)
+    out = []
+    for n, deg in ((4000, 0), (6000, 2), (3000, 3)):
+        out.append(dict(pos=scenes.surface_points(rng, n, 5), sh=scenes.sh_coeffs(rng, n, deg, 0.2),
+                        opacity=np.full(n, 0.8, np.float32),
+                        radius=scenes.log_uniform(rng, n, 0.01, 0.03), deg=deg))
+    return out
+
+
+def _requests(n, seed=1):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for _ in range(n):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        W, H = int(rng.integers(2, 9)) * 16, int(rng.integers(2, 7)) * 16
+        reqs.append((int(rng.integers(0, 3)), scenes.camera(d * rng.uniform(2.5, 4.0), W, H)))
+    return reqs
+
+
+def _alone(pbr, R, sc, cam):
+    s = pbr.Scene(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"])
+    img, _ = R.forward([s], [cam], keep_state=False)
+    return img
+
+
+def test_mixed_batch_equals_alone(env):
+    pbr = env
+    R = pbr.Renderer(0)
+    sv = pbr.Server(R, max_batch_views=16, n_streams=2)
+    data = _scenes()
+    ids = [sv.upload(d) for d in data]
+    reqs = _requests(24)
+    subs = [sv.submit(ids[s], cam) for s, cam in reqs]
+    for rid, _ in subs:
+        assert sv.wait(rid) == 0
+    st = sv.stats()
+    assert st["completed"] == 24 and st["rejected"] == 0
+    assert st["max_batch_views"] > 1  # requests really were batched together
+    for (s, cam), (_, out) in zip(reqs, subs):
+        ref = _alone(pbr, R, data[s], cam)
+        err = float((out - ref).abs().max())
+        assert err <= IMG_TOL, err
+    sv.stop()
+    R.close()
+
+
+def test_arrivals_while_busy_overlap_and_complete(env):
+    pbr = env
+    R = pbr.Renderer(0)
+    sv = pbr.Server(R, max_batch_views=8, n_streams=2)
+    data = _scenes(2)
+    ids = [sv.upload(d) for d in data]
+    reqs = _requests(40, seed=3)
+    subs = []
+    for k, (s, cam) in enumerate(reqs):
+        subs.append(sv.submit(ids[s], cam, arrival=pbr.now()))
+        if k % 10 == 9:
+            time.sleep(0.002)  # later arrivals join while earlier batches run
+    for rid, _ in subs:
+        assert sv.wait(rid) == 0
+    st = sv.stats(reset=True)
+    assert st["completed"] == 40 and st["batches"] >= 5
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+    for (s, cam), (_, out) in list(zip(reqs, subs))[::7]:
+        assert float((out - _alone(pbr, R, data[s], cam)).abs().max()) <= IMG_TOL
+    sv.stop()
+    R.close()
+
+
+def test_admission_by_hbm_budget(env):
+    pbr = env
+    R = pbr.Renderer(0)
+    data = _scenes(4)
+    # budget that fits about one request: batches of one, all complete
+    sv = pbr.Server(R, max_batch_views=16, n_streams=2, hbm_budget=3_000_000)
+    ids = [sv.upload(d) for d in data]
+    reqs = [(1, scenes.camera((0.0, 0.5, 3.0), 64, 48))] * 6
+    subs = [sv.submit(ids[s], cam) for s, cam in reqs]
+    for rid, _ in subs:
+        assert sv.wait(rid) == 0
+    st = sv.stats()
+    assert st["completed"] == 6 and st["max_batch_views"] == 1
+    ref = _alone(pbr, R, data[1], reqs[0][1])
+    for _, out in subs:
+        assert float((out - ref).abs().max()) <= IMG_TOL
+    # a budget below one request: rejected with PBR_ERR_OOM, not run
+    sv.set_budget(1000)
+    rid, _ = sv.submit(ids[1], reqs[0][1])
+    assert sv.wait(rid) == -2
+    sv.set_budget(1 << 34)
+    # eviction while requests are queued is refused; unknown scenes are refused
+    rid, _ = sv.submit(ids[0], reqs[0][1])
+    sv.wait(rid)
+    sv.evict(ids[0])
+    with pytest.raises(pbr.PBRError) as e:
+        sv.submit(ids[0], reqs[0][1])
+    assert e.value.code == -7
+    sv.stop()
+    R.close()
