@@ -232,6 +232,7 @@ def main():
     ap.add_argument("--tile", default="16x16")
     ap.add_argument("--batch-depth", type=int, default=0,
                     help="0 = warp-streamed compositing, else block-staged batch size")
+    ap.add_argument("--persistent", type=int, default=0)
     ap.add_argument("--ref-pixels", type=int, default=2048)
     ap.add_argument("--cpu-pixels", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -264,7 +265,8 @@ def main():
         dist.init_process_group("nccl")
 
     tw, th = (int(x) for x in args.tile.split("x"))
-    opts = pbr.default_opts(tile=(tw, th), batch_depth=args.batch_depth)
+    opts = pbr.default_opts(tile=(tw, th), batch_depth=args.batch_depth,
+                            persistent=args.persistent)
     R = pbr.Renderer(local)
     dev = f"cuda:{local}"
 

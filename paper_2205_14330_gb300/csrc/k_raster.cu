@@ -18,8 +18,8 @@
 //   dL/do = dL/dalpha G,  dL/dp = dL/dalpha alpha q (u - p),
 //   dL/dq = -dL/dalpha alpha d2 / 2          (q = 1/s^2).
 // The 7 per-point terms of a warp are summed with a transposed shuffle
-// reduction (9 shuffles) before they are added to the per-(view, point)
-// buffer.
+// reduction before they are added to the per-(view, point) buffer (two
+// 16-byte atomics per warp and point in the warp-streamed schedule).
 //
 // A block covers one TW x TH screen tile; each warp owns an 8 x 4 sub-block
 // of it and skips list entries whose cutoff disc misses its sub-block.  Two
@@ -134,6 +134,21 @@ __device__ __forceinline__ float warp_sum8_transposed(const float v[8], int lane
     return r;
 }
 
+// Adds the warp's 7 per-point terms to g2d[pv][0..6] with two 16-byte
+// atomics: after the transposed reduction lane 4k holds term k; lanes 0 and
+// 16 gather four terms each.
+__device__ __forceinline__ void warp_add_terms(const float v[8], int lane, float *g2d, uint32_t pv)
+{
+    const float t = warp_sum8_transposed(v, lane);
+    const float t1 = __shfl_down_sync(0xffffffffu, t, 4);
+    const float t2 = __shfl_down_sync(0xffffffffu, t, 8);
+    const float t3 = __shfl_down_sync(0xffffffffu, t, 12);
+    if ((lane & 15) == 0) {
+        float4 *dst = reinterpret_cast<float4 *>(g2d + 8 * (size_t)pv) + (lane >> 4);
+        atomicAdd(dst, make_float4(t, t1, t2, lane ? 0.f : t3));
+    }
+}
+
 // One composited point, front to back.  Returns true when the pixel stops.
 __device__ __forceinline__ bool pixel_blend(float d2, const float4 a, const float4 c,
                                             const DevOpts &o, float &T, float &C0, float &C1,
@@ -158,14 +173,14 @@ __device__ __forceinline__ void pixel_adjoint(float d2, float dx, float dy, cons
     const float G = ex2_approx(d2 * a.w);
     const float raw = c.x * G;
     const float alpha = fminf(amax, raw);
-    const float om = 1.0f - alpha;
-    const float Tb = __fdividef(T, om);
+    const float rom = __frcp_rn(1.0f - alpha);
+    const float Tb = T * rom;
     const float wgt = alpha * Tb;
     const float cg = c.y * g0 + c.z * g1 + c.w * g2;
     v[4] = wgt * g0;
     v[5] = wgt * g1;
     v[6] = wgt * g2;
-    const float dalpha = Tb * cg - __fdividef(S, om);
+    const float dalpha = Tb * cg - S * rom;
     S = fmaf(wgt, cg, S);
     T = Tb;
     if (raw < amax) {
@@ -184,12 +199,6 @@ __device__ __forceinline__ float pixel_d2(float ux, float uy, float px, float py
     dx = __fsub_rn(ux, px);
     dy = __fsub_rn(uy, py);
     return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-}
-
-__device__ __forceinline__ float4 shfl4(const float4 v, int j)
-{
-    return make_float4(__shfl_sync(0xffffffffu, v.x, j), __shfl_sync(0xffffffffu, v.y, j),
-                       __shfl_sync(0xffffffffu, v.z, j), __shfl_sync(0xffffffffu, v.w, j));
 }
 
 __device__ __forceinline__ void write_pixel(const PixelGeom &g, const DevOpts &o, float T,
@@ -221,6 +230,8 @@ __device__ __forceinline__ void add_stats(unsigned long long *stats, uint32_t a,
 
 // ======================================================= warp-streamed
 // One warp composites sub-block `sub` of tile `tile`.
+// wbuf: this warp's 64 float4 of shared memory (a-parts, then b-parts of
+// the current 32-entry chunk).
 template <int TW, int TH>
 __device__ __forceinline__ void fwd_stream_item(const Batch &b, const DevOpts &o, uint32_t tile,
                                                 int sub, int lane, const uint2 *__restrict__ ranges,
@@ -229,7 +240,8 @@ __device__ __forceinline__ void fwd_stream_item(const Batch &b, const DevOpts &o
                                                 float *__restrict__ out_rgb,
                                                 float *__restrict__ T_final,
                                                 uint32_t *__restrict__ n_contrib,
-                                                uint32_t &examined_acc, uint32_t &composited_acc)
+                                                uint32_t &examined_acc, uint32_t &composited_acc,
+                                                float4 *wbuf)
 {
     const PixelGeom g = pixel_geom<TW, TH>(b, tile, sub, lane);
     const uint2 rg = ranges[tile];
@@ -256,14 +268,17 @@ __device__ __forceinline__ void fwd_stream_item(const Batch &b, const DevOpts &o
             }
             const bool hit = valid && disc_meets_rect(a, g);
             uint32_t m = __ballot_sync(0xffffffffu, hit);
-            float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (hit) bb = __ldg(rec + 2 * (size_t)pv + 1);
+            if (hit) {
+                wbuf[lane] = a;
+                wbuf[32 + lane] = __ldg(rec + 2 * (size_t)pv + 1);
+            }
+            __syncwarp();
             bool stop = false;
             while (m) {
                 const int j = __ffs(m) - 1;
                 m &= m - 1;
-                const float4 aj = shfl4(a, j);
-                const float4 cj = shfl4(bb, j);
+                const float4 aj = wbuf[j];
+                const float4 cj = wbuf[32 + j];
                 if (!done) {
                     ++examined;
                     float dx, dy;
@@ -278,6 +293,7 @@ __device__ __forceinline__ void fwd_stream_item(const Batch &b, const DevOpts &o
                     break;
                 }
             }
+            __syncwarp(); // chunk consumed before the buffer is refilled
             if (stop) break;
         }
     }
@@ -296,7 +312,7 @@ __device__ __forceinline__ void bwd_stream_item(const Batch &b, const DevOpts &o
                                                 const uint32_t *__restrict__ n_contrib,
                                                 const float *__restrict__ grad_rgb,
                                                 float *__restrict__ g2d, uint32_t &examined,
-                                                uint32_t &used)
+                                                uint32_t &used, float4 *wbuf, uint32_t *wpv)
 {
     const PixelGeom g = pixel_geom<TW, TH>(b, tile, sub, lane);
     const uint32_t s = ranges[tile].x;
@@ -330,14 +346,17 @@ __device__ __forceinline__ void bwd_stream_item(const Batch &b, const DevOpts &o
         }
         const bool hit = valid && disc_meets_rect(a, g);
         uint32_t m = __ballot_sync(0xffffffffu, hit);
-        float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (hit) bb = __ldg(rec + 2 * (size_t)pv + 1);
+        if (hit) {
+            wbuf[lane] = a;
+            wbuf[32 + lane] = __ldg(rec + 2 * (size_t)pv + 1);
+            wpv[lane] = pv;
+        }
+        __syncwarp();
         while (m) {
             const int j = 31 - __clz(m); // back to front
             m &= ~(1u << j);
-            const float4 aj = shfl4(a, j);
-            const float4 cj = shfl4(bb, j);
-            const uint32_t pvj = __shfl_sync(0xffffffffu, pv, j);
+            const float4 aj = wbuf[j];
+            const float4 cj = wbuf[32 + j];
             float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool contrib = false;
             if ((uint32_t)c + j < L) {
@@ -350,12 +369,9 @@ __device__ __forceinline__ void bwd_stream_item(const Batch &b, const DevOpts &o
                     pixel_adjoint(d2, dx, dy, aj, cj, o.alpha_max, g0, g1, g2, T, S, v);
                 }
             }
-            if (__any_sync(0xffffffffu, contrib)) {
-                const float tot = warp_sum8_transposed(v, lane);
-                const int which = (lane >> 2) & 7;
-                if ((lane & 3) == 0 && which < 7) atomicAdd(g2d + 8 * (size_t)pvj + which, tot);
-            }
+            if (__any_sync(0xffffffffu, contrib)) warp_add_terms(v, lane, g2d, wpv[j]);
         }
+        __syncwarp(); // chunk consumed before the buffer is refilled
     }
 }
 
@@ -366,10 +382,11 @@ raster_fwd_stream_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
                          float *__restrict__ out_rgb, float *__restrict__ T_final,
                          uint32_t *__restrict__ n_contrib, unsigned long long *__restrict__ stats)
 {
+    __shared__ float4 s_buf[TW * TH / 32][64];
     const int lane = threadIdx.x & 31;
     uint32_t ex = 0, co = 0;
     fwd_stream_item<TW, TH>(b, o, blockIdx.x, threadIdx.x >> 5, lane, ranges, pv_list, rec,
-                            out_rgb, T_final, n_contrib, ex, co);
+                            out_rgb, T_final, n_contrib, ex, co, s_buf[threadIdx.x >> 5]);
     add_stats(stats, ex, co, lane);
 }
 
@@ -381,10 +398,13 @@ raster_bwd_stream_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
                          const float *__restrict__ grad_rgb, float *__restrict__ g2d,
                          unsigned long long *__restrict__ stats)
 {
+    __shared__ float4 s_buf[TW * TH / 32][64];
+    __shared__ uint32_t s_pv[TW * TH / 32][32];
     const int lane = threadIdx.x & 31;
     uint32_t ex = 0, us = 0;
     bwd_stream_item<TW, TH>(b, o, blockIdx.x, threadIdx.x >> 5, lane, ranges, pv_list, rec,
-                            T_final, n_contrib, grad_rgb, g2d, ex, us);
+                            T_final, n_contrib, grad_rgb, g2d, ex, us, s_buf[threadIdx.x >> 5],
+                            s_pv[threadIdx.x >> 5]);
     add_stats(stats ? stats + 2 : nullptr, ex, us, lane);
 }
 
@@ -410,12 +430,13 @@ raster_fwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
                           const uint32_t *__restrict__ order, uint32_t *work)
 {
     constexpr uint32_t SUBS = (TW / 8) * (TH / 4);
+    __shared__ float4 s_buf[PERSIST_THREADS / 32][64];
     const int lane = threadIdx.x & 31;
     const uint32_t n_items = b.n_tiles * SUBS;
     uint32_t ex = 0, co = 0;
     for (uint32_t it = next_item(work, lane); it < n_items; it = next_item(work, lane))
         fwd_stream_item<TW, TH>(b, o, order[it / SUBS], (int)(it % SUBS), lane, ranges, pv_list,
-                                rec, out_rgb, T_final, n_contrib, ex, co);
+                                rec, out_rgb, T_final, n_contrib, ex, co, s_buf[threadIdx.x >> 5]);
     add_stats(stats, ex, co, lane);
 }
 
@@ -429,12 +450,15 @@ raster_bwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
                           uint32_t *work)
 {
     constexpr uint32_t SUBS = (TW / 8) * (TH / 4);
+    __shared__ float4 s_buf[PERSIST_THREADS / 32][64];
+    __shared__ uint32_t s_pv[PERSIST_THREADS / 32][32];
     const int lane = threadIdx.x & 31;
     const uint32_t n_items = b.n_tiles * SUBS;
     uint32_t ex = 0, us = 0;
     for (uint32_t it = next_item(work, lane); it < n_items; it = next_item(work, lane))
         bwd_stream_item<TW, TH>(b, o, order[it / SUBS], (int)(it % SUBS), lane, ranges, pv_list,
-                                rec, T_final, n_contrib, grad_rgb, g2d, ex, us);
+                                rec, T_final, n_contrib, grad_rgb, g2d, ex, us,
+                                s_buf[threadIdx.x >> 5], s_pv[threadIdx.x >> 5]);
     add_stats(stats ? stats + 2 : nullptr, ex, us, lane);
 }
 

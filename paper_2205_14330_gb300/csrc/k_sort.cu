@@ -15,8 +15,9 @@
 //   5. tile_ranges      : [start, end) of every tile in the sorted list
 //
 // Scans are reduce-then-scan (three kernels, no inter-block waiting).  The
-// radix pass ranks keys stably inside a block with warp match/ballot and a
-// shared-memory reorder so that the scatter writes contiguous runs.
+// radix pass ranks keys stably inside a block with warp ballots and shared
+// atomics, and reorders them in shared memory so that the scatter writes
+// contiguous runs.
 #include "pbr_internal.cuh"
 
 namespace pbr {
@@ -213,6 +214,20 @@ __device__ __forceinline__ uint32_t digit_of(uint32_t key, uint32_t key_lo, int 
     return ((key - key_lo) >> shift) & mask;
 }
 
+// Peers of each lane: lanes holding the same digit (digits < 2^10, the
+// out-of-range marker RBINS included), built from ballots.
+__device__ __forceinline__ uint32_t peers_by_ballot(uint32_t d)
+{
+    uint32_t peers = 0xffffffffu;
+#pragma unroll
+    for (int bit = 0; bit <= RB; ++bit) {
+        const uint32_t m = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+        peers &= ((d >> bit) & 1u) ? m : ~m;
+    }
+    return peers;
+}
+
+// Per-block digit histogram: shared-memory atomics into per-warp counters.
 __global__ void __launch_bounds__(SORT_THREADS)
 radix_hist_kernel(const uint32_t *__restrict__ keys, const uint32_t *n_dev, int64_t cap,
                   uint32_t key_lo, int shift, int width, uint32_t *__restrict__ hist, int64_t nb)
@@ -230,13 +245,9 @@ radix_hist_kernel(const uint32_t *__restrict__ keys, const uint32_t *n_dev, int6
         d[r] = i < n ? digit_of(keys[i], key_lo, shift, mask) : (uint32_t)RBINS;
     }
     __syncthreads();
-    const uint32_t lt = lanemask_lt();
 #pragma unroll
-    for (int r = 0; r < SORT_ITEMS; ++r) {
-        const uint32_t peers = __match_any_sync(0xffffffffu, d[r]);
-        if (d[r] < RBINS && (peers & lt) == 0) s_h[w][d[r]] += __popc(peers);
-        __syncwarp();
-    }
+    for (int r = 0; r < SORT_ITEMS; ++r)
+        if (d[r] < RBINS) atomicAdd(&s_h[w][d[r]], 1u);
     __syncthreads();
     const int bins = 1 << width;
     for (int dd = threadIdx.x; dd < bins; dd += SORT_THREADS) {
@@ -282,16 +293,26 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
     }
     __syncthreads();
     const uint32_t lt = lanemask_lt();
+    {
+        // stable rank inside the warp: peer masks from ballots, the group
+        // leader's shared-memory atomic on the warp's digit counter (one
+        // warp's shared atomics execute in program order, so rounds stay
+        // ordered), then the broadcast of each group's base
 #pragma unroll
-    for (int r = 0; r < SORT_ITEMS; ++r) {
-        const bool ok = base + r * 32 + lane < n;
-        const uint32_t d = ok ? digit_of(key[r], key_lo, shift, mask) : (uint32_t)RBINS;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t before = d < RBINS ? s_wh[w][d] : 0u;
-        __syncwarp();
-        if (d < RBINS && (peers & lt) == 0) s_wh[w][d] = before + __popc(peers);
-        __syncwarp();
-        rank[r] = before + __popc(peers & lt);
+        for (int r = 0; r < SORT_ITEMS; ++r) {
+            const bool ok = base + r * 32 + lane < n;
+            const uint32_t d = ok ? digit_of(key[r], key_lo, shift, mask) : (uint32_t)RBINS;
+            const uint32_t peers = peers_by_ballot(d);
+            uint32_t old = 0;
+            if (d < RBINS && (peers & lt) == 0) old = atomicAdd(&s_wh[w][d], (uint32_t)__popc(peers));
+            rank[r] = (uint32_t)(__ffs(peers) - 1) | ((uint32_t)__popc(peers & lt) << 5) | (old << 10);
+        }
+#pragma unroll
+        for (int r = 0; r < SORT_ITEMS; ++r) {
+            const uint32_t packed = rank[r];
+            const uint32_t base_r = __shfl_sync(0xffffffffu, packed >> 10, packed & 31);
+            rank[r] = base_r + ((packed >> 5) & 31);
+        }
     }
     __syncthreads();
     // per digit: exclusive prefix over warps, digit total, global base
