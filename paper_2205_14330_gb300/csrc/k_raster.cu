@@ -230,8 +230,13 @@ __device__ __forceinline__ void add_stats(unsigned long long *stats, uint32_t a,
 
 // ======================================================= warp-streamed
 // One warp composites sub-block `sub` of tile `tile`.
-// wbuf: this warp's 64 float4 of shared memory (a-parts, then b-parts of
-// the current 32-entry chunk).
+// Warp-streamed items.  Each step takes 32 list entries (one per lane),
+// culls them against the warp's rectangle with one ballot and stages the
+// hits in the warp's shared buffer; then
+//   phase 1 (warp-uniform): for every hit, every lane runs its exact fp32
+//            cutoff test and records the hit in its own bitmask;
+//   phase 2 (per lane): each lane walks only its own included entries.
+// wbuf: this warp's 64 float4 (a-parts, then b-parts of the chunk).
 template <int TW, int TH>
 __device__ __forceinline__ void fwd_stream_item(const Batch &b, const DevOpts &o, uint32_t tile,
                                                 int sub, int lane, const uint2 *__restrict__ ranges,
@@ -273,28 +278,30 @@ __device__ __forceinline__ void fwd_stream_item(const Batch &b, const DevOpts &o
                 wbuf[32 + lane] = __ldg(rec + 2 * (size_t)pv + 1);
             }
             __syncwarp();
-            bool stop = false;
+            if (!done) examined += (uint32_t)__popc(m);
+            uint32_t mine = 0;
             while (m) {
                 const int j = __ffs(m) - 1;
                 m &= m - 1;
                 const float4 aj = wbuf[j];
-                const float4 cj = wbuf[32 + j];
-                if (!done) {
-                    ++examined;
-                    float dx, dy;
-                    const float d2 = pixel_d2(g.ux, g.uy, aj.x, aj.y, dx, dy);
-                    if (d2 <= aj.z) {
-                        last = c + j - s + 1;
-                        done = pixel_blend(d2, aj, cj, o, T, C0, C1, C2, cnt);
-                    }
-                }
-                if (__all_sync(0xffffffffu, done)) {
-                    stop = true;
+                float dx, dy;
+                if (pixel_d2(g.ux, g.uy, aj.x, aj.y, dx, dy) <= aj.z) mine |= 1u << j;
+            }
+            if (done) mine = 0;
+            while (mine) {
+                const int j = __ffs(mine) - 1;
+                mine &= mine - 1;
+                const float4 aj = wbuf[j];
+                float dx, dy;
+                const float d2 = pixel_d2(g.ux, g.uy, aj.x, aj.y, dx, dy);
+                last = c + j - s + 1;
+                if (pixel_blend(d2, aj, wbuf[32 + j], o, T, C0, C1, C2, cnt)) {
+                    done = true;
                     break;
                 }
             }
             __syncwarp(); // chunk consumed before the buffer is refilled
-            if (stop) break;
+            if (__all_sync(0xffffffffu, done)) break;
         }
     }
     examined_acc += examined;
