@@ -258,7 +258,7 @@ radix_hist_kernel(const uint32_t *__restrict__ keys, const uint32_t *n_dev, int6
     }
 }
 
-constexpr size_t SCATTER_SMEM = sizeof(uint32_t) * (2 * SORT_TILE + SORT_WARPS * RBINS + 3 * RBINS +
+constexpr size_t SCATTER_SMEM = sizeof(uint32_t) * (3 * SORT_TILE + SORT_WARPS * RBINS + 3 * RBINS +
                                                     SORT_WARPS);
 
 __global__ void __launch_bounds__(SORT_THREADS)
@@ -268,10 +268,11 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
                      const uint32_t *__restrict__ hist, int64_t nb)
 {
     extern __shared__ uint32_t s_mem[];
-    uint32_t *s_k = s_mem;                               // [SORT_TILE]
-    uint32_t *s_v = s_k + SORT_TILE;                     // [SORT_TILE]
-    uint32_t(*s_wh)[RBINS] = (uint32_t(*)[RBINS])(s_v + SORT_TILE); // [warps][RBINS]
-    uint32_t *s_tot = s_v + SORT_TILE + SORT_WARPS * RBINS;
+    uint32_t *s_k = s_mem;                               // [SORT_TILE] keys, ranked order
+    uint32_t *s_v = s_k + SORT_TILE;                     // [SORT_TILE] values, ranked order
+    uint32_t *s_vin = s_v + SORT_TILE;                   // [SORT_TILE] values, input order
+    uint32_t(*s_wh)[RBINS] = (uint32_t(*)[RBINS])(s_vin + SORT_TILE); // [warps][RBINS]
+    uint32_t *s_tot = s_vin + SORT_TILE + SORT_WARPS * RBINS;
     uint32_t *s_dbase = s_tot + RBINS;
     uint32_t *s_gbase = s_dbase + RBINS;
     uint32_t *s_scan = s_gbase + RBINS;
@@ -283,13 +284,14 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
     const int bins = 1 << width;
     for (int j = threadIdx.x; j < SORT_WARPS * RBINS; j += SORT_THREADS) (&s_wh[0][0])[j] = 0;
     const int64_t base = blk + (int64_t)w * 32 * SORT_ITEMS;
-    uint32_t key[SORT_ITEMS], val[SORT_ITEMS], rank[SORT_ITEMS];
+    uint32_t key[SORT_ITEMS], rank[SORT_ITEMS];
+    const int lbase = w * 32 * SORT_ITEMS + lane; // local index of round 0
 #pragma unroll
     for (int r = 0; r < SORT_ITEMS; ++r) {
         const int64_t i = base + r * 32 + lane;
         const bool ok = i < n;
         key[r] = ok ? keys_in[i] : 0u;
-        val[r] = ok ? vals_in[i] : 0u;
+        s_vin[lbase + r * 32] = ok ? vals_in[i] : 0u;
     }
     __syncthreads();
     const uint32_t lt = lanemask_lt();
@@ -357,7 +359,7 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
             const uint32_t d = digit_of(key[r], key_lo, shift, mask);
             const uint32_t l = s_dbase[d] + s_wh[w][d] + rank[r];
             s_k[l] = key[r];
-            s_v[l] = val[r];
+            s_v[l] = s_vin[lbase + r * 32];
         }
     }
     __syncthreads();
