@@ -164,6 +164,43 @@ __device__ __forceinline__ bool pixel_blend(float d2, const float4 a, const floa
     return T < o.t_eps || cnt == (uint32_t)o.max_per_pixel;
 }
 
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Branch-free adjoint for a warp-uniform loop: `take` (0 or 1) says whether
+// the point was composited at this pixel; with take = 0 every term is 0 and
+// T, S are unchanged.
+__device__ __forceinline__ void pixel_adjoint_masked(float take, float d2, float dx, float dy,
+                                                     const float4 a, const float4 c, float amax,
+                                                     float g0, float g1, float g2, float &T,
+                                                     float &S, float v[8])
+{
+    const float G = ex2_approx(d2 * a.w);
+    const float raw = c.x * G;
+    const float alpha = fminf(amax, raw) * take;
+    const float rom = rcp_approx(1.0f - alpha);
+    const float Tb = T * rom;
+    const float wgt = alpha * Tb;
+    const float cg = c.y * g0 + c.z * g1 + c.w * g2;
+    v[4] = wgt * g0;
+    v[5] = wgt * g1;
+    v[6] = wgt * g2;
+    const float dalpha = (Tb * cg - S * rom) * take;
+    S = fmaf(wgt, cg, S);
+    T = Tb;
+    const float ca = raw < amax ? dalpha * alpha : 0.0f; // clamped: no geometry terms
+    const float q = a.w * QP_TO_Q;
+    v[0] = ca * q * dx;
+    v[1] = ca * q * dy;
+    v[2] = -0.5f * ca * d2;
+    v[3] = raw < amax ? dalpha * G : 0.0f;
+    v[7] = 0.0f;
+}
+
 // Per-pixel adjoint of one composited point (see the file comment).  On
 // return v[0..6] = {dpx, dpy, dq, do, dr, dg, db}; T and S are updated.
 __device__ __forceinline__ void pixel_adjoint(float d2, float dx, float dy, const float4 a,
@@ -256,21 +293,24 @@ __device__ __forceinline__ void fwd_stream_item(const Batch &b, const DevOpts &o
     uint32_t cnt = 0, last = 0, examined = 0;
     bool done = !g.inside;
     if (!__all_sync(0xffffffffu, done)) {
-        // software pipeline: the next step's entry is loaded one step early
-        uint32_t pv_n = 0;
+        // software pipeline: point ids two steps ahead, records one step
+        // ahead, so the id -> record load chain is hidden behind a step
+        uint32_t pv_n = 0, pv_nn = 0;
         float4 a_n = make_float4(0.f, 0.f, -1.f, 0.f);
         if (s + lane < e) {
             pv_n = __ldg(pv_list + s + lane);
             a_n = __ldg(rec + 2 * (size_t)pv_n);
         }
+        if (s + 32 + lane < e) pv_nn = __ldg(pv_list + s + 32 + lane);
         for (uint32_t c = s; c < e; c += 32) {
             const uint32_t pv = pv_n;
             const float4 a = a_n;
             const bool valid = c + lane < e;
             if (c + 32 + lane < e) {
-                pv_n = __ldg(pv_list + c + 32 + lane);
+                pv_n = pv_nn;
                 a_n = __ldg(rec + 2 * (size_t)pv_n);
             }
+            if (c + 64 + lane < e) pv_nn = __ldg(pv_list + c + 64 + lane);
             const bool hit = valid && disc_meets_rect(a, g);
             uint32_t m = __ballot_sync(0xffffffffu, hit);
             if (hit) {
@@ -337,20 +377,22 @@ __device__ __forceinline__ void bwd_stream_item(const Batch &b, const DevOpts &o
     const uint32_t wmax = __reduce_max_sync(0xffffffffu, L);
     if (wmax == 0) return;
     int64_t c = (int64_t)((wmax - 1) & ~31u);
-    uint32_t pv_n = 0;
+    uint32_t pv_n = 0, pv_nn = 0;
     float4 a_n = make_float4(0.f, 0.f, -1.f, 0.f);
     if ((uint32_t)c + lane < wmax) {
         pv_n = __ldg(pv_list + s + (uint32_t)c + lane);
         a_n = __ldg(rec + 2 * (size_t)pv_n);
     }
+    if (c >= 32) pv_nn = __ldg(pv_list + s + (uint32_t)c - 32 + lane);
     for (; c >= 0; c -= 32) {
         const uint32_t pv = pv_n;
         const float4 a = a_n;
         const bool valid = (uint32_t)c + lane < wmax;
         if (c >= 32) {
-            pv_n = __ldg(pv_list + s + (uint32_t)c - 32 + lane);
+            pv_n = pv_nn;
             a_n = __ldg(rec + 2 * (size_t)pv_n);
         }
+        if (c >= 64) pv_nn = __ldg(pv_list + s + (uint32_t)c - 64 + lane);
         const bool hit = valid && disc_meets_rect(a, g);
         uint32_t m = __ballot_sync(0xffffffffu, hit);
         if (hit) {
@@ -364,19 +406,25 @@ __device__ __forceinline__ void bwd_stream_item(const Batch &b, const DevOpts &o
             m &= ~(1u << j);
             const float4 aj = wbuf[j];
             const float4 cj = wbuf[32 + j];
-            float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            bool contrib = false;
-            if ((uint32_t)c + j < L) {
-                ++examined;
-                float dx, dy;
-                const float d2 = pixel_d2(g.ux, g.uy, aj.x, aj.y, dx, dy);
-                if (d2 <= aj.z) {
-                    contrib = true;
-                    ++used;
-                    pixel_adjoint(d2, dx, dy, aj, cj, o.alpha_max, g0, g1, g2, T, S, v);
+            const bool before = (uint32_t)c + j < L;
+            float dx, dy;
+            const float d2 = pixel_d2(g.ux, g.uy, aj.x, aj.y, dx, dy);
+            const bool contrib = before && d2 <= aj.z;
+            examined += before;
+            used += contrib;
+            const uint32_t cm = __ballot_sync(0xffffffffu, contrib);
+            if (cm) {
+                float v[8];
+                pixel_adjoint_masked(contrib ? 1.0f : 0.0f, d2, dx, dy, aj, cj, o.alpha_max, g0,
+                                     g1, g2, T, S, v);
+                if (cm & (cm - 1)) {
+                    warp_add_terms(v, lane, g2d, wpv[j]);
+                } else if (contrib) { // a single pixel: no reduction needed
+                    float4 *dst = reinterpret_cast<float4 *>(g2d) + 2 * (size_t)wpv[j];
+                    atomicAdd(dst, make_float4(v[0], v[1], v[2], v[3]));
+                    atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], 0.f));
                 }
             }
-            if (__any_sync(0xffffffffu, contrib)) warp_add_terms(v, lane, g2d, wpv[j]);
         }
         __syncwarp(); // chunk consumed before the buffer is refilled
     }
