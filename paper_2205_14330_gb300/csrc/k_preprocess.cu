@@ -193,12 +193,23 @@ __device__ void pre_bwd_point(const Batch &b, const DevOpts &o, const DevScene &
     const float r = __ldg(sc.radius + i);
     float dP0 = 0.f, dP1 = 0.f, dP2 = 0.f, dop = 0.f;
 
+    // the next view's screen-space terms are loaded one view ahead
+    float4 ga_n = make_float4(0.f, 0.f, 0.f, 0.f), gb_n = ga_n;
+    if (sc.view_count > 0) {
+        const int64_t pv0 = b.views[b.view_list[sc.view_begin]].pv_base + i;
+        ga_n = g2d[2 * pv0];
+        gb_n = g2d[2 * pv0 + 1];
+    }
     for (int vv = 0; vv < sc.view_count; ++vv) {
         const int v = b.view_list[sc.view_begin + vv];
         const DevView &V = b.views[v];
-        const int64_t pv = V.pv_base + i;
-        const float4 ga = g2d[2 * pv];     // dpx, dpy, dq, do
-        const float4 gb = g2d[2 * pv + 1]; // dr, dg, db, -
+        const float4 ga = ga_n; // dpx, dpy, dq, do
+        const float4 gb = gb_n; // dr, dg, db, -
+        if (vv + 1 < sc.view_count) {
+            const int64_t pvn = b.views[b.view_list[sc.view_begin + vv + 1]].pv_base + i;
+            ga_n = g2d[2 * pvn];
+            gb_n = g2d[2 * pvn + 1];
+        }
         if (ga.x == 0.f && ga.y == 0.f && ga.z == 0.f && ga.w == 0.f && gb.x == 0.f &&
             gb.y == 0.f && gb.z == 0.f)
             continue; // culled or never composited

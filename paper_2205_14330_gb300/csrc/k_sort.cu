@@ -374,24 +374,43 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
 }
 
 // ------------------------------------------------------------ emission
-__global__ void gather_counts_kernel(const uint32_t *__restrict__ sorted_pv,
-                                     const uint32_t *__restrict__ ntiles, const uint32_t *n_dev,
-                                     int64_t cap, uint32_t *__restrict__ nt_sorted)
+// One gather per depth-sorted point-view: its tile rectangle (the only
+// random access of the emission), turned into the tile count, the global id
+// of the rectangle's first tile and the rectangle width / tiles per row.
+__global__ void gather_rects_kernel(const DevView *__restrict__ views, int32_t n_views,
+                                    const uint32_t *__restrict__ sorted_pv,
+                                    const uint2 *__restrict__ rect, const uint32_t *n_dev,
+                                    int64_t cap, uint32_t *__restrict__ nt_sorted,
+                                    uint32_t *__restrict__ tb_sorted,
+                                    uint32_t *__restrict__ wx_sorted)
 {
     const int64_t n = dev_count(n_dev, cap);
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n) nt_sorted[j] = ntiles[sorted_pv[j]];
+    if (j >= n) return;
+    const uint32_t pv = sorted_pv[j];
+    int lo = 0, hi = n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (views[mid].pv_base <= (int64_t)pv) lo = mid; else hi = mid - 1;
+    }
+    const uint2 rc = rect[pv];
+    const uint32_t tx0 = rc.x & 0xffff, ty0 = rc.x >> 16, tx1 = rc.y & 0xffff, ty1 = rc.y >> 16;
+    const uint32_t tpx = (uint32_t)views[lo].tiles_x;
+    const uint32_t wx = tx1 - tx0 + 1;
+    nt_sorted[j] = wx * (ty1 - ty0 + 1);
+    tb_sorted[j] = views[lo].tile_base + ty0 * tpx + tx0;
+    wx_sorted[j] = wx | (tpx << 16);
 }
 
 // Each warp owns 32 consecutive depth-sorted point-views; their pair runs
 // are contiguous in the output, so the warp writes them together: output q
 // belongs to the last lane whose run starts at or before q.
 __global__ void __launch_bounds__(256)
-emit_pairs_kernel(const DevView *__restrict__ views, int32_t n_views,
-                  const uint32_t *__restrict__ sorted_pv, const uint32_t *__restrict__ nt_sorted,
-                  const uint32_t *__restrict__ offs, const uint2 *__restrict__ rect,
-                  const uint32_t *n_dev, int64_t cap_vis, uint32_t *__restrict__ keys,
-                  uint32_t *__restrict__ vals, int64_t cap_pairs, uint32_t *status)
+emit_pairs_kernel(const uint32_t *__restrict__ sorted_pv, const uint32_t *__restrict__ nt_sorted,
+                  const uint32_t *__restrict__ offs, const uint32_t *__restrict__ tb_sorted,
+                  const uint32_t *__restrict__ wx_sorted, const uint32_t *n_dev, int64_t cap_vis,
+                  uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, int64_t cap_pairs,
+                  uint32_t *status)
 {
     const int64_t n = dev_count(n_dev, cap_vis);
     const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31;
@@ -399,23 +418,13 @@ emit_pairs_kernel(const DevView *__restrict__ views, int32_t n_views,
     const int lane = threadIdx.x & 31;
     const int64_t j = j0 + lane;
     const bool ok = j < n;
-    uint32_t pre = 0, nt = 0, pv = 0, tb = 0, wx = 1, tpx = 1;
+    uint32_t pre = 0xffffffffu, nt = 0, pv = 0, tb = 0, wxt = 1; // invalid lanes own no output
     if (ok) {
         pre = offs[j];
         nt = nt_sorted[j];
         pv = sorted_pv[j];
-        int lo = 0, hi = n_views - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (views[mid].pv_base <= (int64_t)pv) lo = mid; else hi = mid - 1;
-        }
-        const uint2 rc = rect[pv];
-        const uint32_t tx0 = rc.x & 0xffff, ty0 = rc.x >> 16, tx1 = rc.y & 0xffff;
-        tpx = (uint32_t)views[lo].tiles_x;
-        tb = views[lo].tile_base + ty0 * tpx + tx0;
-        wx = tx1 - tx0 + 1;
-    } else {
-        pre = 0xffffffffu; // never owns an output
+        tb = tb_sorted[j];
+        wxt = wx_sorted[j];
     }
     const uint32_t start = __shfl_sync(0xffffffffu, pre, 0);
     const uint32_t last_lane = (uint32_t)(n - 1 - j0 < 31 ? n - 1 - j0 : 31);
@@ -424,35 +433,50 @@ emit_pairs_kernel(const DevView *__restrict__ views, int32_t n_views,
     for (uint32_t q0 = start; q0 < end; q0 += 32) {
         const uint32_t q = q0 + lane;
         // owner: largest lane with pre <= q
-        int o = 0;
+        int ow = 0;
 #pragma unroll
         for (int step = 16; step > 0; step >>= 1) {
-            const uint32_t p = __shfl_sync(0xffffffffu, pre, o + step);
-            if (p <= q) o += step;
+            const uint32_t p = __shfl_sync(0xffffffffu, pre, ow + step);
+            if (p <= q) ow += step;
         }
-        const uint32_t opre = __shfl_sync(0xffffffffu, pre, o);
-        const uint32_t otb = __shfl_sync(0xffffffffu, tb, o);
-        const uint32_t owx = __shfl_sync(0xffffffffu, wx, o);
-        const uint32_t otpx = __shfl_sync(0xffffffffu, tpx, o);
-        const uint32_t opv = __shfl_sync(0xffffffffu, pv, o);
+        const uint32_t opre = __shfl_sync(0xffffffffu, pre, ow);
+        const uint32_t otb = __shfl_sync(0xffffffffu, tb, ow);
+        const uint32_t owxt = __shfl_sync(0xffffffffu, wxt, ow);
+        const uint32_t opv = __shfl_sync(0xffffffffu, pv, ow);
         if (q < end && (int64_t)q < cap_pairs) {
-            const uint32_t t = q - opre;
-            keys[q] = otb + (t / owx) * otpx + (t % owx);
+            const uint32_t t = q - opre, owx = owxt & 0xffff;
+            keys[q] = otb + (t / owx) * (owxt >> 16) + (t % owx);
             vals[q] = opv;
         }
     }
 }
 
+// [start, end) of every tile in the sorted key list; four keys per thread.
 __global__ void tile_ranges_kernel(const uint32_t *__restrict__ keys, const uint32_t *n_dev,
                                    int64_t cap, uint2 *__restrict__ ranges, uint32_t n_tiles)
 {
     const int64_t n = dev_count(n_dev, cap);
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const uint32_t t = keys[j];
-    if (t >= n_tiles) return;
-    if (j == 0 || keys[j - 1] != t) ranges[t].x = (uint32_t)j;
-    if (j == n - 1 || keys[j + 1] != t) ranges[t].y = (uint32_t)(j + 1);
+    const int64_t j4 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (j4 >= n) return;
+    uint32_t k[6]; // k[0] = key before the group, k[5] = key after it
+    if (j4 + 3 < n) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(keys + j4);
+        k[1] = q.x;
+        k[2] = q.y;
+        k[3] = q.z;
+        k[4] = q.w;
+    } else {
+        for (int i = 0; i < 4; ++i) k[1 + i] = j4 + i < n ? keys[j4 + i] : 0xffffffffu;
+    }
+    k[0] = j4 > 0 ? keys[j4 - 1] : 0xffffffffu;
+    k[5] = j4 + 4 < n ? keys[j4 + 4] : 0xffffffffu;
+#pragma unroll
+    for (int i = 1; i <= 4; ++i) {
+        const int64_t j = j4 + i - 1;
+        if (j >= n || k[i] >= n_tiles) continue;
+        if (j == 0 || k[i - 1] != k[i]) ranges[k[i]].x = (uint32_t)j;
+        if (j == n - 1 || k[i + 1] != k[i]) ranges[k[i]].y = (uint32_t)(j + 1);
+    }
 }
 
 } // namespace
@@ -518,7 +542,7 @@ void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *&keys_alt, uin
 
 size_t emit_temp_bytes(int64_t cap_vis)
 {
-    return (size_t)(cap_vis > 0 ? cap_vis : 1) * 2 * sizeof(uint32_t) + scan_temp_bytes(cap_vis);
+    return (size_t)(cap_vis > 0 ? cap_vis : 1) * 4 * sizeof(uint32_t) + scan_temp_bytes(cap_vis);
 }
 
 void launch_emit_pairs(const Batch &b, const DevOpts &o, const uint32_t *sorted_pv,
@@ -528,13 +552,17 @@ void launch_emit_pairs(const Batch &b, const DevOpts &o, const uint32_t *sorted_
 {
     (void)o;
     if (cap_vis <= 0) return;
+    (void)ntiles;
     uint32_t *nt_sorted = (uint32_t *)temp;
     uint32_t *offs = nt_sorted + cap_vis;
-    void *scan_tmp = offs + cap_vis;
+    uint32_t *tb_sorted = offs + cap_vis;
+    uint32_t *wx_sorted = tb_sorted + cap_vis;
+    void *scan_tmp = wx_sorted + cap_vis;
     const unsigned nb = (unsigned)((cap_vis + 255) / 256);
-    gather_counts_kernel<<<nb, 256, 0, s>>>(sorted_pv, ntiles, n_vis, cap_vis, nt_sorted);
+    gather_rects_kernel<<<nb, 256, 0, s>>>(b.views, b.n_views, sorted_pv, rect, n_vis, cap_vis,
+                                           nt_sorted, tb_sorted, wx_sorted);
     run_scan(LoadU32{nt_sorted}, ActStore{offs}, n_vis, cap_vis, scan_tmp, nullptr, status, s);
-    emit_pairs_kernel<<<nb, 256, 0, s>>>(b.views, b.n_views, sorted_pv, nt_sorted, offs, rect, n_vis,
+    emit_pairs_kernel<<<nb, 256, 0, s>>>(sorted_pv, nt_sorted, offs, tb_sorted, wx_sorted, n_vis,
                                          cap_vis, keys, vals, cap_pairs, status);
     count_launches(2);
 }
@@ -544,7 +572,7 @@ void launch_tile_ranges(const uint32_t *keys, const uint32_t *n_pairs, int64_t c
 {
     if (cap_pairs <= 0) return;
     const int th = 256;
-    const int64_t nb = (cap_pairs + th - 1) / th;
+    const int64_t nb = ((cap_pairs + 3) / 4 + th - 1) / th;
     tile_ranges_kernel<<<(unsigned)nb, th, 0, s>>>(keys, n_pairs, cap_pairs, ranges, n_tiles);
     count_launches(1);
 }
