@@ -13,8 +13,10 @@ Parity status (every function is pinned by ``tests/test_oracle_*.py``):
                         printed textbook values, parity under v -> -v
   project ............. pinned: on-axis point lands on the principal point,
                         closed-form pinhole on random points
-  bin_tiles ........... pinned: superset of the per-pixel cutoff test,
-                        brute-force enumeration of covered tiles
+  bin_tiles ........... pinned: every pixel passing the cutoff test has its
+                        tile listed (brute force over pixels), and the
+                        lists equal a brute-force enumeration of the
+                        tile test
   render .............. pinned: isolated splat in closed form, transmittance
                         identity, occlusion, permutation invariance
   backward ............ pinned: central finite differences of ``render``
@@ -55,7 +57,7 @@ class Rec(C.Structure):
                 ("rc32", C.c_float), ("rc2_32", C.c_float),
                 ("px_lo", C.c_int32), ("px_hi", C.c_int32), ("py_lo", C.c_int32), ("py_hi", C.c_int32),
                 ("tx_lo", C.c_int32), ("tx_hi", C.c_int32), ("ty_lo", C.c_int32), ("ty_hi", C.c_int32),
-                ("ntiles", C.c_int64),
+                ("tile_mask", C.c_uint32), ("ntiles", C.c_int64),
                 ("X", C.c_double * 3), ("px", C.c_double), ("py", C.c_double), ("s", C.c_double),
                 ("dir", C.c_double * 3), ("rgb", C.c_double * 3)]
 

@@ -30,6 +30,11 @@
  * those integer decisions in the same precision.  This file must therefore be
  * compiled with -ffp-contract=off and without fast-math.
  *
+ * Tile lists: a point is listed in a tile of its clamped pixel box when the
+ * box spans more than 32 tiles, or else when the fp32 distance from the
+ * splat centre to the tile's rectangle of pixel centres (clipped to the
+ * image) is within the cutoff radius.
+ *
  * Readings of points the paper leaves open (each one also listed in the
  * design notes of the repository):
  *   - the kernel normalisation 1/sqrt(2 pi r^2) is folded into a per-point
@@ -84,6 +89,7 @@ typedef struct {
     float z32, px32, py32, s32, rc32, rc2_32;
     int32_t px_lo, px_hi, py_lo, py_hi; /* clamped inclusive pixel box */
     int32_t tx_lo, tx_hi, ty_lo, ty_hi; /* inclusive tile box */
+    uint32_t tile_mask; /* listed tiles of the box, row-major bits (box <= 32 tiles) */
     int64_t ntiles;
     double X[3];      /* camera-space position, double */
     double px, py, s; /* double screen position and kernel width */
@@ -259,7 +265,6 @@ static void project_point(const double *P, double radius, const orc_camera *cam,
     ylo = ylo < 0.0f ? 0.0f : ylo;
     xhi = xhi > W1 ? W1 : xhi;
     yhi = yhi > H1 ? H1 : yhi;
-    r->visible = 1;
     r->px_lo = (int)xlo;
     r->px_hi = (int)xhi;
     r->py_lo = (int)ylo;
@@ -268,7 +273,38 @@ static void project_point(const double *P, double radius, const orc_camera *cam,
     r->tx_hi = r->px_hi / o->tile_w;
     r->ty_lo = r->py_lo / o->tile_h;
     r->ty_hi = r->py_hi / o->tile_h;
-    r->ntiles = (int64_t)(r->tx_hi - r->tx_lo + 1) * (int64_t)(r->ty_hi - r->ty_lo + 1);
+    {
+        /* Listed tiles: every tile of the box when it spans more than 32
+         * tiles; otherwise the tiles whose rectangle of pixel centres
+         * (clipped to the image) comes within the cutoff of the splat
+         * centre, measured in fp32 from the nearest rectangle point -- never
+         * closer than any pixel centre inside, so no pixel that passes the
+         * per-pixel cutoff test is lost. */
+        const int wx = r->tx_hi - r->tx_lo + 1, wy = r->ty_hi - r->ty_lo + 1;
+        if (wx * wy > 32) {
+            r->tile_mask = 0;
+            r->ntiles = (int64_t)wx * wy;
+        } else {
+            uint32_t mask = 0;
+            for (int ty = r->ty_lo; ty <= r->ty_hi; ++ty)
+                for (int tx = r->tx_lo; tx <= r->tx_hi; ++tx) {
+                    int xe = (tx + 1) * o->tile_w, ye = (ty + 1) * o->tile_h;
+                    if (xe > cam->width) xe = cam->width;
+                    if (ye > cam->height) ye = cam->height;
+                    const float xl = (float)(tx * o->tile_w) + 0.5f, xh = (float)xe - 0.5f;
+                    const float yl = (float)(ty * o->tile_h) + 0.5f, yh = (float)ye - 0.5f;
+                    const float cxr = px < xl ? xl : (px > xh ? xh : px);
+                    const float cyr = py < yl ? yl : (py > yh ? yh : py);
+                    const float ex = cxr - px, ey = cyr - py;
+                    const float d2 = ex * ex + ey * ey;
+                    if (d2 <= rc2) mask |= 1u << ((ty - r->ty_lo) * wx + (tx - r->tx_lo));
+                }
+            r->tile_mask = mask;
+            r->ntiles = __builtin_popcount(mask);
+        }
+    }
+    if (r->ntiles == 0) return; /* no pixel centre within reach */
+    r->visible = 1;
 
     /* double geometry (Eq. 1) */
     for (int a = 0; a < 3; ++a)
@@ -363,8 +399,11 @@ int64_t orc_bin(int64_t n, int ncam, const orc_camera *cams, const orc_opts *o, 
         for (int64_t i = 0; i < n; ++i) {
             const orc_rec *r = &recs[(size_t)v * n + i];
             if (!r->visible) continue;
+            const int wxb = r->tx_hi - r->tx_lo + 1, dense = wxb * (r->ty_hi - r->ty_lo + 1) > 32;
             for (int y = r->ty_lo; y <= r->ty_hi; ++y)
                 for (int x = r->tx_lo; x <= r->tx_hi; ++x) {
+                    if (!dense && !((r->tile_mask >> ((y - r->ty_lo) * wxb + (x - r->tx_lo))) & 1u))
+                        continue;
                     e[w].tile = tile_base + (uint32_t)(y * tx + x);
                     e[w].zbits = f32_bits(r->z32);
                     e[w].pv = (uint32_t)((int64_t)v * n + i);

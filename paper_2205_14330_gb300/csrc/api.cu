@@ -351,9 +351,9 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
     PBR_TRY(dalloc((void **)&st->counters, 128, s));
     TempBufs tmp(s);
     uint32_t *zbits = nullptr;
-    uint2 *rect = nullptr;
+    uint4 *rect = nullptr;
     PBR_TRY(tmp.alloc(&zbits, sizeof(uint32_t) * npv));
-    PBR_TRY(tmp.alloc(&rect, sizeof(uint2) * npv));
+    PBR_TRY(tmp.alloc(&rect, sizeof(uint4) * npv));
     PBR_CUDA(cudaMemsetAsync(st->counters, 0, 128, s));
     PBR_CUDA(cudaMemsetAsync((char *)st->counters + 48, 0xff, 4, s)); // depth-bits minimum
     {

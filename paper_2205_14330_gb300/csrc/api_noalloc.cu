@@ -98,7 +98,7 @@ extern "C" int pbr_render_forward_noalloc(const pbr_points *scenes, int32_t n_sc
     float4 *rec = cv.take<float4>(sizeof(float4) * 2 * npv);
     uint32_t *ntiles = cv.take<uint32_t>(sizeof(uint32_t) * npv);
     uint32_t *zbits = cv.take<uint32_t>(sizeof(uint32_t) * npv);
-    uint2 *rect = cv.take<uint2>(sizeof(uint2) * npv);
+    uint4 *rect = cv.take<uint4>(sizeof(uint4) * npv);
     uint2 *ranges = cv.take<uint2>(sizeof(uint2) * L.n_tiles);
     float *T_final = cv.take<float>(sizeof(float) * L.n_pix);
     uint32_t *n_contrib = cv.take<uint32_t>(sizeof(uint32_t) * L.n_pix);
@@ -151,8 +151,8 @@ extern "C" int pbr_render_forward_noalloc(const pbr_points *scenes, int32_t n_sc
     const uint32_t *n_pairs_dev = (const uint32_t *)(counters + 0);
     launch_compact_visible(ntiles, zbits, npv, vk, vv, nullptr, temp, s);
     radix_sort_pairs(vk, vv, vk2, vv2, n_vis_dev, (int64_t)n_vis, 32, temp, s);
-    launch_emit_pairs(b, o, vv, n_vis_dev, (int64_t)n_vis, ntiles, rect, tk, tv, (int64_t)n_pairs,
-                      status, temp, s);
+    launch_emit_pairs(b, o, vv, n_vis_dev, (int64_t)n_vis, ntiles, rect, tk, tv,
+                      (int64_t)n_pairs, status, temp, s);
     int key_bits = 1;
     while (key_bits < 32 && ((L.n_tiles - 1) >> key_bits)) ++key_bits;
     radix_sort_pairs(tk, tv, pk2, pv2, n_pairs_dev, (int64_t)n_pairs, key_bits, temp, s);

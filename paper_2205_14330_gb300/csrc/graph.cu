@@ -88,7 +88,8 @@ struct pbr_graph {
     int32_t *d_view_list = nullptr;
     float4 *rec = nullptr, *g2d = nullptr;
     uint32_t *ntiles = nullptr, *zbits = nullptr;
-    uint2 *rect = nullptr, *ranges = nullptr;
+    uint4 *rect = nullptr;
+    uint2 *ranges = nullptr;
     unsigned long long *counters = nullptr;
     uint32_t *vk = nullptr, *vv = nullptr, *vk2 = nullptr, *vv2 = nullptr;
     uint32_t *tk = nullptr, *tv = nullptr, *tk2 = nullptr, *tv2 = nullptr;
@@ -163,8 +164,8 @@ void enqueue_forward(pbr_graph *g, cudaStream_t s)
     radix_sort_pairs(vk, vv, vk2, vv2, n_vis_dev, g->cap_vis, g->depth_bits, g->temp, s,
                      g->depth_lo);
     uint32_t *tk = g->tk, *tv = g->tv, *tk2 = g->tk2, *tv2 = g->tv2;
-    launch_emit_pairs(b, o, vv, n_vis_dev, g->cap_vis, g->ntiles, g->rect, tk, tv, g->cap_pairs,
-                      status, g->temp, s);
+    launch_emit_pairs(b, o, vv, n_vis_dev, g->cap_vis, g->ntiles, g->rect, tk, tv,
+                      g->cap_pairs, status, g->temp, s);
     int key_bits = bit_width(L.n_tiles > 0 ? L.n_tiles - 1 : 0);
     if (key_bits < 1) key_bits = 1;
     radix_sort_pairs(tk, tv, tk2, tv2, n_pairs_dev, g->cap_pairs, key_bits, g->temp, s);
@@ -274,7 +275,7 @@ int plan_and_capture(pbr_graph *g, cudaStream_t user_stream)
     PBR_TRY(g->alloc(&g->rec, sizeof(float4) * 2 * npv));
     PBR_TRY(g->alloc(&g->ntiles, sizeof(uint32_t) * npv));
     PBR_TRY(g->alloc(&g->zbits, sizeof(uint32_t) * npv));
-    PBR_TRY(g->alloc(&g->rect, sizeof(uint2) * npv));
+    PBR_TRY(g->alloc(&g->rect, sizeof(uint4) * npv));
     PBR_TRY(g->alloc(&g->vk, 4 * (size_t)g->cap_vis));
     PBR_TRY(g->alloc(&g->vv, 4 * (size_t)g->cap_vis));
     PBR_TRY(g->alloc(&g->vk2, 4 * (size_t)g->cap_vis));

@@ -4,7 +4,8 @@
 // looping over every view of the point's scene, so position, radius,
 // opacity and the [K,3] SH block are read from HBM once per batch.  For each
 // (view, point) it writes a 32-byte record {px, py, rc^2, q'} {o, r, g, b},
-// the fp32 depth bits, the covered tile rectangle and the tile count.
+// the fp32 depth bits, the tile box with the mask of its listed tiles (one
+// 16-byte record) and the tile count.
 //
 // The discrete decisions (cull, cutoff radius, pixel box, tile rectangle,
 // depth key) use IEEE fp32 round-to-nearest operations with no
@@ -13,7 +14,10 @@
 //   px = fx (X0 / X2) + cx,   py = fy (X1 / X2) + cy
 //   s  = (fx r) / X2  (radius_mode 0)  or  (r min(W,H)) 0.5  (mode 1)
 //   rc = cutoff_k s,  rc2 = rc rc
-//   pixel box: [floor(px - rc) - 1, ceil(px + rc)] clamped to the image.
+//   pixel box: [floor(px - rc) - 1, ceil(px + rc)] clamped to the image;
+//   listed tiles of the box: all when it spans more than 32 tiles, else
+//   those whose rectangle of pixel centres (clipped to the image) is within
+//   rc of (px, py) by the same fp32 test.
 //
 // preprocess_bwd (Sec. 3.3): one thread per point; per view it chains the
 // screen-space adjoint {dpx, dpy, dq, do, dr, dg, db} (q = 1/s^2) through the
@@ -49,7 +53,7 @@ template <int DEG>
 __device__ void pre_fwd_point(const Batch &b, const DevOpts &o, const DevScene &sc, int64_t i,
                               const float *hs, float4 *__restrict__ rec,
                               uint32_t *__restrict__ zbits, uint32_t *__restrict__ ntiles,
-                              uint2 *__restrict__ rect, uint32_t &vis_cnt, uint32_t &pair_cnt,
+                              uint4 *__restrict__ rect, uint32_t &vis_cnt, uint32_t &pair_cnt,
                               uint32_t &zlo, uint32_t &zhi)
 {
     constexpr int K = SH<DEG>::K;
@@ -90,14 +94,44 @@ __device__ void pre_fwd_point(const Batch &b, const DevOpts &o, const DevScene &
             float ylo = __fsub_rn(floorf(__fsub_rn(py, rc)), 1.0f);
             float yhi = ceilf(__fadd_rn(py, rc));
             const float W1 = (float)(V.W - 1), H1 = (float)(V.H - 1);
-            if (sg > 0.0f && xhi >= 0.0f && xlo <= W1 && yhi >= 0.0f && ylo <= H1) {
+            if (sg > 0.0f && xhi >= 0.0f && xlo <= W1 && yhi >= 0.0f && ylo <= H1) do {
                 xlo = xlo < 0.0f ? 0.0f : xlo;
                 ylo = ylo < 0.0f ? 0.0f : ylo;
                 xhi = xhi > W1 ? W1 : xhi;
                 yhi = yhi > H1 ? H1 : yhi;
                 const int tx0 = (int)xlo / o.tile_w, tx1 = (int)xhi / o.tile_w;
                 const int ty0 = (int)ylo / o.tile_h, ty1 = (int)yhi / o.tile_h;
-                nt = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+                const int wx = tx1 - tx0 + 1, wy = ty1 - ty0 + 1;
+                // listed tiles: all of a box wider than 32 tiles, else those
+                // whose clipped rectangle of pixel centres is within the
+                // cutoff (fp32 distance from the nearest rectangle point)
+                uint32_t mask = 0;
+                if (wx * wy > 32) {
+                    nt = (uint32_t)(wx * wy);
+                } else {
+                    // tile bounds are integer-valued floats (exact), stepped
+                    // by the tile size; the last tile is clipped to the image
+                    const float tw = (float)o.tile_w, th = (float)o.tile_h;
+                    const float Wm = (float)V.W - 0.5f, Hm = (float)V.H - 0.5f;
+                    const float xl0 = (float)(tx0 * o.tile_w) + 0.5f;
+                    float yl = (float)(ty0 * o.tile_h) + 0.5f;
+                    int bit = 0;
+                    for (int ty = ty0; ty <= ty1; ++ty, yl += th) {
+                        const float yh = fminf(yl + (th - 1.0f), Hm);
+                        const float cyr = py < yl ? yl : (py > yh ? yh : py);
+                        const float ey = __fsub_rn(cyr, py);
+                        const float ey2 = __fmul_rn(ey, ey);
+                        float xl = xl0;
+                        for (int tx = tx0; tx <= tx1; ++tx, xl += tw, ++bit) {
+                            const float xh = fminf(xl + (tw - 1.0f), Wm);
+                            const float cxr = px < xl ? xl : (px > xh ? xh : px);
+                            const float ex = __fsub_rn(cxr, px);
+                            if (__fadd_rn(__fmul_rn(ex, ex), ey2) <= rc2) mask |= 1u << bit;
+                        }
+                    }
+                    nt = (uint32_t)__popc(mask);
+                    if (nt == 0) break; // no pixel centre within reach: not visible
+                }
                 // view direction (Eq. 3) and colour (Eq. 4)
                 const float inv = rsqrtf(X[0] * X[0] + X[1] * X[1] + z * z);
                 float dx = X[0] * inv, dy = X[1] * inv, dz = z * inv;
@@ -122,13 +156,13 @@ __device__ void pre_fwd_point(const Batch &b, const DevOpts &o, const DevScene &
                 rec[2 * pv] = make_float4(px, py, rc2, qp);
                 rec[2 * pv + 1] = make_float4(op, c0, c1, c2);
                 zbits[pv] = __float_as_uint(z);
-                rect[pv] = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16),
-                                      (uint32_t)tx1 | ((uint32_t)ty1 << 16));
+                rect[pv] = make_uint4((uint32_t)tx0 | ((uint32_t)ty0 << 16),
+                                      (uint32_t)tx1 | ((uint32_t)ty1 << 16), mask, 0u);
                 ++vis_cnt;
                 pair_cnt += nt;
                 zlo = min(zlo, __float_as_uint(z));
                 zhi = max(zhi, __float_as_uint(z));
-            }
+            } while (0);
         }
         ntiles[pv] = nt;
     }
@@ -136,7 +170,7 @@ __device__ void pre_fwd_point(const Batch &b, const DevOpts &o, const DevScene &
 
 __global__ void __launch_bounds__(PRE_THREADS)
 preprocess_fwd_kernel(Batch b, DevOpts o, float4 *__restrict__ rec, uint32_t *__restrict__ zbits,
-                      uint32_t *__restrict__ ntiles, uint2 *__restrict__ rect,
+                      uint32_t *__restrict__ ntiles, uint4 *__restrict__ rect,
                       unsigned long long *__restrict__ counters)
 {
     __shared__ float s_sh[PRE_THREADS * 48];
@@ -315,7 +349,7 @@ preprocess_bwd_kernel(Batch b, DevOpts o, const float4 *__restrict__ g2d,
 } // namespace
 
 void launch_preprocess_fwd(const Batch &b, const DevOpts &o, float4 *rec, uint32_t *zbits,
-                           uint32_t *ntiles, uint2 *rect, unsigned long long *counters,
+                           uint32_t *ntiles, uint4 *rect, unsigned long long *counters,
                            cudaStream_t s)
 {
     if (b.n_point_blocks <= 0) return;

@@ -379,10 +379,11 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
 // of the rectangle's first tile and the rectangle width / tiles per row.
 __global__ void gather_rects_kernel(const DevView *__restrict__ views, int32_t n_views,
                                     const uint32_t *__restrict__ sorted_pv,
-                                    const uint2 *__restrict__ rect, const uint32_t *n_dev,
+                                    const uint4 *__restrict__ rect, const uint32_t *n_dev,
                                     int64_t cap, uint32_t *__restrict__ nt_sorted,
                                     uint32_t *__restrict__ tb_sorted,
-                                    uint32_t *__restrict__ wx_sorted)
+                                    uint32_t *__restrict__ wx_sorted,
+                                    uint32_t *__restrict__ mask_sorted)
 {
     const int64_t n = dev_count(n_dev, cap);
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -393,13 +394,15 @@ __global__ void gather_rects_kernel(const DevView *__restrict__ views, int32_t n
         const int mid = (lo + hi + 1) >> 1;
         if (views[mid].pv_base <= (int64_t)pv) lo = mid; else hi = mid - 1;
     }
-    const uint2 rc = rect[pv];
+    const uint4 rc = rect[pv];
     const uint32_t tx0 = rc.x & 0xffff, ty0 = rc.x >> 16, tx1 = rc.y & 0xffff, ty1 = rc.y >> 16;
     const uint32_t tpx = (uint32_t)views[lo].tiles_x;
-    const uint32_t wx = tx1 - tx0 + 1;
-    nt_sorted[j] = wx * (ty1 - ty0 + 1);
+    const uint32_t wx = tx1 - tx0 + 1, wy = ty1 - ty0 + 1;
+    const uint32_t m = wx * wy > 32 ? 0u : rc.z; // 0: every tile of the box
+    nt_sorted[j] = m ? (uint32_t)__popc(m) : wx * wy;
     tb_sorted[j] = views[lo].tile_base + ty0 * tpx + tx0;
     wx_sorted[j] = wx | (tpx << 16);
+    mask_sorted[j] = m;
 }
 
 // Each warp owns 32 consecutive depth-sorted point-views; their pair runs
@@ -408,9 +411,9 @@ __global__ void gather_rects_kernel(const DevView *__restrict__ views, int32_t n
 __global__ void __launch_bounds__(256)
 emit_pairs_kernel(const uint32_t *__restrict__ sorted_pv, const uint32_t *__restrict__ nt_sorted,
                   const uint32_t *__restrict__ offs, const uint32_t *__restrict__ tb_sorted,
-                  const uint32_t *__restrict__ wx_sorted, const uint32_t *n_dev, int64_t cap_vis,
-                  uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, int64_t cap_pairs,
-                  uint32_t *status)
+                  const uint32_t *__restrict__ wx_sorted, const uint32_t *__restrict__ mask_sorted,
+                  const uint32_t *n_dev, int64_t cap_vis, uint32_t *__restrict__ keys,
+                  uint32_t *__restrict__ vals, int64_t cap_pairs, uint32_t *status)
 {
     const int64_t n = dev_count(n_dev, cap_vis);
     const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31;
@@ -418,13 +421,14 @@ emit_pairs_kernel(const uint32_t *__restrict__ sorted_pv, const uint32_t *__rest
     const int lane = threadIdx.x & 31;
     const int64_t j = j0 + lane;
     const bool ok = j < n;
-    uint32_t pre = 0xffffffffu, nt = 0, pv = 0, tb = 0, wxt = 1; // invalid lanes own no output
+    uint32_t pre = 0xffffffffu, nt = 0, pv = 0, tb = 0, wxt = 1, msk = 0; // invalid lanes own no output
     if (ok) {
         pre = offs[j];
         nt = nt_sorted[j];
         pv = sorted_pv[j];
         tb = tb_sorted[j];
         wxt = wx_sorted[j];
+        msk = mask_sorted[j];
     }
     const uint32_t start = __shfl_sync(0xffffffffu, pre, 0);
     const uint32_t last_lane = (uint32_t)(n - 1 - j0 < 31 ? n - 1 - j0 : 31);
@@ -443,8 +447,14 @@ emit_pairs_kernel(const uint32_t *__restrict__ sorted_pv, const uint32_t *__rest
         const uint32_t otb = __shfl_sync(0xffffffffu, tb, ow);
         const uint32_t owxt = __shfl_sync(0xffffffffu, wxt, ow);
         const uint32_t opv = __shfl_sync(0xffffffffu, pv, ow);
+        uint32_t omask = __shfl_sync(0xffffffffu, msk, ow);
         if (q < end && (int64_t)q < cap_pairs) {
-            const uint32_t t = q - opre, owx = owxt & 0xffff;
+            uint32_t t = q - opre;
+            if (omask) { // position of the t-th listed tile of the box
+                for (uint32_t k = 0; k < t; ++k) omask &= omask - 1;
+                t = (uint32_t)(__ffs(omask) - 1);
+            }
+            const uint32_t owx = owxt & 0xffff;
             keys[q] = otb + (t / owx) * (owxt >> 16) + (t % owx);
             vals[q] = opv;
         }
@@ -542,12 +552,12 @@ void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *&keys_alt, uin
 
 size_t emit_temp_bytes(int64_t cap_vis)
 {
-    return (size_t)(cap_vis > 0 ? cap_vis : 1) * 4 * sizeof(uint32_t) + scan_temp_bytes(cap_vis);
+    return (size_t)(cap_vis > 0 ? cap_vis : 1) * 5 * sizeof(uint32_t) + scan_temp_bytes(cap_vis);
 }
 
 void launch_emit_pairs(const Batch &b, const DevOpts &o, const uint32_t *sorted_pv,
                        const uint32_t *n_vis, int64_t cap_vis, const uint32_t *ntiles,
-                       const uint2 *rect, uint32_t *keys, uint32_t *vals, int64_t cap_pairs,
+                       const uint4 *rect, uint32_t *keys, uint32_t *vals, int64_t cap_pairs,
                        uint32_t *status, void *temp, cudaStream_t s)
 {
     (void)o;
@@ -557,13 +567,15 @@ void launch_emit_pairs(const Batch &b, const DevOpts &o, const uint32_t *sorted_
     uint32_t *offs = nt_sorted + cap_vis;
     uint32_t *tb_sorted = offs + cap_vis;
     uint32_t *wx_sorted = tb_sorted + cap_vis;
-    void *scan_tmp = wx_sorted + cap_vis;
+    uint32_t *mask_sorted = wx_sorted + cap_vis;
+    void *scan_tmp = mask_sorted + cap_vis;
     const unsigned nb = (unsigned)((cap_vis + 255) / 256);
     gather_rects_kernel<<<nb, 256, 0, s>>>(b.views, b.n_views, sorted_pv, rect, n_vis, cap_vis,
-                                           nt_sorted, tb_sorted, wx_sorted);
+                                           nt_sorted, tb_sorted, wx_sorted, mask_sorted);
     run_scan(LoadU32{nt_sorted}, ActStore{offs}, n_vis, cap_vis, scan_tmp, nullptr, status, s);
-    emit_pairs_kernel<<<nb, 256, 0, s>>>(sorted_pv, nt_sorted, offs, tb_sorted, wx_sorted, n_vis,
-                                         cap_vis, keys, vals, cap_pairs, status);
+    emit_pairs_kernel<<<nb, 256, 0, s>>>(sorted_pv, nt_sorted, offs, tb_sorted, wx_sorted,
+                                         mask_sorted, n_vis, cap_vis, keys, vals, cap_pairs,
+                                         status);
     count_launches(2);
 }
 

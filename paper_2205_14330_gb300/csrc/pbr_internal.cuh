@@ -94,8 +94,11 @@ constexpr float QP_TO_Q = -2.0f / 1.4426950408889634f;
 // counters[0] += (tile, point-view) pairs, counters[1] += visible point-views;
 // 32-bit words 12 / 13 of counters: min / max depth bits of visible
 // point-views (word 12 must start at 0xffffffff, word 13 at 0).
+// rect[pv] = {tx0 | ty0 << 16, tx1 | ty1 << 16, mask, 0}: the tile box and,
+// for a box of at most 32 tiles, bit (ty - ty0) * wx + (tx - tx0) set for
+// each listed tile (wider boxes list every tile).
 void launch_preprocess_fwd(const Batch &b, const DevOpts &o, float4 *rec, uint32_t *zbits,
-                           uint32_t *ntiles, uint2 *rect, unsigned long long *counters,
+                           uint32_t *ntiles, uint4 *rect, unsigned long long *counters,
                            cudaStream_t s);
 void launch_preprocess_bwd(const Batch &b, const DevOpts &o, const float4 *g2d, float *grad_pos,
                            float *grad_sh, float *grad_opacity, cudaStream_t s);
@@ -123,7 +126,7 @@ size_t emit_temp_bytes(int64_t cap_vis);
 // order, scans them, then writes each warp's runs cooperatively.
 void launch_emit_pairs(const Batch &b, const DevOpts &o, const uint32_t *sorted_pv,
                        const uint32_t *n_vis, int64_t cap_vis, const uint32_t *ntiles,
-                       const uint2 *rect, uint32_t *keys, uint32_t *vals, int64_t cap_pairs,
+                       const uint4 *rect, uint32_t *keys, uint32_t *vals, int64_t cap_pairs,
                        uint32_t *status, void *temp, cudaStream_t s);
 void launch_tile_ranges(const uint32_t *keys, const uint32_t *n_pairs, int64_t cap_pairs,
                         uint2 *ranges, uint32_t n_tiles, cudaStream_t s);

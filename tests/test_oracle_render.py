@@ -220,9 +220,13 @@ def test_sh_degree_zero_padding_is_inert():
 
 # ---------------------------------------------------------------- binning
 def _tiles_by_brute_force(recs, cams, tw, th):
+    """(tile, pv) pairs: tiles of the clamped pixel box -- all of them when
+    the box spans more than 32 tiles, else those whose clipped rectangle of
+    pixel centres is within the fp32 cutoff of the splat centre."""
     out = []
     n = recs.shape[1]
     tile_base = 0
+    f32 = np.float32
     for v, cam in enumerate(cams):
         W, H = cam["width"], cam["height"]
         tx, ty = -(-W // tw), -(-H // th)
@@ -230,13 +234,20 @@ def _tiles_by_brute_force(recs, cams, tw, th):
             r = recs[v, i]
             if not r["visible"]:
                 continue
-            for b in range(ty):
-                for a in range(tx):
-                    # a tile is listed iff it meets the clamped pixel box
-                    if (a * tw <= r["px_hi"] and (a + 1) * tw - 1 >= r["px_lo"]
-                            and b * th <= r["py_hi"] and (b + 1) * th - 1 >= r["py_lo"]):
-                        out.append((tile_base + b * tx + a, int(np.float32(r["z32"]).view(np.uint32)),
-                                    v * n + i))
+            boxes = [(a, b) for b in range(ty) for a in range(tx)
+                     if a * tw <= r["px_hi"] and (a + 1) * tw - 1 >= r["px_lo"]
+                     and b * th <= r["py_hi"] and (b + 1) * th - 1 >= r["py_lo"]]
+            px, py, rc2 = f32(r["px32"]), f32(r["py32"]), f32(r["rc2_32"])
+            for (a, b) in boxes:
+                if len(boxes) <= 32:
+                    xl, xh = f32(a * tw) + f32(0.5), f32(min((a + 1) * tw, W)) - f32(0.5)
+                    yl, yh = f32(b * th) + f32(0.5), f32(min((b + 1) * th, H)) - f32(0.5)
+                    ex = f32(min(max(px, xl), xh)) - px
+                    ey = f32(min(max(py, yl), yh)) - py
+                    if f32(ex * ex) + f32(ey * ey) > rc2:
+                        continue
+                out.append((tile_base + b * tx + a, int(np.float32(r["z32"]).view(np.uint32)),
+                            v * n + i))
         tile_base += tx * ty
     out.sort()
     return np.array([o[0] for o in out], np.uint32), np.array([o[2] for o in out], np.uint32)
@@ -253,6 +264,28 @@ def test_bin_lists_match_brute_force(tw, th):
         s, e = ranges[t]
         assert np.all(keys[s:e] == t)
     assert int((ranges[:, 1] - ranges[:, 0]).sum()) == len(keys)
+
+
+def test_listed_tiles_cover_every_included_pixel():
+    """Every pixel that passes the fp32 cutoff test lies in a listed tile."""
+    pos, sh, op, rad, deg, cams = _random_scene(10, n=80, W=70, H=50)
+    keys, vals, ranges, recs = O.bin_tiles(pos, sh, rad, deg, cams, tile_w=8, tile_h=8)
+    listed = set(zip(keys.tolist(), vals.tolist()))
+    ux = np.arange(70, dtype=np.float32) + np.float32(0.5)
+    uy = np.arange(50, dtype=np.float32) + np.float32(0.5)
+    n_incl = 0
+    for i, r in enumerate(recs[0]):
+        dx = ux[None, :] - np.float32(r["px32"])
+        dy = uy[:, None] - np.float32(r["py32"])
+        d2 = (dx * dx).astype(np.float32) + (dy * dy).astype(np.float32)
+        ys, xs = np.nonzero(d2 <= np.float32(r["rc2_32"]))
+        if xs.size and r["z32"] > 0.01:
+            assert r["visible"]
+        for x, y in zip(xs, ys):
+            if r["visible"]:
+                n_incl += 1
+                assert ((y // 8) * 9 + x // 8, i) in listed
+    assert n_incl > 100
 
 
 def test_pixel_box_covers_every_included_pixel():
