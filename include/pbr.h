@@ -301,7 +301,7 @@ int pbr_stage_times(pbr_ctx *ctx, double *ms, long long *calls, int n);
  * device array of 16 MiB inside the library (held by every GPU that loads
  * it, until exit); scenes, cameras and out_rgb are as for
  * pbr_render_forward.  Calls no cudaMalloc/cudaFree/cudaMallocAsync.
- *   - A pass that needs more than the 16 MiB (roughly: 48 B per point-view,
+ *   - A pass that needs more than the 16 MiB (roughly: 56 B per point-view,
  *     8 B per pixel, 16 B per (tile, point-view) pair, plus sort scratch) is
  *     rejected with PBR_ERR_CAPACITY and a message giving the size needed;
  *     the check on pair counts happens after the per-point stage.

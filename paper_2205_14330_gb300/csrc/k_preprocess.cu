@@ -168,7 +168,7 @@ __device__ void pre_fwd_point(const Batch &b, const DevOpts &o, const DevScene &
     }
 }
 
-__global__ void __launch_bounds__(PRE_THREADS)
+__global__ void __launch_bounds__(PRE_THREADS, 5)
 preprocess_fwd_kernel(Batch b, DevOpts o, float4 *__restrict__ rec, uint32_t *__restrict__ zbits,
                       uint32_t *__restrict__ ntiles, uint4 *__restrict__ rect,
                       unsigned long long *__restrict__ counters)
