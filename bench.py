@@ -263,6 +263,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--serve-rates", default="500",
                     help="comma-separated Poisson arrival rates (req/s); empty = no serving run")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
@@ -372,6 +373,27 @@ def main():
     assert ok, "graph replay outgrew its plan during the timed region"
     value = world * mp / (ms * 1e-3)
     fwd_ms = timed(lambda: G.launch(pbr.Graph.FORWARD), max(1, args.steps // 2))
+
+    # ---- the paper's full training iteration (Sec. 3.3): forward, squared
+    # error + 0.01 anisotropic TV, backward, Adam on positions (8e-4) and SH
+    # (3e-3), as one graph replay; it updates the scene in place, so it runs
+    # on a copy of the point arrays
+    train = None
+    if not args.no_train:
+        tr_scenes = [pbr.Scene(s.pos.clone(), s.sh.clone(), s.opacity, s.radius, s.deg, dev)
+                     for s in scene_list]
+        GT = pbr.Graph(R, tr_scenes, cams, opts, scene_of_view=sov, target=target,
+                       loss=loss_kind)
+        GT.set_optimizer(kind="adam", lr_pos=8e-4, lr_sh=3e-3, lambda_tv=0.01)
+        for _ in range(max(args.warmup, 1)):
+            GT.launch(pbr.Graph.TRAIN)
+        tr_ms = timed(lambda: GT.launch(pbr.Graph.TRAIN), max(1, args.steps // 2))
+        ok_t, _, _ = GT.check()
+        train = {"ms_per_step": tr_ms, "mp_s": world * mp / (tr_ms * 1e-3), "valid": bool(ok_t),
+                 "objective": "sum of squared errors + 0.01 anisotropic TV (Eq. 8)",
+                 "optimizer": "Adam, lr 8e-4 positions / 3e-3 SH"}
+        GT.close()
+        del tr_scenes
 
     # ---- timed region B: the same steps eagerly, with per-stage CUDA events
     for _ in range(2):
@@ -506,6 +528,7 @@ def main():
                 "schedule": sched, "autotune_ms": tune,
                 "timing": "value/fwd: CUDA-graph replays of the whole step; stage_ms and the "
                           "roofline: the same steps launched eagerly with per-stage CUDA events",
+                "train_iteration": train,
                 "plain": plain, "serving": serving, "stage_ms": stage_ms, "roofline": roof,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches // max(1, args.steps)),

@@ -192,8 +192,9 @@ int pbr_state_stats(pbr_state *state, unsigned long long *out4);
  * when gradient buffers are given, the backward pass and a whole training
  * step (forward, image loss against `target`, backward) -- are captured.
  * Graph phases for pbr_graph_launch: 0 forward (writes out_rgb), 1 backward
- * (reads grad_rgb, needs grad_rgb non-NULL), 2 training step (needs target;
- * writes the loss to loss_out when non-NULL and gradients to grad_*).
+ * (reads grad_rgb, needs grad_rgb non-NULL), 2 forward + loss + backward
+ * (needs target; writes the loss to loss_out when non-NULL and gradients to
+ * grad_*), 3 full training iteration (after pbr_graph_set_optimizer).
  * The point arrays and output buffers are bound at capture: update their
  * contents in place between launches (e.g. after an optimiser step).
  * loss_kind: 0 sum of squares, 1 sum of absolute values.  Synchronises the
@@ -233,6 +234,46 @@ int pbr_autotune(pbr_ctx *ctx, const pbr_points *scenes, int32_t n_scenes,
                  const int32_t *scene_of_view, const pbr_camera *cams, int32_t n_cams,
                  pbr_render_opts *opts, int32_t mode, int32_t reps, double *ms_out,
                  int32_t *n_candidates, pbr_stream_t stream);
+
+/* ---------------------------------------------------------- training step */
+/* Optimiser settings of the training step (Sec. 3.3: per-group learning
+ * rates 3e-3 for SH coefficients and 8e-4 for positions, decayed by 0.93 per
+ * epoch by the caller through pbr_graph_set_lr; objective Eq. 8 with the
+ * anisotropic TV weight lambda = 0.01).  The paper says only "stochastic
+ * gradient descent"; kind selects plain SGD or Adam. */
+typedef struct {
+    int32_t kind;                    /* 0 SGD, 1 Adam (default) */
+    float lr_pos, lr_sh, lr_opacity; /* 8e-4, 3e-3, 0 (0 = group frozen) */
+    float beta1, beta2, eps;         /* Adam: 0.9, 0.999, 1e-8 */
+    float lambda_tv;                 /* 0.01 */
+    int32_t loss_kind;               /* 0 squared error (Eq. 8, default), 1 absolute error */
+    int32_t reserved[3];
+} pbr_optimizer_cfg;
+void pbr_default_optimizer(pbr_optimizer_cfg *cfg);
+
+/* Eq. 8 objective over packed views (sizes from cams): adds sum over
+ * pixels and channels of (pred - target)^2 (loss_kind 0) or |pred - target|
+ * (1), plus lambda_tv times the anisotropic TV of pred (l1 norm of forward
+ * differences along x and y, per view, per channel), to *loss_dev (device
+ * double, caller zeroes it) and writes dL/dpred to grad (sign(0) = 0). */
+int pbr_image_loss_tv(const pbr_camera *cams, int32_t n_cams, const float *pred,
+                      const float *target, int32_t loss_kind, float lambda_tv, float *grad,
+                      double *loss_dev, pbr_stream_t stream);
+/* One optimiser update of n parameters in place: SGD (kind 0,
+ * p -= lr g) or Adam (kind 1, moments m, v updated in place, bias
+ * correction with the 1-based step number). */
+int pbr_optimizer_step(int32_t kind, float *param, const float *grad, float *m, float *v,
+                       int64_t n, float lr, float beta1, float beta2, float eps, int32_t step,
+                       pbr_stream_t stream);
+/* Adds graph phase 3, a full training iteration: forward, the Eq. 8
+ * objective against the graph's target, backward, and the optimiser update
+ * of the scenes' positions, SH coefficients (and opacities if lr_opacity >
+ * 0) IN PLACE.  The graph must have been created with a target and gradient
+ * buffers.  Optimiser moments and the step counter live in the graph (reset
+ * by this call).  Synchronises. */
+int pbr_graph_set_optimizer(pbr_graph *graph, const pbr_optimizer_cfg *cfg, pbr_stream_t stream);
+/* New learning rates for the following phase-3 launches (epoch decay). */
+int pbr_graph_set_lr(pbr_graph *graph, float lr_pos, float lr_sh, float lr_opacity);
 
 /* ---------------------------------------------------------------- serving */
 /* Statistics of the serving loop (pbr_serve_stats). */

@@ -587,6 +587,64 @@ extern "C" int pbr_image_loss(int32_t kind, const float *pred, const float *targ
     return PBR_OK;
 }
 
+extern "C" void pbr_default_optimizer(pbr_optimizer_cfg *c)
+{
+    if (!c) return;
+    std::memset(c, 0, sizeof *c);
+    c->kind = 1;
+    c->lr_pos = 8e-4f;
+    c->lr_sh = 3e-3f;
+    c->lr_opacity = 0.0f;
+    c->beta1 = 0.9f;
+    c->beta2 = 0.999f;
+    c->eps = 1e-8f;
+    c->lambda_tv = 0.01f;
+    c->loss_kind = 0;
+}
+
+extern "C" int pbr_image_loss_tv(const pbr_camera *cams, int32_t n_cams, const float *pred,
+                                 const float *target, int32_t loss_kind, float lambda_tv,
+                                 float *grad, double *loss_dev, pbr_stream_t stream)
+{
+    if (!cams || n_cams <= 0 || !pred || !target || !grad || !loss_dev ||
+        (loss_kind != 0 && loss_kind != 1) || !(lambda_tv >= 0.f))
+        return set_error(PBR_ERR_INVALID_ARG, "pbr_image_loss_tv: bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<DevView> views(n_cams);
+    int64_t pix = 0, max_pix = 0;
+    for (int v = 0; v < n_cams; ++v) {
+        if (cams[v].width <= 0 || cams[v].height <= 0)
+            return set_error(PBR_ERR_INVALID_ARG, "camera %d: size", v);
+        std::memset(&views[v], 0, sizeof(DevView));
+        views[v].W = cams[v].width;
+        views[v].H = cams[v].height;
+        views[v].pix_base = pix;
+        const int64_t np = (int64_t)cams[v].width * cams[v].height;
+        pix += np;
+        max_pix = std::max(max_pix, np);
+    }
+    TempBufs tmp(s);
+    DevView *d = nullptr;
+    PBR_TRY(tmp.alloc(&d, sizeof(DevView) * n_cams));
+    PBR_CUDA(cudaMemcpyAsync(d, views.data(), sizeof(DevView) * n_cams, cudaMemcpyHostToDevice, s));
+    launch_loss_tv(d, n_cams, max_pix, loss_kind, lambda_tv, pred, target, grad, loss_dev, s);
+    PBR_CUDA(cudaGetLastError());
+    return PBR_OK;
+}
+
+extern "C" int pbr_optimizer_step(int32_t kind, float *param, const float *grad, float *m,
+                                  float *v, int64_t n, float lr, float beta1, float beta2,
+                                  float eps, int32_t step, pbr_stream_t stream)
+{
+    if ((kind != 0 && kind != 1) || n < 0 || (n > 0 && (!param || !grad)) ||
+        (kind == 1 && n > 0 && (!m || !v || step < 1)))
+        return set_error(PBR_ERR_INVALID_ARG, "pbr_optimizer_step: bad arguments");
+    OptParams prm{kind, lr, beta1, beta2, eps, step};
+    launch_optimizer(prm, nullptr, 0, param, grad, m, v, n, (cudaStream_t)stream);
+    PBR_CUDA(cudaGetLastError());
+    return PBR_OK;
+}
+
 extern "C" int pbr_measure_alu_peaks(int device, double *fp32_flops, double *ex2_ops)
 {
     if (measure_alu_peaks(device, fp32_flops, ex2_ops) != 0)

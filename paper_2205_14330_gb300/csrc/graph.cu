@@ -100,8 +100,15 @@ struct pbr_graph {
     double *own_loss = nullptr;
     uint32_t *keys_final = nullptr, *vals_final = nullptr;
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr}; // forward, backward, step
-    int kernels[3] = {0, 0, 0};
+    cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr}; // fwd, bwd, step, train
+    int kernels[4] = {0, 0, 0, 0};
+    // training phase: optimiser settings, device rates / step, moments
+    bool has_opt = false;
+    pbr_optimizer_cfg opt{};
+    std::vector<void *> opt_allocs; // survive re-planning
+    OptState *d_opt = nullptr;
+    float *m_pos = nullptr, *v_pos = nullptr, *m_sh = nullptr, *v_sh = nullptr;
+    float *m_op = nullptr, *v_op = nullptr;
     unsigned long long *host = nullptr; // pinned status read-back
 
     Batch batch() const
@@ -192,20 +199,48 @@ void enqueue_backward(pbr_graph *g, const float *grad_rgb, cudaStream_t s)
     launch_preprocess_bwd(b, g->dopts, g->g2d, g->grad_pos, g->grad_sh, g->grad_opacity, s);
 }
 
+// Optimiser update of every scene's parameters from the packed gradients.
+void enqueue_optimizer(pbr_graph *g, cudaStream_t s)
+{
+    launch_step_counter(g->d_opt, s);
+    const OptParams prm{g->opt.kind, 0.0f, g->opt.beta1, g->opt.beta2, g->opt.eps, 1};
+    for (const DevScene &sc : g->layout.scenes) {
+        const int64_t n = sc.n;
+        launch_optimizer(prm, g->d_opt, 0, const_cast<float *>(sc.pos), g->grad_pos + 3 * sc.point_base,
+                         g->m_pos + 3 * sc.point_base, g->v_pos + 3 * sc.point_base, 3 * n, s);
+        launch_optimizer(prm, g->d_opt, 1, const_cast<float *>(sc.sh), g->grad_sh + sc.sh_base,
+                         g->m_sh + sc.sh_base, g->v_sh + sc.sh_base, n * sc.K * 3, s);
+        if (g->grad_opacity)
+            launch_optimizer(prm, g->d_opt, 2, const_cast<float *>(sc.opacity),
+                             g->grad_opacity + sc.point_base, g->m_op + sc.point_base,
+                             g->v_op + sc.point_base, n, s);
+    }
+}
+
 int capture(pbr_graph *g, int which, cudaStream_t s)
 {
     cudaGraph_t graph = nullptr;
     const unsigned long long l0 = launches_total();
     PBR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     const float *grad = g->grad_rgb ? g->grad_rgb : g->own_grad;
-    if (which == 0 || which == 2) enqueue_forward(g, s);
+    if (which == 0 || which == 2 || which == 3) enqueue_forward(g, s);
+    double *loss = g->loss_out ? g->loss_out : g->own_loss;
     if (which == 2) {
-        cudaMemsetAsync(g->loss_out ? g->loss_out : g->own_loss, 0, sizeof(double), s);
+        cudaMemsetAsync(loss, 0, sizeof(double), s);
         launch_image_loss(g->loss_kind, g->out_rgb, g->target, g->layout.n_pix * 3, g->own_grad,
-                          g->loss_out ? g->loss_out : g->own_loss, s);
+                          loss, s);
         grad = g->own_grad;
     }
-    if (which == 1 || which == 2) enqueue_backward(g, grad, s);
+    if (which == 3) {
+        int64_t max_pix = 0;
+        for (const DevView &v : g->layout.views) max_pix = std::max<int64_t>(max_pix, (int64_t)v.W * v.H);
+        cudaMemsetAsync(loss, 0, sizeof(double), s);
+        launch_loss_tv(g->d_views, (int)g->layout.views.size(), max_pix, g->opt.loss_kind,
+                       g->opt.lambda_tv, g->out_rgb, g->target, g->own_grad, loss, s);
+        grad = g->own_grad;
+    }
+    if (which == 1 || which == 2 || which == 3) enqueue_backward(g, grad, s);
+    if (which == 3) enqueue_optimizer(g, s);
     const cudaError_t e1 = cudaStreamEndCapture(s, &graph);
     const unsigned long long l1 = launches_total();
     if (e1 != cudaSuccess) {
@@ -309,6 +344,7 @@ int plan_and_capture(pbr_graph *g, cudaStream_t user_stream)
     PBR_TRY(capture(g, 0, g->cap_stream));
     if (want_bwd && (g->grad_rgb || g->target)) PBR_TRY(capture(g, 1, g->cap_stream));
     if (want_bwd && g->target) PBR_TRY(capture(g, 2, g->cap_stream));
+    if (want_bwd && g->target && g->has_opt) PBR_TRY(capture(g, 3, g->cap_stream));
     return PBR_OK;
 }
 
@@ -365,9 +401,60 @@ extern "C" int pbr_graph_create(pbr_ctx *c, const pbr_points *scenes, int32_t n_
     return PBR_OK;
 }
 
+extern "C" int pbr_graph_set_optimizer(pbr_graph *g, const pbr_optimizer_cfg *cfg,
+                                       pbr_stream_t stream)
+{
+    if (!g || !cfg || (cfg->kind != 0 && cfg->kind != 1) || (cfg->loss_kind != 0 && cfg->loss_kind != 1))
+        return set_error(PBR_ERR_INVALID_ARG, "pbr_graph_set_optimizer: bad arguments");
+    if (!g->target || !g->grad_pos || !g->grad_sh)
+        return set_error(PBR_ERR_INVALID_ARG,
+                         "the training phase needs a graph created with a target and gradients");
+    PBR_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    for (void *p : g->opt_allocs) cudaFree(p);
+    g->opt_allocs.clear();
+    const int64_t np = g->layout.n_points_total, nsh = g->layout.n_sh_total;
+    auto al = [&](float **p, int64_t n) -> int {
+        if (cudaMalloc((void **)p, sizeof(float) * (size_t)(n > 0 ? n : 1)) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(PBR_ERR_OOM, "optimiser state");
+        }
+        g->opt_allocs.push_back(*p);
+        cudaMemset(*p, 0, sizeof(float) * (size_t)(n > 0 ? n : 1));
+        return PBR_OK;
+    };
+    PBR_TRY(al(&g->m_pos, 3 * np));
+    PBR_TRY(al(&g->v_pos, 3 * np));
+    PBR_TRY(al(&g->m_sh, nsh));
+    PBR_TRY(al(&g->v_sh, nsh));
+    PBR_TRY(al(&g->m_op, np));
+    PBR_TRY(al(&g->v_op, np));
+    if (cudaMalloc((void **)&g->d_opt, sizeof(OptState)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(PBR_ERR_OOM, "optimiser state");
+    }
+    g->opt_allocs.push_back(g->d_opt);
+    OptState st{{cfg->lr_pos, cfg->lr_sh, cfg->lr_opacity}, 0};
+    PBR_CUDA(cudaMemcpy(g->d_opt, &st, sizeof st, cudaMemcpyHostToDevice));
+    g->opt = *cfg;
+    g->has_opt = true;
+    if (g->exec[3]) {
+        cudaGraphExecDestroy(g->exec[3]);
+        g->exec[3] = nullptr;
+    }
+    return capture(g, 3, g->cap_stream);
+}
+
+extern "C" int pbr_graph_set_lr(pbr_graph *g, float lr_pos, float lr_sh, float lr_opacity)
+{
+    if (!g || !g->d_opt) return set_error(PBR_ERR_INVALID_ARG, "no optimiser on this graph");
+    const float lr[3] = {lr_pos, lr_sh, lr_opacity};
+    PBR_CUDA(cudaMemcpy(g->d_opt, lr, sizeof lr, cudaMemcpyHostToDevice));
+    return PBR_OK;
+}
+
 extern "C" int pbr_graph_launch(pbr_graph *g, int32_t phase, pbr_stream_t stream)
 {
-    if (!g || phase < 0 || phase > 2) return set_error(PBR_ERR_INVALID_ARG, "bad graph or phase");
+    if (!g || phase < 0 || phase > 3) return set_error(PBR_ERR_INVALID_ARG, "bad graph or phase");
     if (!g->exec[phase])
         return set_error(PBR_ERR_INVALID_ARG, "graph phase %d was not captured (backward needs "
                                               "gradient buffers, the step needs a target)", phase);
@@ -431,6 +518,7 @@ extern "C" int pbr_graph_destroy(pbr_graph *g)
     if (!g) return PBR_OK;
     cudaDeviceSynchronize();
     g->release();
+    for (void *p : g->opt_allocs) cudaFree(p);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     if (g->host) cudaFreeHost(g->host);
     delete g;

@@ -149,6 +149,24 @@ void launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, u
                        cudaStream_t s);
 void reset_work_counters(uint32_t *work, cudaStream_t s);
 
+// ---- training step (k_train.cu)
+struct OptParams {
+    int32_t kind;  // 0 SGD, 1 Adam
+    float lr, beta1, beta2, eps;
+    int32_t step;  // 1-based Adam step (eager calls)
+};
+// Device-side rates and step number of a captured training step.
+struct OptState {
+    float lr[3];   // positions, SH coefficients, opacity
+    int32_t step;
+};
+void launch_loss_tv(const DevView *views, int n_views, int64_t max_pix, int kind, float lam,
+                    const float *pred, const float *target, float *grad, double *loss,
+                    cudaStream_t s);
+void launch_optimizer(const OptParams &prm, const OptState *dev, int group, float *p,
+                      const float *g, float *m, float *v, int64_t n, cudaStream_t s);
+void launch_step_counter(OptState *dev, cudaStream_t s);
+
 // ---- misc (k_misc.cu)
 void launch_image_loss(int kind, const float *pred, const float *target, int64_t n, float *grad,
                        double *loss, cudaStream_t s);

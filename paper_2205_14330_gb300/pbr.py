@@ -60,6 +60,13 @@ class StateInfo(C.Structure):
                 ("n_contrib", C.c_void_p)]
 
 
+class OptimizerCfg(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("lr_pos", C.c_float), ("lr_sh", C.c_float),
+                ("lr_opacity", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float), ("lambda_tv", C.c_float), ("loss_kind", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
+
+
 class ServeStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rejected", C.c_int64),
                 ("queued", C.c_int64), ("in_flight_batches", C.c_int64), ("batches", C.c_int64),
@@ -125,6 +132,14 @@ def lib():
             L.pbr_serve_stats.argtypes = [vp, C.POINTER(ServeStats), i32]
             L.pbr_now.restype = C.c_double
             L.pbr_now.argtypes = []
+            L.pbr_default_optimizer.argtypes = [C.POINTER(OptimizerCfg)]
+            L.pbr_default_optimizer.restype = None
+            L.pbr_image_loss_tv.argtypes = [C.POINTER(Camera), i32, vp, vp, i32, C.c_float, vp, vp,
+                                            vp]
+            L.pbr_optimizer_step.argtypes = [i32, vp, vp, vp, vp, i64, C.c_float, C.c_float,
+                                             C.c_float, C.c_float, i32, vp]
+            L.pbr_graph_set_optimizer.argtypes = [vp, C.POINTER(OptimizerCfg), vp]
+            L.pbr_graph_set_lr.argtypes = [vp, C.c_float, C.c_float, C.c_float]
             L.pbr_state_stats.argtypes = [vp, C.POINTER(C.c_ulonglong)]
             L.pbr_kernel_launches.restype = C.c_ulonglong
             L.pbr_kernel_launches.argtypes = []
@@ -338,7 +353,7 @@ class Graph:
     runs forward, the image loss against `target` and backward.  Tensors
     passed here are bound to the graph: update them in place."""
 
-    FORWARD, BACKWARD, STEP = 0, 1, 2
+    FORWARD, BACKWARD, STEP, TRAIN = 0, 1, 2, 3
 
     def __init__(self, renderer, scenes, cams, opts=None, scene_of_view=None, target=None,
                  loss="l2", backward=True, grad_rgb=None, headroom=0.25):
@@ -383,6 +398,16 @@ class Graph:
 
     def replan(self):
         check(lib().pbr_graph_replan(self.handle, _stream()))
+
+    def set_optimizer(self, cfg=None, **kw):
+        """Adds the TRAIN phase (forward, Eq. 8 loss, backward, optimiser
+        update of the scenes' arrays in place)."""
+        cfg = cfg or default_optimizer(**kw)
+        check(lib().pbr_graph_set_optimizer(self.handle, C.byref(cfg), _stream()))
+        self.opt = cfg
+
+    def set_lr(self, lr_pos, lr_sh, lr_opacity=0.0):
+        check(lib().pbr_graph_set_lr(self.handle, float(lr_pos), float(lr_sh), float(lr_opacity)))
 
     def set_cameras(self, cams):
         check(lib().pbr_graph_set_cameras(self.handle, make_cameras(cams), len(cams), _stream()))
@@ -493,6 +518,38 @@ def autotune(renderer, scenes, cams, opts=None, scene_of_view=None, backward=Tru
                              C.byref(n), _stream()))
     table = {TUNE_CANDIDATES[i]: ms[i] for i in range(n.value)} if report else {}
     return opts, table
+
+
+def default_optimizer(**kw) -> OptimizerCfg:
+    c = OptimizerCfg()
+    lib().pbr_default_optimizer(C.byref(c))
+    for k, v in kw.items():
+        if k == "kind":
+            v = {"sgd": 0, "adam": 1}.get(v, v)
+        if k == "loss_kind":
+            v = {"l2": 0, "l1": 1}.get(v, v)
+        cur = getattr(c, k)
+        setattr(c, k, float(v) if isinstance(cur, float) else int(v))
+    return c
+
+
+def image_loss_tv(pred, target, cams, lam=0.01, kind="l2"):
+    """Eq. 8 objective over packed views: (loss, dL/dpred)."""
+    grad = torch.empty_like(pred)
+    loss = torch.zeros(1, dtype=torch.float64, device=pred.device)
+    check(lib().pbr_image_loss_tv(make_cameras(cams), len(cams), _ptr(pred), _ptr(target),
+                                  0 if kind == "l2" else 1, float(lam), _ptr(grad), _ptr(loss),
+                                  _stream()))
+    return loss, grad
+
+
+def optimizer_step(param, grad, m=None, v=None, lr=1e-3, step=1, kind="adam", beta1=0.9,
+                   beta2=0.999, eps=1e-8):
+    """In-place SGD / Adam update of a float32 device tensor."""
+    k = 1 if kind == "adam" else 0
+    check(lib().pbr_optimizer_step(k, _ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(),
+                                   float(lr), float(beta1), float(beta2), float(eps), int(step),
+                                   _stream()))
 
 
 def image_loss(pred, target, kind="l2"):
