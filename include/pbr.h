@@ -358,6 +358,72 @@ int pbr_render_forward_noalloc(const pbr_points *scenes, int32_t n_scenes,
                                int32_t n_cams, const pbr_render_opts *opts, float *out_rgb,
                                pbr_stream_t stream);
 
+/* ----------------------------------------- coarse-to-fine point update */
+/* One pass of the hybrid coarse-to-fine update of Sec. 3.3 ("Hybrid
+ * Coarse-to-Fine Updates") and Algorithm 1, which the paper runs between
+ * training stages:
+ *   1. voxel reduction: the cube anchored at the per-axis minimum of the
+ *      positions, side = their largest per-axis extent, is split into
+ *      n_vox^3 voxels; each non-empty voxel becomes one point whose
+ *      parameters (position, SH, opacity, radius) are the means over the
+ *      voxel's points.  Voxel of p: floor((p - lo) / h) per axis, h = side /
+ *      n_vox, fp32 round-to-nearest, clamped; the reduced points come in
+ *      ascending voxel id (z-major, x fastest).
+ *   2. outlier removal: a reduced point is removed when the population
+ *      standard deviation of the distances to its k nearest other reduced
+ *      points exceeds eps (fp32, sums in neighbour order).  All points are
+ *      judged against the same reduced set.
+ *   3. point generation: every survivor adds one point whose parameters are
+ *      the means over its k nearest other survivors.
+ * Neighbours: ascending fp32 squared distance ((dx dx + dy dy) + dz dz),
+ * ties by lower index; with fewer than k other points all of them are
+ * used, and a point with none is kept (stage 2) and yields nothing
+ * (stage 3).  Positions must be finite with magnitude below 1e18.
+ *   in          : device arrays of the input cloud (pbr_points); the caller
+ *                 keeps ownership; sh_degree fixes K = (sh_degree+1)^2.
+ *   cfg->stages : bit 0 reduction, bit 1 outlier removal, bit 2 generation.
+ *   out_*       : caller-owned device arrays with room for out_capacity
+ *                 points ([cap,3], [cap,K,3], [cap], [cap]); they receive the
+ *                 survivors in reduced order followed by the generated points
+ *                 in the same order.  2 * in->n always suffices.
+ *   counts      : host int64[3]: points after stage 1, after stage 2, and
+ *                 in the output.
+ * Errors: PBR_ERR_INVALID_ARG (null pointer, n_vox outside 1..1024, k
+ * outside 1..32, eps negative or not finite, stages outside 0..7, n >=
+ * 2^31); PBR_ERR_CAPACITY when the output needs more than out_capacity
+ * points (counts are filled, nothing is written to out_*); PBR_ERR_OOM,
+ * PBR_ERR_CUDA.  Synchronises the stream (the point counts are
+ * data-dependent). */
+typedef struct {
+    int32_t n_vox;  /* voxels per axis (Algorithm 1 N), default 256 */
+    int32_t k;      /* neighbours (Algorithm 1 K), default 8 */
+    float eps;      /* threshold on the std of neighbour distances (Algorithm 1
+                       epsilon), world units, default 0.01 */
+    int32_t stages; /* default 7 (all three) */
+} pbr_refine_cfg;
+void pbr_default_refine(pbr_refine_cfg *cfg);
+int pbr_refine_points(pbr_ctx *ctx, const pbr_points *in, const pbr_refine_cfg *cfg,
+                      float *out_pos, float *out_sh, float *out_opacity, float *out_radius,
+                      int64_t out_capacity, int64_t counts[3], pbr_stream_t stream);
+
+/* Exact k nearest neighbours (the neighbour search of Algorithm 1, also
+ * used for the point generation and frame initialisation of Sec. 3.3-3.4):
+ * for each query point the k reference points of smallest fp32 squared
+ * distance ((dx dx + dy dy) + dz dz), ties by lower index, ascending.
+ *   ref_pos [n_ref,3], query_pos [n_query,3]: device, caller-owned.
+ *   self     : 1 = the queries are the reference points (query_pos and
+ *              n_query are ignored) and query i never returns point i.
+ *   grid_n   : cells per axis of the search grid over the reference cube
+ *              (1..1024), 0 = automatic (about 2 n_ref^(1/3)).
+ *   out_idx [n_query,k] int32 and out_d2 [n_query,k] fp32 (device): rows
+ *              padded with -1 / FLT_MAX past the available neighbours.
+ * Errors: PBR_ERR_INVALID_ARG (k outside 1..32, grid_n outside 0..1024,
+ * n_ref >= 2^31, null pointers), PBR_ERR_OOM, PBR_ERR_CUDA.  Asynchronous on
+ * the stream. */
+int pbr_knn(pbr_ctx *ctx, const float *ref_pos, int64_t n_ref, const float *query_pos,
+            int64_t n_query, int32_t k, int32_t self, int32_t grid_n, int32_t *out_idx,
+            float *out_d2, pbr_stream_t stream);
+
 /* ------------------------------------------------------- microbenchmarks */
 /* Measures the device's FP32 FMA rate (flop/s, an FMA counted as 2) and
  * MUFU ex2 rate (op/s) with the library's own kernels; used as the ALU

@@ -508,6 +508,12 @@ void launch_compact_visible(const uint32_t *ntiles, const uint32_t *zbits, int64
              temp, nullptr, nullptr, s);
 }
 
+void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n,
+                           unsigned long long *total, void *temp, cudaStream_t s)
+{
+    run_scan(LoadU32{in}, ActStore{out}, nullptr, n, temp, total, nullptr, s);
+}
+
 size_t radix_temp_bytes(int64_t cap)
 {
     const int64_t nb = (cap + SORT_TILE - 1) / SORT_TILE;

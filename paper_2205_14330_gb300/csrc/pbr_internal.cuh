@@ -110,6 +110,10 @@ size_t scan_temp_bytes(int64_t n);
 void launch_compact_visible(const uint32_t *ntiles, const uint32_t *zbits, int64_t n_pv,
                             uint32_t *keys_out, uint32_t *vals_out, uint32_t *n_vis, void *temp,
                             cudaStream_t s);
+// out[i] = in[0] + ... + in[i-1]; *total (device, may be NULL) = the sum.
+// out may alias in.  Scratch: scan_temp_bytes(n).
+void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n,
+                           unsigned long long *total, void *temp, cudaStream_t s);
 // Radix sort of (key, value) pairs, stable; n read from device *n_dev,
 // capacity cap.  key_bits: number of low key bits that can be non-zero.
 // Sorted result ends in (keys, vals) (buffers are ping-ponged internally).
@@ -130,6 +134,54 @@ void launch_emit_pairs(const Batch &b, const DevOpts &o, const uint32_t *sorted_
                        uint32_t *status, void *temp, cudaStream_t s);
 void launch_tile_ranges(const uint32_t *keys, const uint32_t *n_pairs, int64_t cap_pairs,
                         uint2 *ranges, uint32_t n_tiles, cudaStream_t s);
+
+// ---- coarse-to-fine update and kNN (k_refine.cu)
+// Cube grid over a point set: origin lo, cell side h (0 when all points
+// coincide), n cells per axis, absolute slack of the kNN stop test.
+struct GridParams {
+    float lo[3];
+    float h;
+    int32_t n;
+    float slack;
+};
+// Per-point parameter arrays: pos [n,3], sh [n,nsh], opacity [n], radius [n].
+struct PointArrays {
+    const float *pos, *sh, *op, *rad;
+    int nsh;
+};
+struct PointArraysOut {
+    float *pos, *sh, *op, *rad;
+    int nsh;
+};
+size_t grid_temp_bytes();
+void launch_grid_params(const float *pos, int64_t n, int n_cells, GridParams *gp, void *temp,
+                        cudaStream_t s);
+// keys = clamped cell ids, vals = 0..n-1
+void launch_cell_ids(const float *pos, int64_t n, const GridParams *gp, uint32_t *keys,
+                     uint32_t *vals, cudaStream_t s);
+// Runs of equal sorted keys: starts[r] = first index of run r, *n_runs.
+// flags: n words of scratch; scan_temp: scan_temp_bytes(n).
+void launch_run_starts(const uint32_t *keys, int64_t n, uint32_t *flags, uint32_t *starts,
+                       unsigned long long *n_runs, void *scan_temp, cudaStream_t s);
+void launch_voxel_mean(const uint32_t *order, const uint32_t *starts, int64_t n_runs, int64_t n,
+                       const PointArrays &in, const PointArraysOut &out, cudaStream_t s);
+// K nearest reference points per query (rid/ridx: reference cell ids and
+// indices sorted by id); rows of k entries, keff = entries filled.
+void launch_knn(const float *qpos, int64_t nq, const float *rpos, const uint32_t *rid,
+                const uint32_t *ridx, int64_t nr, const GridParams *gp, int k, int keff,
+                int self_mode, int32_t *out_idx, float *out_d2, cudaStream_t s);
+void launch_outlier_flags(const float *d2, int64_t n, int k, int keff, float eps, uint32_t *keep,
+                          cudaStream_t s);
+void launch_compact_points(const uint32_t *keep, const uint32_t *pos, int64_t n,
+                           const PointArrays &in, const PointArraysOut &out, cudaStream_t s);
+// Restricts a sorted (id, index) list to kept points, renumbering indices
+// with newpos (the exclusive scan of keep).  flags: n words of scratch.
+void launch_list_keep(const uint32_t *rid, const uint32_t *ridx, const uint32_t *keep,
+                      const uint32_t *newpos, int64_t n, uint32_t *flags, uint32_t *rid_out,
+                      uint32_t *ridx_out, void *scan_temp, cudaStream_t s);
+void launch_fill_u32(uint32_t *p, int64_t n, uint32_t v, cudaStream_t s);
+void launch_generate(const int32_t *nbr, int64_t n, int k, int keff, const PointArrays &in,
+                     const PointArraysOut &out, int64_t out_base, cudaStream_t s);
 
 // ---- raster (k_raster.cu)
 // batch_depth 0 = warp-streamed, > 0 = block-staged.  With order/work set

@@ -67,6 +67,11 @@ class OptimizerCfg(C.Structure):
                 ("reserved", C.c_int32 * 3)]
 
 
+class RefineCfg(C.Structure):
+    _fields_ = [("n_vox", C.c_int32), ("k", C.c_int32), ("eps", C.c_float),
+                ("stages", C.c_int32)]
+
+
 class ServeStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rejected", C.c_int64),
                 ("queued", C.c_int64), ("in_flight_batches", C.c_int64), ("batches", C.c_int64),
@@ -148,6 +153,11 @@ def lib():
                                           C.c_int]
             L.pbr_measure_alu_peaks.argtypes = [C.c_int, C.POINTER(C.c_double),
                                                 C.POINTER(C.c_double)]
+            L.pbr_default_refine.restype = None
+            L.pbr_default_refine.argtypes = [C.POINTER(RefineCfg)]
+            L.pbr_refine_points.argtypes = [vp, C.POINTER(Points), C.POINTER(RefineCfg), vp, vp,
+                                            vp, vp, i64, C.POINTER(i64), vp]
+            L.pbr_knn.argtypes = [vp, vp, i64, vp, i64, i32, i32, i32, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -563,6 +573,43 @@ def image_loss(pred, target, kind="l2"):
 
 def kernel_launches() -> int:
     return int(lib().pbr_kernel_launches())
+
+
+def refine_points(renderer, scene, n_vox=256, k=8, eps=0.01, stages=7):
+    """One pass of the coarse-to-fine update (Sec. 3.3, Algorithm 1) of a
+    Scene.  Returns (Scene of the result, (after reduction, after outlier
+    removal, output) point counts)."""
+    cfg = RefineCfg()
+    lib().pbr_default_refine(C.byref(cfg))
+    cfg.n_vox, cfg.k, cfg.eps, cfg.stages = int(n_vox), int(k), float(eps), int(stages)
+    cap = max(1, 2 * scene.n)
+    K = (scene.deg + 1) ** 2
+    dev = scene.pos.device
+    pos = torch.empty((cap, 3), dtype=torch.float32, device=dev)
+    sh = torch.empty((cap, K, 3), dtype=torch.float32, device=dev)
+    op = torch.empty(cap, dtype=torch.float32, device=dev)
+    rad = torch.empty(cap, dtype=torch.float32, device=dev)
+    counts = (C.c_int64 * 3)()
+    pts = scene.points()
+    check(lib().pbr_refine_points(renderer.ctx, C.byref(pts), C.byref(cfg), _ptr(pos), _ptr(sh),
+                                  _ptr(op), _ptr(rad), cap, counts, _stream()))
+    m = int(counts[2])
+    out = Scene(pos[:m], sh[:m], op[:m], rad[:m], scene.deg, device=dev)
+    return out, (int(counts[0]), int(counts[1]), m)
+
+
+def knn(renderer, ref, k, query=None, grid_n=0):
+    """k nearest points of `ref` ([n,3] fp32 device) for every query point
+    (query None: the points of ref themselves, each skipping itself).
+    Returns (idx [nq,k] int32, d2 [nq,k] fp32), padded with -1 / FLT_MAX."""
+    ref = ref.contiguous()
+    q = ref if query is None else query.contiguous()
+    nq = int(q.shape[0])
+    idx = torch.empty((nq, k), dtype=torch.int32, device=ref.device)
+    d2 = torch.empty((nq, k), dtype=torch.float32, device=ref.device)
+    check(lib().pbr_knn(renderer.ctx, _ptr(ref), int(ref.shape[0]), _ptr(q), nq, int(k),
+                        1 if query is None else 0, int(grid_n), _ptr(idx), _ptr(d2), _stream()))
+    return idx, d2
 
 
 def measure_alu_peaks(device: int = 0):

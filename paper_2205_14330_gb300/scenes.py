@@ -185,6 +185,22 @@ def batched_multiview(seed=0, n=1_000_000, n_cams=64, deg=3, resolutions=None):
     return _scene(pos, sh, opacity, radius, deg, cams)
 
 
+def refine_cloud(seed=0, n=1_000_000, n_shapes=40, outlier_frac=0.01, deg=3):
+    """Input of one coarse-to-fine update (Sec. 3.3): surface samples of
+    `n_shapes` random shapes (as in batched_multiview) plus a fraction of
+    uniform outliers in [-1.5, 1.5]^3, SH of degree `deg`, radii
+    log-uniform in [0.003, 0.01], opacity 0.8."""
+    rng = rng_for(seed)
+    n_out = int(round(n * outlier_frac))
+    pos = np.concatenate([surface_points(rng, n - n_out, n_shapes),
+                          rng.uniform(-1.5, 1.5, (n_out, 3)).astype(np.float32)])
+    pos = pos[rng.permutation(n)]
+    sh = sh_coeffs(rng, n, deg)
+    radius = log_uniform(rng, n, 0.003, 0.01)
+    opacity = np.full(n, 0.8, np.float32)
+    return dict(pos=pos, sh=sh, opacity=opacity, radius=radius, deg=deg)
+
+
 def dynamic_video(seed=0, n=200_000, frames=30, n_cams=16, width=1024, height=768, deg=2):
     """Base cloud of 200k surface points deformed per frame by the sum of four
     seeded sinusoidal displacement fields (amplitude 0.05); SH degree 2;
