@@ -23,9 +23,9 @@ Readings where the paper leaves details open (each implemented below):
      voxel 0.
   R2 reduction: every per-point parameter is replaced by the plain mean over
      the voxel; output in ascending voxel id.  The position mean feeds later
-     distance decisions, so it is formed in fp32: a sequential sum over the
-     voxel's points in ascending input index, divided by the count.  The
-     other means are taken in fp64.
+     distance decisions, so its rounding is fixed: an fp64 sequential sum
+     over the voxel's points in ascending input index, divided by the count
+     in fp64 and rounded to fp32.  The other means are plain fp64 means.
   R3 neighbours: the K nearest OTHER points of the same set, by fp32 squared
      distance ((dx dx + dy dy) + dz dz) with dx = x_j - x_i, ties broken by
      lower index, in ascending (distance, index) order; K_eff = min(K, n-1).
@@ -96,12 +96,12 @@ def voxel_reduce(pos, sh, opacity, radius, n_vox):
     sid = ids[order]
     starts = np.flatnonzero(np.r_[True, sid[1:] != sid[:-1]])
     counts = np.diff(np.r_[starts, n])
-    # fp32 sequential sums: add the r-th member of every voxel at step r
-    acc = np.zeros((starts.size, 3), F32)
+    # fp64 sequential sums: add the r-th member of every voxel at step r
+    acc = np.zeros((starts.size, 3), np.float64)
     for r in range(int(counts.max())):
         sel = counts > r
-        acc[sel] = acc[sel] + p[order[starts[sel] + r]]
-    pos_out = acc / counts.astype(F32)[:, None]
+        acc[sel] = acc[sel] + p[order[starts[sel] + r]].astype(np.float64)
+    pos_out = (acc / counts.astype(np.float64)[:, None]).astype(F32)
 
     def mean64(a):
         a = np.asarray(a, np.float64)[order]
@@ -146,9 +146,16 @@ def knn(pos, k, ref=None, exclude_self=True, chunk=256):
 def outlier_delta(pos, k):
     """R4: delta of every point (fp32), and K_eff."""
     _, d2 = knn(pos, k)
+    return delta_of(d2), d2.shape[1]
+
+
+def delta_of(d2):
+    """R4: delta from rows of neighbour squared distances in ascending
+    order ([n, K_eff] fp32)."""
+    d2 = np.asarray(d2, F32)
     n, keff = d2.shape
     if keff == 0:
-        return np.zeros(n, F32), 0
+        return np.zeros(n, F32)
     d = np.sqrt(d2)
     s = np.zeros(n, F32)
     for j in range(keff):
@@ -158,7 +165,7 @@ def outlier_delta(pos, k):
     for j in range(keff):
         e = d[:, j] - mean
         t = t + e * e
-    return np.sqrt(t / F32(keff)), keff
+    return np.sqrt(t / F32(keff))
 
 
 def outlier_keep(pos, k, eps):
