@@ -327,7 +327,9 @@ unsigned long long pbr_kernel_launches(void);
 /* Switches per-stage CUDA-event timing on (enable = 1) or off for the
  * context's forward and backward calls.  Stages: 0 preprocess, 1 compact,
  * 2 depth sort, 3 emit pairs, 4 tile sort, 5 tile ranges, 6 raster forward,
- * 7 raster backward (with its zeroing), 8 preprocess backward, 9 other. */
+ * 7 raster backward (with its zeroing), 8 preprocess backward, 9 other;
+ * pbr_refine_points: 10 voxel reduction, 11 neighbour searches, 12 the rest
+ * (grid, outlier filter, compaction, generation). */
 int pbr_set_stage_timing(pbr_ctx *ctx, int enable);
 /* Accumulated milliseconds and call counts per stage since the last query
  * (arrays of n entries); resets the accumulators.  Synchronises. */

@@ -15,12 +15,18 @@
 // d2 = (dx dx + dy dy) + dz dz in fp32 round-to-nearest, ties by lower
 // index.  The search visits cubic shells of cells around the query's cell,
 // r = r0, r0 + 1, ...; shell r is (2r+1)^2 rows along x (a whole row where
-// |dy| or |dz| is r, else the row's two end cells).  The points of a run of
-// consecutive cells are a contiguous slice of the id-sorted array, found by
-// binary search.  Once shell r is done every unvisited point lies more than
-// r h away along some axis, so the search stops when the K-th best d2 is
-// below (r h)^2, less a relative slack for the roundings of d2 and an
-// absolute one for the cell coordinates, or when every cell has been seen.
+// |dy| or |dz| is r, else the row's two end cells), one row per lane.  The
+// points of a run of consecutive cells are a contiguous slice of the
+// id-sorted array, read from a dense cell-start table (binary search when
+// the grid is too large for one).  Runs of up to 32 points are walked by
+// their lanes side by side, longer ones by the whole warp.  Once shell r is
+// done every unvisited point lies beyond a face of the visited cube of
+// cells, so the search stops when the K-th best d2 is below the squared
+// distance to the nearest such face (less a relative slack for the
+// roundings of d2 and an absolute one for the cell coordinates), or when
+// every cell has been seen.  A query still open after a fixed number of
+// shells (neighbours across a wide empty region) is finished by an
+// exhaustive scan, one block per query.
 //
 // Outlier removal: per point, the population standard deviation of its K
 // neighbour distances, fp32 sums in neighbour order; survivors are
@@ -209,16 +215,11 @@ __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t *__restrict__
     return lo;
 }
 
-// Cells between coordinate c and the grid [0, n-1] along one axis, and the
-// shell radius that reaches the grid's far end from c.
+// Cells between coordinate c and the grid [0, n-1] along one axis.
 __device__ __forceinline__ int axis_gap(int c, int n)
 {
     if (c < 0) return -c;
     return c > n - 1 ? c - (n - 1) : 0;
-}
-__device__ __forceinline__ int axis_span(int c, int n)
-{
-    return c > n - 1 - c ? c : n - 1 - c;
 }
 
 // Inserts (cd, cj) into the warp's sorted list (lane j = j-th best, j <
@@ -243,66 +244,137 @@ __device__ __forceinline__ void knn_insert(float &bd, uint32_t &bi, float cd, ui
     ki = __shfl_sync(FULL, bi, keff - 1);
 }
 
-// Visits the sorted slice of cells with ids [id_lo, id_hi] starting at
-// index `start`, 32 points per step.
-__device__ __forceinline__ void knn_scan_run(uint32_t start, uint32_t id_hi,
-                                             const uint32_t *__restrict__ rid,
-                                             const uint32_t *__restrict__ ridx,
-                                             const float *__restrict__ rpos, uint32_t nr,
-                                             float qx, float qy, float qz, uint32_t self_idx,
-                                             int keff, uint32_t kmask, int lane, float &bd,
-                                             uint32_t &bi, float &kd, uint32_t &ki)
+// Index range [s, t) of the points in cells [a, b] (consecutive ids) of
+// the sorted list: from the dense cell-start table when there is one, else
+// by binary search for s and a galloping search for t.
+__device__ __forceinline__ void cell_range(const uint32_t *__restrict__ cs,
+                                           const uint32_t *__restrict__ rid, uint32_t nr,
+                                           uint32_t a, uint32_t b, uint32_t &s, uint32_t &t)
 {
-    for (uint32_t j0 = start;; j0 += 32) {
-        const uint32_t j = j0 + lane;
-        const bool in_run = j < nr && __ldg(rid + j) <= id_hi;
-        uint32_t ri = 0;
-        float d2 = FLT_MAX;
-        bool ok = false;
-        if (in_run) {
-            ri = __ldg(ridx + j);
-            ok = ri != self_idx;
-            if (ok) d2 = sq_dist(qx, qy, qz, __ldg(rpos + 3 * (size_t)ri),
-                                 __ldg(rpos + 3 * (size_t)ri + 1), __ldg(rpos + 3 * (size_t)ri + 2));
-        }
-        const bool better = ok && (d2 < kd || (d2 == kd && ri < ki));
-        uint32_t m = __ballot_sync(FULL, better);
-        while (m) {
-            const int src = __ffs(m) - 1;
-            m &= m - 1;
-            const float cd = __shfl_sync(FULL, d2, src);
-            const uint32_t cj = __shfl_sync(FULL, ri, src);
-            knn_insert(bd, bi, cd, cj, keff, kmask, lane, kd, ki);
-        }
-        if (!__all_sync(FULL, in_run)) break;
+    if (cs) {
+        s = __ldg(cs + a);
+        t = __ldg(cs + b + 1);
+        return;
+    }
+    s = lower_bound_u32(rid, nr, a);
+    if (s >= nr || __ldg(rid + s) > b) {
+        t = s;
+        return;
+    }
+    uint32_t lo = s, step = 1, hi = s + 1; // rid[lo] <= b
+    while (hi < nr && __ldg(rid + hi) <= b) {
+        lo = hi;
+        step <<= 1;
+        hi = s + step;
+    }
+    if (hi > nr) hi = nr;
+    while (hi - lo > 1) { // rid[lo] <= b, hi == nr or rid[hi] > b
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(rid + mid) <= b) lo = mid;
+        else hi = mid;
+    }
+    t = hi;
+}
+
+// Candidate j of the sorted list against the query: squared distance and
+// whether it would enter the current list.
+__device__ __forceinline__ bool knn_candidate(uint32_t j, const uint32_t *__restrict__ ridx,
+                                              const float *__restrict__ rpos, float qx, float qy,
+                                              float qz, uint32_t self_idx, float kd, uint32_t ki,
+                                              float &d2, uint32_t &ri)
+{
+    ri = __ldg(ridx + j);
+    if (ri == self_idx) return false;
+    d2 = sq_dist(qx, qy, qz, __ldg(rpos + 3 * (size_t)ri), __ldg(rpos + 3 * (size_t)ri + 1),
+                 __ldg(rpos + 3 * (size_t)ri + 2));
+    return d2 < kd || (d2 == kd && ri < ki);
+}
+
+// Inserts the candidates of the lanes set in m, lowest lane first.
+__device__ __forceinline__ void knn_insert_all(uint32_t m, float d2, uint32_t ri, float &bd,
+                                               uint32_t &bi, int keff, uint32_t kmask, int lane,
+                                               float &kd, uint32_t &ki)
+{
+    while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const float cd = __shfl_sync(FULL, d2, src);
+        const uint32_t cj = __shfl_sync(FULL, ri, src);
+        knn_insert(bd, bi, cd, cj, keff, kmask, lane, kd, ki);
     }
 }
 
-// One warp per query.  self_mode: the queries are the reference points
-// (query q is reference q and is skipped; its cell is clamped like theirs).
-__global__ void __launch_bounds__(256)
-knn_kernel(const float *__restrict__ qpos, int64_t nq, const float *__restrict__ rpos,
-           const uint32_t *__restrict__ rid, const uint32_t *__restrict__ ridx, uint32_t nr,
-           const GridParams *__restrict__ gp, int k, int keff, int self_mode,
-           int32_t *__restrict__ out_idx, float *__restrict__ out_d2)
+// Lower bound on the distance from the query to any point of a cell
+// outside the cube of cells [c - r, c + r] (per axis), counting only faces
+// with grid cells beyond them; FLT_MAX when the cube covers the grid.  The
+// slack covers the rounding of cell coordinates and face positions.
+__device__ __forceinline__ float unvisited_bound(const GridParams &g, int r, int cx, int cy,
+                                                 int cz, float qx, float qy, float qz)
 {
-    const GridParams g = *gp;
+    const int c[3] = {cx, cy, cz};
+    const float q[3] = {qx, qy, qz};
+    float bound = FLT_MAX;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (c[a] - r > 0)
+            bound = fminf(bound, q[a] - (g.lo[a] + (float)(c[a] - r) * g.h));
+        if (c[a] + r < g.n - 1)
+            bound = fminf(bound, (g.lo[a] + (float)(c[a] + r + 1) * g.h) - q[a]);
+    }
+    return bound == FLT_MAX ? FLT_MAX : bound * 0.99999f - g.slack;
+}
+
+// Writes the warp's list (lane j = j-th best) as row q of the output.
+__device__ __forceinline__ void knn_write(int64_t q, int k, int keff, int lane, float bd,
+                                          uint32_t bi, int32_t *__restrict__ out_idx,
+                                          float *__restrict__ out_d2)
+{
+    if (lane < k) {
+        const bool have = lane < keff;
+        out_idx[q * k + lane] = have ? (int32_t)bi : -1;
+        out_d2[q * k + lane] = have ? bd : FLT_MAX;
+    }
+}
+
+// Shells searched on one grid before a query moves on (to the coarser grid,
+// then to the exhaustive kernel): a query whose neighbours lie across a wide
+// empty region would otherwise walk (2r+1)^2 rows per shell alone while the
+// rest of the GPU idles.
+constexpr int KNN_MAX_SHELLS = 16;
+
+// One warp per query.  Queries are 0..nq-1, or qlist[0..*nq_dev) when qlist
+// is set.  self_mode: the queries are the reference points (query q is
+// reference q and is skipped; its cell is clamped like theirs).  Queries
+// still open after KNN_MAX_SHELLS shells are appended to `defer` (count in
+// *n_defer) and their rows left unwritten.
+__global__ void __launch_bounds__(256)
+knn_kernel(const float *__restrict__ qpos, int64_t nq_all, const uint32_t *__restrict__ qlist,
+           const uint32_t *__restrict__ nq_dev, const float *__restrict__ rpos, uint32_t nr,
+           KnnGrid grid, int k, int keff, int self_mode, int32_t *__restrict__ out_idx,
+           float *__restrict__ out_d2, uint32_t *__restrict__ defer, uint32_t *__restrict__ n_defer)
+{
+    const GridParams g = *grid.gp;
+    const uint32_t *__restrict__ rid = grid.rid;
+    const uint32_t *__restrict__ ridx = grid.ridx;
+    const uint32_t *__restrict__ cs = grid.cs;
     const int lane = threadIdx.x & 31;
     const int n = g.n;
     const uint32_t kmask = keff >= 32 ? FULL : ((1u << keff) - 1u);
-    for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq;
-         q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t nq = qlist ? (int64_t)*nq_dev : nq_all;
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nq;
+         t += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t q = qlist ? (int64_t)qlist[t] : t;
         const float qx = qpos[3 * q], qy = qpos[3 * q + 1], qz = qpos[3 * q + 2];
         const uint32_t self_idx = self_mode ? (uint32_t)q : 0xffffffffu;
         float bd = FLT_MAX, kd = FLT_MAX;
         uint32_t bi = 0xffffffffu, ki = 0xffffffffu;
+        bool keff_done = true;
         if (keff > 0) {
             const int cx = cell_coord(qx, g.lo[0], g.h, n, self_mode);
             const int cy = cell_coord(qy, g.lo[1], g.h, n, self_mode);
             const int cz = cell_coord(qz, g.lo[2], g.h, n, self_mode);
-            // first shell that meets the grid, last shell needed to cover it
+            // first shell that meets the grid
             const int r0 = max(axis_gap(cx, n), max(axis_gap(cy, n), axis_gap(cz, n)));
-            const int rmax = max(axis_span(cx, n), max(axis_span(cy, n), axis_span(cz, n)));
             for (int r = r0;; ++r) {
                 // rows (dy, dz) of shell r that meet the grid
                 const int dy0 = max(-r, -cy), dy1 = min(r, n - 1 - cy);
@@ -310,63 +382,133 @@ knn_kernel(const float *__restrict__ qpos, int64_t nq, const float *__restrict__
                 const int ny = dy1 - dy0 + 1;
                 const int rows = ny * (dz1 - dz0 + 1);
                 for (int base = 0; base < rows; base += 32) {
-                    // this lane's row: up to two runs of cells
+                    // this lane's row: up to two index ranges of the sorted list
                     const int row = base + lane;
-                    uint32_t s0 = 0xffffffffu, e0 = 0, s1 = 0xffffffffu, e1 = 0;
+                    uint32_t s0 = 0, t0 = 0, s1 = 0, t1 = 0;
                     if (row < rows) {
                         const int dy = dy0 + row % ny, dz = dz0 + row / ny;
-                        const int yy = cy + dy, zz = cz + dz;
-                        {
-                            const uint32_t rb = ((uint32_t)zz * (uint32_t)n + (uint32_t)yy) *
-                                                (uint32_t)n;
-                            if (abs(dy) == r || abs(dz) == r) {
-                                const int x0 = max(cx - r, 0), x1 = min(cx + r, n - 1);
-                                if (x0 <= x1) {
-                                    e0 = rb + (uint32_t)x1;
-                                    s0 = lower_bound_u32(rid, nr, rb + (uint32_t)x0);
-                                }
-                            } else {
-                                if (cx - r >= 0 && cx - r < n) {
-                                    e0 = rb + (uint32_t)(cx - r);
-                                    s0 = lower_bound_u32(rid, nr, e0);
-                                }
-                                if (cx + r >= 0 && cx + r < n) {
-                                    e1 = rb + (uint32_t)(cx + r);
-                                    s1 = lower_bound_u32(rid, nr, e1);
-                                }
-                            }
-                            // empty runs (the first id at or after the run's
-                            // start is past its end) are dropped here
-                            if (s0 < nr && __ldg(rid + s0) > e0) s0 = 0xffffffffu;
-                            if (s1 < nr && __ldg(rid + s1) > e1) s1 = 0xffffffffu;
+                        const uint32_t rb =
+                            ((uint32_t)(cz + dz) * (uint32_t)n + (uint32_t)(cy + dy)) * (uint32_t)n;
+                        if (abs(dy) == r || abs(dz) == r) {
+                            const int x0 = max(cx - r, 0), x1 = min(cx + r, n - 1);
+                            if (x0 <= x1)
+                                cell_range(cs, rid, nr, rb + (uint32_t)x0, rb + (uint32_t)x1, s0, t0);
+                        } else {
+                            if (cx - r >= 0 && cx - r < n)
+                                cell_range(cs, rid, nr, rb + (uint32_t)(cx - r),
+                                           rb + (uint32_t)(cx - r), s0, t0);
+                            if (cx + r >= 0 && cx + r < n)
+                                cell_range(cs, rid, nr, rb + (uint32_t)(cx + r),
+                                           rb + (uint32_t)(cx + r), s1, t1);
                         }
                     }
+                    // runs longer than a warp: the whole warp, 32 points a step
+#pragma unroll
                     for (int part = 0; part < 2; ++part) {
-                        const uint32_t st = part ? s1 : s0, en = part ? e1 : e0;
-                        uint32_t m = __ballot_sync(FULL, st < nr);
+                        const uint32_t st = part ? s1 : s0, en = part ? t1 : t0;
+                        uint32_t m = __ballot_sync(FULL, en - st > 32u);
                         while (m) {
                             const int src = __ffs(m) - 1;
                             m &= m - 1;
-                            const uint32_t s_run = __shfl_sync(FULL, st, src);
-                            const uint32_t e_run = __shfl_sync(FULL, en, src);
-                            knn_scan_run(s_run, e_run, rid, ridx, rpos, nr, qx, qy, qz, self_idx,
-                                         keff, kmask, lane, bd, bi, kd, ki);
+                            const uint32_t rs = __shfl_sync(FULL, st, src);
+                            const uint32_t re = __shfl_sync(FULL, en, src);
+                            for (uint32_t j0 = rs; j0 < re; j0 += 32) {
+                                const uint32_t j = j0 + lane;
+                                float d2 = FLT_MAX;
+                                uint32_t ri = 0;
+                                const bool better = j < re && knn_candidate(j, ridx, rpos, qx, qy, qz,
+                                                                            self_idx, kd, ki, d2, ri);
+                                knn_insert_all(__ballot_sync(FULL, better), d2, ri, bd, bi, keff,
+                                               kmask, lane, kd, ki);
+                            }
                         }
                     }
+                    // short runs: every lane walks its own, one point a step
+                    if (t0 - s0 > 32u) s0 = t0;
+                    if (t1 - s1 > 32u) s1 = t1;
+                    while (true) {
+                        const bool has = s0 < t0 || s1 < t1;
+                        if (!__any_sync(FULL, has)) break;
+                        float d2 = FLT_MAX;
+                        uint32_t ri = 0;
+                        bool better = false;
+                        if (has) {
+                            const uint32_t j = s0 < t0 ? s0++ : s1++;
+                            better = knn_candidate(j, ridx, rpos, qx, qy, qz, self_idx, kd, ki, d2, ri);
+                        }
+                        knn_insert_all(__ballot_sync(FULL, better), d2, ri, bd, bi, keff, kmask,
+                                       lane, kd, ki);
+                    }
                 }
-                if (r >= rmax) break;
-                if (kd < FLT_MAX) {
-                    const float bound = __fsub_rn(__fmul_rn((float)r * g.h, 0.99999f), g.slack);
-                    if (bound > 0.0f && kd < __fmul_rn(bound, bound)) break;
+                const float bound = unvisited_bound(g, r, cx, cy, cz, qx, qy, qz);
+                if (bound == FLT_MAX) break; // every cell visited
+                if (kd < FLT_MAX && bound > 0.0f && kd < __fmul_rn(bound, bound)) break;
+                if (r - r0 + 1 >= KNN_MAX_SHELLS) {
+                    if (lane == 0) defer[atomicAdd(n_defer, 1u)] = (uint32_t)q;
+                    keff_done = false;
+                    break;
                 }
             }
         }
-        if (lane < k) {
-            const bool have = lane < keff;
-            out_idx[q * k + lane] = have ? (int32_t)bi : -1;
-            out_d2[q * k + lane] = have ? bd : FLT_MAX;
-        }
+        if (keff_done) knn_write(q, k, keff, lane, bd, bi, out_idx, out_d2);
     }
+}
+
+// Deferred queries, one block each: its 8 warps scan every reference point
+// (warp w takes points w*32 + lane, w*32 + lane + 256, ...) into their own
+// lists, which warp 0 then merges.  Exact, like the grid search.
+__global__ void __launch_bounds__(256)
+knn_exhaustive_kernel(const float *__restrict__ qpos, const float *__restrict__ rpos, uint32_t nr,
+                      int k, int keff, int self_mode, const uint32_t *__restrict__ defer,
+                      const uint32_t *__restrict__ n_defer, int32_t *__restrict__ out_idx,
+                      float *__restrict__ out_d2)
+{
+    __shared__ float s_d[8][32];
+    __shared__ uint32_t s_i[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t kmask = keff >= 32 ? FULL : ((1u << keff) - 1u);
+    const uint32_t nd = *n_defer;
+    for (uint32_t t = blockIdx.x; t < nd; t += gridDim.x) {
+        const uint32_t q = defer[t];
+        const float qx = qpos[3 * (size_t)q], qy = qpos[3 * (size_t)q + 1],
+                    qz = qpos[3 * (size_t)q + 2];
+        const uint32_t self_idx = self_mode ? q : 0xffffffffu;
+        float bd = FLT_MAX, kd = FLT_MAX;
+        uint32_t bi = 0xffffffffu, ki = 0xffffffffu;
+        for (uint32_t j0 = (uint32_t)w * 32; j0 < nr; j0 += 256) {
+            const uint32_t j = j0 + lane;
+            float d2 = FLT_MAX;
+            bool better = false;
+            if (j < nr && j != self_idx) {
+                d2 = sq_dist(qx, qy, qz, __ldg(rpos + 3 * (size_t)j), __ldg(rpos + 3 * (size_t)j + 1),
+                             __ldg(rpos + 3 * (size_t)j + 2));
+                better = d2 < kd || (d2 == kd && j < ki);
+            }
+            knn_insert_all(__ballot_sync(FULL, better), d2, j, bd, bi, keff, kmask, lane, kd, ki);
+        }
+        s_d[w][lane] = bd;
+        s_i[w][lane] = bi;
+        __syncthreads();
+        if (w == 0) {
+            for (int v = 1; v < 8; ++v) {
+                const float d2 = s_d[v][lane];
+                const uint32_t ri = s_i[v][lane];
+                const bool better = lane < keff && (d2 < kd || (d2 == kd && ri < ki));
+                knn_insert_all(__ballot_sync(FULL, better), d2, ri, bd, bi, keff, kmask, lane, kd,
+                               ki);
+            }
+            knn_write(q, k, keff, lane, bd, bi, out_idx, out_d2);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void cell_count_kernel(const uint32_t *__restrict__ rid, int64_t n,
+                                  uint32_t *__restrict__ count)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(count + rid[i], 1u);
 }
 
 // ---------------------------------------------------------- outliers
@@ -514,14 +656,41 @@ void launch_voxel_mean(const uint32_t *order, const uint32_t *starts, int64_t n_
     count_launches(1);
 }
 
-void launch_knn(const float *qpos, int64_t nq, const float *rpos, const uint32_t *rid,
-                const uint32_t *ridx, int64_t nr, const GridParams *gp, int k, int keff,
-                int self_mode, int32_t *out_idx, float *out_d2, cudaStream_t s)
+size_t knn_temp_bytes(int64_t nq) { return sizeof(uint32_t) * (size_t)(2 * nq + 2); }
+
+void launch_knn(const float *qpos, int64_t nq, const float *rpos, int64_t nr, const KnnGrid &fine,
+                const KnnGrid *coarse, int k, int keff, int self_mode, int32_t *out_idx,
+                float *out_d2, void *temp, cudaStream_t s)
 {
     if (nq <= 0) return;
-    knn_kernel<<<grid_for(nq, 8, MAX_BLOCKS), 256, 0, s>>>(qpos, nq, rpos, rid, ridx, (uint32_t)nr,
-                                                          gp, k, keff, self_mode, out_idx, out_d2);
-    count_launches(1);
+    uint32_t *cnt = (uint32_t *)temp, *d1 = cnt + 2, *d2 = d1 + nq;
+    cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), s);
+    knn_kernel<<<grid_for(nq, 8, MAX_BLOCKS), 256, 0, s>>>(qpos, nq, nullptr, nullptr, rpos,
+                                                          (uint32_t)nr, fine, k, keff, self_mode,
+                                                          out_idx, out_d2, d1, cnt);
+    const uint32_t *last = d1, *n_last = cnt;
+    if (coarse) {
+        knn_kernel<<<grid_for(nq, 8, 152 * 8), 256, 0, s>>>(qpos, 0, d1, cnt, rpos, (uint32_t)nr,
+                                                          *coarse, k, keff, self_mode, out_idx,
+                                                          out_d2, d2, cnt + 1);
+        last = d2;
+        n_last = cnt + 1;
+        count_launches(1);
+    }
+    knn_exhaustive_kernel<<<304, 256, 0, s>>>(qpos, rpos, (uint32_t)nr, k, keff, self_mode, last,
+                                              n_last, out_idx, out_d2);
+    count_launches(2);
+}
+
+void launch_cell_start(const uint32_t *rid, int64_t n, int64_t n_cells_total,
+                       uint32_t *cell_start, void *scan_temp, cudaStream_t s)
+{
+    cudaMemsetAsync(cell_start, 0, sizeof(uint32_t) * (size_t)(n_cells_total + 1), s);
+    if (n > 0) {
+        cell_count_kernel<<<grid_for(n, 256, MAX_BLOCKS), 256, 0, s>>>(rid, n, cell_start);
+        count_launches(1);
+    }
+    launch_exclusive_scan(cell_start, cell_start, n_cells_total + 1, nullptr, scan_temp, s);
 }
 
 void launch_outlier_flags(const float *d2, int64_t n, int k, int keff, float eps, uint32_t *keep,

@@ -79,6 +79,9 @@ enum Stage : int {
     STG_RASTER_BWD,
     STG_PREPROCESS_BWD,
     STG_OTHER,
+    STG_VOXEL_REDUCE, // coarse-to-fine update: voxel reduction
+    STG_KNN,          // coarse-to-fine update: neighbour searches
+    STG_REFINE_OTHER, // coarse-to-fine update: grid, filter, compaction, generation
     STG_COUNT
 };
 
@@ -165,11 +168,24 @@ void launch_run_starts(const uint32_t *keys, int64_t n, uint32_t *flags, uint32_
                        unsigned long long *n_runs, void *scan_temp, cudaStream_t s);
 void launch_voxel_mean(const uint32_t *order, const uint32_t *starts, int64_t n_runs, int64_t n,
                        const PointArrays &in, const PointArraysOut &out, cudaStream_t s);
-// K nearest reference points per query (rid/ridx: reference cell ids and
-// indices sorted by id); rows of k entries, keff = entries filled.
-void launch_knn(const float *qpos, int64_t nq, const float *rpos, const uint32_t *rid,
-                const uint32_t *ridx, int64_t nr, const GridParams *gp, int k, int keff,
-                int self_mode, int32_t *out_idx, float *out_d2, cudaStream_t s);
+// One search grid over the reference points: parameters, (cell id, index)
+// list sorted by id, dense cell-start table (or NULL).
+struct KnnGrid {
+    const GridParams *gp;
+    const uint32_t *rid, *ridx, *cs;
+};
+// Exact K nearest reference points per query; rows of k entries, keff =
+// entries filled.  Searches `fine`, then `coarse` (may be NULL) for queries
+// left open, then scans every point for what is still open.
+// temp: knn_temp_bytes(nq).
+size_t knn_temp_bytes(int64_t nq);
+void launch_knn(const float *qpos, int64_t nq, const float *rpos, int64_t nr, const KnnGrid &fine,
+                const KnnGrid *coarse, int k, int keff, int self_mode, int32_t *out_idx,
+                float *out_d2, void *temp, cudaStream_t s);
+// cell_start[c] = first index of cell c in the sorted list (c <= cells);
+// scan_temp: scan_temp_bytes(cells + 1).
+void launch_cell_start(const uint32_t *rid, int64_t n, int64_t n_cells_total,
+                       uint32_t *cell_start, void *scan_temp, cudaStream_t s);
 void launch_outlier_flags(const float *d2, int64_t n, int k, int keff, float eps, uint32_t *keep,
                           cudaStream_t s);
 void launch_compact_points(const uint32_t *keep, const uint32_t *pos, int64_t n,

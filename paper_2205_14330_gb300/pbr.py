@@ -82,7 +82,8 @@ class ServeStats(C.Structure):
 
 
 STAGES = ["preprocess_fwd", "compact", "depth_sort", "emit_pairs", "tile_sort", "tile_ranges",
-          "raster_fwd", "raster_bwd", "preprocess_bwd", "other"]
+          "raster_fwd", "raster_bwd", "preprocess_bwd", "other", "voxel_reduce", "knn",
+          "refine_other"]
 
 _lib = None
 _lock = threading.Lock()

@@ -64,6 +64,19 @@ def test_knn_queries_inside_and_outside_the_grid(env):
         assert np.array_equal(d2.cpu().numpy(), rd)
 
 
+def test_knn_isolated_cluster_uses_the_exhaustive_path(env):
+    """A small cluster far from the rest: its neighbours lie many cells away,
+    beyond the shell limit of the grid search."""
+    pbr, r = env
+    pos = np.concatenate([_cloud(3000)["pos"],
+                          np.array([[8, 8, 8], [8.01, 8, 8], [8, 8.02, 8.01]], F32)])
+    for k, grid_n in ((8, 0), (2, 0), (8, 40)):
+        idx, d2 = pbr.knn(r, _cuda(pos), k, grid_n=grid_n)
+        ri, rd = RR.knn(pos, k)
+        assert np.array_equal(idx.cpu().numpy(), ri)
+        assert np.array_equal(d2.cpu().numpy(), rd)
+
+
 def test_knn_ties_duplicates_and_short_sets(env):
     pbr, r = env
     # an integer lattice: many equal distances, ties broken by index
