@@ -45,9 +45,10 @@ FLOP_TEST, FLOP_FWD, FLOP_BWD = 6, 11, 31
 # ncu capture of the kernel on the full-size batched workload; valid only for
 # the kernel source it was taken on (sha256 of the file), else reported null.
 CAPTURED_TRAFFIC = {
-    ("raster_bwd", "16x16", 0, 0): {
-        "bytes": 5.60e9 + 0.70647e9, "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
-        "sha256": "5bd53d3f2d1ee2f7c75f8516ef1ceae5ce171bb9ff009fd593e0ddcea720a8ab", "profile": "profiles/raster_bwd_dram_batched_1M_64views.md"},
+    ("raster_bwd", "16x16", 0, 1): {
+        "bytes": 14.15e9 + 1.24e9, "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
+        "sha256": "fb43993112fc18653adbfed5c8abad478d5f91db97d8c7766865d9182c615b24",
+        "profile": "profiles/raster_persist_dram_batched_1M_64views.md"},
 }
 
 
@@ -244,6 +245,59 @@ def serving_report(pbr, R, rates, seconds):
     return out
 
 
+def refine_report(pbr, R, hbm_peak, hbm_src, with_cpu, reps=5):
+    """One coarse-to-fine update (Sec. 3.3, Algorithm 1) of a 1M-point cloud
+    (surface samples of 40 shapes plus 1% uniform outliers, SH degree 3):
+    N = 256 voxels per axis, K = 8 neighbours, eps = 0.01."""
+    import torch
+    from oracle import refine_ref as RR
+    n, n_vox, k, eps = 1_000_000, 256, 8, 0.01
+    d = scenes.refine_cloud(seed=0, n=n)
+    sc = pbr.Scene(d["pos"], d["sh"], d["opacity"], d["radius"], d["deg"])
+    for _ in range(2):
+        pbr.refine_points(R, sc, n_vox=n_vox, k=k, eps=eps)
+    torch.cuda.synchronize()
+    R.set_stage_timing(True)
+    R.stage_times()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, counts = pbr.refine_points(R, sc, n_vox=n_vox, k=k, eps=eps)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    st = R.stage_times()
+    R.set_stage_timing(False)
+    ms = float(np.median(ts))
+    m, m2, tot = counts
+    per_point = 4 * (5 + 3 * (d["deg"] + 1) ** 2)  # position, SH, opacity, radius
+    # the traffic the definition implies: input read, reduced set written and
+    # read, output written, K neighbours' parameters read per generated point
+    alg = per_point * (n + 2 * m + tot + k * m2)
+    gbs = alg / (ms * 1e-3) / 1e9
+    out = {"workload": "1M points (40 shapes + 1% uniform outliers), SH degree 3; "
+                       f"N={n_vox}, K={k}, eps={eps}",
+           "ms": ms, "mpoints_s": n / (ms * 1e-3) / 1e6, "counts": list(counts),
+           "stage_ms": {kk: v[0] / reps for kk, v in st.items() if v[1]},
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": gbs / hbm_peak if hbm_peak else None, "bytes": alg,
+                        "peak_source": hbm_src,
+                        "note": "the neighbour search is latency-bound; bytes are the "
+                                "parameters the definition reads and writes"}}
+    if with_cpu:
+        ns = 12_000
+        ds = scenes.refine_cloud(seed=0, n=ns)
+        t0 = time.perf_counter()
+        RR.refine(ds["pos"], ds["sh"], ds["opacity"], ds["radius"], n_vox, k, eps)
+        secs = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": ns / secs / 1e6, "unit": "Mpoints/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"the same update of a {ns}-point cloud from the same "
+                                         f"generator, brute-force neighbours ({secs:.1f} s)"}
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -264,6 +318,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--no-refine", action="store_true")
     ap.add_argument("--serve-rates", default="500",
                     help="comma-separated Poisson arrival rates (req/s); empty = no serving run")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
@@ -512,6 +567,10 @@ def main():
         serving = serving_report(pbr, R, [float(x) for x in args.serve_rates.split(",")],
                                  args.serve_seconds)
 
+    refine = None
+    if rank == 0 and not args.no_refine:
+        refine = refine_report(pbr, R, hbm_peak, hbm_src, not args.no_cpu_baseline)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MP/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -529,7 +588,8 @@ def main():
                 "timing": "value/fwd: CUDA-graph replays of the whole step; stage_ms and the "
                           "roofline: the same steps launched eagerly with per-stage CUDA events",
                 "train_iteration": train,
-                "plain": plain, "serving": serving, "stage_ms": stage_ms, "roofline": roof,
+                "plain": plain, "serving": serving, "refine": refine, "stage_ms": stage_ms,
+                "roofline": roof,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches // max(1, args.steps)),
                 "gpu_launches_timed_region": int(launches), "clocks": clk,

@@ -551,15 +551,42 @@ __global__ void tile_bucket_scan_kernel(uint32_t *work)
     }
 }
 
-__global__ void tile_bucket_scatter_kernel(const uint2 *__restrict__ ranges, uint32_t n_tiles,
-                                           uint32_t *work, uint32_t *__restrict__ order)
+// Stable inside a block: the block's tiles of one bucket keep their id
+// order and take one contiguous range of the bucket (one atomic per block
+// and bucket), so neighbouring tiles of similar length run close together
+// in time and share their records through L2.
+__global__ void __launch_bounds__(256)
+tile_bucket_scatter_kernel(const uint2 *__restrict__ ranges, uint32_t n_tiles, uint32_t *work,
+                           uint32_t *__restrict__ order)
 {
+    __shared__ uint32_t s_w[8][33]; // per warp and bucket: count, then offset
+    __shared__ uint32_t s_base[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int j = threadIdx.x; j < 8 * 33; j += 256) (&s_w[0][0])[j] = 0;
+    __syncthreads();
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_tiles) return;
-    const uint2 r = ranges[t];
-    const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
-    const uint32_t pos = atomicAdd(work + 2 + (31 - (len ? __clz(len) : 31)), 1u);
-    order[pos] = t;
+    uint32_t bkt = 32; // none
+    if (t < n_tiles) {
+        const uint2 r = ranges[t];
+        const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
+        bkt = 31 - (len ? __clz(len) : 31);
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, bkt);
+    const uint32_t rank = __popc(peers & lanemask_lt_r());
+    if (bkt < 32 && rank == 0) s_w[w][bkt] = __popc(peers);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int b = threadIdx.x;
+        uint32_t run = 0;
+        for (int v = 0; v < 8; ++v) {
+            const uint32_t c = s_w[v][b];
+            s_w[v][b] = run;
+            run += c;
+        }
+        s_base[b] = run ? atomicAdd(work + 2 + b, run) : 0u;
+    }
+    __syncthreads();
+    if (bkt < 32) order[s_base[bkt] + s_w[w][bkt] + rank] = t;
 }
 
 // ========================================================= block-staged
