@@ -426,6 +426,52 @@ int pbr_knn(pbr_ctx *ctx, const float *ref_pos, int64_t n_ref, const float *quer
             int64_t n_query, int32_t k, int32_t self, int32_t grid_n, int32_t *out_idx,
             float *out_d2, pbr_stream_t stream);
 
+/* --------------------------------------------- video frame initialisation */
+/* Chamfer distance between two clouds (the equation of Sec. 3.4, "Video
+ * Synthesis"):
+ *   CD = 1/n1 sum_i min_j |x_i - y_j|^2 + 1/n2 sum_j min_i |x_i - y_j|^2
+ * and its gradient with respect to the second cloud's positions, with the
+ * nearest points held fixed:
+ *   dCD/dy_j = 2/n2 (y_j - x_nn(j)) + 2/n1 sum_{i: nn(i) = j} (y_j - x_i).
+ * Nearest points by the exact neighbour search of pbr_knn (fp32 squared
+ * distances, ties by lower index); distances in CD in fp64.
+ *   p1 [n1,3], p2 [n2,3]: device, caller-owned, n1, n2 >= 1.
+ *   loss_dev: device double, overwritten with CD.
+ *   grad2 [n2,3] (device, nullable): overwritten with dCD/dp2.
+ *   nn12 [n1], nn21 [n2] (device int32, nullable): the nearest-point maps.
+ * Errors: PBR_ERR_INVALID_ARG, PBR_ERR_OOM, PBR_ERR_CUDA.  Asynchronous. */
+int pbr_chamfer(pbr_ctx *ctx, const float *p1, int64_t n1, const float *p2, int64_t n2,
+                double *loss_dev, float *grad2, int32_t *nn12, int32_t *nn21,
+                pbr_stream_t stream);
+
+/* Initialisation of a new frame from the trained previous one (Sec. 3.4):
+ * `iters` Adam steps on the positions pos2 of the new cloud minimising the
+ * Chamfer distance to the previous cloud, then every new point takes the
+ * mean SH coefficients, opacity and radius of its k closest previous
+ * points (the paper averages the SH "of the top-k closest points"; opacity
+ * and radius are averaged the same way).  The paper gives no iteration
+ * count, learning rate or k; the defaults are 100, 1e-3 and 4.
+ *   prev   : the previous frame (device arrays, caller-owned, n >= 1).
+ *   pos2   : [n2,3] device, updated in place (fp32 after every step).
+ *   sh2 [n2,K,3] (K of prev->sh_degree), opacity2 [n2], radius2 [n2]:
+ *            device, caller-owned, overwritten.
+ *   loss_history: host double[iters + 1] (nullable): CD before every step
+ *            and after the last one.
+ * Errors: PBR_ERR_INVALID_ARG (null pointers, iters < 0, k outside 1..32,
+ * lr negative or not finite, betas outside [0, 1), eps <= 0), PBR_ERR_OOM,
+ * PBR_ERR_CUDA.  Synchronises the stream. */
+typedef struct {
+    int32_t iters;           /* Adam steps (default 100) */
+    float lr;                /* learning rate (default 1e-3) */
+    float beta1, beta2, eps; /* 0.9, 0.999, 1e-8 */
+    int32_t k;               /* closest previous points per new point (default 4) */
+    int32_t reserved[2];
+} pbr_frame_cfg;
+void pbr_default_frame_cfg(pbr_frame_cfg *cfg);
+int pbr_frame_init(pbr_ctx *ctx, const pbr_points *prev, float *pos2, int64_t n2,
+                   const pbr_frame_cfg *cfg, float *sh2, float *opacity2, float *radius2,
+                   double *loss_history, pbr_stream_t stream);
+
 /* ------------------------------------------------------- microbenchmarks */
 /* Measures the device's FP32 FMA rate (flop/s, an FMA counted as 2) and
  * MUFU ex2 rate (op/s) with the library's own kernels; used as the ALU

@@ -117,6 +117,35 @@ struct TempBufs {
 } // namespace pbr
 
 namespace pbr {
+// ---- exact neighbour search over a point set (api_refine.cu)
+// One search grid: device parameters, sorted (cell id, index) list, table.
+struct Grid {
+    GridParams *gp = nullptr;
+    uint32_t *rid = nullptr, *ridx = nullptr, *cs = nullptr;
+    int cells = 0;
+    KnnGrid view() const { return KnnGrid{gp, rid, ridx, cs}; }
+};
+// The fine search grid and, for fine grids of 16 cells or more, a second
+// one 8 times coarser for queries the fine search leaves open.
+struct SearchIndex {
+    Grid fine, coarse;
+    bool has_coarse = false;
+};
+// Cells per axis of an automatic grid over n points (about 2 n^(1/3)).
+int auto_cells(int64_t n);
+// Grid parameters of both levels over the cube of the n points `pos`.
+int make_params(TempBufs &tb, const float *pos, int64_t n, int cells, SearchIndex &S,
+                cudaStream_t s);
+// Sorted lists and tables of both levels for the n reference points.
+int index_points(TempBufs &tb, const float *ref, int64_t n, SearchIndex &S, cudaStream_t s);
+// Both levels restricted to kept points (indices renumbered by newpos).
+int keep_points(TempBufs &tb, SearchIndex &S, int64_t m, int64_t m2, const uint32_t *keep,
+                const uint32_t *newpos, void *scan_tmp, cudaStream_t s);
+// Exact k nearest reference points of each query (rows of k entries).
+int run_knn(TempBufs &tb, const float *q, int64_t nq, const float *ref, int64_t nr,
+            const SearchIndex &S, int k, int keff, int self_mode, int32_t *out_idx, float *out_d2,
+            cudaStream_t s);
+
 int forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s);
 
 // Records CUDA events around one stage on stream s when the context has

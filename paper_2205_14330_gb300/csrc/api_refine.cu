@@ -59,29 +59,16 @@ int sorted_cells(TempBufs &tb, const float *pos, int64_t n, const GridParams *gp
     return PBR_OK;
 }
 
-int auto_cells(int64_t n)
+} // namespace
+
+int pbr::auto_cells(int64_t n)
 {
     const double c = 2.0 * std::cbrt((double)std::max<int64_t>(n, 1));
     return (int)std::min(1024.0, std::max(1.0, std::ceil(c)));
 }
 
-// One search grid: device parameters, sorted (cell id, index) list, table.
-struct Grid {
-    GridParams *gp = nullptr;
-    uint32_t *rid = nullptr, *ridx = nullptr, *cs = nullptr;
-    int cells = 0;
-    KnnGrid view() const { return KnnGrid{gp, rid, ridx, cs}; }
-};
-
-// The fine search grid and, for fine grids of 16 cells or more, a second
-// one 8 times coarser for queries the fine search leaves open.
-struct SearchIndex {
-    Grid fine, coarse;
-    bool has_coarse = false;
-};
-
 // Parameters of both levels over the cube of the n points `pos`.
-int make_params(TempBufs &tb, const float *pos, int64_t n, int cells, SearchIndex &S,
+int pbr::make_params(TempBufs &tb, const float *pos, int64_t n, int cells, SearchIndex &S,
                 cudaStream_t s)
 {
     void *gtmp;
@@ -100,7 +87,7 @@ int make_params(TempBufs &tb, const float *pos, int64_t n, int cells, SearchInde
 }
 
 // Sorted lists and tables of both levels for the n reference points.
-int index_points(TempBufs &tb, const float *ref, int64_t n, SearchIndex &S, cudaStream_t s)
+int pbr::index_points(TempBufs &tb, const float *ref, int64_t n, SearchIndex &S, cudaStream_t s)
 {
     if (n <= 0) return PBR_OK;
     PBR_TRY(sorted_cells(tb, ref, n, S.fine.gp, S.fine.cells, &S.fine.rid, &S.fine.ridx, s,
@@ -113,7 +100,7 @@ int index_points(TempBufs &tb, const float *ref, int64_t n, SearchIndex &S, cuda
 
 // Both levels restricted to the kept points (indices renumbered by newpos,
 // the exclusive scan of keep), tables rebuilt in place.
-int keep_points(TempBufs &tb, SearchIndex &S, int64_t m, int64_t m2, const uint32_t *keep,
+int pbr::keep_points(TempBufs &tb, SearchIndex &S, int64_t m, int64_t m2, const uint32_t *keep,
                 const uint32_t *newpos, void *scan_tmp, cudaStream_t s)
 {
     uint32_t *flags;
@@ -136,7 +123,7 @@ int keep_points(TempBufs &tb, SearchIndex &S, int64_t m, int64_t m2, const uint3
     return PBR_OK;
 }
 
-int run_knn(TempBufs &tb, const float *q, int64_t nq, const float *ref, int64_t nr,
+int pbr::run_knn(TempBufs &tb, const float *q, int64_t nq, const float *ref, int64_t nr,
             const SearchIndex &S, int k, int keff, int self_mode, int32_t *out_idx, float *out_d2,
             cudaStream_t s)
 {
@@ -147,8 +134,6 @@ int run_knn(TempBufs &tb, const float *q, int64_t nq, const float *ref, int64_t 
                out_idx, out_d2, ktmp, s);
     return PBR_OK;
 }
-
-} // namespace
 
 extern "C" void pbr_default_refine(pbr_refine_cfg *cfg)
 {

@@ -31,7 +31,8 @@
 // Outlier removal: per point, the population standard deviation of its K
 // neighbour distances, fp32 sums in neighbour order; survivors are
 // compacted in order.  Generation: one warp per survivor averages its K
-// nearest survivors' parameters (fp64 sums in neighbour order).
+// nearest survivors' parameters (fp64 sums in neighbour order); the same
+// kernel, from attribute 3 on, moves parameters between frames.
 #include <cfloat>
 
 #include "pbr_internal.cuh"
@@ -586,7 +587,7 @@ __global__ void fill_u32_kernel(uint32_t *__restrict__ p, int64_t n, uint32_t v)
 // ---------------------------------------------------------- generation
 __global__ void __launch_bounds__(256)
 generate_kernel(const int32_t *__restrict__ nbr, int64_t n, int k, int keff, Params in,
-                OutParams out, int64_t out_base)
+                OutParams out, int64_t out_base, int a_begin)
 {
     const int lane = threadIdx.x & 31;
     const int nattr = 5 + in.nsh;
@@ -594,7 +595,7 @@ generate_kernel(const int32_t *__restrict__ nbr, int64_t n, int k, int keff, Par
     for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < n;
          q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const int32_t *row = nbr + q * k;
-        for (int a = lane; a < nattr; a += 32) {
+        for (int a = a_begin + lane; a < nattr; a += 32) {
             double acc = 0.0;
             for (int j = 0; j < keff; ++j)
                 acc = __dadd_rn(acc, (double)in.get((uint32_t)__ldg(row + j), a));
@@ -731,12 +732,12 @@ void launch_fill_u32(uint32_t *p, int64_t n, uint32_t v, cudaStream_t s)
 }
 
 void launch_generate(const int32_t *nbr, int64_t n, int k, int keff, const PointArrays &in,
-                     const PointArraysOut &out, int64_t out_base, cudaStream_t s)
+                     const PointArraysOut &out, int64_t out_base, cudaStream_t s, int a_begin)
 {
     if (n <= 0 || keff <= 0) return;
     generate_kernel<<<grid_for(n, 8, MAX_BLOCKS), 256, 0, s>>>(
         nbr, n, k, keff, Params{in.pos, in.sh, in.op, in.rad, in.nsh},
-        OutParams{out.pos, out.sh, out.op, out.rad, out.nsh}, out_base);
+        OutParams{out.pos, out.sh, out.op, out.rad, out.nsh}, out_base, a_begin);
     count_launches(1);
 }
 

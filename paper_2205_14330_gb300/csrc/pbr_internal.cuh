@@ -196,8 +196,20 @@ void launch_list_keep(const uint32_t *rid, const uint32_t *ridx, const uint32_t 
                       const uint32_t *newpos, int64_t n, uint32_t *flags, uint32_t *rid_out,
                       uint32_t *ridx_out, void *scan_temp, cudaStream_t s);
 void launch_fill_u32(uint32_t *p, int64_t n, uint32_t v, cudaStream_t s);
+// Row out_base + q of `out` = mean of the parameters of points nbr[q][0..keff)
+// of `in`, for parameters a_begin.. (0: position first; 3: SH, opacity,
+// radius only).
 void launch_generate(const int32_t *nbr, int64_t n, int k, int keff, const PointArrays &in,
-                     const PointArraysOut &out, int64_t out_base, cudaStream_t s);
+                     const PointArraysOut &out, int64_t out_base, cudaStream_t s,
+                     int a_begin = 0);
+
+// ---- frame initialisation (k_frame.cu)
+// Chamfer distance of two clouds given the nearest-point maps (nn12[i]:
+// nearest point of p2 to p1[i]; nn21[j]: nearest of p1 to p2[j]): adds CD to
+// *loss (fp64, device) and, when grad2 is set, writes dCD/dp2 ([n2,3]).
+void launch_chamfer(const float *p1, int64_t n1, const float *p2, int64_t n2,
+                    const int32_t *nn12, const int32_t *nn21, float *grad2, double *loss,
+                    cudaStream_t s);
 
 // ---- raster (k_raster.cu)
 // batch_depth 0 = warp-streamed, > 0 = block-staged.  With order/work set

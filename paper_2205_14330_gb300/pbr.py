@@ -72,6 +72,12 @@ class RefineCfg(C.Structure):
                 ("stages", C.c_int32)]
 
 
+class FrameCfg(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("k", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
+
+
 class ServeStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rejected", C.c_int64),
                 ("queued", C.c_int64), ("in_flight_batches", C.c_int64), ("batches", C.c_int64),
@@ -159,6 +165,11 @@ def lib():
             L.pbr_refine_points.argtypes = [vp, C.POINTER(Points), C.POINTER(RefineCfg), vp, vp,
                                             vp, vp, i64, C.POINTER(i64), vp]
             L.pbr_knn.argtypes = [vp, vp, i64, vp, i64, i32, i32, i32, vp, vp, vp]
+            L.pbr_default_frame_cfg.restype = None
+            L.pbr_default_frame_cfg.argtypes = [C.POINTER(FrameCfg)]
+            L.pbr_chamfer.argtypes = [vp, vp, i64, vp, i64, vp, vp, vp, vp, vp]
+            L.pbr_frame_init.argtypes = [vp, C.POINTER(Points), vp, i64, C.POINTER(FrameCfg), vp,
+                                         vp, vp, C.POINTER(C.c_double), vp]
             _lib = L
     return _lib
 
@@ -611,6 +622,44 @@ def knn(renderer, ref, k, query=None, grid_n=0):
     check(lib().pbr_knn(renderer.ctx, _ptr(ref), int(ref.shape[0]), _ptr(q), nq, int(k),
                         1 if query is None else 0, int(grid_n), _ptr(idx), _ptr(d2), _stream()))
     return idx, d2
+
+
+def chamfer(renderer, p1, p2, grad=True):
+    """Chamfer distance of Sec. 3.4 between two [n,3] fp32 device clouds.
+    Returns (CD as a 0-d fp64 device tensor, dCD/dp2 or None, nn12, nn21)."""
+    p1, p2 = p1.contiguous(), p2.contiguous()
+    dev = p1.device
+    loss = torch.zeros((), dtype=torch.float64, device=dev)
+    g = torch.empty_like(p2) if grad else None
+    nn12 = torch.empty(p1.shape[0], dtype=torch.int32, device=dev)
+    nn21 = torch.empty(p2.shape[0], dtype=torch.int32, device=dev)
+    check(lib().pbr_chamfer(renderer.ctx, _ptr(p1), int(p1.shape[0]), _ptr(p2),
+                            int(p2.shape[0]), _ptr(loss), _ptr(g), _ptr(nn12), _ptr(nn21),
+                            _stream()))
+    return loss, g, nn12, nn21
+
+
+def frame_init(renderer, prev, pos2, iters=100, lr=1e-3, k=4, beta1=0.9, beta2=0.999,
+               eps=1e-8):
+    """Initialises the next frame from the Scene `prev` (Sec. 3.4): pos2 ([n2,3]
+    fp32 device, updated in place) descends on the Chamfer distance, then the
+    new points take the mean parameters of their k closest previous points.
+    Returns (Scene of the new frame, loss history as a list)."""
+    cfg = FrameCfg()
+    lib().pbr_default_frame_cfg(C.byref(cfg))
+    cfg.iters, cfg.lr, cfg.k = int(iters), float(lr), int(k)
+    cfg.beta1, cfg.beta2, cfg.eps = float(beta1), float(beta2), float(eps)
+    n2 = int(pos2.shape[0])
+    K = (prev.deg + 1) ** 2
+    dev = pos2.device
+    sh = torch.empty((n2, K, 3), dtype=torch.float32, device=dev)
+    op = torch.empty(n2, dtype=torch.float32, device=dev)
+    rad = torch.empty(n2, dtype=torch.float32, device=dev)
+    hist = (C.c_double * (int(iters) + 1))()
+    pts = prev.points()
+    check(lib().pbr_frame_init(renderer.ctx, C.byref(pts), _ptr(pos2), n2, C.byref(cfg),
+                               _ptr(sh), _ptr(op), _ptr(rad), hist, _stream()))
+    return Scene(pos2, sh, op, rad, prev.deg, device=dev), list(hist)
 
 
 def measure_alu_peaks(device: int = 0):

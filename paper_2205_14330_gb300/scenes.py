@@ -230,6 +230,19 @@ SERVE_SIZES = [100_000, 200_000, 300_000, 500_000, 750_000, 1_000_000, 1_500_000
 SERVE_DEGS = [0, 1, 2, 3, 0, 1, 2, 3]
 
 
+def frame_pair(seed=0, n=200_000, deg=2, jitter=0.005, frames=30):
+    """Input of one frame initialisation (Sec. 3.4): the cloud of frame 0 of
+    `dynamic_video` with its SH, opacity and radii as the trained previous
+    frame, and frame 1's positions with N(0, jitter) noise, in a random
+    order, as the new frame's initial cloud (no point correspondence)."""
+    d = dynamic_video(seed=seed, n=n, frames=frames, deg=deg)
+    rng = rng_for(seed + 1)
+    p2 = d["frames"][1] + rng.normal(0.0, jitter, d["frames"][1].shape)
+    p2 = p2[rng.permutation(n)].astype(np.float32)
+    return dict(p1=d["frames"][0], sh=d["sh"], opacity=d["opacity"], radius=d["radius"],
+                deg=deg, p2=p2)
+
+
 def serving_scenes(seed=0, sizes=None, degs=None):
     """Eight resident scenes of 100k-2M points with SH degree 0-3."""
     rng = rng_for(seed)
