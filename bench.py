@@ -298,6 +298,56 @@ def refine_report(pbr, R, hbm_peak, hbm_src, with_cpu, reps=5):
     return out
 
 
+def frame_init_report(pbr, R, hbm_peak, hbm_src, with_cpu, iters=100, reps=3):
+    """Initialisation of frame 1 from frame 0 of the dynamic-video workload
+    (Sec. 3.4): 200k points, SH degree 2, 100 Adam steps on the Chamfer
+    distance (lr 1e-3), then parameters from the 4 closest previous points."""
+    import torch
+    from oracle import frame_init_ref as FI
+    n = 200_000
+    d = scenes.frame_pair(seed=0, n=n)
+    prev = pbr.Scene(d["p1"], d["sh"], d["opacity"], d["radius"], d["deg"])
+    p2 = torch.from_numpy(d["p2"]).cuda()
+    pbr.frame_init(R, prev, p2.clone(), iters=2)
+    ts, hist = [], None
+    for _ in range(reps):
+        pos2 = p2.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, hist = pbr.frame_init(R, prev, pos2, iters=iters)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = float(np.median(ts))
+    # bytes the definition touches per step: both clouds' positions read for
+    # the nearest points, dCD/dp2 written, Adam's p, g, m, v read and p, m, v
+    # written; per point of the previous frame 4 (1 + 3K) + 8 B read once
+    per_step = 12 * (n + n) + 12 * n + 4 * 3 * n * 7
+    alg = iters * per_step + n * (4 * (3 * (d["deg"] + 1) ** 2 + 2) + 12)
+    gbs = alg / (ms * 1e-3) / 1e9
+    out = {"workload": "frame 0 -> 1 of the dynamic-video scene (200k points, SH degree 2), "
+                       f"{iters} Adam steps (lr 1e-3) on the Chamfer distance, k = 4",
+           "ms": ms, "ms_per_step": ms / iters,
+           "mpoint_steps_s": n * iters / (ms * 1e-3) / 1e6,
+           "chamfer_before": hist[0], "chamfer_after": hist[-1],
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": gbs / hbm_peak if hbm_peak else None, "bytes": alg,
+                        "peak_source": hbm_src,
+                        "note": "each step rebuilds the moving cloud's search index and runs "
+                                "two neighbour searches: launch- and latency-bound"}}
+    if with_cpu:
+        ns, its = 1500, 20
+        ds = scenes.frame_pair(seed=0, n=ns)
+        t0 = time.perf_counter()
+        FI.frame_init(ds["p1"], [ds["sh"], ds["opacity"], ds["radius"]], ds["p2"], iters=its)
+        secs = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": ns * its / secs / 1e6, "unit": "Mpoint-steps/s",
+                               "cores": 1, "kind": "oracle",
+                               "sample": f"the same initialisation of an {ns}-point pair, {its} "
+                                         f"steps, brute-force nearest points ({secs:.1f} s)"}
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -319,6 +369,7 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-refine", action="store_true")
+    ap.add_argument("--no-frame-init", action="store_true")
     ap.add_argument("--serve-rates", default="500",
                     help="comma-separated Poisson arrival rates (req/s); empty = no serving run")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
@@ -570,6 +621,9 @@ def main():
     refine = None
     if rank == 0 and not args.no_refine:
         refine = refine_report(pbr, R, hbm_peak, hbm_src, not args.no_cpu_baseline)
+    frame = None
+    if rank == 0 and not args.no_frame_init:
+        frame = frame_init_report(pbr, R, hbm_peak, hbm_src, not args.no_cpu_baseline)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MP/s", "n_gpus": world,
@@ -588,7 +642,8 @@ def main():
                 "timing": "value/fwd: CUDA-graph replays of the whole step; stage_ms and the "
                           "roofline: the same steps launched eagerly with per-stage CUDA events",
                 "train_iteration": train,
-                "plain": plain, "serving": serving, "refine": refine, "stage_ms": stage_ms,
+                "plain": plain, "serving": serving, "refine": refine, "frame_init": frame,
+                "stage_ms": stage_ms,
                 "roofline": roof,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches // max(1, args.steps)),
