@@ -243,6 +243,43 @@ def frame_pair(seed=0, n=200_000, deg=2, jitter=0.005, frames=30):
                 deg=deg, p2=p2)
 
 
+def sphere_masks(cams, centres, radii):
+    """Foreground masks ([H, W] uint8 per camera) of a union of spheres:
+    pixel (x, y) is foreground when the ray through its centre (x + 0.5,
+    y + 0.5) hits a sphere in front of the camera."""
+    out = []
+    for c in cams:
+        W, H = int(c["width"]), int(c["height"])
+        R = np.asarray(c["R"], np.float64).reshape(3, 3)
+        t = np.asarray(c["t"], np.float64).reshape(3)
+        eye = -R.T @ t
+        xs, ys = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
+        d = np.stack([(xs - float(c["cx"])) / float(c["fx"]), (ys - float(c["cy"])) / float(c["fy"]),
+                      np.ones_like(xs)], -1) @ R  # world directions (R^T d per pixel)
+        d /= np.linalg.norm(d, axis=-1, keepdims=True)
+        hit = np.zeros((H, W), bool)
+        for ctr, r in zip(centres, radii):
+            oc = eye - ctr
+            b = d @ oc
+            disc = b * b - (oc @ oc - r * r)
+            hit |= (disc >= 0) & (-b + np.sqrt(np.maximum(disc, 0)) > 0)
+        out.append(hit.astype(np.uint8))
+    return out
+
+
+def hull_scene(seed=0, n_spheres=8, n_cams=16, width=256, height=256):
+    """Silhouette input of the visual-hull initialisation (Sec. 3.1): a union
+    of `n_spheres` spheres (centres in [-0.7, 0.7]^3, radii in [0.15, 0.4])
+    seen by `n_cams` cameras on a Fibonacci hemisphere of radius 4; the
+    scene box is [-1.5, 1.5]^3."""
+    rng = rng_for(seed)
+    centres = rng.uniform(-0.7, 0.7, (n_spheres, 3))
+    radii = rng.uniform(0.15, 0.4, n_spheres)
+    cams = [camera(e, width, height) for e in fibonacci_hemisphere(n_cams, 4.0)]
+    return dict(cams=cams, masks=sphere_masks(cams, centres, radii), centres=centres,
+                radii=radii, lo=np.full(3, -1.5, np.float32), hi=np.full(3, 1.5, np.float32))
+
+
 def serving_scenes(seed=0, sizes=None, degs=None):
     """Eight resident scenes of 100k-2M points with SH degree 0-3."""
     rng = rng_for(seed)
