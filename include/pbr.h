@@ -472,6 +472,55 @@ int pbr_frame_init(pbr_ctx *ctx, const pbr_points *prev, float *pos2, int64_t n2
                    const pbr_frame_cfg *cfg, float *sh2, float *opacity2, float *radius2,
                    double *loss_history, pbr_stream_t stream);
 
+/* ----------------------------------- visual hull and consistency check */
+/* Consistency check of the paper's initialisation appendix (Sec. 3.1):
+ * CC(p) = 1 iff p projects (Eq. 1) onto a foreground pixel of every view.
+ * Projection in fp32 round-to-nearest, X = ((R0 px + R1 py) + R2 pz) + t
+ * per row, u = fx (X.x / X.z) + cx, v = fy (X.y / X.z) + cy, pixel (floor
+ * u, floor v); X.z <= z_near or a pixel outside the image is background.
+ *   masks : device uint8, the views' [H, W] masks packed in camera order
+ *           (> 0 = foreground), sum over views of W H bytes.
+ *   keep  : device uint8 [n], overwritten with CC.
+ * Errors: PBR_ERR_INVALID_ARG (null pointers, no camera, a camera of size
+ * <= 0, z_near negative or not finite), PBR_ERR_OOM, PBR_ERR_CUDA.
+ * Asynchronous. */
+int pbr_consistency_check(pbr_ctx *ctx, const float *pos, int64_t n, const pbr_camera *cams,
+                          int32_t n_cams, const uint8_t *masks, float z_near, uint8_t *keep,
+                          pbr_stream_t stream);
+
+/* The filter the paper applies after every training epoch: copies the
+ * points with CC = 1, in order, to out_* (device, caller-owned, room for
+ * in->n points) and writes their number to *n_out (host).  Errors as
+ * pbr_consistency_check.  Synchronises the stream. */
+int pbr_consistency_filter(pbr_ctx *ctx, const pbr_points *in, const pbr_camera *cams,
+                           int32_t n_cams, const uint8_t *masks, float z_near, float *out_pos,
+                           float *out_sh, float *out_opacity, float *out_radius, int64_t *n_out,
+                           pbr_stream_t stream);
+
+/* Visual-hull initialisation (Sec. 3.1): rejection sampling of uniform
+ * points in the box [lo, hi) keeping those with CC = 1; the result is the
+ * first n_target kept candidates of the counter-based stream `seed`.
+ * Candidate j = lo + u (hi - lo) per axis (fp32, product then sum
+ * rounded), u = the top 24 bits of SplitMix64 output 3 j + axis (Steele,
+ * Lea and Flood 2014: output i of stream s is the generator's finaliser of
+ * s + (i + 1) 0x9E3779B97F4A7C15) times 2^-24.  With out_sh set, the kept
+ * points' SH coefficients ([n, (sh_degree+1)^2, 3], flattened index c) are
+ * standard normals by Box-Muller (fp64) on stream seed ^ 0x5DEECE66D,
+ * pair c / 2 from outputs c - c % 2 and c - c % 2 + 1 (even c: cosine,
+ * odd: sine; u1 = (top 24 bits + 1) 2^-24).
+ *   out_pos [n_target,3] (device, caller-owned); out_sh nullable.
+ *   max_candidates: candidates drawn at most (0 = 2^40).
+ *   *n_out: points kept (< n_target when the limit was reached first);
+ *   *n_drawn: candidates drawn up to and including the last kept one.
+ * Errors: PBR_ERR_INVALID_ARG (as above, a box with hi < lo or not finite,
+ * n_target outside 0..2^31-1, sh_degree outside 0..3), PBR_ERR_OOM,
+ * PBR_ERR_CUDA.  Synchronises the stream. */
+int pbr_visual_hull_init(pbr_ctx *ctx, const float lo[3], const float hi[3],
+                         const pbr_camera *cams, int32_t n_cams, const uint8_t *masks,
+                         float z_near, uint64_t seed, int64_t n_target, int64_t max_candidates,
+                         int32_t sh_degree, float *out_pos, float *out_sh, int64_t *n_out,
+                         int64_t *n_drawn, pbr_stream_t stream);
+
 /* ------------------------------------------------------- microbenchmarks */
 /* Measures the device's FP32 FMA rate (flop/s, an FMA counted as 2) and
  * MUFU ex2 rate (op/s) with the library's own kernels; used as the ALU

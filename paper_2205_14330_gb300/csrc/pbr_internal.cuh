@@ -211,6 +211,34 @@ void launch_chamfer(const float *p1, int64_t n1, const float *p2, int64_t n2,
                     const int32_t *nn12, const int32_t *nn21, float *grad2, double *loss,
                     cudaStream_t s);
 
+// ---- visual hull and consistency check (k_hull.cu)
+// One view of the check: camera of Eq. 1, image size, offset of its mask
+// in the packed masks (uint8, [H, W] per view, > 0 = foreground).
+struct HullView {
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    int32_t W, H;
+    int64_t pix_base;
+};
+// Consistency flag of every point (either output may be NULL).
+void launch_consistency(const float *pos, int64_t n, const HullView *views, int nv,
+                        const uint8_t *masks, float z_near, uint8_t *flags8, uint32_t *flags32,
+                        cudaStream_t s);
+// Candidates first .. first + count - 1 of stream `seed` in the box lo +
+// [0, ext): positions and flags.
+void launch_hull_candidates(uint64_t seed, uint64_t first, int64_t count, const float lo[3],
+                            const float ext[3], const HullView *views, int nv,
+                            const uint8_t *masks, float z_near, float *cand, uint32_t *flags,
+                            cudaStream_t s);
+// Accepted candidates of rank (exclusive scan of flags) below `need` to
+// out[done + rank]; *last = index of the candidate of rank need - 1.
+void launch_hull_take(const float *cand, const uint32_t *flags, const uint32_t *rank,
+                      int64_t count, uint32_t need, float *out, int64_t done,
+                      unsigned long long *last, cudaStream_t s);
+// out[i] = standard normal number c0 + i of stream `seed` (Box-Muller).
+void launch_sh_normals(uint64_t seed, int64_t c0, int64_t count, float *out, cudaStream_t s);
+
 // ---- raster (k_raster.cu)
 // batch_depth 0 = warp-streamed, > 0 = block-staged.  With order/work set
 // (warp-streamed only) the launch is persistent: warps pull (tile,

@@ -170,6 +170,15 @@ def lib():
             L.pbr_chamfer.argtypes = [vp, vp, i64, vp, i64, vp, vp, vp, vp, vp]
             L.pbr_frame_init.argtypes = [vp, C.POINTER(Points), vp, i64, C.POINTER(FrameCfg), vp,
                                          vp, vp, C.POINTER(C.c_double), vp]
+            L.pbr_consistency_check.argtypes = [vp, vp, i64, C.POINTER(Camera), i32, vp,
+                                                C.c_float, vp, vp]
+            L.pbr_consistency_filter.argtypes = [vp, C.POINTER(Points), C.POINTER(Camera), i32,
+                                                 vp, C.c_float, vp, vp, vp, vp, C.POINTER(i64),
+                                                 vp]
+            L.pbr_visual_hull_init.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                               C.POINTER(Camera), i32, vp, C.c_float,
+                                               C.c_uint64, i64, i64, i32, vp, vp,
+                                               C.POINTER(i64), C.POINTER(i64), vp]
             _lib = L
     return _lib
 
@@ -660,6 +669,62 @@ def frame_init(renderer, prev, pos2, iters=100, lr=1e-3, k=4, beta1=0.9, beta2=0
     check(lib().pbr_frame_init(renderer.ctx, C.byref(pts), _ptr(pos2), n2, C.byref(cfg),
                                _ptr(sh), _ptr(op), _ptr(rad), hist, _stream()))
     return Scene(pos2, sh, op, rad, prev.deg, device=dev), list(hist)
+
+
+def pack_masks(masks, device="cuda"):
+    """[H, W] foreground masks (one per camera, > 0 = foreground) packed into
+    one uint8 device array in camera order."""
+    flat = [np.ascontiguousarray(np.asarray(m) > 0, np.uint8).ravel() for m in masks]
+    return torch.from_numpy(np.concatenate(flat)).to(device)
+
+
+def consistency_check(renderer, pos, cams, masks, z_near=0.01):
+    """CC of every point of pos ([n,3] fp32 device) against packed masks
+    (see pack_masks): uint8 [n] device tensor."""
+    pos = pos.contiguous()
+    keep = torch.empty(pos.shape[0], dtype=torch.uint8, device=pos.device)
+    arr = make_cameras(cams)
+    check(lib().pbr_consistency_check(renderer.ctx, _ptr(pos), int(pos.shape[0]), arr, len(cams),
+                                      _ptr(masks), float(z_near), _ptr(keep), _stream()))
+    return keep
+
+
+def consistency_filter(renderer, scene, cams, masks, z_near=0.01):
+    """The points of a Scene that pass the check, as a new Scene."""
+    n = scene.n
+    K = (scene.deg + 1) ** 2
+    dev = scene.pos.device
+    pos = torch.empty((max(n, 1), 3), dtype=torch.float32, device=dev)
+    sh = torch.empty((max(n, 1), K, 3), dtype=torch.float32, device=dev)
+    op = torch.empty(max(n, 1), dtype=torch.float32, device=dev)
+    rad = torch.empty(max(n, 1), dtype=torch.float32, device=dev)
+    m = C.c_int64()
+    arr = make_cameras(cams)
+    pts = scene.points()
+    check(lib().pbr_consistency_filter(renderer.ctx, C.byref(pts), arr, len(cams), _ptr(masks),
+                                       float(z_near), _ptr(pos), _ptr(sh), _ptr(op), _ptr(rad),
+                                       C.byref(m), _stream()))
+    k = m.value
+    return Scene(pos[:k], sh[:k], op[:k], rad[:k], scene.deg, device=dev)
+
+
+def visual_hull_init(renderer, lo, hi, cams, masks, n_target, seed=0, sh_degree=2,
+                     max_candidates=0, z_near=0.01):
+    """Visual-hull initialisation (Sec. 3.1).  Returns (positions [n,3],
+    SH [n,K,3] drawn from N(0, 1), candidates drawn)."""
+    pos = torch.empty((max(n_target, 1), 3), dtype=torch.float32, device="cuda")
+    K = (sh_degree + 1) ** 2
+    sh = torch.empty((max(n_target, 1), K, 3), dtype=torch.float32, device="cuda")
+    lo3 = (C.c_float * 3)(*[float(v) for v in lo])
+    hi3 = (C.c_float * 3)(*[float(v) for v in hi])
+    n_out, n_drawn = C.c_int64(), C.c_int64()
+    arr = make_cameras(cams)
+    check(lib().pbr_visual_hull_init(renderer.ctx, lo3, hi3, arr, len(cams), _ptr(masks),
+                                     float(z_near), int(seed) & (2 ** 64 - 1), int(n_target),
+                                     int(max_candidates), int(sh_degree), _ptr(pos), _ptr(sh),
+                                     C.byref(n_out), C.byref(n_drawn), _stream()))
+    k = n_out.value
+    return pos[:k], sh[:k], n_drawn.value
 
 
 def measure_alu_peaks(device: int = 0):
