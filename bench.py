@@ -348,6 +348,57 @@ def frame_init_report(pbr, R, hbm_peak, hbm_src, with_cpu, iters=100, reps=3):
     return out
 
 
+def hull_report(pbr, R, hbm_peak, hbm_src, with_cpu, n_target=200_000, reps=5):
+    """Visual-hull initialisation (Sec. 3.1): 200k points from the
+    silhouettes of 8 spheres in 16 views of 1024 x 768 (the dynamic-video
+    workload's image size and view count), then the consistency check of the
+    kept points."""
+    import torch
+    from oracle import hull_ref as H
+    h = scenes.hull_scene(seed=0, n_spheres=8, n_cams=16, width=1024, height=768)
+    masks = pbr.pack_masks(h["masks"])
+    pbr.visual_hull_init(R, h["lo"], h["hi"], h["cams"], masks, n_target, seed=1)
+    ts, drawn, pos = [], 0, None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pos, _, drawn = pbr.visual_hull_init(R, h["lo"], h["hi"], h["cams"], masks, n_target,
+                                             seed=1)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = float(np.median(ts))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    pbr.consistency_check(R, pos, h["cams"], masks)
+    e1.record()
+    torch.cuda.synchronize()
+    # candidate written (12 B) and flagged (4 B), flags scanned (4 B read,
+    # 4 B written), kept points read back and written (24 B each)
+    alg = drawn * 24 + n_target * 24
+    gbs = alg / (ms * 1e-3) / 1e9
+    out = {"workload": f"{n_target} points inside the visual hull of 8 spheres, 16 views of "
+                       "1024x768, box [-1.5, 1.5]^3",
+           "ms": ms, "candidates": drawn, "gcandidates_s": drawn / (ms * 1e-3) / 1e9,
+           "check_ms": e0.elapsed_time(e1),
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": gbs / hbm_peak if hbm_peak else None, "bytes": alg,
+                        "peak_source": hbm_src,
+                        "note": "per candidate: three SplitMix64 draws and the projection "
+                                "into views until the first background pixel (ALU); the "
+                                "batches' host synchronisations count in the time"}}
+    if with_cpu:
+        ns = n_target
+        t0 = time.perf_counter()
+        _, od = H.hull_init(h["lo"], h["hi"], h["cams"], h["masks"], ns, 1)
+        secs = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": od / secs / 1e9, "unit": "Gcandidates/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"the whole workload: {ns} kept points of the same stream "
+                                         f"({od} candidates, {secs:.1f} s)"}
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -370,6 +421,7 @@ def main():
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-refine", action="store_true")
     ap.add_argument("--no-frame-init", action="store_true")
+    ap.add_argument("--no-hull", action="store_true")
     ap.add_argument("--serve-rates", default="500",
                     help="comma-separated Poisson arrival rates (req/s); empty = no serving run")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
@@ -624,6 +676,9 @@ def main():
     frame = None
     if rank == 0 and not args.no_frame_init:
         frame = frame_init_report(pbr, R, hbm_peak, hbm_src, not args.no_cpu_baseline)
+    hull = None
+    if rank == 0 and not args.no_hull:
+        hull = hull_report(pbr, R, hbm_peak, hbm_src, not args.no_cpu_baseline)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MP/s", "n_gpus": world,
@@ -643,6 +698,7 @@ def main():
                           "roofline: the same steps launched eagerly with per-stage CUDA events",
                 "train_iteration": train,
                 "plain": plain, "serving": serving, "refine": refine, "frame_init": frame,
+                "visual_hull": hull,
                 "stage_ms": stage_ms,
                 "roofline": roof,
                 "cpu_baseline": cpu, "e2e": e2e,
