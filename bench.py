@@ -422,6 +422,8 @@ def main():
     ap.add_argument("--no-refine", action="store_true")
     ap.add_argument("--no-frame-init", action="store_true")
     ap.add_argument("--no-hull", action="store_true")
+    ap.add_argument("--views", type=int, default=0,
+                    help="use only the first N cameras (a smaller case for profiling)")
     ap.add_argument("--serve-rates", default="500",
                     help="comma-separated Poisson arrival rates (req/s); empty = no serving run")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
@@ -432,6 +434,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     sc, desc = workload(args.workload)
+    if args.views and "cams" in sc and args.views < len(sc["cams"]):
+        # a smaller case of the same workload (profiling captures)
+        sc["cams"] = sc["cams"][:args.views]
+        desc += f"; first {args.views} cameras only"
     if args.impl == "reference":
         if rank == 0:
             run_reference(args, sc, desc)

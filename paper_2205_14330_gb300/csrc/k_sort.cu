@@ -405,6 +405,22 @@ __global__ void gather_rects_kernel(const DevView *__restrict__ views, int32_t n
     mask_sorted[j] = m;
 }
 
+// Position of the (t+1)-th set bit of m (t < popc(m)), by halving.
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t t)
+{
+    uint32_t pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const uint32_t c = (uint32_t)__popc(m & ((1u << w) - 1u));
+        if (t >= c) {
+            t -= c;
+            pos += w;
+            m >>= w;
+        }
+    }
+    return pos;
+}
+
 // Each warp owns 32 consecutive depth-sorted point-views; their pair runs
 // are contiguous in the output, so the warp writes them together: output q
 // belongs to the last lane whose run starts at or before q.
@@ -450,12 +466,15 @@ emit_pairs_kernel(const uint32_t *__restrict__ sorted_pv, const uint32_t *__rest
         uint32_t omask = __shfl_sync(0xffffffffu, msk, ow);
         if (q < end && (int64_t)q < cap_pairs) {
             uint32_t t = q - opre;
-            if (omask) { // position of the t-th listed tile of the box
-                for (uint32_t k = 0; k < t; ++k) omask &= omask - 1;
-                t = (uint32_t)(__ffs(omask) - 1);
-            }
+            if (omask) t = nth_set_bit(omask, t); // position of the t-th listed tile
             const uint32_t owx = owxt & 0xffff;
-            keys[q] = otb + (t / owx) * (owxt >> 16) + (t % owx);
+            // row = floor(t / owx), exactly: (t + 0.5) / owx is at least
+            // 0.5 / owx away from an integer and the two roundings move it
+            // by less than 2^-23 of itself, which is smaller for t < 2^22
+            // (a box has fewer tiles)
+            const uint32_t row =
+                (uint32_t)__fmul_rn((float)t + 0.5f, __frcp_rn((float)owx));
+            keys[q] = otb + row * (owxt >> 16) + (t - row * owx);
             vals[q] = opv;
         }
     }
