@@ -23,9 +23,12 @@ Readings where the paper leaves details open (each implemented below):
      voxel 0.
   R2 reduction: every per-point parameter is replaced by the plain mean over
      the voxel; output in ascending voxel id.  The position mean feeds later
-     distance decisions, so its rounding is fixed: an fp64 sequential sum
-     over the voxel's points in ascending input index, divided by the count
-     in fp64 and rounded to fp32.  The other means are plain fp64 means.
+     distance decisions, so its rounding is fixed: a compensated (Kahan)
+     fp32 sum over the voxel's points in ascending input index (y = x - c,
+     t = s + y, c = (t - s) - y, s = t, each operation rounded to fp32),
+     divided by the count in fp32.  Its error stays within a few ulps
+     whatever the voxel's size, like an fp64 sum, without fp64 arithmetic.
+     The other means are plain fp64 means.
   R3 neighbours: the K nearest OTHER points of the same set, by fp32 squared
      distance ((dx dx + dy dy) + dz dz) with dx = x_j - x_i, ties broken by
      lower index, in ascending (distance, index) order; K_eff = min(K, n-1).
@@ -96,12 +99,16 @@ def voxel_reduce(pos, sh, opacity, radius, n_vox):
     sid = ids[order]
     starts = np.flatnonzero(np.r_[True, sid[1:] != sid[:-1]])
     counts = np.diff(np.r_[starts, n])
-    # fp64 sequential sums: add the r-th member of every voxel at step r
-    acc = np.zeros((starts.size, 3), np.float64)
+    # compensated fp32 sums: add the r-th member of every voxel at step r
+    acc = np.zeros((starts.size, 3), F32)
+    comp = np.zeros((starts.size, 3), F32)
     for r in range(int(counts.max())):
         sel = counts > r
-        acc[sel] = acc[sel] + p[order[starts[sel] + r]].astype(np.float64)
-    pos_out = (acc / counts.astype(np.float64)[:, None]).astype(F32)
+        y = p[order[starts[sel] + r]] - comp[sel]
+        t = acc[sel] + y
+        comp[sel] = (t - acc[sel]) - y
+        acc[sel] = t
+    pos_out = acc / counts.astype(F32)[:, None]
 
     def mean64(a):
         a = np.asarray(a, np.float64)[order]
