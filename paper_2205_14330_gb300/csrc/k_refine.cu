@@ -9,7 +9,7 @@
 // Voxel reduction: (id, index) pairs are radix-sorted (stable, so a voxel's
 // points stay in input order); each run of equal ids becomes one point
 // whose parameters are the run's means, one warp per voxel with lanes over
-// the parameters, fp64 sums in ascending input index rounded to fp32.
+// the parameters, compensated fp32 sums in ascending input index.
 //
 // kNN: one warp per query; lane j holds the j-th best (d2, index) so far,
 // d2 = (dx dx + dy dy) + dz dz in fp32 round-to-nearest, ties by lower
@@ -31,7 +31,7 @@
 // Outlier removal: per point, the population standard deviation of its K
 // neighbour distances, fp32 sums in neighbour order; survivors are
 // compacted in order.  Generation: one warp per survivor averages its K
-// nearest survivors' parameters (fp64 sums in neighbour order); the same
+// nearest survivors' parameters (compensated fp32 sums in neighbour order); the same
 // kernel, from attribute 3 on, moves parameters between frames.
 #include <cfloat>
 
@@ -159,6 +159,20 @@ __global__ void run_starts_kernel(const uint32_t *__restrict__ keys, const uint3
         if (i == 0 || keys[i] != keys[i - 1]) starts[pos[i]] = (uint32_t)i;
 }
 
+// Compensated (Kahan) fp32 sum, every operation rounded to nearest (no
+// contraction): the error stays within a few ulps of the total whatever the
+// number of terms, with fp32 arithmetic only.
+struct KahanSum {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = __fsub_rn(x, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+};
+
 // Parameter `a` of point i: position (a < 3), SH (a < 3 + nsh), opacity,
 // radius.
 struct Params {
@@ -193,12 +207,11 @@ voxel_mean_kernel(const uint32_t *__restrict__ order, const uint32_t *__restrict
          r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const uint32_t b = starts[r];
         const uint32_t e = r + 1 < n_runs ? starts[r + 1] : (uint32_t)n;
-        const double cnt = (double)(e - b);
+        const float cnt = (float)(e - b);
         for (int a = lane; a < nattr; a += 32) {
-            double acc = 0.0;
-            for (uint32_t m = b; m < e; ++m)
-                acc = __dadd_rn(acc, (double)in.get(__ldg(order + m), a));
-            out.put(r, a, __double2float_rn(__ddiv_rn(acc, cnt)));
+            KahanSum acc;
+            for (uint32_t m = b; m < e; ++m) acc.add(in.get(__ldg(order + m), a));
+            out.put(r, a, __fdiv_rn(acc.s, cnt));
         }
     }
 }
@@ -591,15 +604,14 @@ generate_kernel(const int32_t *__restrict__ nbr, int64_t n, int k, int keff, Par
 {
     const int lane = threadIdx.x & 31;
     const int nattr = 5 + in.nsh;
-    const double cnt = (double)keff;
+    const float cnt = (float)keff;
     for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < n;
          q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const int32_t *row = nbr + q * k;
         for (int a = a_begin + lane; a < nattr; a += 32) {
-            double acc = 0.0;
-            for (int j = 0; j < keff; ++j)
-                acc = __dadd_rn(acc, (double)in.get((uint32_t)__ldg(row + j), a));
-            out.put(out_base + q, a, __double2float_rn(__ddiv_rn(acc, cnt)));
+            KahanSum acc;
+            for (int j = 0; j < keff; ++j) acc.add(in.get((uint32_t)__ldg(row + j), a));
+            out.put(out_base + q, a, __fdiv_rn(acc.s, cnt));
         }
     }
 }

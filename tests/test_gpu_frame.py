@@ -75,7 +75,7 @@ def test_parameter_transfer_without_descent(env):
         assert abs(hist[0] - FI.chamfer(d["p1"], d["p2"][:1500])[0]) <= 1e-12 * hist[0]
         want, _ = FI.mean_params(d["p2"][:1500], d["p1"], [d["sh"], d["opacity"], d["radius"]], k)
         for got, w in zip((new.sh, new.opacity, new.radius), want):
-            assert np.allclose(got.cpu().numpy(), w, rtol=2e-7, atol=2e-7 * np.abs(w).max())
+            assert np.allclose(got.cpu().numpy(), w, rtol=4e-7, atol=4e-7 * np.abs(w).max())
 
 
 def test_descent_matches_oracle(env):
@@ -94,7 +94,7 @@ def test_descent_matches_oracle(env):
     # position difference of a few ulps may reorder a near tie elsewhere
     got = new.sh.cpu().numpy().reshape(len(y), -1)
     w = params[0].reshape(len(y), -1)
-    close = np.all(np.abs(got - w) <= 2e-7 * np.abs(w).max() + 1e-12, axis=1)
+    close = np.all(np.abs(got - w) <= 4e-7 * np.abs(w).max() + 1e-12, axis=1)
     assert close.mean() >= 0.99
 
 

@@ -4,8 +4,8 @@ the GPU against the plain definitions in oracle/refine_ref.py.
 Integer results (voxel ids and counts, neighbour indices, outlier
 decisions) and every value those decisions are taken from (reduced
 positions, squared distances) must match bit for bit; the other means
-(SH, opacity, radius; generated points) are FP64 means on both sides,
-rounded to fp32 on the GPU, so they agree to a few 1e-7 relative."""
+(SH, opacity, radius; generated points) are FP64 means in the oracle and
+compensated fp32 means on the GPU, so they agree to a few 1e-7 relative."""
 import numpy as np
 import pytest
 
@@ -107,18 +107,19 @@ def _compare_refine(pbr, r, d, n_vox, k, eps, stages):
     assert counts == (nred, nsurv, ntot)
     got = [out.pos.cpu().numpy(), out.sh.cpu().numpy(), out.opacity.cpu().numpy(),
            out.radius.cpu().numpy()]
-    # survivors: positions bit-exact, other parameters to fp32 rounding of
-    # an FP64 mean (half an ulp, plus summation order)
+    # survivors: positions bit-exact, other parameters within a few ulps of
+    # the FP64 mean (compensated fp32 sums on the GPU)
     assert np.array_equal(got[0][:nsurv], ref["survivors"][0].astype(F32))
     for g, w in zip(got[1:], ref["survivors"][1:]):
-        assert np.allclose(g[:nsurv], w, rtol=2e-7, atol=1e-12)
-    # generated points: means of fp32 parameters taken in FP64 and rounded;
-    # the oracle averages its FP64 survivor parameters, which differ from the
-    # GPU's fp32 ones by half an ulp
+        # a compensated sum errs by a few ulps of the sum of magnitudes
+        scale = float(np.abs(w).max()) if len(w) else 0.0
+        assert np.allclose(g[:nsurv], w, rtol=4e-7, atol=4e-7 * scale)
+    # generated points: compensated fp32 means of fp32 parameters; the oracle
+    # averages its FP64 survivor parameters, a few ulps away from the GPU's
     for g, w in zip(got, ref["result"]):
         if len(w) > nsurv:
             scale = float(np.abs(w[:nsurv]).max())
-            assert np.allclose(g[nsurv:], w[nsurv:], rtol=3e-7, atol=3e-7 * scale)
+            assert np.allclose(g[nsurv:], w[nsurv:], rtol=5e-7, atol=5e-7 * scale)
     return counts
 
 
@@ -211,4 +212,4 @@ def test_refine_full_size_sampled(env):
     for row, q in zip(gi, gs):
         nb = [j for j in row if j != q][:k]
         want = surv[nb].astype(np.float64).mean(0)
-        assert np.allclose(got[nsurv + q], want, rtol=2e-7, atol=1e-12)
+        assert np.allclose(got[nsurv + q], want, rtol=4e-7, atol=1e-12)
