@@ -245,6 +245,17 @@ def serving_report(pbr, R, rates, seconds):
     return out
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest value of x over all ranks (x itself without a process
+    group): a multi-rank step takes as long as its slowest rank."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def refine_report(pbr, R, hbm_peak, hbm_src, with_cpu, reps=5, n=1_000_000):
     """One coarse-to-fine update (Sec. 3.3, Algorithm 1) of a 1M-point cloud
     (surface samples of 40 shapes plus 1% uniform outliers, SH degree 3):
@@ -505,12 +516,7 @@ def main():
             fn()
         e1.record(stream)
         barrier()
-        ms = e0.elapsed_time(e1) / k
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1) / k, dist, dev)
 
     # ---- schedule: autotuned over tile size x compositing schedule
     tune = None
@@ -674,11 +680,7 @@ def main():
             return e0.elapsed_time(e1) / k
 
         e2e_run(2)
-        e_ms = e2e_run(max(2, args.steps // 2))
-        if dist is not None:
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
+        e_ms = max_over_ranks(e2e_run(max(2, args.steps // 2)), dist, dev)
         Gb.close()
         e2e = {"value": world * mp / (e_ms * 1e-3), "unit": "MP/s", "ms_per_step": e_ms,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
