@@ -11,7 +11,12 @@
  *   Sec. 3.2, Eqs. 6-7 depth sort and front-to-back alpha blending, limited
  *                      to points within a cutoff distance of the pixel;
  *   Sec. 3.3           gradients of the image w.r.t. positions and SH
- *                      coefficients for end-to-end training.
+ *                      coefficients for end-to-end training, the Eq. 8
+ *                      objective and optimiser step, and the hybrid
+ *                      coarse-to-fine point update (Algorithm 1);
+ *   Sec. 3.4           video frame initialisation (Chamfer descent and
+ *                      parameter transfer);
+ *   Sec. 3.1, appendix visual-hull initialisation and consistency check.
  *
  * Conventions shared by every entry point
  *   - Every function returns an int status: PBR_OK (0) or a negative
