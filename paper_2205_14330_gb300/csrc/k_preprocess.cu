@@ -41,12 +41,23 @@ __device__ __forceinline__ int find_scene(const Batch &b, int64_t block)
 
 // Cooperative, coalesced copy of the block's SH coefficients into shared
 // memory (the per-thread slice is then read with a stride of K*3 floats).
+// The block's SH coefficients in shared memory, transposed and padded:
+// coefficient j of the block's point p at s_sh[j * SH_STRIDE + p].  A
+// thread walking its own point's coefficients then touches consecutive
+// banks across the warp (a row-per-point layout of 48 floats puts threads
+// two apart on the same bank), and the coalesced global read maps to
+// consecutive banks too (SH_STRIDE = 1 mod 32).
+constexpr int SH_STRIDE = PRE_THREADS + 1;
+
 __device__ __forceinline__ void stage_sh(const float *__restrict__ sh, int64_t first, int count,
                                          int K3, float *s_sh)
 {
     const int64_t base = first * K3;
     const int total = count * K3;
-    for (int j = threadIdx.x; j < total; j += blockDim.x) s_sh[j] = __ldg(sh + base + j);
+    for (int f = threadIdx.x; f < total; f += blockDim.x) {
+        const int p = f / K3;
+        s_sh[(f - p * K3) * SH_STRIDE + p] = __ldg(sh + base + f);
+    }
 }
 
 template <int DEG>
@@ -57,9 +68,6 @@ __device__ void pre_fwd_point(const Batch &b, const DevOpts &o, const DevScene &
                               uint32_t &zlo, uint32_t &zhi)
 {
     constexpr int K = SH<DEG>::K;
-    float h[K * 3];
-#pragma unroll
-    for (int j = 0; j < K * 3; ++j) h[j] = hs[j];
     const float P0 = __ldg(sc.pos + 3 * i), P1 = __ldg(sc.pos + 3 * i + 1),
                 P2 = __ldg(sc.pos + 3 * i + 2);
     const float r = __ldg(sc.radius + i);
@@ -148,9 +156,9 @@ __device__ void pre_fwd_point(const Batch &b, const DevOpts &o, const DevScene &
                 float c0 = 0.f, c1 = 0.f, c2 = 0.f;
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
-                    c0 = fmaf(h[3 * k], Y[k], c0);
-                    c1 = fmaf(h[3 * k + 1], Y[k], c1);
-                    c2 = fmaf(h[3 * k + 2], Y[k], c2);
+                    c0 = fmaf(hs[(3 * k) * SH_STRIDE], Y[k], c0);
+                    c1 = fmaf(hs[(3 * k + 1) * SH_STRIDE], Y[k], c1);
+                    c2 = fmaf(hs[(3 * k + 2) * SH_STRIDE], Y[k], c2);
                 }
                 const float qp = -0.5f * LOG2E / (sg * sg);
                 rec[2 * pv] = make_float4(px, py, rc2, qp);
@@ -168,12 +176,12 @@ __device__ void pre_fwd_point(const Batch &b, const DevOpts &o, const DevScene &
     }
 }
 
-__global__ void __launch_bounds__(PRE_THREADS, 5)
+__global__ void __launch_bounds__(PRE_THREADS, 6)
 preprocess_fwd_kernel(Batch b, DevOpts o, float4 *__restrict__ rec, uint32_t *__restrict__ zbits,
                       uint32_t *__restrict__ ntiles, uint4 *__restrict__ rect,
                       unsigned long long *__restrict__ counters)
 {
-    __shared__ float s_sh[PRE_THREADS * 48];
+    __shared__ float s_sh[48 * SH_STRIDE];
     const int s = find_scene(b, blockIdx.x);
     const DevScene sc = b.scenes[s];
     const int64_t first = (int64_t)(blockIdx.x - sc.block_begin) * PRE_THREADS;
@@ -185,7 +193,7 @@ preprocess_fwd_kernel(Batch b, DevOpts o, float4 *__restrict__ rec, uint32_t *__
     uint32_t vis = 0, pairs = 0, zlo = 0xffffffffu, zhi = 0u;
     if ((int)threadIdx.x < count) {
         const int64_t i = first + threadIdx.x;
-        const float *hs = s_sh + threadIdx.x * K3;
+        const float *hs = s_sh + threadIdx.x; // coefficient j at hs[j * SH_STRIDE]
         switch (sc.deg) {
         case 0: pre_fwd_point<0>(b, o, sc, i, hs, rec, zbits, ntiles, rect, vis, pairs, zlo, zhi); break;
         case 1: pre_fwd_point<1>(b, o, sc, i, hs, rec, zbits, ntiles, rect, vis, pairs, zlo, zhi); break;
@@ -216,12 +224,9 @@ __device__ void pre_bwd_point(const Batch &b, const DevOpts &o, const DevScene &
                               float *__restrict__ grad_pos, float *__restrict__ grad_opacity)
 {
     constexpr int K = SH<DEG>::K;
-    float h[K * 3], dh[K * 3];
+    float dh[K * 3];
 #pragma unroll
-    for (int j = 0; j < K * 3; ++j) {
-        h[j] = hs[j];
-        dh[j] = 0.0f;
-    }
+    for (int j = 0; j < K * 3; ++j) dh[j] = 0.0f;
     const float P0 = __ldg(sc.pos + 3 * i), P1 = __ldg(sc.pos + 3 * i + 1),
                 P2 = __ldg(sc.pos + 3 * i + 2);
     const float r = __ldg(sc.radius + i);
@@ -282,7 +287,8 @@ __device__ void pre_bwd_point(const Batch &b, const DevOpts &o, const DevScene &
             dh[3 * k] = fmaf(Y[k], gb.x, dh[3 * k]);
             dh[3 * k + 1] = fmaf(Y[k], gb.y, dh[3 * k + 1]);
             dh[3 * k + 2] = fmaf(Y[k], gb.z, dh[3 * k + 2]);
-            w[k] = h[3 * k] * gb.x + h[3 * k + 1] * gb.y + h[3 * k + 2] * gb.z;
+            w[k] = hs[(3 * k) * SH_STRIDE] * gb.x + hs[(3 * k + 1) * SH_STRIDE] * gb.y +
+                   hs[(3 * k + 2) * SH_STRIDE] * gb.z;
         }
         if (DEG > 0) {
             float gx = 0.f, gy = 0.f, gz = 0.f;
@@ -312,7 +318,7 @@ __device__ void pre_bwd_point(const Batch &b, const DevOpts &o, const DevScene &
     grad_pos[3 * gi + 2] = dP2;
     if (grad_opacity) grad_opacity[gi] = dop;
 #pragma unroll
-    for (int j = 0; j < K * 3; ++j) hs[j] = dh[j];
+    for (int j = 0; j < K * 3; ++j) hs[j * SH_STRIDE] = dh[j];
 }
 
 __global__ void __launch_bounds__(PRE_THREADS)
@@ -320,7 +326,7 @@ preprocess_bwd_kernel(Batch b, DevOpts o, const float4 *__restrict__ g2d,
                       float *__restrict__ grad_pos, float *__restrict__ grad_sh,
                       float *__restrict__ grad_opacity)
 {
-    __shared__ float s_sh[PRE_THREADS * 48];
+    __shared__ float s_sh[48 * SH_STRIDE];
     const int s = find_scene(b, blockIdx.x);
     const DevScene sc = b.scenes[s];
     const int64_t first = (int64_t)(blockIdx.x - sc.block_begin) * PRE_THREADS;
@@ -331,7 +337,7 @@ preprocess_bwd_kernel(Batch b, DevOpts o, const float4 *__restrict__ g2d,
     __syncthreads();
     if ((int)threadIdx.x < count) {
         const int64_t i = first + threadIdx.x;
-        float *hs = s_sh + threadIdx.x * K3;
+        float *hs = s_sh + threadIdx.x; // coefficient j at hs[j * SH_STRIDE]
         switch (sc.deg) {
         case 0: pre_bwd_point<0>(b, o, sc, i, hs, g2d, grad_pos, grad_opacity); break;
         case 1: pre_bwd_point<1>(b, o, sc, i, hs, g2d, grad_pos, grad_opacity); break;
@@ -343,7 +349,10 @@ preprocess_bwd_kernel(Batch b, DevOpts o, const float4 *__restrict__ g2d,
     // coalesced write-back of the SH gradient slice
     float *dst = grad_sh + sc.sh_base + first * K3;
     const int total = count * K3;
-    for (int j = threadIdx.x; j < total; j += blockDim.x) dst[j] = s_sh[j];
+    for (int f = threadIdx.x; f < total; f += blockDim.x) {
+        const int p = f / K3;
+        dst[f] = s_sh[(f - p * K3) * SH_STRIDE + p];
+    }
 }
 
 } // namespace
