@@ -92,15 +92,38 @@ __device__ __forceinline__ PixelGeom pixel_geom(const Batch &b, uint32_t tile, i
     return g;
 }
 
-// Culling test of one record against a rectangle of pixel centres: the same
-// fp32 round-to-nearest operations as the per-pixel cutoff test, applied to
-// the rectangle point nearest the splat centre, so it never drops a point
-// that some pixel of the rectangle would include.
+// Culling test of one record against a rectangle of pixel centres: the
+// per-pixel cutoff test (the same fp32 round-to-nearest operations) applied
+// to the rectangle's pixel centre nearest the splat centre, floor(p) + 0.5
+// clamped into the rectangle per axis.  Rounding is monotone, so that
+// centre has the smallest fp32 squared distance of all the rectangle's
+// centres: the test keeps exactly the points some pixel of the rectangle
+// includes.
 __device__ __forceinline__ bool disc_meets_rect(const float4 a, const PixelGeom &g)
 {
-    const float cx = fminf(fmaxf(a.x, g.xl), g.xh), cy = fminf(fmaxf(a.y, g.yl), g.yh);
+    const float cx = fminf(fmaxf(floorf(a.x) + 0.5f, g.xl), g.xh);
+    const float cy = fminf(fmaxf(floorf(a.y) + 0.5f, g.yl), g.yh);
     const float ex = __fsub_rn(cx, a.x), ey = __fsub_rn(cy, a.y);
     return __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)) <= a.z;
+}
+
+// The rectangle of pixel centres of the warp's lanes that are still
+// active (g's own rectangle when every lane is).  Warp-wide reductions: all
+// 32 lanes must call it together, outside any lane-dependent branch or
+// short-circuit.
+__device__ __forceinline__ PixelGeom active_rect(const PixelGeom &g, bool active)
+{
+    PixelGeom r = g;
+    const uint32_t x = (uint32_t)g.x, y = (uint32_t)g.y;
+    const uint32_t x0 = __reduce_min_sync(0xffffffffu, active ? x : 0xffffffffu);
+    const uint32_t x1 = __reduce_max_sync(0xffffffffu, active ? x : 0u);
+    const uint32_t y0 = __reduce_min_sync(0xffffffffu, active ? y : 0xffffffffu);
+    const uint32_t y1 = __reduce_max_sync(0xffffffffu, active ? y : 0u);
+    r.xl = (float)x0 + 0.5f;
+    r.xh = (float)x1 + 0.5f;
+    r.yl = (float)y0 + 0.5f;
+    r.yh = (float)y1 + 0.5f;
+    return r;
 }
 
 // Sum of 8 per-lane values over the warp; lane l returns the total of value
@@ -312,7 +335,9 @@ __device__ __forceinline__ void fwd_stream_item(const Batch &b, const DevOpts &o
                 a_n = __ldg(rec + 2 * (size_t)pv_n);
             }
             if (c + 64 + lane < e) pv_nn = __ldg(pv_list + c + 64 + lane);
-            const bool hit = valid && disc_meets_rect(a, g);
+            // every lane takes part in the reductions, whatever its entry
+            const PixelGeom ar = active_rect(g, !done);
+            const bool hit = valid && disc_meets_rect(a, ar);
             uint32_t m = __ballot_sync(0xffffffffu, hit);
             if (hit) {
                 wbuf[lane] = a;
@@ -402,7 +427,10 @@ __device__ __forceinline__ void bwd_stream_item(const Batch &b, const DevOpts &o
             a_n = __ldg(rec + 2 * (size_t)pv_n);
         }
         if (c >= 64) pv_nn = __ldg(pv_list + s + (uint32_t)c - 64 + lane);
-        const bool hit = valid && disc_meets_rect(a, g);
+        // lanes whose composited list reaches into this chunk; every lane
+        // takes part in the reductions, whatever its entry
+        const PixelGeom ar = active_rect(g, (int64_t)L > c);
+        const bool hit = valid && disc_meets_rect(a, ar);
         uint32_t m = __ballot_sync(0xffffffffu, hit);
         if (hit) {
             wbuf[lane] = a;
