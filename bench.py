@@ -46,8 +46,12 @@ FLOP_TEST, FLOP_FWD, FLOP_BWD = 6, 11, 31
 # the kernel source it was taken on (sha256 of the file), else reported null.
 CAPTURED_TRAFFIC = {
     ("raster_bwd", "16x16", 0, 1): {
-        "bytes": 14.15e9 + 1.24e9, "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
-        "sha256": "fb43993112fc18653adbfed5c8abad478d5f91db97d8c7766865d9182c615b24",
+        "bytes": 13.39e9 + 1.19e9, "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
+        "sha256": "a072cbbdadd14dbdf1ae105a822430739ab1d6bfdb2221c1141f8f50e3b94cf7",
+        "profile": "profiles/raster_persist_dram_batched_1M_64views.md"},
+    ("raster_bwd", "16x32", 0, 1): {
+        "bytes": 16.55e9 + 1.14e9, "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
+        "sha256": "a072cbbdadd14dbdf1ae105a822430739ab1d6bfdb2221c1141f8f50e3b94cf7",
         "profile": "profiles/raster_persist_dram_batched_1M_64views.md"},
 }
 
