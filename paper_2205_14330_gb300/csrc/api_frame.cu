@@ -29,6 +29,83 @@ int nearest_maps(TempBufs &tb, const float *p1, int64_t n1, const SearchIndex &S
 
 bool finite_pos(float x) { return std::isfinite(x) && x >= 0.0f; }
 
+// Records one descent step on stream cs (capturing): nearest-point maps,
+// CD into *cur, dCD/dp2, Adam with the step number and rate of *ost.
+int record_step(const float *p1, int64_t n1, const SearchIndex &S1, float *pos2, int64_t n2,
+                const pbr_frame_cfg &cfg, float *grad, float *m, float *v, int32_t *nn12,
+                int32_t *nn21, double *cur, OptState *ost, cudaStream_t cs)
+{
+    TempBufs it(cs);
+    PBR_TRY(nearest_maps(it, p1, n1, S1, pos2, n2, nn12, nn21, cs));
+    PBR_CUDA(cudaMemsetAsync(cur, 0, sizeof(double), cs));
+    launch_chamfer(p1, n1, pos2, n2, nn12, nn21, grad, cur, cs);
+    launch_step_counter(ost, cs);
+    const OptParams prm{1, cfg.lr, cfg.beta1, cfg.beta2, cfg.eps, 0};
+    launch_optimizer(prm, ost, 0, pos2, grad, m, v, 3 * n2, cs);
+    PBR_CUDA(cudaGetLastError());
+    return PBR_OK;
+}
+
+// cfg.iters descent steps on pos2, the loss before step t in hist[t - 1]:
+// the step is captured once on a private stream and replayed.
+int descend(TempBufs &tb, const float *p1, int64_t n1, const SearchIndex &S1, float *pos2,
+            int64_t n2, const pbr_frame_cfg &cfg, float *grad, float *m, float *v,
+            int32_t *nn12, int32_t *nn21, double *hist, cudaStream_t s)
+{
+    OptState *ost;
+    double *cur;
+    PBR_TRY(tb.alloc(&ost, sizeof(OptState)));
+    PBR_TRY(tb.alloc(&cur, sizeof(double)));
+    const OptState init{{cfg.lr, 0.0f, 0.0f}, 0};
+    PBR_CUDA(cudaMemcpyAsync(ost, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int rc = PBR_OK;
+    do {
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            rc = set_error(PBR_ERR_CUDA, "pbr_frame_init: stream or event creation failed");
+            break;
+        }
+        // cs starts after everything queued on s so far
+        if (cudaEventRecord(ev, s) != cudaSuccess || cudaStreamWaitEvent(cs, ev, 0) != cudaSuccess) {
+            rc = set_error(PBR_ERR_CUDA, "pbr_frame_init: stream ordering failed");
+            break;
+        }
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            rc = set_error(PBR_ERR_CUDA, "pbr_frame_init: capture failed to start");
+            break;
+        }
+        rc = record_step(p1, n1, S1, pos2, n2, cfg, grad, m, v, nn12, nn21, cur, ost, cs);
+        const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+        if (rc != PBR_OK) break;
+        if (ec != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+            cudaGetLastError();
+            rc = set_error(PBR_ERR_CUDA, "pbr_frame_init: step capture failed");
+            break;
+        }
+        for (int t = 1; t <= cfg.iters && rc == PBR_OK; ++t) {
+            if (cudaGraphLaunch(exec, cs) != cudaSuccess ||
+                cudaMemcpyAsync(hist + t - 1, cur, sizeof(double), cudaMemcpyDeviceToDevice,
+                                cs) != cudaSuccess)
+                rc = set_error(PBR_ERR_CUDA, "pbr_frame_init: step replay failed");
+        }
+        // s continues after the replays
+        if (cudaEventRecord(ev, cs) != cudaSuccess || cudaStreamWaitEvent(s, ev, 0) != cudaSuccess)
+            rc = set_error(PBR_ERR_CUDA, "pbr_frame_init: stream ordering failed");
+    } while (false);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) {
+        cudaStreamSynchronize(cs);
+        cudaStreamDestroy(cs);
+    }
+    if (ev) cudaEventDestroy(ev);
+    return rc;
+}
+
 } // namespace
 
 extern "C" void pbr_default_frame_cfg(pbr_frame_cfg *cfg)
@@ -104,16 +181,16 @@ extern "C" int pbr_frame_init(pbr_ctx *ctx, const pbr_points *prev, float *pos2,
     PBR_CUDA(cudaMemsetAsync(hist, 0, sizeof(double) * (iters + 1), s));
 
     // Adam descent of the new positions on the Chamfer distance; the loss
-    // before each step, and after the last, goes to the history
-    for (int t = 1; t <= iters + 1; ++t) {
+    // before each step, and after the last, goes to the history.  One step
+    // (index of the moving cloud, both nearest-point searches, CD and its
+    // gradient, Adam) has the same shape every time, so it is captured once
+    // as a CUDA graph on a private stream and replayed; Adam's step number
+    // and rate live in device memory.
+    if (iters > 0) PBR_TRY(descend(tb, p1, n1, S1, pos2, n2, *cfg, grad, m, v, nn12, nn21, hist, s));
+    {
         TempBufs it(s);
         PBR_TRY(nearest_maps(it, p1, n1, S1, pos2, n2, nn12, nn21, s));
-        launch_chamfer(p1, n1, pos2, n2, nn12, nn21, t <= iters ? grad : nullptr, hist + t - 1,
-                       s);
-        if (t <= iters) {
-            const OptParams prm{1, cfg->lr, cfg->beta1, cfg->beta2, cfg->eps, t};
-            launch_optimizer(prm, nullptr, 0, pos2, grad, m, v, 3 * n2, s);
-        }
+        launch_chamfer(p1, n1, pos2, n2, nn12, nn21, nullptr, hist + iters, s);
     }
 
     // parameters: means over the k closest points of the previous frame
