@@ -41,7 +41,10 @@ def _cloud(n, shapes=6, frac=0.02, deg=2, seed=0):
 
 
 # ---------------------------------------------------------------- kNN
-@pytest.mark.parametrize("k,grid_n", [(8, 0), (1, 0), (32, 0), (8, 1), (8, 5), (8, 200)])
+# grid_n = 700: 700^3 cells exceed the dense cell-table limit (2^28), so the
+# fine level looks cells up by binary search
+@pytest.mark.parametrize("k,grid_n", [(8, 0), (1, 0), (32, 0), (8, 1), (8, 5), (8, 200),
+                                      (8, 700)])
 def test_knn_self_exact(env, k, grid_n):
     pbr, r = env
     pos = _cloud(3000)["pos"]
@@ -136,7 +139,7 @@ def test_refine_stages_match_oracle(env, stages):
         assert 0 < counts[1] < counts[0]
 
 
-@pytest.mark.parametrize("n_vox,k", [(1, 4), (2, 3), (7, 1), (64, 16), (300, 32)])
+@pytest.mark.parametrize("n_vox,k", [(1, 4), (2, 3), (7, 1), (64, 16), (300, 32), (700, 8)])
 def test_refine_grid_sizes_and_k(env, n_vox, k):
     pbr, r = env
     d = _cloud(2500, deg=1, seed=1)
