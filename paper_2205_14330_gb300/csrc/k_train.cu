@@ -23,7 +23,14 @@ __global__ void loss_tv_kernel(const DevView *__restrict__ views, int kind, floa
 {
     const DevView &V = views[blockIdx.y];
     const int64_t npx = (int64_t)V.W * V.H;
-    double acc = 0.0;
+    // compensated fp32 per thread, fp64 across threads: no per-element fp64
+    float acc = 0.0f, comp = 0.0f;
+    auto add = [&](float x) {
+        const float y = __fsub_rn(x, comp);
+        const float t = __fadd_rn(acc, y);
+        comp = __fsub_rn(__fsub_rn(t, acc), y);
+        acc = t;
+    };
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npx;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(p % V.W), y = (int)(p / V.W);
@@ -34,23 +41,23 @@ __global__ void loss_tv_kernel(const DevView *__restrict__ views, int kind, floa
             const float d = a - target[3 * q + c];
             float gv;
             if (kind == 0) {
-                acc += (double)d * (double)d;
+                add(d * d);
                 gv = 2.0f * d;
             } else {
-                acc += fabs((double)d);
+                add(fabsf(d));
                 gv = sgnf(d);
             }
             if (lam != 0.0f) {
                 float tv = 0.0f;
                 if (x + 1 < V.W) {
                     const float dx = pred[3 * (q + 1) + c] - a;
-                    acc += (double)lam * fabs((double)dx);
+                    add(lam * fabsf(dx));
                     tv -= sgnf(dx);
                 }
                 if (x > 0) tv += sgnf(a - pred[3 * (q - 1) + c]);
                 if (y + 1 < V.H) {
                     const float dy = pred[3 * (q + V.W) + c] - a;
-                    acc += (double)lam * fabs((double)dy);
+                    add(lam * fabsf(dy));
                     tv -= sgnf(dy);
                 }
                 if (y > 0) tv += sgnf(a - pred[3 * (q - V.W) + c]);
@@ -59,9 +66,10 @@ __global__ void loss_tv_kernel(const DevView *__restrict__ views, int kind, floa
             grad[3 * q + c] = gv;
         }
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    double tot = (double)acc - (double)comp;
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
     __shared__ double s_w[32];
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = tot;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
