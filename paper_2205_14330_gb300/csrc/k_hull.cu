@@ -107,19 +107,23 @@ __global__ void hull_take_kernel(const float *__restrict__ cand, const uint32_t 
 }
 
 // Standard normals for coefficients [c0, c0 + count) of the flattened
-// [points, coefficients] array, Box-Muller in fp64 on stream seed:
-// pair p = c / 2 uses outputs 2p and 2p + 1.
+// [points, coefficients] array, Box-Muller on stream seed: pair p = c / 2
+// uses outputs 2p and 2p + 1.  fp32 (logf, sincospif): no decision depends
+// on these values, and fp64 transcendentals run at a small fraction of the
+// fp32 rate on this GPU.  u1 and u2 are exact in fp32 (24-bit integers times
+// 2^-24).
 __global__ void sh_normals_kernel(uint64_t seed, int64_t c0, int64_t count,
                                   float *__restrict__ out)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t c = (uint64_t)(c0 + i), p = c >> 1;
-        const double u1 = ((double)(splitmix64(seed, 2 * p) >> 40) + 1.0) * 0x1p-24;
-        const double u2 = (double)(splitmix64(seed, 2 * p + 1) >> 40) * 0x1p-24;
-        const double r = sqrt(-2.0 * log(u1));
-        const double a = 6.283185307179586 * u2;
-        out[i] = (float)((c & 1) ? r * sin(a) : r * cos(a));
+        const float u1 = ((float)(uint32_t)(splitmix64(seed, 2 * p) >> 40) + 1.0f) * 0x1p-24f;
+        const float u2 = (float)(uint32_t)(splitmix64(seed, 2 * p + 1) >> 40) * 0x1p-24f;
+        const float r = sqrtf(-2.0f * logf(u1));
+        float sn, cs;
+        sincospif(2.0f * u2, &sn, &cs);
+        out[i] = (c & 1) ? r * sn : r * cs;
     }
 }
 

@@ -77,7 +77,8 @@ def test_sampler_matches_oracle(env, hull, n_target, seed):
     assert drawn == wdrawn
     assert np.array_equal(pos.cpu().numpy(), want)
     z = H.sh_normals(seed, n_target, 27).reshape(n_target, 9, 3)
-    assert np.allclose(sh.cpu().numpy(), z, rtol=1e-6, atol=1e-6)
+    # fp32 logarithm and sine/cosine on the GPU against fp64: a few ulps
+    assert np.allclose(sh.cpu().numpy(), z, rtol=1e-5, atol=1e-6)
 
 
 def test_sampler_limits_and_empty_masks(env, hull):
