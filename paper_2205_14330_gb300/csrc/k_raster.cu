@@ -107,6 +107,19 @@ __device__ __forceinline__ bool disc_meets_rect(const float4 a, const PixelGeom 
     return __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)) <= a.z;
 }
 
+// Whether the cutoff disc of a record holds every pixel centre of the
+// rectangle: the per-pixel fp32 test applied to the centre farthest from the
+// splat centre (per axis the edge with the larger rounded offset), which by
+// monotone rounding has the largest fp32 squared distance.
+__device__ __forceinline__ bool disc_covers_rect(const float4 a, const PixelGeom &g)
+{
+    const float lx = __fsub_rn(g.xl, a.x), hx = __fsub_rn(g.xh, a.x);
+    const float ly = __fsub_rn(g.yl, a.y), hy = __fsub_rn(g.yh, a.y);
+    const float ex = fabsf(lx) > fabsf(hx) ? lx : hx;
+    const float ey = fabsf(ly) > fabsf(hy) ? ly : hy;
+    return __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)) <= a.z;
+}
+
 // The rectangle of pixel centres of the warp's lanes that are still
 // active (g's own rectangle when every lane is).  Warp-wide reductions: all
 // 32 lanes must call it together, outside any lane-dependent branch or
@@ -338,14 +351,17 @@ __device__ __forceinline__ void fwd_stream_item(const Batch &b, const DevOpts &o
             // every lane takes part in the reductions, whatever its entry
             const PixelGeom ar = active_rect(g, !done);
             const bool hit = valid && disc_meets_rect(a, ar);
+            const bool covers = hit && disc_covers_rect(a, ar);
             uint32_t m = __ballot_sync(0xffffffffu, hit);
+            // entries whose disc holds every active pixel need no per-pixel test
+            uint32_t mine = __ballot_sync(0xffffffffu, covers);
             if (hit) {
                 wbuf[lane] = a;
                 wbuf[32 + lane] = __ldg(rec + 2 * (size_t)pv + 1);
             }
             __syncwarp();
             if (!done) examined += (uint32_t)__popc(m);
-            uint32_t mine = 0;
+            m &= ~mine;
             while (m) {
                 const int j = __ffs(m) - 1;
                 m &= m - 1;
