@@ -702,12 +702,12 @@ def main():
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
     if dom in ("raster_fwd", "raster_bwd"):
+        # the work every correct schedule does, whatever its culling: the
+        # cutoff test and the blend (or adjoint) of each composited pair
         if dom == "raster_fwd":
-            flops = (pair_stats["fwd_examined"] * FLOP_TEST
-                     + pair_stats["fwd_composited"] * FLOP_FWD)
+            flops = pair_stats["fwd_composited"] * (FLOP_TEST + FLOP_FWD)
         else:
-            flops = (pair_stats["bwd_examined"] * FLOP_TEST
-                     + pair_stats["bwd_contributing"] * FLOP_BWD)
+            flops = pair_stats["bwd_contributing"] * (FLOP_TEST + FLOP_BWD)
         achieved = flops / (stage_ms[dom] * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                 "unit": "TFLOP/s", "frac": achieved / fp32_peak,

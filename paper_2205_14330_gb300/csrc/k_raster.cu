@@ -23,7 +23,8 @@
 // atomics per warp and point) in the warp-streamed schedule.
 //
 // A block covers one TW x TH screen tile; each warp owns an 8 x 4 sub-block
-// of it and skips list entries whose cutoff disc misses its sub-block.  Two
+// of it (an 8 x 8 one, two pixels per lane, in the persistent backward) and
+// skips list entries whose cutoff disc misses its still active pixels.  Two
 // schedules:
 //   - warp-streamed (batch depth 0, default): every warp walks the tile list
 //     by itself, 32 entries per step (loads shared through L1), culls them
@@ -71,15 +72,12 @@ struct PixelGeom {
     float ux, uy, xl, xh, yl, yh;
 };
 
-// Sub-block `w` of tile `tile` (sub-blocks numbered row-major, TW/8 per row).
-template <int TW, int TH>
-__device__ __forceinline__ PixelGeom pixel_geom(const Batch &b, uint32_t tile, int w, int lane)
+// Pixel (sx0 + (lane & 7), sy0 + (lane >> 3)) of view V and the 8 x 4
+// rectangle of pixel centres with corner (sx0, sy0).
+__device__ __forceinline__ PixelGeom pixel_geom_at(const DevView *V, int sx0, int sy0, int lane)
 {
     PixelGeom g;
-    g.V = &b.views[find_view_by_tile(b, tile)];
-    const uint32_t local = tile - g.V->tile_base;
-    const int tx = (int)(local % (uint32_t)g.V->tiles_x), ty = (int)(local / (uint32_t)g.V->tiles_x);
-    const int sx0 = tx * TW + (w % (TW / 8)) * 8, sy0 = ty * TH + (w / (TW / 8)) * 4;
+    g.V = V;
     g.x = sx0 + (lane & 7);
     g.y = sy0 + (lane >> 3);
     g.inside = g.x < g.V->W && g.y < g.V->H;
@@ -90,6 +88,16 @@ __device__ __forceinline__ PixelGeom pixel_geom(const Batch &b, uint32_t tile, i
     g.yl = (float)sy0 + 0.5f;
     g.yh = (float)sy0 + 3.5f;
     return g;
+}
+
+// Sub-block `w` of tile `tile` (sub-blocks numbered row-major, TW/8 per row).
+template <int TW, int TH>
+__device__ __forceinline__ PixelGeom pixel_geom(const Batch &b, uint32_t tile, int w, int lane)
+{
+    const DevView *V = &b.views[find_view_by_tile(b, tile)];
+    const uint32_t local = tile - V->tile_base;
+    const int tx = (int)(local % (uint32_t)V->tiles_x), ty = (int)(local / (uint32_t)V->tiles_x);
+    return pixel_geom_at(V, tx * TW + (w % (TW / 8)) * 8, ty * TH + (w / (TW / 8)) * 4, lane);
 }
 
 // Culling test of one record against a rectangle of pixel centres: the
@@ -132,6 +140,28 @@ __device__ __forceinline__ PixelGeom active_rect(const PixelGeom &g, bool active
     const uint32_t x1 = __reduce_max_sync(0xffffffffu, active ? x : 0u);
     const uint32_t y0 = __reduce_min_sync(0xffffffffu, active ? y : 0xffffffffu);
     const uint32_t y1 = __reduce_max_sync(0xffffffffu, active ? y : 0u);
+    r.xl = (float)x0 + 0.5f;
+    r.xh = (float)x1 + 0.5f;
+    r.yl = (float)y0 + 0.5f;
+    r.yh = (float)y1 + 0.5f;
+    return r;
+}
+
+// active_rect for a warp that owns two pixels per lane, a and b (b in the
+// same column, below a): the rectangle of the centres of its still active
+// pixels.  The same calling rule holds.
+__device__ __forceinline__ PixelGeom active_rect2(const PixelGeom &a, bool act_a,
+                                                  const PixelGeom &b, bool act_b)
+{
+    PixelGeom r = a;
+    const bool act = act_a || act_b;
+    const uint32_t x = (uint32_t)a.x;
+    const uint32_t ylo = act_a ? (uint32_t)a.y : act_b ? (uint32_t)b.y : 0xffffffffu;
+    const uint32_t yhi = act_b ? (uint32_t)b.y : act_a ? (uint32_t)a.y : 0u;
+    const uint32_t x0 = __reduce_min_sync(0xffffffffu, act ? x : 0xffffffffu);
+    const uint32_t x1 = __reduce_max_sync(0xffffffffu, act ? x : 0u);
+    const uint32_t y0 = __reduce_min_sync(0xffffffffu, ylo);
+    const uint32_t y1 = __reduce_max_sync(0xffffffffu, yhi);
     r.xl = (float)x0 + 0.5f;
     r.xh = (float)x1 + 0.5f;
     r.yl = (float)y0 + 0.5f;
@@ -398,6 +428,10 @@ __device__ __forceinline__ void fwd_stream_item(const Batch &b, const DevOpts &o
 // workload, the backward runs fastest between 12 and 16 (13.0 ms against
 // 14.8 ms with the reduction for 2 or more and 22 ms with atomics only).
 constexpr int BWD_DIRECT_MAX = 16;
+// The same for the two-pixels-per-lane backward, whose lanes add the terms
+// of both their pixels: fastest at 24 (11.1 ms; 11.4 ms at 16, 11.9 ms at
+// 8, 15.8 ms with atomics only) on the same workload.
+constexpr int BWD_PAIR_DIRECT_MAX = 24;
 
 // One warp back-propagates through sub-block `sub` of tile `tile`.
 template <int TW, int TH>
@@ -483,6 +517,122 @@ __device__ __forceinline__ void bwd_stream_item(const Batch &b, const DevOpts &o
     }
 }
 
+// Adjoint state of one pixel: T after its last composited point, the colour
+// behind (S, starting from the background term), dL/dC and the list length.
+struct BwdPixel {
+    float T, S, g0, g1, g2;
+    uint32_t L;
+};
+
+__device__ __forceinline__ BwdPixel bwd_pixel(const PixelGeom &g, const DevOpts &o,
+                                              const float *__restrict__ T_final,
+                                              const uint32_t *__restrict__ n_contrib,
+                                              const float *__restrict__ grad_rgb)
+{
+    BwdPixel p{1.0f, 0.f, 0.f, 0.f, 0.f, 0u};
+    if (g.inside) {
+        const int64_t pix = g.V->pix_base + (int64_t)g.y * g.V->W + g.x;
+        p.T = T_final[pix];
+        p.L = n_contrib[pix];
+        p.g0 = grad_rgb[3 * pix];
+        p.g1 = grad_rgb[3 * pix + 1];
+        p.g2 = grad_rgb[3 * pix + 2];
+    }
+    p.S = p.T * (o.bg[0] * p.g0 + o.bg[1] * p.g1 + o.bg[2] * p.g2);
+    return p;
+}
+
+// Backward of one 8 x 8 sub-block (sub-blocks numbered row-major, TW/8 per
+// row) by one warp, for the persistent schedule: lane l owns the pixels
+// (l & 7, l >> 3) and (l & 7, 4 + (l >> 3)).  Per listed point the lane
+// forms the adjoint at both of its pixels and adds the two term vectors,
+// so the per-point warp work (staging, cull, reduction or atomics) serves
+// 64 pixels instead of 32.  Each pixel's T and S recursions are the same
+// operations as in the one-pixel walk.
+template <int TW, int TH>
+__device__ __forceinline__ void bwd_pair_item(const Batch &b, const DevOpts &o, uint32_t tile,
+                                              int sub, int lane, const uint2 *__restrict__ ranges,
+                                              const uint32_t *__restrict__ pv_list,
+                                              const float4 *__restrict__ rec,
+                                              const float *__restrict__ T_final,
+                                              const uint32_t *__restrict__ n_contrib,
+                                              const float *__restrict__ grad_rgb,
+                                              float *__restrict__ g2d, uint32_t &examined,
+                                              uint32_t &used, float4 *wbuf, uint32_t *wpv)
+{
+    const DevView *V = &b.views[find_view_by_tile(b, tile)];
+    const uint32_t local = tile - V->tile_base;
+    const int tx = (int)(local % (uint32_t)V->tiles_x), ty = (int)(local / (uint32_t)V->tiles_x);
+    const int sx0 = tx * TW + (sub % (TW / 8)) * 8, sy0 = ty * TH + (sub / (TW / 8)) * 8;
+    const PixelGeom gA = pixel_geom_at(V, sx0, sy0, lane);
+    const PixelGeom gB = pixel_geom_at(V, sx0, sy0 + 4, lane);
+    BwdPixel pA = bwd_pixel(gA, o, T_final, n_contrib, grad_rgb);
+    BwdPixel pB = bwd_pixel(gB, o, T_final, n_contrib, grad_rgb);
+    const uint32_t s = ranges[tile].x;
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, pA.L > pB.L ? pA.L : pB.L);
+    if (wmax == 0) return;
+    int64_t c = (int64_t)((wmax - 1) & ~31u);
+    uint32_t pv_n = 0, pv_nn = 0;
+    float4 a_n = make_float4(0.f, 0.f, -1.f, 0.f);
+    if ((uint32_t)c + lane < wmax) {
+        pv_n = __ldg(pv_list + s + (uint32_t)c + lane);
+        a_n = __ldg(rec + 2 * (size_t)pv_n);
+    }
+    if (c >= 32) pv_nn = __ldg(pv_list + s + (uint32_t)c - 32 + lane);
+    for (; c >= 0; c -= 32) {
+        const uint32_t pv = pv_n;
+        const float4 a = a_n;
+        const bool valid = (uint32_t)c + lane < wmax;
+        if (c >= 32) {
+            pv_n = pv_nn;
+            a_n = __ldg(rec + 2 * (size_t)pv_n);
+        }
+        if (c >= 64) pv_nn = __ldg(pv_list + s + (uint32_t)c - 64 + lane);
+        // every lane takes part in the reductions, whatever its entry
+        const PixelGeom ar = active_rect2(gA, (int64_t)pA.L > c, gB, (int64_t)pB.L > c);
+        const bool hit = valid && disc_meets_rect(a, ar);
+        uint32_t m = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+            wbuf[lane] = a;
+            wbuf[32 + lane] = __ldg(rec + 2 * (size_t)pv + 1);
+            wpv[lane] = pv;
+        }
+        __syncwarp();
+        while (m) {
+            const int j = 31 - __clz(m); // back to front
+            m &= ~(1u << j);
+            const float4 aj = wbuf[j];
+            const float4 cj = wbuf[32 + j];
+            const uint32_t idx = (uint32_t)c + j;
+            const bool bA = idx < pA.L, bB = idx < pB.L;
+            float dxA, dyA, dxB, dyB;
+            const float d2A = pixel_d2(gA.ux, gA.uy, aj.x, aj.y, dxA, dyA);
+            const float d2B = pixel_d2(gB.ux, gB.uy, aj.x, aj.y, dxB, dyB);
+            const bool cA = bA && d2A <= aj.z, cB = bB && d2B <= aj.z;
+            examined += (uint32_t)bA + (uint32_t)bB;
+            used += (uint32_t)cA + (uint32_t)cB;
+            const uint32_t cm = __ballot_sync(0xffffffffu, cA || cB);
+            if (cm) {
+                float v[8], u[8];
+                pixel_adjoint_masked(cA ? 1.0f : 0.0f, d2A, dxA, dyA, aj, cj, o.alpha_max, pA.g0,
+                                     pA.g1, pA.g2, pA.T, pA.S, v);
+                pixel_adjoint_masked(cB ? 1.0f : 0.0f, d2B, dxB, dyB, aj, cj, o.alpha_max, pB.g0,
+                                     pB.g1, pB.g2, pB.T, pB.S, u);
+#pragma unroll
+                for (int k = 0; k < 7; ++k) v[k] += u[k];
+                if (__popc(cm) > BWD_PAIR_DIRECT_MAX) {
+                    warp_add_terms(v, lane, g2d, wpv[j]);
+                } else if (cA || cB) { // few lanes: each adds its own terms
+                    float4 *dst = reinterpret_cast<float4 *>(g2d) + 2 * (size_t)wpv[j];
+                    atomicAdd(dst, make_float4(v[0], v[1], v[2], v[3]));
+                    atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], 0.f));
+                }
+            }
+        }
+        __syncwarp(); // chunk consumed before the buffer is refilled
+    }
+}
+
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW * TH)
 raster_fwd_stream_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
@@ -557,14 +707,14 @@ raster_bwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
                           unsigned long long *__restrict__ stats, const uint32_t *__restrict__ order,
                           uint32_t *work)
 {
-    constexpr uint32_t SUBS = (TW / 8) * (TH / 4);
+    constexpr uint32_t SUBS = (TW / 8) * (TH / 8);
     __shared__ float4 s_buf[PERSIST_THREADS / 32][64];
     __shared__ uint32_t s_pv[PERSIST_THREADS / 32][32];
     const int lane = threadIdx.x & 31;
     const uint32_t n_items = b.n_tiles * SUBS;
     uint32_t ex = 0, us = 0;
     for (uint32_t it = next_item(work, lane); it < n_items; it = next_item(work, lane))
-        bwd_stream_item<TW, TH>(b, o, order[it / SUBS], (int)(it % SUBS), lane, ranges, pv_list,
+        bwd_pair_item<TW, TH>(b, o, order[it / SUBS], (int)(it % SUBS), lane, ranges, pv_list,
                                 rec, T_final, n_contrib, grad_rgb, g2d, ex, us,
                                 s_buf[threadIdx.x >> 5], s_pv[threadIdx.x >> 5]);
     add_stats(stats ? stats + 2 : nullptr, ex, us, lane);

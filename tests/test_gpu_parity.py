@@ -272,9 +272,11 @@ def test_tiny_config_gradients(R):
                                 dict(bg=(0.3, 0.1, 0.7)), dict(tile=(8, 8)), dict(tile=(16, 32)),
                                 dict(batch_depth=256), dict(tile=(8, 8), batch_depth=64),
                                 dict(max_per_pixel=15, batch_depth=128), dict(persistent=1),
-                                dict(persistent=1, tile=(16, 32), max_per_pixel=15)],
+                                dict(persistent=1, tile=(16, 32), max_per_pixel=15),
+                                dict(persistent=1, tile=(8, 8))],
                          ids=["world-dir", "ndc", "n15", "bg", "8x8", "16x32", "staged",
-                              "staged-8x8", "staged-n15", "persistent", "persistent-16x32-n15"])
+                              "staged-8x8", "staged-n15", "persistent", "persistent-16x32-n15",
+                              "persistent-8x8"])
 def test_gradient_variants(R, kw):
     import torch
     sc = _small_scene(20, n=400, deg=3)
