@@ -218,9 +218,47 @@ preprocess_fwd_kernel(Batch b, DevOpts o, float4 *__restrict__ rec, uint32_t *__
 }
 
 // ------------------------------------------------------------- backward
+// The screen-space terms of a point's views are fetched BWD_AHEAD views
+// ahead with per-thread asynchronous copies into shared memory, so that
+// several 32-byte reads per thread are in flight while earlier views are
+// computed (the kernel is otherwise bound by the latency of one read per
+// view).  BWD_AHEAD + 1 slots per thread: a slot is refilled one view after
+// its contents were read.
+constexpr int BWD_AHEAD = 4;
+constexpr int BWD_SLOTS = BWD_AHEAD + 1;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N> __device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Starts the copy of view slot `vv`'s two float4 terms of point i into the
+// thread's slot.  sg: this thread's slots, [slot][half] with a stride of
+// PRE_THREADS float4 between entries.
+__device__ __forceinline__ void fetch_view_terms(const Batch &b, const DevScene &sc, int64_t i,
+                                                 int vv, const float4 *__restrict__ g2d,
+                                                 float4 *sg)
+{
+    const int64_t pv = b.views[b.view_list[sc.view_begin + vv]].pv_base + i;
+    float4 *dst = sg + (vv % BWD_SLOTS) * 2 * PRE_THREADS;
+    cp_async16(dst, g2d + 2 * pv);
+    cp_async16(dst + PRE_THREADS, g2d + 2 * pv + 1);
+}
+
 template <int DEG>
 __device__ void pre_bwd_point(const Batch &b, const DevOpts &o, const DevScene &sc, int64_t i,
-                              float *hs, const float4 *__restrict__ g2d,
+                              float *hs, float4 *sg, const float4 *__restrict__ g2d,
                               float *__restrict__ grad_pos, float *__restrict__ grad_opacity)
 {
     constexpr int K = SH<DEG>::K;
@@ -232,23 +270,21 @@ __device__ void pre_bwd_point(const Batch &b, const DevOpts &o, const DevScene &
     const float r = __ldg(sc.radius + i);
     float dP0 = 0.f, dP1 = 0.f, dP2 = 0.f, dop = 0.f;
 
-    // the next view's screen-space terms are loaded one view ahead
-    float4 ga_n = make_float4(0.f, 0.f, 0.f, 0.f), gb_n = ga_n;
-    if (sc.view_count > 0) {
-        const int64_t pv0 = b.views[b.view_list[sc.view_begin]].pv_base + i;
-        ga_n = g2d[2 * pv0];
-        gb_n = g2d[2 * pv0 + 1];
+    const int nv = sc.view_count;
+#pragma unroll
+    for (int d = 0; d < BWD_AHEAD; ++d) {
+        if (d < nv) fetch_view_terms(b, sc, i, d, g2d, sg);
+        cp_async_commit(); // one group per view slot, empty past the end
     }
-    for (int vv = 0; vv < sc.view_count; ++vv) {
+    for (int vv = 0; vv < nv; ++vv) {
         const int v = b.view_list[sc.view_begin + vv];
         const DevView &V = b.views[v];
-        const float4 ga = ga_n; // dpx, dpy, dq, do
-        const float4 gb = gb_n; // dr, dg, db, -
-        if (vv + 1 < sc.view_count) {
-            const int64_t pvn = b.views[b.view_list[sc.view_begin + vv + 1]].pv_base + i;
-            ga_n = g2d[2 * pvn];
-            gb_n = g2d[2 * pvn + 1];
-        }
+        cp_async_wait<BWD_AHEAD - 1>(); // the copies of views 0..vv have landed
+        const float4 *slot = sg + (vv % BWD_SLOTS) * 2 * PRE_THREADS;
+        const float4 ga = slot[0];           // dpx, dpy, dq, do
+        const float4 gb = slot[PRE_THREADS]; // dr, dg, db, -
+        if (vv + BWD_AHEAD < nv) fetch_view_terms(b, sc, i, vv + BWD_AHEAD, g2d, sg);
+        cp_async_commit();
         if (ga.x == 0.f && ga.y == 0.f && ga.z == 0.f && ga.w == 0.f && gb.x == 0.f &&
             gb.y == 0.f && gb.z == 0.f)
             continue; // culled or never composited
@@ -327,6 +363,7 @@ preprocess_bwd_kernel(Batch b, DevOpts o, const float4 *__restrict__ g2d,
                       float *__restrict__ grad_opacity)
 {
     __shared__ float s_sh[48 * SH_STRIDE];
+    __shared__ float4 s_g[BWD_SLOTS * 2 * PRE_THREADS]; // [slot][half][thread]
     const int s = find_scene(b, blockIdx.x);
     const DevScene sc = b.scenes[s];
     const int64_t first = (int64_t)(blockIdx.x - sc.block_begin) * PRE_THREADS;
@@ -338,11 +375,12 @@ preprocess_bwd_kernel(Batch b, DevOpts o, const float4 *__restrict__ g2d,
     if ((int)threadIdx.x < count) {
         const int64_t i = first + threadIdx.x;
         float *hs = s_sh + threadIdx.x; // coefficient j at hs[j * SH_STRIDE]
+        float4 *sg = s_g + threadIdx.x;
         switch (sc.deg) {
-        case 0: pre_bwd_point<0>(b, o, sc, i, hs, g2d, grad_pos, grad_opacity); break;
-        case 1: pre_bwd_point<1>(b, o, sc, i, hs, g2d, grad_pos, grad_opacity); break;
-        case 2: pre_bwd_point<2>(b, o, sc, i, hs, g2d, grad_pos, grad_opacity); break;
-        default: pre_bwd_point<3>(b, o, sc, i, hs, g2d, grad_pos, grad_opacity); break;
+        case 0: pre_bwd_point<0>(b, o, sc, i, hs, sg, g2d, grad_pos, grad_opacity); break;
+        case 1: pre_bwd_point<1>(b, o, sc, i, hs, sg, g2d, grad_pos, grad_opacity); break;
+        case 2: pre_bwd_point<2>(b, o, sc, i, hs, sg, g2d, grad_pos, grad_opacity); break;
+        default: pre_bwd_point<3>(b, o, sc, i, hs, sg, g2d, grad_pos, grad_opacity); break;
         }
     }
     __syncthreads();
