@@ -183,7 +183,7 @@ void enqueue_forward(pbr_graph *g, cudaStream_t s)
     const bool persist = g->opts.persistent && g->opts.batch_depth == 0;
     if (persist) launch_tile_order(g->ranges, L.n_tiles, g->order, g->work, s);
     launch_raster_fwd(b, o, g->opts.batch_depth, g->ranges, tv, g->rec, g->out_rgb, g->T_final,
-                      g->n_contrib, g->counters + 2, s, persist ? g->order : nullptr, g->work);
+                      g->n_contrib, nullptr, s, persist ? g->order : nullptr, g->work);
 }
 
 void enqueue_backward(pbr_graph *g, const float *grad_rgb, cudaStream_t s)
@@ -194,7 +194,7 @@ void enqueue_backward(pbr_graph *g, const float *grad_rgb, cudaStream_t s)
     const bool persist = g->opts.persistent && g->opts.batch_depth == 0;
     if (persist) reset_work_counters(g->work, s);
     launch_raster_bwd(b, g->dopts, g->opts.batch_depth, g->ranges, g->vals_final, g->rec,
-                      g->T_final, g->n_contrib, grad_rgb, g->g2d, g->counters + 2, s,
+                      g->T_final, g->n_contrib, grad_rgb, g->g2d, nullptr, s,
                       persist ? g->order : nullptr, g->work);
     launch_preprocess_bwd(b, g->dopts, g->g2d, g->grad_pos, g->grad_sh, g->grad_opacity, s);
 }

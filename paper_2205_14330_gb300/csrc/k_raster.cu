@@ -348,7 +348,7 @@ __device__ __forceinline__ void add_stats(unsigned long long *stats, uint32_t a,
 //            cutoff test and records the hit in its own bitmask;
 //   phase 2 (per lane): each lane walks only its own included entries.
 // wbuf: this warp's 64 float4 (a-parts, then b-parts of the chunk).
-template <int TW, int TH>
+template <int TW, int TH, bool STATS = true>
 __device__ __forceinline__ void fwd_stream_item(const Batch &b, const DevOpts &o, uint32_t tile,
                                                 int sub, int lane, const uint2 *__restrict__ ranges,
                                                 const uint32_t *__restrict__ pv_list,
@@ -397,7 +397,7 @@ __device__ __forceinline__ void fwd_stream_item(const Batch &b, const DevOpts &o
                 wbuf[32 + lane] = __ldg(rec + 2 * (size_t)pv + 1);
             }
             __syncwarp();
-            if (!done) examined += (uint32_t)__popc(m);
+            if (STATS && !done) examined += (uint32_t)__popc(m);
             m &= ~mine;
             while (m) {
                 const int j = __ffs(m) - 1;
@@ -560,7 +560,7 @@ __device__ __forceinline__ BwdPixel bwd_pixel(const PixelGeom &g, const DevOpts 
 // per-point warp work (staging, cull, reduction or atomics) serves 32P
 // pixels instead of 32.  Each pixel's T and S recursions are the same
 // operations as in the one-pixel walk.
-template <int TW, int TH, int P>
+template <int TW, int TH, int P, bool STATS>
 __device__ __forceinline__ void bwd_rows_item(const Batch &b, const DevOpts &o, uint32_t tile,
                                               int sub, int lane, const uint2 *__restrict__ ranges,
                                               const uint32_t *__restrict__ pv_list,
@@ -632,8 +632,10 @@ __device__ __forceinline__ void bwd_rows_item(const Batch &b, const DevOpts &o, 
                 const bool bq = idx < px[q].L;
                 d2[q] = pixel_d2(g[q].ux, g[q].uy, aj.x, aj.y, dx[q], dy[q]);
                 ct[q] = bq && d2[q] <= aj.z;
-                examined += (uint32_t)bq;
-                used += (uint32_t)ct[q];
+                if (STATS) {
+                    examined += (uint32_t)bq;
+                    used += (uint32_t)ct[q];
+                }
                 any = any || ct[q];
             }
             const uint32_t cm = __ballot_sync(0xffffffffu, any);
@@ -710,7 +712,9 @@ __device__ __forceinline__ uint32_t next_item(uint32_t *work, int lane)
     return __shfl_sync(0xffffffffu, it, 0);
 }
 
-template <int TW, int TH>
+// STATS: count examined / composited pairs into stats (which must then be
+// non-null); without, the loops carry no counting.
+template <int TW, int TH, bool STATS>
 __global__ void __launch_bounds__(PERSIST_THREADS)
 raster_fwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
                           const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
@@ -724,12 +728,13 @@ raster_fwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
     const uint32_t n_items = b.n_tiles * SUBS;
     uint32_t ex = 0, co = 0;
     for (uint32_t it = next_item(work, lane); it < n_items; it = next_item(work, lane))
-        fwd_stream_item<TW, TH>(b, o, order[it / SUBS], (int)(it % SUBS), lane, ranges, pv_list,
-                                rec, out_rgb, T_final, n_contrib, ex, co, s_buf[threadIdx.x >> 5]);
-    add_stats(stats, ex, co, lane);
+        fwd_stream_item<TW, TH, STATS>(b, o, order[it / SUBS], (int)(it % SUBS), lane, ranges,
+                                       pv_list, rec, out_rgb, T_final, n_contrib, ex, co,
+                                       s_buf[threadIdx.x >> 5]);
+    if (STATS) add_stats(stats, ex, co, lane);
 }
 
-template <int TW, int TH>
+template <int TW, int TH, bool STATS>
 __global__ void __launch_bounds__(PERSIST_THREADS)
 raster_bwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
                           const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
@@ -746,10 +751,10 @@ raster_bwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
     const uint32_t n_items = b.n_tiles * SUBS;
     uint32_t ex = 0, us = 0;
     for (uint32_t it = next_item(work, lane); it < n_items; it = next_item(work, lane))
-        bwd_rows_item<TW, TH, P>(b, o, order[it / SUBS], (int)(it % SUBS), lane, ranges, pv_list,
-                                rec, T_final, n_contrib, grad_rgb, g2d, ex, us,
-                                s_buf[threadIdx.x >> 5], s_pv[threadIdx.x >> 5]);
-    add_stats(stats ? stats + 2 : nullptr, ex, us, lane);
+        bwd_rows_item<TW, TH, P, STATS>(b, o, order[it / SUBS], (int)(it % SUBS), lane, ranges,
+                                        pv_list, rec, T_final, n_contrib, grad_rgb, g2d, ex, us,
+                                        s_buf[threadIdx.x >> 5], s_pv[threadIdx.x >> 5]);
+    if (STATS) add_stats(stats + 2, ex, us, lane);
 }
 
 // Tile order, longest list first: bucket = floor(log2(length)), buckets in
@@ -1000,9 +1005,17 @@ void fwd_dispatch(const Batch &b, const DevOpts &o, int depth, const uint2 *rang
                   uint32_t *work, cudaStream_t s)
 {
     if (depth == 0 && order) {
-        static const int grid = persist_grid((const void *)raster_fwd_persist_kernel<TW, TH>);
-        raster_fwd_persist_kernel<TW, TH><<<grid, PERSIST_THREADS, 0, s>>>(
-            b, o, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats, order, work);
+        if (stats) {
+            static const int grid =
+                persist_grid((const void *)raster_fwd_persist_kernel<TW, TH, true>);
+            raster_fwd_persist_kernel<TW, TH, true><<<grid, PERSIST_THREADS, 0, s>>>(
+                b, o, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats, order, work);
+        } else {
+            static const int grid =
+                persist_grid((const void *)raster_fwd_persist_kernel<TW, TH, false>);
+            raster_fwd_persist_kernel<TW, TH, false><<<grid, PERSIST_THREADS, 0, s>>>(
+                b, o, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats, order, work);
+        }
     } else if (depth == 0) {
         raster_fwd_stream_kernel<TW, TH><<<b.n_tiles, TW * TH, 0, s>>>(
             b, o, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats);
@@ -1027,10 +1040,19 @@ void bwd_dispatch(const Batch &b, const DevOpts &o, int depth, const uint2 *rang
                   cudaStream_t s)
 {
     if (depth == 0 && order) {
-        static const int grid = persist_grid((const void *)raster_bwd_persist_kernel<TW, TH>);
-        raster_bwd_persist_kernel<TW, TH><<<grid, PERSIST_THREADS, 0, s>>>(
-            b, o, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d, stats, order,
-            work + 1);
+        if (stats) {
+            static const int grid =
+                persist_grid((const void *)raster_bwd_persist_kernel<TW, TH, true>);
+            raster_bwd_persist_kernel<TW, TH, true><<<grid, PERSIST_THREADS, 0, s>>>(
+                b, o, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d, stats,
+                order, work + 1);
+        } else {
+            static const int grid =
+                persist_grid((const void *)raster_bwd_persist_kernel<TW, TH, false>);
+            raster_bwd_persist_kernel<TW, TH, false><<<grid, PERSIST_THREADS, 0, s>>>(
+                b, o, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d, stats,
+                order, work + 1);
+        }
     } else if (depth == 0) {
         raster_bwd_stream_kernel<TW, TH><<<b.n_tiles, TW * TH, 0, s>>>(
             b, o, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d, stats);
