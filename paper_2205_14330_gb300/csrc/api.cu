@@ -370,7 +370,15 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
     const uint64_t n_pairs = host[0], n_vis = host[1];
     const uint32_t zlo = ((const uint32_t *)host)[12];
     const uint32_t zhi = ((const uint32_t *)host)[13];
-    const int depth_bits = (n_vis > 0 && zhi > zlo) ? 32 - __builtin_clz(zhi - zlo) : 0;
+    // With most point-views visible, all of them are sorted by depth
+    // directly: the invisible ones (key 0xffffffff, clamped to one above the
+    // deepest visible key) land behind the visible ones, and no compaction
+    // pass is needed.  Otherwise the visible ones are compacted first.
+    const bool direct = n_vis > 0 && 4 * n_vis >= 3 * (uint64_t)npv;
+    const uint32_t marker = n_vis > 0 ? zhi - zlo + 1 : 0u;
+    const int depth_bits = direct ? 32 - __builtin_clz(marker)
+                                  : (n_vis > 0 && zhi > zlo) ? 32 - __builtin_clz(zhi - zlo) : 0;
+    const int64_t n_sort = direct ? npv : (int64_t)n_vis;
     if (n_pairs >= UINT32_MAX) {
         return set_error(PBR_ERR_CAPACITY, "%llu (tile, point-view) pairs exceed 2^32-1",
                          (unsigned long long)n_pairs);
@@ -380,13 +388,13 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
     uint32_t *vk = nullptr, *vv = nullptr, *vk2 = nullptr, *vv2 = nullptr;
     uint32_t *pk2 = nullptr, *pv2 = nullptr;
     void *temp = nullptr;
-    const int64_t cap_sort = std::max<int64_t>(n_vis, n_pairs);
+    const int64_t cap_sort = std::max<int64_t>(n_sort, n_pairs);
     const size_t temp_bytes = std::max(std::max(scan_temp_bytes(npv), radix_temp_bytes(cap_sort)),
                                        emit_temp_bytes((int64_t)n_vis));
-    PBR_TRY(tmp.alloc(&vk, sizeof(uint32_t) * n_vis));
-    PBR_TRY(tmp.alloc(&vv, sizeof(uint32_t) * n_vis));
-    PBR_TRY(tmp.alloc(&vk2, sizeof(uint32_t) * n_vis));
-    PBR_TRY(tmp.alloc(&vv2, sizeof(uint32_t) * n_vis));
+    if (!direct) PBR_TRY(tmp.alloc(&vk, sizeof(uint32_t) * n_sort));
+    PBR_TRY(tmp.alloc(&vv, sizeof(uint32_t) * n_sort));
+    PBR_TRY(tmp.alloc(&vk2, sizeof(uint32_t) * n_sort));
+    PBR_TRY(tmp.alloc(&vv2, sizeof(uint32_t) * n_sort));
     PBR_TRY(dalloc((void **)&st->tile_keys, sizeof(uint32_t) * n_pairs, s));
     PBR_TRY(dalloc((void **)&st->tile_vals, sizeof(uint32_t) * n_pairs, s));
     PBR_TRY(tmp.alloc(&pk2, sizeof(uint32_t) * n_pairs));
@@ -399,14 +407,19 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
     const uint32_t *n_vis_dev = (const uint32_t *)(st->counters + 1);  // low word (< 2^32)
     const uint32_t *n_pairs_dev = (const uint32_t *)(st->counters + 0); // low word (< 2^32)
     // 1. visible point-views with their depth keys, in point-view order
-    {
+    if (!direct) {
         StageScope t(c, STG_COMPACT, s);
         launch_compact_visible(st->ntiles, zbits, npv, vk, vv, nullptr, temp, s);
     }
-    // 2. stable sort by fp32 depth bits
+    // 2. stable sort by fp32 depth bits (ties keep point-view order)
     {
         StageScope t(c, STG_DEPTH_SORT, s);
-        radix_sort_pairs(vk, vv, vk2, vv2, n_vis_dev, (int64_t)n_vis, depth_bits, temp, s, zlo);
+        if (direct)
+            radix_sort_pairs(zbits, vv, vk2, vv2, nullptr, npv, depth_bits, temp, s, zlo, marker,
+                             true);
+        else
+            radix_sort_pairs(vk, vv, vk2, vv2, n_vis_dev, (int64_t)n_vis, depth_bits, temp, s,
+                             zlo);
     }
     // 3. duplicate per covered tile, in depth order
     uint32_t *tk = st->tile_keys, *tv = st->tile_vals;

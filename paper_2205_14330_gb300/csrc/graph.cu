@@ -27,14 +27,13 @@ namespace {
 constexpr uint32_t ST_DEPTH_RANGE = 1u << 3;
 
 // Raises ST_DEPTH_RANGE when a visible depth falls outside the planned key
-// range [lo, lo + 2^bits).
+// range [lo, lo + span).
 __global__ void check_depth_range_kernel(const unsigned long long *counters, uint32_t lo,
-                                         int bits, uint32_t *status)
+                                         uint64_t span, uint32_t *status)
 {
     const uint32_t *w = (const uint32_t *)counters;
     if (counters[1] == 0) return;
     const uint32_t zmin = w[12], zmax = w[13];
-    const uint64_t span = bits >= 32 ? (1ull << 32) : (1ull << bits);
     if (zmin < lo || (uint64_t)(zmax - lo) >= span) atomicOr(status, ST_DEPTH_RANGE);
 }
 
@@ -81,6 +80,10 @@ struct pbr_graph {
     int64_t cap_vis = 0, cap_pairs = 0;
     uint32_t depth_lo = 0;
     int depth_bits = 32;
+    // all point-views sorted by depth, the invisible ones behind (key clamped
+    // to depth_marker), instead of compacting the visible ones first
+    bool direct_depth = false;
+    uint32_t depth_marker = 0xffffffffu;
     // buffers (cudaMalloc, stable addresses for the graphs)
     std::vector<void *> allocs;
     DevView *d_views = nullptr;
@@ -164,12 +167,21 @@ void enqueue_forward(pbr_graph *g, cudaStream_t s)
     cudaMemsetAsync(g->counters, 0, 128, s);
     cudaMemsetAsync((char *)g->counters + 48, 0xff, 4, s);
     launch_preprocess_fwd(b, o, g->rec, g->zbits, g->ntiles, g->rect, g->counters, s);
-    check_depth_range_kernel<<<1, 1, 0, s>>>(g->counters, g->depth_lo, g->depth_bits, status);
+    // visible keys must lie below the marker (direct) or inside the bits
+    const uint64_t span = g->direct_depth ? (uint64_t)g->depth_marker
+                          : g->depth_bits >= 32 ? (1ull << 32) : (1ull << g->depth_bits);
+    check_depth_range_kernel<<<1, 1, 0, s>>>(g->counters, g->depth_lo, span, status);
     count_launches(1);
-    launch_compact_visible(g->ntiles, g->zbits, L.n_pv, g->vk, g->vv, nullptr, g->temp, s);
     uint32_t *vk = g->vk, *vv = g->vv, *vk2 = g->vk2, *vv2 = g->vv2;
-    radix_sort_pairs(vk, vv, vk2, vv2, n_vis_dev, g->cap_vis, g->depth_bits, g->temp, s,
-                     g->depth_lo);
+    if (g->direct_depth) {
+        vk = g->zbits;
+        radix_sort_pairs(vk, vv, vk2, vv2, nullptr, L.n_pv, g->depth_bits, g->temp, s,
+                         g->depth_lo, g->depth_marker, true);
+    } else {
+        launch_compact_visible(g->ntiles, g->zbits, L.n_pv, g->vk, g->vv, nullptr, g->temp, s);
+        radix_sort_pairs(vk, vv, vk2, vv2, n_vis_dev, g->cap_vis, g->depth_bits, g->temp, s,
+                         g->depth_lo);
+    }
     uint32_t *tk = g->tk, *tv = g->tv, *tk2 = g->tk2, *tv2 = g->tv2;
     launch_emit_pairs(b, o, vv, n_vis_dev, g->cap_vis, g->ntiles, g->rect, tk, tv,
                       g->cap_pairs, status, g->temp, s);
@@ -291,16 +303,20 @@ int plan_and_capture(pbr_graph *g, cudaStream_t user_stream)
     g->cap_vis = L.n_pv;
     g->cap_pairs = (int64_t)std::ceil((double)n_pairs * (1.0 + g->headroom)) + 4096;
     if (g->cap_pairs >= (int64_t)UINT32_MAX) g->cap_pairs = (int64_t)UINT32_MAX - 1;
+    g->direct_depth = n_vis > 0 && 4 * n_vis >= 3 * (uint64_t)L.n_pv;
     if (n_vis > 0 && zhi >= zlo) {
         // key range with a factor-2 margin in depth on both sides
         const uint32_t lo = float_to_bits(bits_to_float(zlo) * 0.5f);
         const uint32_t hi = float_to_bits(std::min(bits_to_float(zhi) * 2.0f, 3.0e38f));
         g->depth_lo = lo;
-        g->depth_bits = bit_width(hi - lo);
+        // direct sort: one key value above the range is the invisible marker
+        g->depth_bits = bit_width(g->direct_depth ? hi - lo + 1 : hi - lo);
     } else {
         g->depth_lo = 0;
         g->depth_bits = 32;
     }
+    if (g->direct_depth)
+        g->depth_marker = g->depth_bits >= 32 ? 0xffffffffu : (1u << g->depth_bits) - 1u;
     // 2. buffers
     const int64_t npv = L.n_pv;
     PBR_TRY(g->alloc(&g->d_views, sizeof(DevView) * L.views.size()));
@@ -311,7 +327,7 @@ int plan_and_capture(pbr_graph *g, cudaStream_t user_stream)
     PBR_TRY(g->alloc(&g->ntiles, sizeof(uint32_t) * npv));
     PBR_TRY(g->alloc(&g->zbits, sizeof(uint32_t) * npv));
     PBR_TRY(g->alloc(&g->rect, sizeof(uint4) * npv));
-    PBR_TRY(g->alloc(&g->vk, 4 * (size_t)g->cap_vis));
+    if (!g->direct_depth) PBR_TRY(g->alloc(&g->vk, 4 * (size_t)g->cap_vis));
     PBR_TRY(g->alloc(&g->vv, 4 * (size_t)g->cap_vis));
     PBR_TRY(g->alloc(&g->vk2, 4 * (size_t)g->cap_vis));
     PBR_TRY(g->alloc(&g->vv2, 4 * (size_t)g->cap_vis));

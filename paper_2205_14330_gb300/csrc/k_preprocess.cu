@@ -4,8 +4,9 @@
 // looping over every view of the point's scene, so position, radius,
 // opacity and the [K,3] SH block are read from HBM once per batch.  For each
 // (view, point) it writes a 32-byte record {px, py, rc^2, q'} {o, r, g, b},
-// the fp32 depth bits, the tile box with the mask of its listed tiles (one
-// 16-byte record) and the tile count.
+// the fp32 depth bits (0xffffffff when the point-view lists no tile), the
+// tile box with the mask of its listed tiles (one 16-byte record) and the
+// tile count.
 //
 // The discrete decisions (cull, cutoff radius, pixel box, tile rectangle,
 // depth key) use IEEE fp32 round-to-nearest operations with no
@@ -173,6 +174,7 @@ __device__ void pre_fwd_point(const Batch &b, const DevOpts &o, const DevScene &
             } while (0);
         }
         ntiles[pv] = nt;
+        if (nt == 0) zbits[pv] = 0xffffffffu; // not visible: sorts behind every depth
     }
 }
 

@@ -209,9 +209,13 @@ struct ActStore {
 constexpr int RB = 9;
 constexpr int RBINS = 1 << RB;
 
-__device__ __forceinline__ uint32_t digit_of(uint32_t key, uint32_t key_lo, int shift, uint32_t mask)
+// Digit of min(key - key_lo, key_max): keys above the range (the marker of
+// an invisible point-view) all take the largest value.
+__device__ __forceinline__ uint32_t digit_of(uint32_t key, uint32_t key_lo, uint32_t key_max,
+                                             int shift, uint32_t mask)
 {
-    return ((key - key_lo) >> shift) & mask;
+    const uint32_t k = key - key_lo;
+    return ((k < key_max ? k : key_max) >> shift) & mask;
 }
 
 // Peers of each lane: lanes holding the same digit (digits < 2^10, the
@@ -230,7 +234,8 @@ __device__ __forceinline__ uint32_t peers_by_ballot(uint32_t d)
 // Per-block digit histogram: shared-memory atomics into per-warp counters.
 __global__ void __launch_bounds__(SORT_THREADS)
 radix_hist_kernel(const uint32_t *__restrict__ keys, const uint32_t *n_dev, int64_t cap,
-                  uint32_t key_lo, int shift, int width, uint32_t *__restrict__ hist, int64_t nb)
+                  uint32_t key_lo, uint32_t key_max, int shift, int width,
+                  uint32_t *__restrict__ hist, int64_t nb)
 {
     __shared__ uint32_t s_h[SORT_WARPS][RBINS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -242,7 +247,7 @@ radix_hist_kernel(const uint32_t *__restrict__ keys, const uint32_t *n_dev, int6
 #pragma unroll
     for (int r = 0; r < SORT_ITEMS; ++r) {
         const int64_t i = base + r * 32 + lane;
-        d[r] = i < n ? digit_of(keys[i], key_lo, shift, mask) : (uint32_t)RBINS;
+        d[r] = i < n ? digit_of(keys[i], key_lo, key_max, shift, mask) : (uint32_t)RBINS;
     }
     __syncthreads();
 #pragma unroll
@@ -264,8 +269,9 @@ constexpr size_t SCATTER_SMEM = sizeof(uint32_t) * (3 * SORT_TILE + SORT_WARPS *
 __global__ void __launch_bounds__(SORT_THREADS)
 radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                      uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
-                     const uint32_t *n_dev, int64_t cap, uint32_t key_lo, int shift, int width,
-                     const uint32_t *__restrict__ hist, int64_t nb)
+                     const uint32_t *n_dev, int64_t cap, uint32_t key_lo, uint32_t key_max,
+                     int shift, int width, const uint32_t *__restrict__ hist, int64_t nb,
+                     bool index_vals)
 {
     extern __shared__ uint32_t s_mem[];
     uint32_t *s_k = s_mem;                               // [SORT_TILE] keys, ranked order
@@ -291,7 +297,7 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
         const int64_t i = base + r * 32 + lane;
         const bool ok = i < n;
         key[r] = ok ? keys_in[i] : 0u;
-        s_vin[lbase + r * 32] = ok ? vals_in[i] : 0u;
+        s_vin[lbase + r * 32] = ok ? (index_vals ? (uint32_t)i : vals_in[i]) : 0u;
     }
     __syncthreads();
     const uint32_t lt = lanemask_lt();
@@ -303,7 +309,7 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
 #pragma unroll
         for (int r = 0; r < SORT_ITEMS; ++r) {
             const bool ok = base + r * 32 + lane < n;
-            const uint32_t d = ok ? digit_of(key[r], key_lo, shift, mask) : (uint32_t)RBINS;
+            const uint32_t d = ok ? digit_of(key[r], key_lo, key_max, shift, mask) : (uint32_t)RBINS;
             const uint32_t peers = peers_by_ballot(d);
             uint32_t old = 0;
             if (d < RBINS && (peers & lt) == 0) old = atomicAdd(&s_wh[w][d], (uint32_t)__popc(peers));
@@ -356,7 +362,7 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
 #pragma unroll
     for (int r = 0; r < SORT_ITEMS; ++r) {
         if (base + r * 32 + lane < n) {
-            const uint32_t d = digit_of(key[r], key_lo, shift, mask);
+            const uint32_t d = digit_of(key[r], key_lo, key_max, shift, mask);
             const uint32_t l = s_dbase[d] + s_wh[w][d] + rank[r];
             s_k[l] = key[r];
             s_v[l] = s_vin[lbase + r * 32];
@@ -366,7 +372,7 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
     const int cnt = (int)(n - blk < SORT_TILE ? n - blk : SORT_TILE);
     for (int j = threadIdx.x; j < cnt; j += SORT_THREADS) {
         const uint32_t k = s_k[j];
-        const uint32_t d = digit_of(k, key_lo, shift, mask);
+        const uint32_t d = digit_of(k, key_lo, key_max, shift, mask);
         const uint32_t g = s_gbase[d] + (uint32_t)j - s_dbase[d];
         keys_out[g] = k;
         vals_out[g] = s_v[j];
@@ -547,9 +553,13 @@ int radix_passes(int key_bits)
 
 void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *&keys_alt, uint32_t *&vals_alt,
                       const uint32_t *n_dev, int64_t cap, int key_bits, void *temp,
-                      cudaStream_t s, uint32_t key_lo)
+                      cudaStream_t s, uint32_t key_lo, uint32_t key_max, bool index_vals)
 {
-    if (cap <= 0 || key_bits <= 0) return; // all keys equal: already in stable order
+    if (cap <= 0) return;
+    if (key_bits <= 0) {
+        if (!index_vals) return; // all keys equal: already in stable order
+        key_bits = 1;            // one pass still writes the index values
+    }
     static const bool attr = cudaFuncSetAttribute(radix_scatter_kernel,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   (int)SCATTER_SMEM) == cudaSuccess;
@@ -561,11 +571,12 @@ void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *&keys_alt, uin
     const int width = (key_bits + passes - 1) / passes;
     for (int shift = 0; shift < key_bits; shift += width) {
         const int wd = key_bits - shift < width ? key_bits - shift : width;
-        radix_hist_kernel<<<(unsigned)nb, SORT_THREADS, 0, s>>>(keys, n_dev, cap, key_lo, shift, wd,
-                                                                hist, nb);
+        radix_hist_kernel<<<(unsigned)nb, SORT_THREADS, 0, s>>>(keys, n_dev, cap, key_lo, key_max,
+                                                                shift, wd, hist, nb);
         run_scan(LoadU32{hist}, ActStore{hist}, nullptr, nb << wd, scan_tmp, nullptr, nullptr, s);
         radix_scatter_kernel<<<(unsigned)nb, SORT_THREADS, SCATTER_SMEM, s>>>(
-            keys, vals, keys_alt, vals_alt, n_dev, cap, key_lo, shift, wd, hist, nb);
+            keys, vals, keys_alt, vals_alt, n_dev, cap, key_lo, key_max, shift, wd, hist, nb,
+            index_vals && shift == 0);
         count_launches(2);
         uint32_t *tk = keys, *tv = vals;
         keys = keys_alt;

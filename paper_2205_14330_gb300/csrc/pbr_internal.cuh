@@ -97,6 +97,8 @@ constexpr float QP_TO_Q = -2.0f / 1.4426950408889634f;
 // counters[0] += (tile, point-view) pairs, counters[1] += visible point-views;
 // 32-bit words 12 / 13 of counters: min / max depth bits of visible
 // point-views (word 12 must start at 0xffffffff, word 13 at 0).
+// zbits[pv] = fp32 bits of the depth, 0xffffffff for a point-view listing no
+// tile (every finite depth's bits are smaller).
 // rect[pv] = {tx0 | ty0 << 16, tx1 | ty1 << 16, mask, 0}: the tile box and,
 // for a box of at most 32 tiles, bit (ty - ty0) * wx + (tx - tx0) set for
 // each listed tile (wider boxes list every tile).
@@ -120,13 +122,15 @@ void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n,
 // Radix sort of (key, value) pairs, stable; n read from device *n_dev,
 // capacity cap.  key_bits: number of low key bits that can be non-zero.
 // Sorted result ends in (keys, vals) (buffers are ping-ponged internally).
-// Keys are ordered by (key - key_lo); key_bits = bits of (max key - key_lo).
-// Digits of up to 9 bits, ceil(key_bits / 9) passes.
+// Keys are ordered by min(key - key_lo, key_max); key_bits = bits of the
+// largest such value.  Digits of up to 9 bits, ceil(key_bits / 9) passes.
+// index_vals: the input values are not read; value i is taken to be i.
 size_t radix_temp_bytes(int64_t cap);
 int radix_passes(int key_bits);
 void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *&keys_alt, uint32_t *&vals_alt,
                       const uint32_t *n_dev, int64_t cap, int key_bits, void *temp,
-                      cudaStream_t s, uint32_t key_lo = 0);
+                      cudaStream_t s, uint32_t key_lo = 0, uint32_t key_max = 0xffffffffu,
+                      bool index_vals = false);
 // Scratch of launch_emit_pairs (depth-ordered counts, offsets, scan).
 size_t emit_temp_bytes(int64_t cap_vis);
 // Emits (tile, pv) pairs in depth order: gathers the tile counts in depth

@@ -105,6 +105,41 @@ def test_bins_and_records_bit_exact(R, tile):
     st.close()
 
 
+@pytest.mark.parametrize("hidden", [0.0, 0.6], ids=["all-visible", "mostly-hidden"])
+def test_bins_exact_in_both_depth_orderings(R, hidden):
+    """The depth order is built either by sorting all point-views (the
+    invisible ones keyed behind every depth) or by compacting the visible
+    ones first, chosen by the visible fraction (3/4).  Both must give the
+    oracle's lists, including the order of equal depths (duplicated points);
+    a captured graph must render the same image."""
+    pbr = _pbr()
+    rng = np.random.default_rng(11)
+    n = 600
+    pos = rng.uniform(-0.3, 0.3, (n, 3)).astype(np.float32)
+    pos[n // 2:n // 2 + 60] = pos[:60]  # equal depths in every view
+    k = int(hidden * n)
+    pos[n - k:] += np.float32(40.0)     # far outside every view
+    sc = dict(pos=pos, sh=scenes.sh_coeffs(rng, n, 1, std=0.3),
+              opacity=rng.uniform(0.2, 0.9, n).astype(np.float32),
+              radius=rng.uniform(0.01, 0.04, n).astype(np.float32), deg=1)
+    cams = [scenes.camera((0.2, 0.1, 2.4), 80, 60, fov_deg=60.0),
+            scenes.camera((-2.0, 0.5, 1.2), 64, 64, fov_deg=60.0)]
+    img, st, scene = _gpu_render(R, sc, cams)
+    keys, vals, ranges, recs = O.bin_tiles(sc["pos"], sc["sh"], sc["radius"], sc["deg"], cams)
+    vis_frac = float((recs.reshape(-1)["visible"] == 1).mean())
+    assert (vis_frac >= 0.75) == (hidden == 0.0), vis_frac
+    assert np.array_equal(st.read("tile_keys"), keys)
+    assert np.array_equal(st.read("tile_vals"), vals)
+    assert np.array_equal(st.read("ranges"), ranges)
+    G = pbr.Graph(R, [scene], cams, pbr.default_opts(), backward=False)
+    G.launch(pbr.Graph.FORWARD)
+    assert G.check()[0]
+    import torch
+    assert torch.equal(G.out, img)
+    G.close()
+    st.close()
+
+
 def test_image_independent_of_tile_size_and_batch_depth(R):
     sc = _small_scene(2, n=500)
     cams = [scenes.camera((0.5, -0.3, 2.4), 97, 61)]
