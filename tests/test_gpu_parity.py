@@ -231,6 +231,25 @@ def test_edge_cases(R):
         _gpu_render(R, sc, [scenes.camera((0, 0, 2), 0, 10)])
 
 
+def test_many_views_of_one_scene(R):
+    """More views of one scene than the per-point kernels stage at a time
+    (64): image and gradients of 70 small views against the oracle."""
+    import torch
+    sc = _small_scene(14, n=150, deg=2)
+    cams = scenes.ring_cameras(70, 2.3, 12, 10)
+    img, st, _ = _gpu_render(R, sc, cams)
+    ref, _, _ = O.render(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], cams)
+    assert np.abs(img.cpu().numpy() - ref).max() <= IMG_TOL
+    g = np.random.default_rng(2).normal(size=img.shape).astype(np.float32)
+    gpos, gsh, gop = R.backward(st, torch.from_numpy(g).cuda())
+    dpos, dsh, dop = O.backward(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], cams,
+                                g.astype(np.float64))
+    assert _rel(gpos.cpu().numpy(), dpos) <= GRAD_TOL
+    assert _rel(gsh.cpu().numpy().reshape(dsh.shape), dsh) <= GRAD_TOL
+    assert _rel(gop.cpu().numpy(), dop) <= GRAD_TOL
+    st.close()
+
+
 def test_multi_scene_multi_view(R):
     pbr = _pbr()
     a = _small_scene(12, n=300, deg=1)
