@@ -46,12 +46,12 @@ FLOP_TEST, FLOP_FWD, FLOP_BWD = 6, 11, 31
 # the kernel source it was taken on (sha256 of the file), else reported null.
 CAPTURED_TRAFFIC = {
     ("raster_bwd", "16x16", 0, 1): {
-        "bytes": 13.39e9 + 1.19e9, "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
-        "sha256": "a072cbbdadd14dbdf1ae105a822430739ab1d6bfdb2221c1141f8f50e3b94cf7",
+        "bytes": 13.28e9 + 1.22e9, "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
+        "sha256": "058506ad497f11d46aaae21230c5956bd59eafa40a822d0855f25dd91ab9f973",
         "profile": "profiles/raster_persist_dram_batched_1M_64views.md"},
-    ("raster_bwd", "16x32", 0, 1): {
-        "bytes": 16.55e9 + 1.14e9, "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
-        "sha256": "a072cbbdadd14dbdf1ae105a822430739ab1d6bfdb2221c1141f8f50e3b94cf7",
+    ("raster_fwd", "16x16", 0, 1): {
+        "bytes": 7.45e9 + 1.20e9, "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
+        "sha256": "058506ad497f11d46aaae21230c5956bd59eafa40a822d0855f25dd91ab9f973",
         "profile": "profiles/raster_persist_dram_batched_1M_64views.md"},
 }
 
@@ -684,7 +684,9 @@ def main():
             return e0.elapsed_time(e1) / k
 
         e2e_run(2)
-        e_ms = max_over_ranks(e2e_run(max(2, args.steps // 2)), dist, dev)
+        # as many steps as the device-resident timed region: the pipeline's
+        # fill (first upload) and drain (last download) count once per run
+        e_ms = max_over_ranks(e2e_run(max(2, args.steps)), dist, dev)
         Gb.close()
         e2e = {"value": world * mp / (e_ms * 1e-3), "unit": "MP/s", "ms_per_step": e_ms,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
