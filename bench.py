@@ -47,11 +47,11 @@ FLOP_TEST, FLOP_FWD, FLOP_BWD = 6, 11, 31
 CAPTURED_TRAFFIC = {
     ("raster_bwd", "16x16", 0, 1): {
         "bytes": 13.28e9 + 1.22e9, "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
-        "sha256": "058506ad497f11d46aaae21230c5956bd59eafa40a822d0855f25dd91ab9f973",
+        "sha256": "2fb8f5b32bf2ffa70f078fdca8cc1c53ebf4f2cc366eddf9518da72cba53016c",
         "profile": "profiles/raster_persist_dram_batched_1M_64views.md"},
     ("raster_fwd", "16x16", 0, 1): {
         "bytes": 7.45e9 + 1.20e9, "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
-        "sha256": "058506ad497f11d46aaae21230c5956bd59eafa40a822d0855f25dd91ab9f973",
+        "sha256": "2fb8f5b32bf2ffa70f078fdca8cc1c53ebf4f2cc366eddf9518da72cba53016c",
         "profile": "profiles/raster_persist_dram_batched_1M_64views.md"},
 }
 

@@ -18,9 +18,9 @@
 //   dL/do = dL/dalpha G,  dL/dp = dL/dalpha alpha q (u - p),
 //   dL/dq = -dL/dalpha alpha d2 / 2          (q = 1/s^2).
 // The 7 per-point terms of a warp go to the per-(view, point) buffer with
-// 16-byte atomics: straight from each contributing pixel when few pixels
+// 16-byte atomics: straight from each contributing lane when few lanes
 // contribute, else summed first with a transposed shuffle reduction (two
-// atomics per warp and point) in the warp-streamed schedule.
+// atomics per warp and point) in the warp-streamed schedules.
 //
 // A block covers one TW x TH screen tile; each warp owns an 8 x 4 sub-block
 // of it (an 8 x 8 one, two pixels per lane, in the persistent backward) and

@@ -5,7 +5,10 @@
 //
 // Pipeline (all counts live on the device; grids are sized by capacity and
 // idle blocks exit, so the chain has no host synchronisation):
-//   1. compact_visible  : scan of the visibility flags -> (depth bits, pv)
+//   1. compact_visible  : scan of the visibility flags -> (depth bits, pv);
+//                         skipped when most point-views are visible: the
+//                         sort then takes every point-view, the invisible
+//                         ones keyed behind every depth
 //   2. radix_sort_pairs : stable LSD radix sort by fp32 depth bits
 //   3. emit_pairs       : scan of tile counts in depth order, writing one
 //                         (global tile id, pv) pair per covered tile
