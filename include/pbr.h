@@ -185,8 +185,12 @@ int pbr_image_loss(int32_t kind, const float *pred, const float *target, int64_t
 
 /* Raster pair counts of a forward state (and of the backward passes run on
  * it): out4 = {forward pairs examined, forward pairs composited, backward
- * pairs examined, backward pairs contributing}.  These are the work units of
- * the compositing kernels' ALU roofline.  Synchronises the state's stream. */
+ * pairs examined, backward pairs contributing}.  Composited and contributing
+ * pairs are the work units of the compositing kernels' ALU roofline; the
+ * examined counts depend on the schedule's culling.  Only eager passes
+ * (pbr_render_forward / pbr_render_backward) count; captured graphs
+ * (pbr_graph_*) run kernels without the counting.  Synchronises the state's
+ * stream. */
 int pbr_state_stats(pbr_state *state, unsigned long long *out4);
 
 /* ------------------------------------------------------- batched graphs */
