@@ -50,13 +50,28 @@ __device__ __forceinline__ int find_scene(const Batch &b, int64_t block)
 // consecutive banks too (SH_STRIDE = 1 mod 32).
 constexpr int SH_STRIDE = PRE_THREADS + 1;
 
+// f / K3 for 0 <= f <= 48 * PRE_THREADS by a multiply-high: with
+// M = floor(2^32 / K3) + 1 = (2^32 + e) / K3, 0 < e <= K3, the product
+// f M / 2^32 exceeds f / K3 by f e / (K3 2^32) < 1 / K3, so its floor is
+// exact while f < 2^32 / K3.
+__device__ __forceinline__ uint32_t div_k3(uint32_t f, uint32_t magic)
+{
+    return __umulhi(f, magic);
+}
+
+__device__ __forceinline__ uint32_t k3_magic(int K3)
+{
+    return 0xffffffffu / (uint32_t)K3 + 1u;
+}
+
 __device__ __forceinline__ void stage_sh(const float *__restrict__ sh, int64_t first, int count,
                                          int K3, float *s_sh)
 {
     const int64_t base = first * K3;
     const int total = count * K3;
+    const uint32_t magic = k3_magic(K3);
     for (int f = threadIdx.x; f < total; f += blockDim.x) {
-        const int p = f / K3;
+        const int p = (int)div_k3((uint32_t)f, magic);
         s_sh[(f - p * K3) * SH_STRIDE + p] = __ldg(sh + base + f);
     }
 }
@@ -73,6 +88,7 @@ __device__ void pre_fwd_point(const Batch &b, const DevOpts &o, const DevScene &
                 P2 = __ldg(sc.pos + 3 * i + 2);
     const float r = __ldg(sc.radius + i);
     const float op = __ldg(sc.opacity + i);
+    const int tws = __ffs(o.tile_w) - 1, ths = __ffs(o.tile_h) - 1;
 
     for (int vv = 0; vv < sc.view_count; ++vv) {
         const int v = b.view_list[sc.view_begin + vv];
@@ -108,8 +124,9 @@ __device__ void pre_fwd_point(const Batch &b, const DevOpts &o, const DevScene &
                 ylo = ylo < 0.0f ? 0.0f : ylo;
                 xhi = xhi > W1 ? W1 : xhi;
                 yhi = yhi > H1 ? H1 : yhi;
-                const int tx0 = (int)xlo / o.tile_w, tx1 = (int)xhi / o.tile_w;
-                const int ty0 = (int)ylo / o.tile_h, ty1 = (int)yhi / o.tile_h;
+                // tile sizes are powers of two and the box is non-negative
+                const int tx0 = (int)xlo >> tws, tx1 = (int)xhi >> tws;
+                const int ty0 = (int)ylo >> ths, ty1 = (int)yhi >> ths;
                 const int wx = tx1 - tx0 + 1, wy = ty1 - ty0 + 1;
                 // listed tiles: all of a box wider than 32 tiles, else those
                 // whose clipped rectangle of pixel centres is within the
@@ -389,8 +406,9 @@ preprocess_bwd_kernel(Batch b, DevOpts o, const float4 *__restrict__ g2d,
     // coalesced write-back of the SH gradient slice
     float *dst = grad_sh + sc.sh_base + first * K3;
     const int total = count * K3;
+    const uint32_t magic = k3_magic(K3);
     for (int f = threadIdx.x; f < total; f += blockDim.x) {
-        const int p = f / K3;
+        const int p = (int)div_k3((uint32_t)f, magic);
         dst[f] = s_sh[(f - p * K3) * SH_STRIDE + p];
     }
 }
