@@ -47,19 +47,19 @@ FLOP_TEST, FLOP_FWD, FLOP_BWD = 6, 11, 31
 CAPTURED_TRAFFIC = {
     ("raster_bwd", "16x16", 0, 1): {
         "bytes": 13.26e9 + 1.22e9, "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
-        "sha256": "5b167fcda483f450ffde262823945b5b0328eb154cb761e003efb78c1f00e625",
+        "sha256": "fef4b4383ca628a03bbc175ceb800f19eb4c0a6e792cf8d62df81ea9d782775f",
         "profile": "profiles/raster_persist_dram_batched_1M_64views.md"},
     ("raster_fwd", "16x16", 0, 1): {
         "bytes": 8.86e9 + 1.31e9, "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
-        "sha256": "5b167fcda483f450ffde262823945b5b0328eb154cb761e003efb78c1f00e625",
+        "sha256": "fef4b4383ca628a03bbc175ceb800f19eb4c0a6e792cf8d62df81ea9d782775f",
         "profile": "profiles/raster_persist_dram_batched_1M_64views.md"},
     ("raster_bwd", "16x32", 0, 1): {
         "bytes": 16.02e9 + 1.17e9, "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
-        "sha256": "5b167fcda483f450ffde262823945b5b0328eb154cb761e003efb78c1f00e625",
+        "sha256": "fef4b4383ca628a03bbc175ceb800f19eb4c0a6e792cf8d62df81ea9d782775f",
         "profile": "profiles/raster_persist_dram_batched_1M_64views.md"},
     ("raster_fwd", "16x32", 0, 1): {
         "bytes": 10.65e9 + 1.32e9, "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
-        "sha256": "5b167fcda483f450ffde262823945b5b0328eb154cb761e003efb78c1f00e625",
+        "sha256": "fef4b4383ca628a03bbc175ceb800f19eb4c0a6e792cf8d62df81ea9d782775f",
         "profile": "profiles/raster_persist_dram_batched_1M_64views.md"},
 }
 

@@ -804,7 +804,7 @@ tile_bucket_scatter_kernel(const uint2 *__restrict__ ranges, uint32_t n_tiles, u
 {
     __shared__ uint32_t s_w[8][33]; // per warp and bucket: count, then offset
     __shared__ uint32_t s_base[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int w = threadIdx.x >> 5;
     for (int j = threadIdx.x; j < 8 * 33; j += 256) (&s_w[0][0])[j] = 0;
     __syncthreads();
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
