@@ -222,14 +222,19 @@ __device__ __forceinline__ uint32_t digit_of(uint32_t key, uint32_t key_lo, uint
 }
 
 // Peers of each lane: lanes holding the same digit (digits < 2^10, the
-// out-of-range marker RBINS included), built from ballots.
-__device__ __forceinline__ uint32_t peers_by_ballot(uint32_t d)
+// out-of-range marker RBINS included), built from ballots.  full: no lane
+// holds the marker (warp-uniform), so its bit needs no ballot.
+__device__ __forceinline__ uint32_t peers_by_ballot(uint32_t d, bool full)
 {
     uint32_t peers = 0xffffffffu;
 #pragma unroll
-    for (int bit = 0; bit <= RB; ++bit) {
+    for (int bit = 0; bit < RB; ++bit) {
         const uint32_t m = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
         peers &= ((d >> bit) & 1u) ? m : ~m;
+    }
+    if (!full) {
+        const uint32_t m = __ballot_sync(0xffffffffu, (d >> RB) & 1u);
+        peers &= ((d >> RB) & 1u) ? m : ~m;
     }
     return peers;
 }
@@ -304,6 +309,7 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
     }
     __syncthreads();
     const uint32_t lt = lanemask_lt();
+    const bool full = blk + SORT_TILE <= n; // every key of the block is in range
     {
         // stable rank inside the warp: peer masks from ballots, the group
         // leader's shared-memory atomic on the warp's digit counter (one
@@ -313,7 +319,7 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
         for (int r = 0; r < SORT_ITEMS; ++r) {
             const bool ok = base + r * 32 + lane < n;
             const uint32_t d = ok ? digit_of(key[r], key_lo, key_max, shift, mask) : (uint32_t)RBINS;
-            const uint32_t peers = peers_by_ballot(d);
+            const uint32_t peers = peers_by_ballot(d, full);
             uint32_t old = 0;
             if (d < RBINS && (peers & lt) == 0) old = atomicAdd(&s_wh[w][d], (uint32_t)__popc(peers));
             rank[r] = (uint32_t)(__ffs(peers) - 1) | ((uint32_t)__popc(peers & lt) << 5) | (old << 10);
@@ -459,15 +465,19 @@ emit_pairs_kernel(const uint32_t *__restrict__ sorted_pv, const uint32_t *__rest
     const uint32_t last_lane = (uint32_t)(n - 1 - j0 < 31 ? n - 1 - j0 : 31);
     const uint32_t end = __shfl_sync(0xffffffffu, pre + nt, last_lane);
     if (lane == 0 && (int64_t)end > cap_pairs) atomicOr(status, ST_PAIR_OVERFLOW);
+    // Owner of output q: the last lane whose run starts at or before q.  Every
+    // valid lane's run is non-empty (a listed point-view covers a tile), so
+    // the runs starting inside a window of 32 outputs are one bit each of a
+    // mask, and the owner is the lane owning the window's first output
+    // minus one, plus the starts at or before q.
+    const uint32_t le = lanemask_lt() | (1u << lane);
+    int before = -1; // owner of output q0 - 1 (none before the first window)
     for (uint32_t q0 = start; q0 < end; q0 += 32) {
         const uint32_t q = q0 + lane;
-        // owner: largest lane with pre <= q
-        int ow = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const uint32_t p = __shfl_sync(0xffffffffu, pre, ow + step);
-            if (p <= q) ow += step;
-        }
+        const uint32_t rel = pre - q0; // valid lanes: pre >= q0 once their run is due
+        const uint32_t starts = __reduce_or_sync(0xffffffffu, rel < 32u ? 1u << rel : 0u);
+        const int ow = before + __popc(starts & le);
+        before += __popc(starts);
         const uint32_t opre = __shfl_sync(0xffffffffu, pre, ow);
         const uint32_t otb = __shfl_sync(0xffffffffu, tb, ow);
         const uint32_t owxt = __shfl_sync(0xffffffffu, wxt, ow);
