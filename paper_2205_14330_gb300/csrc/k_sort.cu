@@ -296,6 +296,15 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t mask = (1u << width) - 1u;
     const int bins = 1 << width;
+    // the block's global digit bases, loaded now so that their latency
+    // hides behind the ranking (digits threadIdx.x + k SORT_THREADS)
+    constexpr int PER_T = RBINS / SORT_THREADS;
+    uint32_t gb[PER_T];
+#pragma unroll
+    for (int k = 0; k < PER_T; ++k) {
+        const int dd = threadIdx.x + k * SORT_THREADS;
+        gb[k] = dd < bins ? hist[(int64_t)dd * nb + blockIdx.x] : 0u;
+    }
     for (int j = threadIdx.x; j < SORT_WARPS * RBINS; j += SORT_THREADS) (&s_wh[0][0])[j] = 0;
     const int64_t base = blk + (int64_t)w * 32 * SORT_ITEMS;
     uint32_t key[SORT_ITEMS], rank[SORT_ITEMS];
@@ -333,7 +342,9 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
     }
     __syncthreads();
     // per digit: exclusive prefix over warps, digit total, global base
-    for (int dd = threadIdx.x; dd < RBINS; dd += SORT_THREADS) {
+#pragma unroll
+    for (int k = 0; k < PER_T; ++k) {
+        const int dd = threadIdx.x + k * SORT_THREADS;
         uint32_t t = 0;
         if (dd < bins) {
 #pragma unroll
@@ -342,7 +353,7 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
                 s_wh[j][dd] = t;
                 t += x;
             }
-            s_gbase[dd] = hist[(int64_t)dd * nb + blockIdx.x];
+            s_gbase[dd] = gb[k];
         }
         s_tot[dd] = t;
     }
@@ -368,6 +379,12 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
         }
     }
     __syncthreads();
+    // output position of ranked slot j of digit d: s_gbase[d] + j - s_dbase[d]
+#pragma unroll
+    for (int k = 0; k < PER_T; ++k) {
+        const int dd = threadIdx.x + k * SORT_THREADS;
+        s_gbase[dd] -= s_dbase[dd];
+    }
 #pragma unroll
     for (int r = 0; r < SORT_ITEMS; ++r) {
         if (base + r * 32 + lane < n) {
@@ -382,7 +399,7 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
     for (int j = threadIdx.x; j < cnt; j += SORT_THREADS) {
         const uint32_t k = s_k[j];
         const uint32_t d = digit_of(k, key_lo, key_max, shift, mask);
-        const uint32_t g = s_gbase[d] + (uint32_t)j - s_dbase[d];
+        const uint32_t g = s_gbase[d] + (uint32_t)j;
         keys_out[g] = k;
         vals_out[g] = s_v[j];
     }
