@@ -239,15 +239,16 @@ __device__ __forceinline__ uint32_t peers_by_ballot(uint32_t d, bool full)
     return peers;
 }
 
-// Per-block digit histogram: shared-memory atomics into per-warp counters.
+// Per-block digit histogram: shared-memory atomics into one block counter
+// per digit.
 __global__ void __launch_bounds__(SORT_THREADS)
 radix_hist_kernel(const uint32_t *__restrict__ keys, const uint32_t *n_dev, int64_t cap,
                   uint32_t key_lo, uint32_t key_max, int shift, int width,
                   uint32_t *__restrict__ hist, int64_t nb)
 {
-    __shared__ uint32_t s_h[SORT_WARPS][RBINS];
+    __shared__ uint32_t s_h[RBINS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int j = threadIdx.x; j < SORT_WARPS * RBINS; j += SORT_THREADS) (&s_h[0][0])[j] = 0;
+    for (int j = threadIdx.x; j < RBINS; j += SORT_THREADS) s_h[j] = 0;
     const int64_t n = dev_count(n_dev, cap);
     const int64_t base = (int64_t)blockIdx.x * SORT_TILE + (int64_t)w * 32 * SORT_ITEMS;
     const uint32_t mask = (1u << width) - 1u;
@@ -260,15 +261,11 @@ radix_hist_kernel(const uint32_t *__restrict__ keys, const uint32_t *n_dev, int6
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < SORT_ITEMS; ++r)
-        if (d[r] < RBINS) atomicAdd(&s_h[w][d[r]], 1u);
+        if (d[r] < RBINS) atomicAdd(&s_h[d[r]], 1u);
     __syncthreads();
     const int bins = 1 << width;
-    for (int dd = threadIdx.x; dd < bins; dd += SORT_THREADS) {
-        uint32_t t = 0;
-#pragma unroll
-        for (int j = 0; j < SORT_WARPS; ++j) t += s_h[j][dd];
-        hist[(int64_t)dd * nb + blockIdx.x] = t;
-    }
+    for (int dd = threadIdx.x; dd < bins; dd += SORT_THREADS)
+        hist[(int64_t)dd * nb + blockIdx.x] = s_h[dd];
 }
 
 constexpr size_t SCATTER_SMEM = sizeof(uint32_t) * (3 * SORT_TILE + SORT_WARPS * RBINS + 3 * RBINS +
