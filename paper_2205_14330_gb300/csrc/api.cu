@@ -452,12 +452,12 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
     // 6. composite (optionally as one persistent launch over a longest-first tile order)
     const bool persist = st->opts.persistent && st->batch_depth == 0;
     if (persist) {
-        PBR_TRY(dalloc((void **)&st->tile_order, sizeof(uint32_t) * L.n_tiles, s));
+        PBR_TRY(dalloc((void **)&st->tile_order, sizeof(uint4) * L.n_tiles, s));
         PBR_TRY(dalloc((void **)&st->work, 64 * sizeof(uint32_t), s));
     }
     {
         StageScope t(c, STG_RASTER_FWD, s);
-        if (persist) launch_tile_order(st->ranges, L.n_tiles, st->tile_order, st->work, s);
+        if (persist) launch_tile_order(b, st->ranges, L.n_tiles, st->tile_order, st->work, s);
         launch_raster_fwd(b, o, st->batch_depth, st->ranges, st->tile_vals, st->rec, out_rgb,
                           st->T_final, st->n_contrib, st->counters + 2, s, st->tile_order,
                           st->work);

@@ -77,7 +77,7 @@ struct pbr_state {
     uint2 *ranges = nullptr;
     float *T_final = nullptr;
     uint32_t *n_contrib = nullptr;
-    uint32_t *tile_order = nullptr; // persistent raster: tiles, longest list first
+    uint4 *tile_order = nullptr; // persistent raster: tile descriptors, longest list first
     uint32_t *work = nullptr;       // persistent raster: item counters + buckets
 
     pbr::Batch batch() const

@@ -97,7 +97,8 @@ struct pbr_graph {
     uint32_t *vk = nullptr, *vv = nullptr, *vk2 = nullptr, *vv2 = nullptr;
     uint32_t *tk = nullptr, *tv = nullptr, *tk2 = nullptr, *tv2 = nullptr;
     float *T_final = nullptr;
-    uint32_t *n_contrib = nullptr, *order = nullptr, *work = nullptr;
+    uint32_t *n_contrib = nullptr, *work = nullptr;
+    uint4 *order = nullptr; // persistent raster: tile descriptors, longest list first
     void *temp = nullptr;
     float *own_grad = nullptr;
     double *own_loss = nullptr;
@@ -193,7 +194,7 @@ void enqueue_forward(pbr_graph *g, cudaStream_t s)
     cudaMemsetAsync(g->ranges, 0, sizeof(uint2) * L.n_tiles, s);
     launch_tile_ranges(tk, n_pairs_dev, g->cap_pairs, g->ranges, L.n_tiles, s);
     const bool persist = g->opts.persistent && g->opts.batch_depth == 0;
-    if (persist) launch_tile_order(g->ranges, L.n_tiles, g->order, g->work, s);
+    if (persist) launch_tile_order(b, g->ranges, L.n_tiles, g->order, g->work, s);
     launch_raster_fwd(b, o, g->opts.batch_depth, g->ranges, tv, g->rec, g->out_rgb, g->T_final,
                       g->n_contrib, nullptr, s, persist ? g->order : nullptr, g->work);
 }
@@ -338,7 +339,7 @@ int plan_and_capture(pbr_graph *g, cudaStream_t user_stream)
     PBR_TRY(g->alloc(&g->ranges, sizeof(uint2) * L.n_tiles));
     PBR_TRY(g->alloc(&g->T_final, sizeof(float) * L.n_pix));
     PBR_TRY(g->alloc(&g->n_contrib, sizeof(uint32_t) * L.n_pix));
-    PBR_TRY(g->alloc(&g->order, sizeof(uint32_t) * (L.n_tiles ? L.n_tiles : 1)));
+    PBR_TRY(g->alloc(&g->order, sizeof(uint4) * (L.n_tiles ? L.n_tiles : 1)));
     PBR_TRY(g->alloc(&g->work, 64 * sizeof(uint32_t)));
     const size_t temp = std::max(std::max(scan_temp_bytes(npv),
                                           radix_temp_bytes(std::max(g->cap_vis, g->cap_pairs))),

@@ -348,9 +348,10 @@ __device__ __forceinline__ void add_stats(unsigned long long *stats, uint32_t a,
 //            cutoff test and records the hit in its own bitmask;
 //   phase 2 (per lane): each lane walks only its own included entries.
 // wbuf: this warp's 64 float4 (a-parts, then b-parts of the chunk).
-template <int TW, int TH, bool STATS = true>
-__device__ __forceinline__ void fwd_stream_item(const Batch &b, const DevOpts &o, uint32_t tile,
-                                                int sub, int lane, const uint2 *__restrict__ ranges,
+// g: the lane's pixel and the warp's rectangle; [s, e): the tile's list.
+template <bool STATS = true>
+__device__ __forceinline__ void fwd_stream_item(const PixelGeom &g, uint32_t s, uint32_t e,
+                                                const DevOpts &o, int lane,
                                                 const uint32_t *__restrict__ pv_list,
                                                 const float4 *__restrict__ rec,
                                                 float *__restrict__ out_rgb,
@@ -359,10 +360,6 @@ __device__ __forceinline__ void fwd_stream_item(const Batch &b, const DevOpts &o
                                                 uint32_t &examined_acc, uint32_t &composited_acc,
                                                 float4 *wbuf)
 {
-    const PixelGeom g = pixel_geom<TW, TH>(b, tile, sub, lane);
-    const uint2 rg = ranges[tile];
-    const uint32_t s = rg.x, e = rg.y > rg.x ? rg.y : rg.x;
-
     float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     uint32_t cnt = 0, last = 0, examined = 0;
     bool done = !g.inside;
@@ -560,9 +557,10 @@ __device__ __forceinline__ BwdPixel bwd_pixel(const PixelGeom &g, const DevOpts 
 // per-point warp work (staging, cull, reduction or atomics) serves 32P
 // pixels instead of 32.  Each pixel's T and S recursions are the same
 // operations as in the one-pixel walk.
+// V, (tx, ty): the tile's view and position; s: the start of its list.
 template <int TW, int TH, int P, bool STATS>
-__device__ __forceinline__ void bwd_rows_item(const Batch &b, const DevOpts &o, uint32_t tile,
-                                              int sub, int lane, const uint2 *__restrict__ ranges,
+__device__ __forceinline__ void bwd_rows_item(const DevView *V, int tx, int ty, uint32_t s,
+                                              const DevOpts &o, int sub, int lane,
                                               const uint32_t *__restrict__ pv_list,
                                               const float4 *__restrict__ rec,
                                               const float *__restrict__ T_final,
@@ -572,9 +570,6 @@ __device__ __forceinline__ void bwd_rows_item(const Batch &b, const DevOpts &o, 
                                               uint32_t &used, float4 *wbuf, uint32_t *wpv)
 {
     static_assert(TH % (4 * P) == 0, "sub-block rows must tile the tile");
-    const DevView *V = &b.views[find_view_by_tile(b, tile)];
-    const uint32_t local = tile - V->tile_base;
-    const int tx = (int)(local % (uint32_t)V->tiles_x), ty = (int)(local / (uint32_t)V->tiles_x);
     const int sx0 = tx * TW + (sub % (TW / 8)) * 8, sy0 = ty * TH + (sub / (TW / 8)) * (4 * P);
     PixelGeom g[P];
     BwdPixel px[P];
@@ -585,7 +580,6 @@ __device__ __forceinline__ void bwd_rows_item(const Batch &b, const DevOpts &o, 
         px[q] = bwd_pixel(g[q], o, T_final, n_contrib, grad_rgb);
         lmax = px[q].L > lmax ? px[q].L : lmax;
     }
-    const uint32_t s = ranges[tile].x;
     const uint32_t wmax = __reduce_max_sync(0xffffffffu, lmax);
     if (wmax == 0) return;
     int64_t c = (int64_t)((wmax - 1) & ~31u);
@@ -676,8 +670,10 @@ raster_fwd_stream_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
     __shared__ float4 s_buf[TW * TH / 32][64];
     const int lane = threadIdx.x & 31;
     uint32_t ex = 0, co = 0;
-    fwd_stream_item<TW, TH>(b, o, blockIdx.x, threadIdx.x >> 5, lane, ranges, pv_list, rec,
-                            out_rgb, T_final, n_contrib, ex, co, s_buf[threadIdx.x >> 5]);
+    const uint2 rg = ranges[blockIdx.x];
+    fwd_stream_item(pixel_geom<TW, TH>(b, blockIdx.x, threadIdx.x >> 5, lane), rg.x,
+                    rg.y > rg.x ? rg.y : rg.x, o, lane, pv_list, rec, out_rgb, T_final, n_contrib,
+                    ex, co, s_buf[threadIdx.x >> 5]);
     add_stats(stats, ex, co, lane);
 }
 
@@ -712,6 +708,19 @@ __device__ __forceinline__ uint32_t next_item(uint32_t *work, int lane)
     return __shfl_sync(0xffffffffu, it, 0);
 }
 
+// Tile descriptor of the persistent order: {view, tx | ty << 16, list start,
+// list end}, so that a warp starting an item needs one load, not a search
+// of the view table, a division and the ranges.
+__device__ __forceinline__ uint4 tile_desc(const Batch &b, const uint2 *ranges, uint32_t tile)
+{
+    const int v = find_view_by_tile(b, tile);
+    const DevView &V = b.views[v];
+    const uint32_t local = tile - V.tile_base;
+    const uint32_t tx = local % (uint32_t)V.tiles_x, ty = local / (uint32_t)V.tiles_x;
+    const uint2 r = ranges[tile];
+    return make_uint4((uint32_t)v, tx | (ty << 16), r.x, r.y > r.x ? r.y : r.x);
+}
+
 // STATS: count examined / composited pairs into stats (which must then be
 // non-null); without, the loops carry no counting.  Six blocks per SM (40
 // registers): the counting variant otherwise takes 48 and five blocks,
@@ -723,17 +732,22 @@ raster_fwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
                           const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
                           float *__restrict__ out_rgb, float *__restrict__ T_final,
                           uint32_t *__restrict__ n_contrib, unsigned long long *__restrict__ stats,
-                          const uint32_t *__restrict__ order, uint32_t *work)
+                          const uint4 *__restrict__ order, uint32_t *work)
 {
     constexpr uint32_t SUBS = (TW / 8) * (TH / 4);
     __shared__ float4 s_buf[PERSIST_THREADS / 32][64];
     const int lane = threadIdx.x & 31;
     const uint32_t n_items = b.n_tiles * SUBS;
     uint32_t ex = 0, co = 0;
-    for (uint32_t it = next_item(work, lane); it < n_items; it = next_item(work, lane))
-        fwd_stream_item<TW, TH, STATS>(b, o, order[it / SUBS], (int)(it % SUBS), lane, ranges,
-                                       pv_list, rec, out_rgb, T_final, n_contrib, ex, co,
-                                       s_buf[threadIdx.x >> 5]);
+    for (uint32_t it = next_item(work, lane); it < n_items; it = next_item(work, lane)) {
+        const uint4 d = order[it / SUBS];
+        const int sub = (int)(it % SUBS);
+        const PixelGeom g =
+            pixel_geom_at(&b.views[d.x], (int)(d.y & 0xffffu) * TW + (sub % (TW / 8)) * 8,
+                          (int)(d.y >> 16) * TH + (sub / (TW / 8)) * 4, lane);
+        fwd_stream_item<STATS>(g, d.z, d.w, o, lane, pv_list, rec, out_rgb, T_final, n_contrib,
+                               ex, co, s_buf[threadIdx.x >> 5]);
+    }
     if (STATS) add_stats(stats, ex, co, lane);
 }
 
@@ -743,7 +757,7 @@ raster_bwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
                           const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
                           const float *__restrict__ T_final, const uint32_t *__restrict__ n_contrib,
                           const float *__restrict__ grad_rgb, float *__restrict__ g2d,
-                          unsigned long long *__restrict__ stats, const uint32_t *__restrict__ order,
+                          unsigned long long *__restrict__ stats, const uint4 *__restrict__ order,
                           uint32_t *work)
 {
     constexpr int P = (TH % (4 * BWD_ROWS) == 0) ? BWD_ROWS : 2;
@@ -753,10 +767,13 @@ raster_bwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
     const int lane = threadIdx.x & 31;
     const uint32_t n_items = b.n_tiles * SUBS;
     uint32_t ex = 0, us = 0;
-    for (uint32_t it = next_item(work, lane); it < n_items; it = next_item(work, lane))
-        bwd_rows_item<TW, TH, P, STATS>(b, o, order[it / SUBS], (int)(it % SUBS), lane, ranges,
-                                        pv_list, rec, T_final, n_contrib, grad_rgb, g2d, ex, us,
-                                        s_buf[threadIdx.x >> 5], s_pv[threadIdx.x >> 5]);
+    for (uint32_t it = next_item(work, lane); it < n_items; it = next_item(work, lane)) {
+        const uint4 d = order[it / SUBS];
+        bwd_rows_item<TW, TH, P, STATS>(&b.views[d.x], (int)(d.y & 0xffffu), (int)(d.y >> 16),
+                                        d.z, o, (int)(it % SUBS), lane, pv_list, rec, T_final,
+                                        n_contrib, grad_rgb, g2d, ex, us, s_buf[threadIdx.x >> 5],
+                                        s_pv[threadIdx.x >> 5]);
+    }
     if (STATS) add_stats(stats + 2, ex, us, lane);
 }
 
@@ -799,8 +816,8 @@ __global__ void tile_bucket_scan_kernel(uint32_t *work)
 // and bucket), so neighbouring tiles of similar length run close together
 // in time and share their records through L2.
 __global__ void __launch_bounds__(256)
-tile_bucket_scatter_kernel(const uint2 *__restrict__ ranges, uint32_t n_tiles, uint32_t *work,
-                           uint32_t *__restrict__ order)
+tile_bucket_scatter_kernel(Batch b, const uint2 *__restrict__ ranges, uint32_t n_tiles,
+                           uint32_t *work, uint4 *__restrict__ order)
 {
     __shared__ uint32_t s_w[8][33]; // per warp and bucket: count, then offset
     __shared__ uint32_t s_base[32];
@@ -829,7 +846,7 @@ tile_bucket_scatter_kernel(const uint2 *__restrict__ ranges, uint32_t n_tiles, u
         s_base[b] = run ? atomicAdd(work + 2 + b, run) : 0u;
     }
     __syncthreads();
-    if (bkt < 32) order[s_base[bkt] + s_w[w][bkt] + rank] = t;
+    if (bkt < 32) order[s_base[bkt] + s_w[w][bkt] + rank] = tile_desc(b, ranges, t);
 }
 
 // ========================================================= block-staged
@@ -1004,7 +1021,7 @@ int persist_grid(const void *kernel)
 template <int TW, int TH>
 void fwd_dispatch(const Batch &b, const DevOpts &o, int depth, const uint2 *ranges,
                   const uint32_t *pv_list, const float4 *rec, float *out_rgb, float *T_final,
-                  uint32_t *n_contrib, unsigned long long *stats, const uint32_t *order,
+                  uint32_t *n_contrib, unsigned long long *stats, const uint4 *order,
                   uint32_t *work, cudaStream_t s)
 {
     if (depth == 0 && order) {
@@ -1039,7 +1056,7 @@ template <int TW, int TH>
 void bwd_dispatch(const Batch &b, const DevOpts &o, int depth, const uint2 *ranges,
                   const uint32_t *pv_list, const float4 *rec, const float *T_final,
                   const uint32_t *n_contrib, const float *grad_rgb, float4 *g2d,
-                  unsigned long long *stats, const uint32_t *order, uint32_t *work,
+                  unsigned long long *stats, const uint4 *order, uint32_t *work,
                   cudaStream_t s)
 {
     if (depth == 0 && order) {
@@ -1074,15 +1091,15 @@ void bwd_dispatch(const Batch &b, const DevOpts &o, int depth, const uint2 *rang
 
 } // namespace
 
-void launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, uint32_t *work,
-                       cudaStream_t s)
+void launch_tile_order(const Batch &b, const uint2 *ranges, uint32_t n_tiles, uint4 *order,
+                       uint32_t *work, cudaStream_t s)
 {
     cudaMemsetAsync(work, 0, 34 * sizeof(uint32_t), s);
     if (n_tiles == 0) return;
     const unsigned nb = (n_tiles + 255) / 256;
     tile_bucket_count_kernel<<<nb, 256, 0, s>>>(ranges, n_tiles, work);
     tile_bucket_scan_kernel<<<1, 32, 0, s>>>(work);
-    tile_bucket_scatter_kernel<<<nb, 256, 0, s>>>(ranges, n_tiles, work, order);
+    tile_bucket_scatter_kernel<<<nb, 256, 0, s>>>(b, ranges, n_tiles, work, order);
     count_launches(3);
 }
 
@@ -1094,7 +1111,7 @@ void reset_work_counters(uint32_t *work, cudaStream_t s)
 void launch_raster_fwd(const Batch &b, const DevOpts &o, int depth, const uint2 *ranges,
                        const uint32_t *pv_list, const float4 *rec, float *out_rgb,
                        float *T_final, uint32_t *n_contrib, unsigned long long *stats,
-                       cudaStream_t s, const uint32_t *order, uint32_t *work)
+                       cudaStream_t s, const uint4 *order, uint32_t *work)
 {
     if (b.n_tiles == 0) return;
     if (o.tile_w == 8 && o.tile_h == 8)
@@ -1111,7 +1128,7 @@ void launch_raster_fwd(const Batch &b, const DevOpts &o, int depth, const uint2 
 void launch_raster_bwd(const Batch &b, const DevOpts &o, int depth, const uint2 *ranges,
                        const uint32_t *pv_list, const float4 *rec, const float *T_final,
                        const uint32_t *n_contrib, const float *grad_rgb, float4 *g2d,
-                       unsigned long long *stats, cudaStream_t s, const uint32_t *order,
+                       unsigned long long *stats, cudaStream_t s, const uint4 *order,
                        uint32_t *work)
 {
     if (b.n_tiles == 0) return;

@@ -250,15 +250,16 @@ void launch_sh_normals(uint64_t seed, int64_t c0, int64_t count, float *out, cud
 void launch_raster_fwd(const Batch &b, const DevOpts &o, int batch_depth, const uint2 *ranges,
                        const uint32_t *pv_list, const float4 *rec, float *out_rgb,
                        float *T_final, uint32_t *n_contrib, unsigned long long *stats,
-                       cudaStream_t s, const uint32_t *order = nullptr, uint32_t *work = nullptr);
+                       cudaStream_t s, const uint4 *order = nullptr, uint32_t *work = nullptr);
 void launch_raster_bwd(const Batch &b, const DevOpts &o, int batch_depth, const uint2 *ranges,
                        const uint32_t *pv_list, const float4 *rec, const float *T_final,
                        const uint32_t *n_contrib, const float *grad_rgb, float4 *g2d,
                        unsigned long long *stats, cudaStream_t s,
-                       const uint32_t *order = nullptr, uint32_t *work = nullptr);
-// Longest-first tile order for the persistent raster; work: 34 u32 words.
-void launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, uint32_t *work,
-                       cudaStream_t s);
+                       const uint4 *order = nullptr, uint32_t *work = nullptr);
+// Longest-first tile order for the persistent raster, as tile descriptors
+// {view, tx | ty << 16, list start, list end}; work: 34 u32 words.
+void launch_tile_order(const Batch &b, const uint2 *ranges, uint32_t n_tiles, uint4 *order,
+                       uint32_t *work, cudaStream_t s);
 void reset_work_counters(uint32_t *work, cudaStream_t s);
 
 // ---- training step (k_train.cu)

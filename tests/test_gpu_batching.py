@@ -70,6 +70,27 @@ def test_graph_replay_matches_eager(env, sched):
     G.close()
 
 
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (16, 32)])
+def test_persistent_matches_streamed_on_a_batch(env, tile):
+    """The persistent schedule (tile descriptors over several views and
+    scenes of uneven sizes) against the one-block-per-tile schedule: the
+    same image bit for bit, the same gradients to atomic-order rounding."""
+    import torch
+    pbr, R = env
+    sc, cams, sov = _batch(pbr, seed=7)
+    target = torch.rand((pbr.n_pixels(cams), 3), device="cuda")
+    out = []
+    for per in (0, 1):
+        img, st = R.forward(sc, cams, pbr.default_opts(tile=tile, persistent=per),
+                            scene_of_view=sov)
+        _, g = pbr.image_loss(img, target, "l2")
+        out.append((img, R.backward(st, g)))
+        st.close()
+    assert torch.equal(out[0][0], out[1][0])
+    for a, b in zip(out[0][1], out[1][1]):
+        assert _rel(b, a) <= 1e-5
+
+
 def test_graph_follows_in_place_updates_and_replans(env):
     import torch
     pbr, R = env
