@@ -23,7 +23,7 @@
 // atomics per warp and point) in the warp-streamed schedules.
 //
 // A block covers one TW x TH screen tile; each warp owns an 8 x 4 sub-block
-// of it (an 8 x 8 one, two pixels per lane, in the persistent backward) and
+// of it (an 8 x 8 one, two pixels per lane, in the persistent schedule) and
 // skips list entries whose cutoff disc misses its still active pixels.  Two
 // schedules:
 //   - warp-streamed (batch depth 0, default): every warp walks the tile list
@@ -425,6 +425,106 @@ __device__ __forceinline__ void fwd_stream_item(const PixelGeom &g, uint32_t s, 
     write_pixel(g, o, T, C0, C1, C2, last, out_rgb, T_final, n_contrib);
 }
 
+// Forward of one 8 x 8 sub-block by one warp, for the persistent schedule:
+// lane l owns the pixels (l & 7, l >> 3) and (l & 7, 4 + (l >> 3)), gA and
+// gB.  The per-chunk staging, culling and ballots serve 64 pixels; every
+// lane tests each hit at both of its pixels, then walks the first pixel's
+// included entries and the second's.  Each pixel's blend sequence is the
+// one-pixel walk's.
+template <bool STATS>
+__device__ __forceinline__ void fwd_pair_item(const PixelGeom &gA, const PixelGeom &gB,
+                                              uint32_t s, uint32_t e, const DevOpts &o, int lane,
+                                              const uint32_t *__restrict__ pv_list,
+                                              const float4 *__restrict__ rec,
+                                              float *__restrict__ out_rgb,
+                                              float *__restrict__ T_final,
+                                              uint32_t *__restrict__ n_contrib,
+                                              uint32_t &examined_acc, uint32_t &composited_acc,
+                                              float4 *wbuf)
+{
+    float TA = 1.0f, A0 = 0.f, A1 = 0.f, A2 = 0.f;
+    float TB = 1.0f, B0 = 0.f, B1 = 0.f, B2 = 0.f;
+    uint32_t cntA = 0, cntB = 0, lastA = 0, lastB = 0, examined = 0;
+    bool doneA = !gA.inside, doneB = !gB.inside;
+    if (!__all_sync(0xffffffffu, doneA && doneB)) {
+        // software pipeline as in fwd_stream_item
+        uint32_t pv_n = 0, pv_nn = 0;
+        float4 a_n = make_float4(0.f, 0.f, -1.f, 0.f);
+        if (s + lane < e) {
+            pv_n = __ldg(pv_list + s + lane);
+            a_n = __ldg(rec + 2 * (size_t)pv_n);
+        }
+        if (s + 32 + lane < e) pv_nn = __ldg(pv_list + s + 32 + lane);
+        const PixelGeom g2[2] = {gA, gB};
+        for (uint32_t c = s; c < e; c += 32) {
+            const uint32_t pv = pv_n;
+            const float4 a = a_n;
+            const bool valid = c + lane < e;
+            if (c + 32 + lane < e) {
+                pv_n = pv_nn;
+                a_n = __ldg(rec + 2 * (size_t)pv_n);
+            }
+            if (c + 64 + lane < e) pv_nn = __ldg(pv_list + c + 64 + lane);
+            // every lane takes part in the reductions, whatever its entry
+            const bool act[2] = {!doneA, !doneB};
+            const PixelGeom ar = active_rect_rows<2>(g2, act);
+            const bool hit = valid && disc_meets_rect(a, ar);
+            const bool covers = hit && disc_covers_rect(a, ar);
+            uint32_t m = __ballot_sync(0xffffffffu, hit);
+            // entries whose disc holds every active pixel need no per-pixel test
+            const uint32_t full = __ballot_sync(0xffffffffu, covers);
+            if (hit) {
+                wbuf[lane] = a;
+                wbuf[32 + lane] = __ldg(rec + 2 * (size_t)pv + 1);
+            }
+            __syncwarp();
+            if (STATS) examined += (uint32_t)__popc(m) * ((uint32_t)!doneA + (uint32_t)!doneB);
+            uint32_t mA = full, mB = full;
+            m &= ~full;
+            while (m) {
+                const int j = __ffs(m) - 1;
+                m &= m - 1;
+                const float4 aj = wbuf[j];
+                float dx, dy;
+                if (pixel_d2(gA.ux, gA.uy, aj.x, aj.y, dx, dy) <= aj.z) mA |= 1u << j;
+                if (pixel_d2(gB.ux, gB.uy, aj.x, aj.y, dx, dy) <= aj.z) mB |= 1u << j;
+            }
+            if (doneA) mA = 0;
+            if (doneB) mB = 0;
+            while (mA) {
+                const int j = __ffs(mA) - 1;
+                mA &= mA - 1;
+                const float4 aj = wbuf[j];
+                float dx, dy;
+                const float d2 = pixel_d2(gA.ux, gA.uy, aj.x, aj.y, dx, dy);
+                lastA = c + j - s + 1;
+                if (pixel_blend(d2, aj, wbuf[32 + j], o, TA, A0, A1, A2, cntA)) {
+                    doneA = true;
+                    break;
+                }
+            }
+            while (mB) {
+                const int j = __ffs(mB) - 1;
+                mB &= mB - 1;
+                const float4 aj = wbuf[j];
+                float dx, dy;
+                const float d2 = pixel_d2(gB.ux, gB.uy, aj.x, aj.y, dx, dy);
+                lastB = c + j - s + 1;
+                if (pixel_blend(d2, aj, wbuf[32 + j], o, TB, B0, B1, B2, cntB)) {
+                    doneB = true;
+                    break;
+                }
+            }
+            __syncwarp(); // chunk consumed before the buffer is refilled
+            if (__all_sync(0xffffffffu, doneA && doneB)) break;
+        }
+    }
+    examined_acc += examined;
+    composited_acc += cntA + cntB;
+    write_pixel(gA, o, TA, A0, A1, A2, lastA, out_rgb, T_final, n_contrib);
+    write_pixel(gB, o, TB, B0, B1, B2, lastB, out_rgb, T_final, n_contrib);
+}
+
 // Up to this many contributing pixels of a warp add their terms with their
 // own vector atomics; more go through the transposed warp reduction.  The
 // reduction costs some 35 instructions whatever the count, the atomics
@@ -700,6 +800,7 @@ raster_bwd_stream_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
 // counter over `order` (tiles sorted longest list first), so long tiles
 // start early and no warp idles while work remains.
 constexpr int PERSIST_THREADS = 256;
+constexpr int FWD_PERSIST_BLOCKS = 5; // forward blocks per SM (see the kernel)
 
 __device__ __forceinline__ uint32_t next_item(uint32_t *work, int lane)
 {
@@ -722,19 +823,19 @@ __device__ __forceinline__ uint4 tile_desc(const Batch &b, const uint2 *ranges, 
 }
 
 // STATS: count examined / composited pairs into stats (which must then be
-// non-null); without, the loops carry no counting.  Six blocks per SM (40
-// registers): the counting variant otherwise takes 48 and five blocks,
-// 0.24 ms slower on the 1M-point, 64-view step.  The backward runs best at
-// its natural four blocks (five: 11.1 -> 11.9 ms).
+// non-null); without, the loops carry no counting.  The forward's 8 x 8
+// warps run five blocks per SM (48 registers): 5.84 ms on the 1M-point,
+// 64-view step against 6.05 at four and 6.10 at six.  The backward runs
+// best at its natural four blocks (five: 11.1 -> 11.9 ms).
 template <int TW, int TH, bool STATS>
-__global__ void __launch_bounds__(PERSIST_THREADS, 6)
+__global__ void __launch_bounds__(PERSIST_THREADS, FWD_PERSIST_BLOCKS)
 raster_fwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
                           const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
                           float *__restrict__ out_rgb, float *__restrict__ T_final,
                           uint32_t *__restrict__ n_contrib, unsigned long long *__restrict__ stats,
                           const uint4 *__restrict__ order, uint32_t *work)
 {
-    constexpr uint32_t SUBS = (TW / 8) * (TH / 4);
+    constexpr uint32_t SUBS = (TW / 8) * (TH / 8);
     __shared__ float4 s_buf[PERSIST_THREADS / 32][64];
     const int lane = threadIdx.x & 31;
     const uint32_t n_items = b.n_tiles * SUBS;
@@ -742,11 +843,12 @@ raster_fwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
     for (uint32_t it = next_item(work, lane); it < n_items; it = next_item(work, lane)) {
         const uint4 d = order[it / SUBS];
         const int sub = (int)(it % SUBS);
-        const PixelGeom g =
-            pixel_geom_at(&b.views[d.x], (int)(d.y & 0xffffu) * TW + (sub % (TW / 8)) * 8,
-                          (int)(d.y >> 16) * TH + (sub / (TW / 8)) * 4, lane);
-        fwd_stream_item<STATS>(g, d.z, d.w, o, lane, pv_list, rec, out_rgb, T_final, n_contrib,
-                               ex, co, s_buf[threadIdx.x >> 5]);
+        const DevView *V = &b.views[d.x];
+        const int sx0 = (int)(d.y & 0xffffu) * TW + (sub % (TW / 8)) * 8;
+        const int sy0 = (int)(d.y >> 16) * TH + (sub / (TW / 8)) * 8;
+        fwd_pair_item<STATS>(pixel_geom_at(V, sx0, sy0, lane), pixel_geom_at(V, sx0, sy0 + 4, lane),
+                             d.z, d.w, o, lane, pv_list, rec, out_rgb, T_final, n_contrib, ex, co,
+                             s_buf[threadIdx.x >> 5]);
     }
     if (STATS) add_stats(stats, ex, co, lane);
 }
