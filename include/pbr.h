@@ -94,10 +94,13 @@ typedef struct {
                               32..1024 (multiple of 32) = block-staged batches of
                               that many points in shared memory */
     int32_t persistent;    /* 1: warp-streamed compositing as one persistent launch
-                              (SM-count grid, warps pull (tile, 8x4 sub-block)
+                              (SM-count grid, warps pull (tile, 8x8 sub-block)
                               items longest tile first); 0 (default): one block
                               per tile.  Ignored by the block-staged schedule. */
-    int32_t reserved[3];
+    int32_t no_pair_stats; /* 1: the compositing kernels skip the pair counting
+                              that pbr_state_stats reports (as captured graphs
+                              always do); 0 (default): count */
+    int32_t reserved[2];
 } pbr_render_opts;
 
 /* One scene: n points with position [n,3], SH coefficients [n,K,3]
@@ -188,9 +191,9 @@ int pbr_image_loss(int32_t kind, const float *pred, const float *target, int64_t
  * pairs examined, backward pairs contributing}.  Composited and contributing
  * pairs are the work units of the compositing kernels' ALU roofline; the
  * examined counts depend on the schedule's culling.  Only eager passes
- * (pbr_render_forward / pbr_render_backward) count; captured graphs
- * (pbr_graph_*) run kernels without the counting.  Synchronises the state's
- * stream. */
+ * (pbr_render_forward / pbr_render_backward) without opts.no_pair_stats
+ * count; captured graphs (pbr_graph_*) run kernels without the counting.
+ * Synchronises the state's stream. */
 int pbr_state_stats(pbr_state *state, unsigned long long *out4);
 
 /* ------------------------------------------------------- batched graphs */

@@ -180,6 +180,8 @@ int pbr::check_opts(const pbr_render_opts *o)
         return set_error(PBR_ERR_INVALID_ARG, "t_eps >= 0, cutoff_k > 0, max_per_pixel >= 0");
     if (o->radius_mode < 0 || o->radius_mode > 1 || o->dir_frame < 0 || o->dir_frame > 1)
         return set_error(PBR_ERR_INVALID_ARG, "radius_mode and dir_frame are 0 or 1");
+    if (o->no_pair_stats < 0 || o->no_pair_stats > 1)
+        return set_error(PBR_ERR_INVALID_ARG, "no_pair_stats is 0 or 1");
     return PBR_OK;
 }
 
@@ -459,7 +461,8 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
         StageScope t(c, STG_RASTER_FWD, s);
         if (persist) launch_tile_order(b, st->ranges, L.n_tiles, st->tile_order, st->work, s);
         launch_raster_fwd(b, o, st->batch_depth, st->ranges, st->tile_vals, st->rec, out_rgb,
-                          st->T_final, st->n_contrib, st->counters + 2, s, st->tile_order,
+                          st->T_final, st->n_contrib,
+                          st->opts.no_pair_stats ? nullptr : st->counters + 2, s, st->tile_order,
                           st->work);
     }
     PBR_CUDA(cudaGetLastError());
@@ -511,7 +514,8 @@ extern "C" int pbr_render_backward(pbr_ctx *c, pbr_state *st, const float *grad_
         PBR_CUDA(cudaMemsetAsync(g2d, 0, sizeof(float4) * 2 * L.n_pv, s));
         if (st->work) reset_work_counters(st->work, s);
         launch_raster_bwd(b, st->dopts, st->batch_depth, st->ranges, st->tile_vals, st->rec,
-                          st->T_final, st->n_contrib, grad_rgb, g2d, st->counters + 2, s,
+                          st->T_final, st->n_contrib, grad_rgb, g2d,
+                          st->opts.no_pair_stats ? nullptr : st->counters + 2, s,
                           st->tile_order, st->work);
     }
     {

@@ -602,6 +602,7 @@ extern "C" int pbr_autotune(pbr_ctx *c, const pbr_points *scenes, int32_t n_scen
             o.tile_h = t[1];
             o.batch_depth = sc[0];
             o.persistent = sc[1];
+            o.no_pair_stats = 1; // time the kernels the captured graphs run
             float total = 0.f;
             for (int r = 0; r <= reps && rc == PBR_OK; ++r) {
                 cudaEventRecord(e0, s);
@@ -628,6 +629,7 @@ extern "C" int pbr_autotune(pbr_ctx *c, const pbr_points *scenes, int32_t n_scen
         }
         if (rc != PBR_OK) break;
     }
+    best_o.no_pair_stats = opts->no_pair_stats;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(img);

@@ -43,7 +43,7 @@ class Opts(C.Structure):
                 ("alpha_max", C.c_float), ("t_eps", C.c_float), ("max_per_pixel", C.c_int32),
                 ("bg", C.c_float * 3), ("z_near", C.c_float), ("tile_w", C.c_int32),
                 ("tile_h", C.c_int32), ("batch_depth", C.c_int32), ("persistent", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("no_pair_stats", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class Points(C.Structure):

@@ -154,6 +154,28 @@ def test_image_independent_of_tile_size_and_batch_depth(R):
         assert np.array_equal(im, imgs[0])
 
 
+@pytest.mark.parametrize("per", [0, 1])
+def test_pair_counting_is_optional(R, per):
+    """no_pair_stats = 1 runs the compositing kernels without the pair
+    counting: the same image and gradients, zero counts."""
+    import torch
+    sc = _small_scene(6, n=800, r=(0.01, 0.05))
+    cams = [scenes.camera((0.2, -0.1, 2.3), 96, 72), scenes.camera((-1.7, 0.4, 1.4), 40, 56)]
+    g = torch.from_numpy(np.random.default_rng(3).normal(size=(96 * 72 + 40 * 56, 3))
+                         .astype(np.float32)).cuda()
+    out = []
+    for nps in (0, 1):
+        img, st, _ = _gpu_render(R, sc, cams, persistent=per, no_pair_stats=nps)
+        grads = R.backward(st, g)
+        out.append((img, grads, st.stats()))
+        st.close()
+    assert torch.equal(out[0][0], out[1][0])
+    for a, b in zip(out[0][1], out[1][1]):
+        assert _rel(b.cpu().numpy(), a.cpu().numpy().astype(np.float64)) <= 1e-5
+    assert out[0][2]["fwd_composited"] > 0 and out[0][2]["bwd_contributing"] > 0
+    assert all(v == 0 for v in out[1][2].values())
+
+
 def test_forward_is_deterministic(R):
     sc = _small_scene(3, n=2000, r=(0.01, 0.05))
     cams = [scenes.camera((0.1, 0.1, 2.5), 128, 96)]
