@@ -239,11 +239,12 @@ preprocess_fwd_kernel(Batch b, DevOpts o, float4 *__restrict__ rec, uint32_t *__
 // ------------------------------------------------------------- backward
 // The screen-space terms of a point's views are fetched BWD_AHEAD views
 // ahead with per-thread asynchronous copies into shared memory, so that
-// several 32-byte reads per thread are in flight while earlier views are
-// computed (the kernel is otherwise bound by the latency of one read per
-// view).  BWD_AHEAD + 1 slots per thread: a slot is refilled one view after
-// its contents were read.
-constexpr int BWD_AHEAD = 4;
+// their reads are in flight while earlier views are computed.
+// BWD_AHEAD + 1 slots per thread: a slot is refilled one view after its
+// contents were read.  Measured on the 1M-point, 64-view step: 1.27-1.29 ms
+// at one or two views ahead, 1.37 ms at three or four (the deeper buffer
+// takes shared memory from the L1 cache).
+constexpr int BWD_AHEAD = 2;
 constexpr int BWD_SLOTS = BWD_AHEAD + 1;
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
