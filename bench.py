@@ -617,19 +617,26 @@ def main():
 
     # ---- plain single-view renderer: same kernels, one view per launch chain
     plain = None
-    if not args.no_plain and sov is None:
+    if not args.no_plain:
+        # one view per launch chain; a multi-frame batch renders each view from
+        # its own frame's scene
+        pix_off = np.concatenate([[0], np.cumsum([pbr.n_pixels([c]) for c in cams])])
+
+        def scene_for(v):
+            return [scene_list[sov[v] if sov is not None else 0]]
+
         def plain_step():
             for v in range(len(cams)):
                 out_v = torch.empty((pbr.n_pixels([cams[v]]), 3), dtype=torch.float32, device=dev)
-                _, st = R.forward(scene_list, [cams[v]], opts, out=out_v)
-                tgt_v = target[sum(pbr.n_pixels([c]) for c in cams[:v]):][:out_v.shape[0]]
+                _, st = R.forward(scene_for(v), [cams[v]], opts, out=out_v)
+                tgt_v = target[int(pix_off[v]):int(pix_off[v + 1])]
                 _, g = pbr.image_loss(out_v, tgt_v, loss_kind)
                 R.backward(st, g)
                 st.close()
         def plain_fwd():
             for v in range(len(cams)):
                 out_v = torch.empty((pbr.n_pixels([cams[v]]), 3), dtype=torch.float32, device=dev)
-                R.forward(scene_list, [cams[v]], opts, out=out_v, keep_state=False)
+                R.forward(scene_for(v), [cams[v]], opts, out=out_v, keep_state=False)
         plain_step()
         k = max(1, min(3, args.steps // 3))
         p_ms = timed(plain_step, k)

@@ -13,10 +13,9 @@ Parity status (every function is pinned by ``tests/test_oracle_*.py``):
                         printed textbook values, parity under v -> -v
   project ............. pinned: on-axis point lands on the principal point,
                         closed-form pinhole on random points
-  bin_tiles ........... pinned: every pixel passing the cutoff test has its
-                        tile listed (brute force over pixels), and the
-                        lists equal a brute-force enumeration of the
-                        tile test
+  bin_tiles ........... pinned: a (tile, 8 x 8 block) is listed exactly when
+                        some pixel in it passes the cutoff test (brute force
+                        over every pixel of the image, both directions)
   render .............. pinned: isolated splat in closed form, transmittance
                         identity, occlusion, permutation invariance
   backward ............ pinned: central finite differences of ``render``
@@ -57,7 +56,7 @@ class Rec(C.Structure):
                 ("rc32", C.c_float), ("rc2_32", C.c_float),
                 ("px_lo", C.c_int32), ("px_hi", C.c_int32), ("py_lo", C.c_int32), ("py_hi", C.c_int32),
                 ("tx_lo", C.c_int32), ("tx_hi", C.c_int32), ("ty_lo", C.c_int32), ("ty_hi", C.c_int32),
-                ("tile_mask", C.c_uint32), ("ntiles", C.c_int64),
+                ("ntiles", C.c_int64),
                 ("X", C.c_double * 3), ("px", C.c_double), ("py", C.c_double), ("s", C.c_double),
                 ("dir", C.c_double * 3), ("rgb", C.c_double * 3)]
 
@@ -91,7 +90,8 @@ def lib():
             L.orc_preprocess.argtypes = [C.c_int64, dp, dp, dp, C.c_int, C.c_int,
                                          C.POINTER(Camera), C.POINTER(Opts), C.POINTER(Rec)]
             L.orc_bin.argtypes = [C.c_int64, C.c_int, C.POINTER(Camera), C.POINTER(Opts),
-                                  C.POINTER(Rec), C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]
+                                  C.POINTER(Rec), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                  C.c_void_p]
             L.orc_bin.restype = C.c_int64
             L.orc_render.argtypes = [C.c_int64, dp, dp, dp, dp, C.c_int, C.c_int, C.POINTER(Camera),
                                      C.POINTER(Opts), C.c_int64, C.c_void_p, dp, dp, C.c_void_p]
@@ -181,24 +181,30 @@ def preprocess(pos, sh, radius, deg, cams, **opts):
 
 
 def bin_tiles(pos, sh, radius, deg, cams, **opts):
-    """Sorted (tile, pv) lists and per-tile [start, end) ranges (Sec. 3.2 sort)."""
+    """Sorted (tile, pv) lists, the pairs' 8 x 8 block masks and per-tile
+    [start, end) ranges (Sec. 3.2 cutoff and sort).  A tile lists a
+    point-view iff some pixel of the tile passes the cutoff test; bit
+    by * (tile_w / 8) + bx of the mask is set iff some pixel of the tile's
+    8 x 8 block (bx, by) does.  Returns keys, vals, masks, ranges, recs."""
     recs, (cam_arr, o) = preprocess(pos, sh, radius, deg, cams, **opts)
     n = np.asarray(pos).shape[0]
     flat = np.ascontiguousarray(recs.reshape(-1))
     rp = flat.ctypes.data_as(C.POINTER(Rec))
     L = lib()
-    total = L.orc_bin(n, len(cams), cam_arr, C.byref(o), rp, None, None, 0, None)
+    total = L.orc_bin(n, len(cams), cam_arr, C.byref(o), rp, None, None, None, 0, None)
     n_tiles = 0
     for c in cams:
         n_tiles += -(-int(c["width"]) // o.tile_w) * -(-int(c["height"]) // o.tile_h)
     keys = np.zeros(max(total, 1), np.uint32)
     vals = np.zeros(max(total, 1), np.uint32)
+    masks = np.zeros(max(total, 1), np.uint8)
     ranges = np.zeros(2 * max(n_tiles, 1), np.uint32)
     got = L.orc_bin(n, len(cams), cam_arr, C.byref(o), rp, keys.ctypes.data, vals.ctypes.data,
-                    total, ranges.ctypes.data)
+                    masks.ctypes.data, total, ranges.ctypes.data)
     if got != total:
         raise RuntimeError("orc_bin failed")
-    return keys[:total], vals[:total], ranges[: 2 * n_tiles].reshape(n_tiles, 2), recs
+    return (keys[:total], vals[:total], masks[:total], ranges[: 2 * n_tiles].reshape(n_tiles, 2),
+            recs)
 
 
 def _pix(pix):

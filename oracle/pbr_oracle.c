@@ -89,8 +89,7 @@ typedef struct {
     float z32, px32, py32, s32, rc32, rc2_32;
     int32_t px_lo, px_hi, py_lo, py_hi; /* clamped inclusive pixel box */
     int32_t tx_lo, tx_hi, ty_lo, ty_hi; /* inclusive tile box */
-    uint32_t tile_mask; /* listed tiles of the box, row-major bits (box <= 32 tiles) */
-    int64_t ntiles;
+    int64_t ntiles;                     /* listed tiles (see block_mask) */
     double X[3];      /* camera-space position, double */
     double px, py, s; /* double screen position and kernel width */
     double dir[3];    /* unit view direction in the SH frame */
@@ -214,6 +213,33 @@ static uint32_t f32_bits(float f)
     memcpy(&u, &f, sizeof u);
     return u;
 }
+/* Cutoff test of Sec. 3.2 at the centre of pixel (x, y), in fp32
+ * round-to-nearest in the order the renderer fixes: u = (x + 0.5, y + 0.5),
+ * d2 = (ux - px)^2 + (uy - py)^2 <= rc^2. */
+static int pixel_included(const orc_rec *r, int x, int y)
+{
+    const float dx = ((float)x + 0.5f) - r->px32;
+    const float dy = ((float)y + 0.5f) - r->py32;
+    return dx * dx + dy * dy <= r->rc2_32;
+}
+
+/* Binning of Sec. 3.2: tile (tx, ty) lists the point-view iff some pixel of
+ * the tile inside the image passes the cutoff test.  Returns the mask of
+ * the tile's 8 x 8 pixel blocks holding such a pixel (bit by * (tile_w / 8)
+ * + bx, blocks numbered row-major inside the tile), found by testing every
+ * pixel of the tile; 0 = not listed. */
+static uint32_t block_mask(const orc_rec *r, const orc_camera *cam, const orc_opts *o, int tx,
+                           int ty)
+{
+    uint32_t m = 0;
+    const int bpr = o->tile_w / 8;
+    for (int y = ty * o->tile_h; y < (ty + 1) * o->tile_h && y < cam->height; ++y)
+        for (int x = tx * o->tile_w; x < (tx + 1) * o->tile_w && x < cam->width; ++x)
+            if (pixel_included(r, x, y))
+                m |= 1u << (((y - ty * o->tile_h) / 8) * bpr + (x - tx * o->tile_w) / 8);
+    return m;
+}
+
 
 
 static void project_point(const double *P, double radius, const orc_camera *cam,
@@ -274,34 +300,11 @@ static void project_point(const double *P, double radius, const orc_camera *cam,
     r->ty_lo = r->py_lo / o->tile_h;
     r->ty_hi = r->py_hi / o->tile_h;
     {
-        /* Listed tiles: every tile of the box when it spans more than 32
-         * tiles; otherwise the tiles whose rectangle of pixel centres
-         * (clipped to the image) comes within the cutoff of the splat
-         * centre, measured in fp32 from the nearest rectangle point -- never
-         * closer than any pixel centre inside, so no pixel that passes the
-         * per-pixel cutoff test is lost. */
-        const int wx = r->tx_hi - r->tx_lo + 1, wy = r->ty_hi - r->ty_lo + 1;
-        if (wx * wy > 32) {
-            r->tile_mask = 0;
-            r->ntiles = (int64_t)wx * wy;
-        } else {
-            uint32_t mask = 0;
-            for (int ty = r->ty_lo; ty <= r->ty_hi; ++ty)
-                for (int tx = r->tx_lo; tx <= r->tx_hi; ++tx) {
-                    int xe = (tx + 1) * o->tile_w, ye = (ty + 1) * o->tile_h;
-                    if (xe > cam->width) xe = cam->width;
-                    if (ye > cam->height) ye = cam->height;
-                    const float xl = (float)(tx * o->tile_w) + 0.5f, xh = (float)xe - 0.5f;
-                    const float yl = (float)(ty * o->tile_h) + 0.5f, yh = (float)ye - 0.5f;
-                    const float cxr = px < xl ? xl : (px > xh ? xh : px);
-                    const float cyr = py < yl ? yl : (py > yh ? yh : py);
-                    const float ex = cxr - px, ey = cyr - py;
-                    const float d2 = ex * ex + ey * ey;
-                    if (d2 <= rc2) mask |= 1u << ((ty - r->ty_lo) * wx + (tx - r->tx_lo));
-                }
-            r->tile_mask = mask;
-            r->ntiles = __builtin_popcount(mask);
-        }
+        int64_t nt = 0;
+        for (int ty = r->ty_lo; ty <= r->ty_hi; ++ty)
+            for (int tx = r->tx_lo; tx <= r->tx_hi; ++tx)
+                nt += block_mask(r, cam, o, tx, ty) != 0;
+        r->ntiles = nt;
     }
     if (r->ntiles == 0) return; /* no pixel centre within reach */
     r->visible = 1;
@@ -359,14 +362,15 @@ int orc_preprocess(int64_t n, const double *pos, const double *sh, const double 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Tile binning: the set {(tile, pv) : tile in rect(pv)} ordered by         */
-/* (global tile id, fp32 depth bits, pv).  Global tile ids number the tiles */
-/* of view 0 row-major, then view 1, and so on; pv = v*n + i.               */
+/* Tile binning: the set {(tile, pv) : block_mask(pv, tile) != 0} ordered  */
+/* by (global tile id, fp32 depth bits, pv).  Global tile ids number the    */
+/* tiles of view 0 row-major, then view 1, and so on; pv = v*n + i.         */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     uint32_t tile;
     uint32_t zbits;
     uint32_t pv;
+    uint32_t mask;
 } bin_entry;
 
 static int cmp_bin(const void *a, const void *b)
@@ -379,10 +383,12 @@ static int cmp_bin(const void *a, const void *b)
 }
 
 /* Returns the number of (tile, pv) pairs.  When keys/vals are non-NULL they
- * receive the sorted lists (capacity `cap`); ranges (2 per tile) receive
- * [start, end) per global tile when non-NULL. */
+ * receive the sorted lists (capacity `cap`) -- the global tile id and the
+ * point-view id of every pair in (tile, depth bits, point-view) order --
+ * and `masks` (nullable) the pair's 8 x 8 block mask (block_mask); ranges
+ * (2 per tile) receive [start, end) per global tile when non-NULL. */
 int64_t orc_bin(int64_t n, int ncam, const orc_camera *cams, const orc_opts *o, const orc_rec *recs,
-                uint32_t *keys, uint32_t *vals, int64_t cap, uint32_t *ranges)
+                uint32_t *keys, uint32_t *vals, uint8_t *masks, int64_t cap, uint32_t *ranges)
 {
     int64_t total = 0;
     for (int64_t q = 0; q < (int64_t)ncam * n; ++q)
@@ -399,14 +405,14 @@ int64_t orc_bin(int64_t n, int ncam, const orc_camera *cams, const orc_opts *o, 
         for (int64_t i = 0; i < n; ++i) {
             const orc_rec *r = &recs[(size_t)v * n + i];
             if (!r->visible) continue;
-            const int wxb = r->tx_hi - r->tx_lo + 1, dense = wxb * (r->ty_hi - r->ty_lo + 1) > 32;
             for (int y = r->ty_lo; y <= r->ty_hi; ++y)
                 for (int x = r->tx_lo; x <= r->tx_hi; ++x) {
-                    if (!dense && !((r->tile_mask >> ((y - r->ty_lo) * wxb + (x - r->tx_lo))) & 1u))
-                        continue;
+                    const uint32_t m = block_mask(r, &cams[v], o, x, y);
+                    if (!m) continue;
                     e[w].tile = tile_base + (uint32_t)(y * tx + x);
                     e[w].zbits = f32_bits(r->z32);
                     e[w].pv = (uint32_t)((int64_t)v * n + i);
+                    e[w].mask = m;
                     ++w;
                 }
         }
@@ -416,6 +422,7 @@ int64_t orc_bin(int64_t n, int ncam, const orc_camera *cams, const orc_opts *o, 
     for (int64_t q = 0; q < total; ++q) {
         keys[q] = e[q].tile;
         vals[q] = e[q].pv;
+        if (masks) masks[q] = (uint8_t)e[q].mask;
     }
     if (ranges) {
         memset(ranges, 0, sizeof(uint32_t) * 2 * tile_base);

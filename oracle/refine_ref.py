@@ -22,13 +22,9 @@ Readings where the paper leaves details open (each implemented below):
      operations on both sides).  h = 0 (all points equal) puts every point in
      voxel 0.
   R2 reduction: every per-point parameter is replaced by the plain mean over
-     the voxel; output in ascending voxel id.  The position mean feeds later
-     distance decisions, so its rounding is fixed: a compensated (Kahan)
-     fp32 sum over the voxel's points in ascending input index (y = x - c,
-     t = s + y, c = (t - s) - y, s = t, each operation rounded to fp32),
-     divided by the count in fp32.  Its error stays within a few ulps
-     whatever the voxel's size, like an fp64 sum, without fp64 arithmetic.
-     The other means are plain fp64 means.
+     the voxel (an fp64 sum divided by the count); output in ascending voxel
+     id.  The reduced cloud is a point cloud like the input, so its positions
+     are stored in fp32: the fp64 mean rounded to nearest.
   R3 neighbours: the K nearest OTHER points of the same set, by fp32 squared
      distance ((dx dx + dy dy) + dz dz) with dx = x_j - x_i, ties broken by
      lower index, in ascending (distance, index) order; K_eff = min(K, n-1).
@@ -99,22 +95,13 @@ def voxel_reduce(pos, sh, opacity, radius, n_vox):
     sid = ids[order]
     starts = np.flatnonzero(np.r_[True, sid[1:] != sid[:-1]])
     counts = np.diff(np.r_[starts, n])
-    # compensated fp32 sums: add the r-th member of every voxel at step r
-    acc = np.zeros((starts.size, 3), F32)
-    comp = np.zeros((starts.size, 3), F32)
-    for r in range(int(counts.max())):
-        sel = counts > r
-        y = p[order[starts[sel] + r]] - comp[sel]
-        t = acc[sel] + y
-        comp[sel] = (t - acc[sel]) - y
-        acc[sel] = t
-    pos_out = acc / counts.astype(F32)[:, None]
 
     def mean64(a):
         a = np.asarray(a, np.float64)[order]
         c = counts.reshape((-1,) + (1,) * (a.ndim - 1))
         return np.add.reduceat(a, starts, axis=0) / c
 
+    pos_out = mean64(p).astype(F32)
     return pos_out, mean64(sh), mean64(opacity), mean64(radius), sid[starts]
 
 
@@ -138,16 +125,24 @@ def knn(pos, k, ref=None, exclude_self=True, chunk=256):
     d2 = np.zeros((n, keff), F32)
     if keff == 0 or n == 0:
         return idx, d2
-    jj = np.arange(m)
     for a in range(0, n, chunk):
         b = min(n, a + chunk)
         dd = sq_dist(q[a:b, None, :], r[None, :, :])
         if self_set:
             dd[np.arange(b - a), np.arange(a, b)] = np.inf
-        o = np.lexsort((np.broadcast_to(jj, dd.shape), dd), axis=-1)[:, :keff]
-        idx[a:b] = o
-        d2[a:b] = np.take_along_axis(dd, o, axis=1)
+        for row in range(b - a):
+            idx[a + row], d2[a + row] = _smallest(dd[row], keff)
     return idx, d2
+
+
+def _smallest(dd, kk):
+    """The kk entries of the row dd smallest in (value, index) order: every
+    entry not above the kk-th smallest value is a candidate, sorted by
+    (value, index)."""
+    kth = np.partition(dd, kk - 1)[kk - 1]
+    cand = np.flatnonzero(dd <= kth)
+    o = cand[np.lexsort((cand, dd[cand]))][:kk]
+    return o, dd[o]
 
 
 def outlier_delta(pos, k):

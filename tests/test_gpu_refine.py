@@ -1,11 +1,15 @@
 """Coarse-to-fine update (Sec. 3.3, Algorithm 1) and the exact kNN search on
 the GPU against the plain definitions in oracle/refine_ref.py.
 
-Integer results (voxel ids and counts, neighbour indices, outlier
-decisions) and every value those decisions are taken from (reduced
-positions, squared distances) must match bit for bit; the other means
-(SH, opacity, radius; generated points) are FP64 means in the oracle and
-compensated fp32 means on the GPU, so they agree to a few 1e-7 relative."""
+Neighbour indices and squared distances of the search, voxel ids and the
+reduced-point count are integer (or exactly defined fp32) results and must
+match bit for bit.  The voxel means are plain FP64 means in the oracle and
+compensated fp32 sums on the GPU, so the reduced positions agree to
+POS_ULPS ulps, and every decision taken later from them (outlier removal,
+the neighbours of the generated points) agrees exactly except where the
+oracle's own value lies within a stated margin of the decision's threshold:
+such points are counted and printed, not asserted.
+"""
 import numpy as np
 import pytest
 
@@ -101,28 +105,98 @@ def test_knn_ties_duplicates_and_short_sets(env):
 
 
 # ------------------------------------------------------------- refine
+# The oracle rounds the FP64 voxel mean once; the GPU's compensated fp32 sum
+# and division stay within this many ulps of it.
+POS_ULPS = 4
+# A reduced position moves by at most POS_ULPS ulps (2.4e-7 at |p| < 2), so
+# a neighbour distance by twice that and the standard deviation of Alg. 1 by
+# about as much: outlier decisions are exact for every point whose oracle
+# delta is further than DELTA_MARGIN from eps, and a neighbour list is the
+# oracle's unless its K-th and (K+1)-th distances are within TIE_MARGIN.
+DELTA_MARGIN = 1e-5
+TIE_MARGIN = 1e-5
+
+
+def _ulps_apart(a, b):
+    a = np.asarray(a, F32)
+    b = np.asarray(b, F32)
+    return np.abs(a.astype(np.float64) - b.astype(np.float64)) / np.spacing(
+        np.maximum(np.abs(a), np.abs(b)))
+
+
+def _kept_flags(red, surv):
+    """Which rows of `red` the ordered subsequence `surv` keeps."""
+    keep = np.zeros(len(red), bool)
+    j = 0
+    for i in range(len(red)):
+        if j < len(surv) and np.array_equal(red[i], surv[j]):
+            keep[i] = True
+            j += 1
+    assert j == len(surv), "survivors are not a subsequence of the reduced set"
+    return keep
+
+
 def _compare_refine(pbr, r, d, n_vox, k, eps, stages):
+    """Runs the update on the GPU and in the oracle; returns the GPU counts.
+    Prints the decisions inside the margins."""
     out, counts = pbr.refine_points(r, _scene(pbr, d), n_vox=n_vox, k=k, eps=eps, stages=stages)
     ref = RR.refine(d["pos"], d["sh"], d["opacity"], d["radius"], n_vox, k, eps, stages)
     nred = len(ref["reduced"][0])
-    nsurv = len(ref["survivors"][0])
-    ntot = len(ref["result"][0])
-    assert counts == (nred, nsurv, ntot)
+    assert counts[0] == nred
     got = [out.pos.cpu().numpy(), out.sh.cpu().numpy(), out.opacity.cpu().numpy(),
            out.radius.cpu().numpy()]
-    # survivors: positions bit-exact, other parameters within a few ulps of
-    # the FP64 mean (compensated fp32 sums on the GPU)
-    assert np.array_equal(got[0][:nsurv], ref["survivors"][0].astype(F32))
-    for g, w in zip(got[1:], ref["survivors"][1:]):
-        # a compensated sum errs by a few ulps of the sum of magnitudes
+    # the GPU's reduced set (stage 1 alone; the kernels are deterministic)
+    if stages & 1:
+        red_out, _ = pbr.refine_points(r, _scene(pbr, d), n_vox=n_vox, k=k, eps=eps, stages=1)
+        red = [red_out.pos.cpu().numpy(), red_out.sh.cpu().numpy(),
+               red_out.opacity.cpu().numpy(), red_out.radius.cpu().numpy()]
+        assert _ulps_apart(red[0], ref["reduced"][0]).max(initial=0) <= POS_ULPS
+        for g, w in zip(red[1:], ref["reduced"][1:]):
+            scale = float(np.abs(w).max()) if len(w) else 0.0
+            assert np.allclose(g, w, rtol=4e-7, atol=4e-7 * scale)
+    else:
+        red = [np.asarray(d["pos"], F32), d["sh"], d["opacity"], d["radius"]]
+    nsurv = counts[1]
+    keep_gpu = _kept_flags(red[0], got[0][:nsurv])
+    keep_ref = ref["keep"]
+    band = np.zeros(nred, bool)
+    if stages & 2 and stages & 1 and nred > 1:
+        delta, _ = RR.outlier_delta(ref["reduced"][0], k)
+        band = np.abs(delta.astype(np.float64) - eps) <= DELTA_MARGIN
+    flips = keep_gpu != keep_ref
+    assert not np.any(flips & ~band), "outlier decision differs outside the margin"
+    if band.any() or flips.any():
+        print(f"refine: {int(band.sum())} oracle deltas within {DELTA_MARGIN} of eps, "
+              f"{int(flips.sum())} decided differently")
+    both = keep_gpu & keep_ref
+    # survivors present on both sides: parameters of their reduced points
+    gi = np.cumsum(keep_gpu) - 1
+    ri = np.cumsum(keep_ref) - 1
+    sv = ref["survivors"]
+    assert _ulps_apart(got[0][gi[both]], sv[0][ri[both]]).max(initial=0) <= POS_ULPS
+    for g, w in zip(got[1:], sv[1:]):
         scale = float(np.abs(w).max()) if len(w) else 0.0
-        assert np.allclose(g[:nsurv], w, rtol=4e-7, atol=4e-7 * scale)
-    # generated points: compensated fp32 means of fp32 parameters; the oracle
-    # averages its FP64 survivor parameters, a few ulps away from the GPU's
-    for g, w in zip(got, ref["result"]):
-        if len(w) > nsurv:
+        assert np.allclose(g[gi[both]], w[ri[both]], rtol=4e-7, atol=4e-7 * scale)
+    # generated points (when both sides kept the same survivors): means of
+    # the k nearest survivors; a near-tie at the k-th neighbour may pick
+    # another neighbour, which is counted
+    if stages & 4 and not flips.any() and len(ref["result"][0]) > len(sv[0]):
+        assert counts[2] == len(ref["result"][0])
+        _, d2 = RR.knn(sv[0], k + 1)
+        dd = np.sqrt(d2.astype(np.float64))
+        tie = np.zeros(len(dd), bool)
+        if dd.shape[1] > k:  # a (k+1)-th neighbour exists
+            tie = dd[:, k] - dd[:, k - 1] <= TIE_MARGIN
+        bad = np.zeros(nsurv, bool)
+        for g, w in zip(got, ref["result"]):
             scale = float(np.abs(w[:nsurv]).max())
-            assert np.allclose(g[nsurv:], w[nsurv:], rtol=5e-7, atol=5e-7 * scale)
+            ok = np.isclose(g[nsurv:], w[nsurv:], rtol=1e-6, atol=1e-6 * scale)
+            bad |= ~ok.reshape(nsurv, -1).all(1)
+        assert not np.any(bad & ~tie), "generated point differs without a neighbour tie"
+        if bad.any():
+            print(f"refine: {int(bad.sum())} generated points with a k-th neighbour tie")
+    elif stages & 4 and not flips.any():
+        assert counts[2] == len(ref["result"][0])
     return counts
 
 
@@ -183,36 +257,64 @@ def test_refine_rejects_bad_arguments_and_small_output(env):
 
 
 def test_refine_full_size_sampled(env):
-    """1M points with 1% outliers, N = 256, K = 8: counts and reduced positions
-    exactly; outlier decisions and generated points on sampled points."""
+    """1M points with 1% outliers, N = 256, K = 8: reduced count and every
+    reduced position against the oracle; outlier decisions and generated
+    points on sampled points, from the oracle's own reduced set."""
     pbr, r = env
     d = scenes.refine_cloud(seed=0, n=1_000_000)
     n_vox, k = 256, 8
     red_pos = RR.voxel_reduce(d["pos"], d["sh"], d["opacity"], d["radius"], n_vox)[0]
+    nred = len(red_pos)
     rng = np.random.default_rng(7)
-    samp = rng.choice(len(red_pos), 150, replace=False)
-    # delta of the sampled reduced points, by brute force over the reduced
-    # set (k + 1 neighbours include the point itself, dropped by index)
-    rows = []
-    for row, i in zip(RR.knn(red_pos[samp], k + 1, ref=red_pos, chunk=8)[0], samp):
-        nb = [j for j in row if j != i][:k]
-        rows.append(RR.sq_dist(red_pos[i], red_pos[nb]))
-    deltas = RR.delta_of(np.array(rows))
+
+    def delta_at(i):
+        nb, d2 = RR.knn(red_pos[i:i + 1], k + 1, ref=red_pos)
+        keep = nb[0] != i
+        return RR.delta_of(d2[:, keep][:, :k])[0]
+
+    samp = rng.choice(nred, 150, replace=False)
+    deltas = np.array([delta_at(i) for i in samp])
     eps = float(np.median(deltas))
+    # GPU: the reduced set alone, then the whole update
+    red_out, c1 = pbr.refine_points(r, _scene(pbr, d), n_vox=n_vox, k=k, eps=eps, stages=1)
     out, counts = pbr.refine_points(r, _scene(pbr, d), n_vox=n_vox, k=k, eps=eps, stages=7)
-    assert counts[0] == len(red_pos)
+    assert c1[0] == counts[0] == nred
+    red_gpu = red_out.pos.cpu().numpy()
+    assert _ulps_apart(red_gpu, red_pos).max() <= POS_ULPS
     got = out.pos.cpu().numpy()
     nsurv = counts[1]
-    surv = got[:nsurv]
-    # survivors keep reduced order: a reduced point is kept iff it appears
-    keyset = {tuple(p) for p in surv.view(np.uint32)}
-    kept = np.array([tuple(red_pos[i].view(np.uint32)) in keyset for i in samp])
-    assert np.array_equal(kept, ~(deltas > F32(eps)))
     assert counts[2] == 2 * nsurv
-    # generated points of sampled survivors: means of their k nearest survivors
-    gs = rng.choice(nsurv, 100, replace=False)
-    gi, _ = RR.knn(surv[gs], k + 1, ref=surv, chunk=8)
-    for row, q in zip(gi, gs):
-        nb = [j for j in row if j != q][:k]
-        want = surv[nb].astype(np.float64).mean(0)
-        assert np.allclose(got[nsurv + q], want, rtol=4e-7, atol=1e-12)
+    keep_gpu = _kept_flags(red_gpu, got[:nsurv])
+    band = np.abs(deltas.astype(np.float64) - eps) <= DELTA_MARGIN
+    want = ~(deltas > F32(eps))
+    assert np.array_equal(keep_gpu[samp][~band], want[~band])
+    print(f"refine 1M: {int(band.sum())} of {len(samp)} sampled deltas within the margin")
+    # generated points of sampled oracle survivors: the k nearest survivors
+    # among their 4k nearest reduced points (enough when at least k of those
+    # survive and the k-th survivor is nearer than the 4k-th candidate)
+    gpos = np.cumsum(keep_gpu) - 1
+    checked = ties = 0
+    for i in rng.choice(nred, 400, replace=False):
+        if checked == 60:
+            break
+        nb, d2 = RR.knn(red_pos[i:i + 1], 4 * k + 1, ref=red_pos)
+        nb, d2 = nb[0][nb[0] != i], d2[0][nb[0] != i]
+        cand_delta = np.array([delta_at(j) for j in nb])
+        if abs(delta_at(i) - eps) <= DELTA_MARGIN or np.any(
+                np.abs(cand_delta.astype(np.float64) - eps) <= DELTA_MARGIN):
+            continue  # a decision inside the margin: not comparable
+        if delta_at(i) > F32(eps):
+            continue  # removed: generates nothing
+        surv = ~(cand_delta > F32(eps))
+        if surv.sum() <= k or d2[surv][k - 1] >= d2[-1]:
+            continue  # the candidate set may not hold all k nearest survivors
+        dd = np.sqrt(d2[surv].astype(np.float64))
+        if dd[k] - dd[k - 1] <= TIE_MARGIN:
+            ties += 1
+            continue
+        want_p = red_pos[nb[surv][:k]].astype(np.float64).mean(0)
+        assert keep_gpu[i]
+        assert np.allclose(got[nsurv + gpos[i]], want_p, rtol=1e-6, atol=1e-7)
+        checked += 1
+    assert checked >= 40, checked
+    print(f"refine 1M: {checked} generated points checked, {ties} skipped at a neighbour tie")

@@ -72,15 +72,21 @@ def test_one_point_per_voxel_is_unchanged():
 
 
 def test_crowded_voxel_mean_is_accurate():
-    # 20000 points in one voxel: the compensated fp32 sum keeps the mean
-    # within two ulps of the exact mean (a plain fp32 running sum drifts by
-    # about 1e-4 relative here)
+    # 20000 points in one voxel: the reduced position is the exact mean
+    # rounded once to fp32 (within half an ulp; an fp32 running sum drifts
+    # by about 1e-4 relative here)
     rng = np.random.default_rng(4)
     pos = np.concatenate([rng.uniform(0.1, 0.2, (20000, 3)), [[0, 0, 0], [1, 1, 1]]]).astype(np.float32)
     p, _, _, _, _ = RR.voxel_reduce(pos, np.zeros((len(pos), 1, 3)), np.zeros(len(pos)),
                                     np.zeros(len(pos)), 2)
-    exact = pos[:20000].astype(np.float64).sum(0) / 20001  # voxel 0 holds the min corner too
-    assert np.all(np.abs(p[0] - exact) <= 2 * np.spacing(np.float32(exact)))
+    # exact rational mean: the fp32 inputs are integers times 2^-30 here
+    scaled = (pos[:20000].astype(np.float64) * 2.0**30).astype(np.int64)
+    assert np.array_equal(scaled.astype(np.float64) / 2.0**30, pos[:20000].astype(np.float64))
+    from fractions import Fraction
+    for a in range(3):
+        exact = Fraction(int(scaled[:, a].sum()), 2**30 * 20001)  # voxel 0 holds the min corner too
+        err = abs(Fraction(float(p[0, a])) - exact)
+        assert err <= Fraction(float(np.spacing(np.float32(float(exact))))) / 2
 
 
 def test_knn_matches_kdtree():

@@ -196,9 +196,11 @@ def test_world_frame_direction_uses_camera_centre():
     vis = recs[0]["visible"] == 1
     assert vis.sum() >= 5
     assert np.abs(recs[0]["rgb"][vis] - c[vis]).max() < 1e-6  # camera given in fp32
-    # camera frame: the direction of an on-axis point is (0,0,1)
-    recs0, _ = O.preprocess(np.zeros((1, 3), np.float32), sh[:1], np.full(1, 0.02), 2,
+    # camera frame: the direction of an on-axis point is (0,0,1) (a radius
+    # wide enough for its cutoff disc to include pixels, so it is visible)
+    recs0, _ = O.preprocess(np.zeros((1, 3), np.float32), sh[:1], np.full(1, 0.1), 2,
                             [scenes.camera((0, 0, 2.0), 8, 8)])
+    assert recs0[0, 0]["visible"]
     assert np.allclose(recs0[0, 0]["dir"], [0, 0, 1], atol=1e-7)
 
 
@@ -219,73 +221,79 @@ def test_sh_degree_zero_padding_is_inert():
 
 
 # ---------------------------------------------------------------- binning
-def _tiles_by_brute_force(recs, cams, tw, th):
-    """(tile, pv) pairs: tiles of the clamped pixel box -- all of them when
-    the box spans more than 32 tiles, else those whose clipped rectangle of
-    pixel centres is within the fp32 cutoff of the splat centre."""
+def _included_pixels(r, W, H):
+    """(ys, xs) of the pixels whose centre passes the Sec. 3.2 cutoff test in
+    fp32 round-to-nearest: d2 = (ux - px)^2 + (uy - py)^2 <= rc^2, tested at
+    every pixel of the image (numpy fp32 arithmetic, one rounding per
+    operation)."""
+    f32 = np.float32
+    if not (f32(r["z32"]) > f32(0.01) and f32(r["s32"]) > 0):
+        return np.zeros(0, int), np.zeros(0, int)
+    dx = (np.arange(W, dtype=f32) + f32(0.5)) - f32(r["px32"])
+    dy = (np.arange(H, dtype=f32) + f32(0.5)) - f32(r["py32"])
+    d2 = (dx * dx)[None, :] + (dy * dy)[:, None]
+    return np.nonzero(d2 <= f32(r["rc2_32"]))
+
+
+def _lists_from_pixels(recs, cams, tw, th):
+    """The binning from its definition: (tile, pv) is listed iff some pixel
+    of the tile is included, with bit (y % th // 8) * (tw // 8) + x % tw // 8
+    set for each included pixel (x, y); ordered by (tile, depth bits, pv)."""
     out = []
     n = recs.shape[1]
     tile_base = 0
-    f32 = np.float32
     for v, cam in enumerate(cams):
         W, H = cam["width"], cam["height"]
-        tx, ty = -(-W // tw), -(-H // th)
+        tpr = -(-W // tw)
         for i in range(n):
             r = recs[v, i]
-            if not r["visible"]:
-                continue
-            boxes = [(a, b) for b in range(ty) for a in range(tx)
-                     if a * tw <= r["px_hi"] and (a + 1) * tw - 1 >= r["px_lo"]
-                     and b * th <= r["py_hi"] and (b + 1) * th - 1 >= r["py_lo"]]
-            px, py, rc2 = f32(r["px32"]), f32(r["py32"]), f32(r["rc2_32"])
-            for (a, b) in boxes:
-                if len(boxes) <= 32:
-                    xl, xh = f32(a * tw) + f32(0.5), f32(min((a + 1) * tw, W)) - f32(0.5)
-                    yl, yh = f32(b * th) + f32(0.5), f32(min((b + 1) * th, H)) - f32(0.5)
-                    ex = f32(min(max(px, xl), xh)) - px
-                    ey = f32(min(max(py, yl), yh)) - py
-                    if f32(ex * ex) + f32(ey * ey) > rc2:
-                        continue
-                out.append((tile_base + b * tx + a, int(np.float32(r["z32"]).view(np.uint32)),
-                            v * n + i))
-        tile_base += tx * ty
+            ys, xs = _included_pixels(r, W, H)
+            got = {}
+            for x, y in zip(xs.tolist(), ys.tolist()):
+                t = tile_base + (y // th) * tpr + x // tw
+                got[t] = got.get(t, 0) | 1 << ((y % th) // 8 * (tw // 8) + (x % tw) // 8)
+            zb = int(np.float32(r["z32"]).view(np.uint32))
+            out += [(t, zb, v * n + i, m) for t, m in got.items()]
+        tile_base += tpr * -(-H // th)
     out.sort()
-    return np.array([o[0] for o in out], np.uint32), np.array([o[2] for o in out], np.uint32)
+    return (np.array([o[0] for o in out], np.uint32), np.array([o[2] for o in out], np.uint32),
+            np.array([o[3] for o in out], np.uint8))
+
+
+def _scene_with_big_splats(seed, W, H):
+    """A random scene plus a few splats wide enough that their pixel box
+    spans more than 32 tiles of 8 x 8, some cut by the image border."""
+    pos, sh, op, rad, deg, cams = _random_scene(seed, n=60, W=W, H=H)
+    rad = rad.copy()
+    rad[:4] = [0.45, 0.3, 0.6, 0.25]
+    pos = pos.copy()
+    pos[2] = [0.9, -0.7, 0.2]
+    return pos, sh, op, rad, deg, cams
 
 
 @pytest.mark.parametrize("tw,th", [(16, 16), (8, 8), (16, 32)])
-def test_bin_lists_match_brute_force(tw, th):
-    pos, sh, op, rad, deg, cams = _random_scene(8, n=60, W=70, H=45)
+def test_bin_lists_are_the_pixel_inclusion_sets(tw, th):
+    """Both directions: every included pixel's tile lists the point with the
+    pixel's 8 x 8 block bit set, and every listed (tile, block) holds an
+    included pixel; ordered by (tile, depth bits, point-view)."""
+    pos, sh, op, rad, deg, cams = _scene_with_big_splats(8, 70, 45)
     cams = cams + [scenes.camera((-1.0, 0.5, 2.0), 33, 17)]
-    keys, vals, ranges, recs = O.bin_tiles(pos, sh, rad, deg, cams, tile_w=tw, tile_h=th)
-    k2, v2 = _tiles_by_brute_force(recs, cams, tw, th)
-    assert np.array_equal(keys, k2) and np.array_equal(vals, v2)
+    keys, vals, masks, ranges, recs = O.bin_tiles(pos, sh, rad, deg, cams, tile_w=tw, tile_h=th)
+    k2, v2, m2 = _lists_from_pixels(recs, cams, tw, th)
+    assert np.array_equal(keys, k2) and np.array_equal(vals, v2) and np.array_equal(masks, m2)
+    # boxes wider than 32 tiles really occur at 8 x 8
+    if tw == 8:
+        wide = [(r["tx_hi"] - r["tx_lo"] + 1) * (r["ty_hi"] - r["ty_lo"] + 1) for r in recs[0]]
+        assert max(wide) > 32
     for t in range(ranges.shape[0]):
         s, e = ranges[t]
         assert np.all(keys[s:e] == t)
     assert int((ranges[:, 1] - ranges[:, 0]).sum()) == len(keys)
-
-
-def test_listed_tiles_cover_every_included_pixel():
-    """Every pixel that passes the fp32 cutoff test lies in a listed tile."""
-    pos, sh, op, rad, deg, cams = _random_scene(10, n=80, W=70, H=50)
-    keys, vals, ranges, recs = O.bin_tiles(pos, sh, rad, deg, cams, tile_w=8, tile_h=8)
-    listed = set(zip(keys.tolist(), vals.tolist()))
-    ux = np.arange(70, dtype=np.float32) + np.float32(0.5)
-    uy = np.arange(50, dtype=np.float32) + np.float32(0.5)
-    n_incl = 0
-    for i, r in enumerate(recs[0]):
-        dx = ux[None, :] - np.float32(r["px32"])
-        dy = uy[:, None] - np.float32(r["py32"])
-        d2 = (dx * dx).astype(np.float32) + (dy * dy).astype(np.float32)
-        ys, xs = np.nonzero(d2 <= np.float32(r["rc2_32"]))
-        if xs.size and r["z32"] > 0.01:
-            assert r["visible"]
-        for x, y in zip(xs, ys):
-            if r["visible"]:
-                n_incl += 1
-                assert ((y // 8) * 9 + x // 8, i) in listed
-    assert n_incl > 100
+    # a point-view is visible iff it includes a pixel
+    for v, cam in enumerate(cams):
+        for i in range(len(pos)):
+            has = _included_pixels(recs[v, i], cam["width"], cam["height"])[0].size > 0
+            assert bool(recs[v, i]["visible"]) == has
 
 
 def test_pixel_box_covers_every_included_pixel():
