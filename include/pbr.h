@@ -124,7 +124,12 @@ typedef struct {
     int64_t n_tiles;       /* tiles over all views */
     int64_t n_pixels;      /* pixels over all views */
     /* device pointers into the state (valid until pbr_state_free) */
-    const uint32_t *tile_keys;  /* [n_pairs] global tile id, sorted */
+    const uint32_t *tile_keys;  /* [n_pairs] sorted keys: global tile id << B | block mask,
+                                   B = (tile_w / 8) (tile_h / 8) when that exceeds 1, else 0;
+                                   bit by (tile_w / 8) + bx of the mask is set iff a pixel of
+                                   the tile's 8 x 8 block (bx, by) passes the point-view's
+                                   cutoff test.  A tile lists a point-view iff one of its
+                                   pixels does (Sec. 3.2 cutoff). */
     const uint32_t *tile_vals;  /* [n_pairs] point-view id, (tile, depth, id) order */
     const uint32_t *ranges;     /* [n_tiles][2] start, end into the lists */
     const float *records;       /* [n_point_views][8] px, py, rc^2, q', o, r, g, b */
@@ -172,7 +177,8 @@ int pbr_state_free(pbr_ctx *ctx, pbr_state *state);
 int pbr_state_info(pbr_state *state, pbr_state_info_t *info);
 
 /* Copies one array of a forward state into host memory (inspection and
- * tests).  which: 0 tile keys, 1 tile values (point-view ids), 2 ranges,
+ * tests).  which: 0 tile keys (as in pbr_state_info_t), 1 tile values
+ * (point-view ids), 2 ranges,
  * 3 records, 4 tile counts, 5 T_final, 6 n_contrib.  Copies
  * min(cap_bytes, size) bytes; *size_bytes receives the full size.
  * Synchronises the state's stream. */
@@ -366,7 +372,13 @@ int pbr_stage_times(pbr_ctx *ctx, double *ms, long long *calls, int n);
  *   - Every call shares the array and it keeps the last call's contents
  *     (counters and tile ranges are cleared on each call); calls whose GPU
  *     work overlaps -- other streams or other host threads -- race on it.
- *   - Synchronises the stream once, like pbr_render_forward. */
+ *   - Compositing is always one block per tile (opts->persistent is
+ *     ignored: the persistent schedule's tile order would need more
+ *     scratch); opts->batch_depth is honoured.
+ *   - Synchronises the stream twice: once to size the lists, like
+ *     pbr_render_forward, and once at the end to read the kernels' status
+ *     word; a set status (e.g. more pairs than counted) returns
+ *     PBR_ERR_DEVICE_STATUS. */
 int pbr_render_forward_noalloc(const pbr_points *scenes, int32_t n_scenes,
                                const int32_t *scene_of_view, const pbr_camera *cams,
                                int32_t n_cams, const pbr_render_opts *opts, float *out_rgb,

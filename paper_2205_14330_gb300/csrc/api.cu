@@ -281,7 +281,9 @@ int pbr::build_layout(const pbr_points *scenes, int32_t n_scenes, const int32_t 
         pix += (int64_t)c.width * c.height;
         pv += scenes[sov[v]].n;
     }
-    if (pv >= (int64_t)UINT32_MAX || tiles >= UINT32_MAX)
+    // tile ids and their 8 x 8 block masks share the 32-bit pair keys
+    const int sb = block_bits(o->tile_w, o->tile_h);
+    if (pv >= (int64_t)UINT32_MAX || tiles >= (UINT32_MAX >> sb))
         return set_error(PBR_ERR_CAPACITY, "batch too large: %lld point-views, %llu tiles",
                          (long long)pv, (unsigned long long)tiles);
     L.n_pv = pv;
@@ -434,7 +436,8 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
     {
         StageScope t(c, STG_TILE_SORT, s);
         radix_sort_pairs(tk, tv, pk2, pv2, n_pairs_dev, (int64_t)n_pairs,
-                         key_bits_for(L.n_tiles), temp, s);
+                         key_bits_for(L.n_tiles), temp, s, 0, 0xffffffffu, false,
+                         block_bits(o.tile_w, o.tile_h));
     }
     if (tk != st->tile_keys) { // result landed in the alternate buffers: swap ownership
         for (void *&p : tmp.ptrs) {
@@ -449,7 +452,7 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
         StageScope t(c, STG_RANGES, s);
         PBR_CUDA(cudaMemsetAsync(st->ranges, 0, sizeof(uint2) * L.n_tiles, s));
         launch_tile_ranges(st->tile_keys, n_pairs_dev, (int64_t)n_pairs, st->ranges, L.n_tiles,
-                           s);
+                           block_bits(o.tile_w, o.tile_h), s);
     }
     // 6. composite (optionally as one persistent launch over a longest-first tile order)
     const bool persist = st->opts.persistent && st->batch_depth == 0;
@@ -460,7 +463,8 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
     {
         StageScope t(c, STG_RASTER_FWD, s);
         if (persist) launch_tile_order(b, st->ranges, L.n_tiles, st->tile_order, st->work, s);
-        launch_raster_fwd(b, o, st->batch_depth, st->ranges, st->tile_vals, st->rec, out_rgb,
+        launch_raster_fwd(b, o, st->batch_depth, st->ranges, st->tile_keys, st->tile_vals,
+                          st->rec, out_rgb,
                           st->T_final, st->n_contrib,
                           st->opts.no_pair_stats ? nullptr : st->counters + 2, s, st->tile_order,
                           st->work);
@@ -513,7 +517,8 @@ extern "C" int pbr_render_backward(pbr_ctx *c, pbr_state *st, const float *grad_
         StageScope t(c, STG_RASTER_BWD, s);
         PBR_CUDA(cudaMemsetAsync(g2d, 0, sizeof(float4) * 2 * L.n_pv, s));
         if (st->work) reset_work_counters(st->work, s);
-        launch_raster_bwd(b, st->dopts, st->batch_depth, st->ranges, st->tile_vals, st->rec,
+        launch_raster_bwd(b, st->dopts, st->batch_depth, st->ranges, st->tile_keys,
+                          st->tile_vals, st->rec,
                           st->T_final, st->n_contrib, grad_rgb, g2d,
                           st->opts.no_pair_stats ? nullptr : st->counters + 2, s,
                           st->tile_order, st->work);

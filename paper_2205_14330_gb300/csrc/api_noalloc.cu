@@ -155,11 +155,21 @@ extern "C" int pbr_render_forward_noalloc(const pbr_points *scenes, int32_t n_sc
                       (int64_t)n_pairs, status, temp, s);
     int key_bits = 1;
     while (key_bits < 32 && ((L.n_tiles - 1) >> key_bits)) ++key_bits;
-    radix_sort_pairs(tk, tv, pk2, pv2, n_pairs_dev, (int64_t)n_pairs, key_bits, temp, s);
+    const int sb = block_bits(o.tile_w, o.tile_h);
+    radix_sort_pairs(tk, tv, pk2, pv2, n_pairs_dev, (int64_t)n_pairs, key_bits, temp, s, 0,
+                     0xffffffffu, false, sb);
     PBR_CUDA(cudaMemsetAsync(ranges, 0, sizeof(uint2) * L.n_tiles, s));
-    launch_tile_ranges(tk, n_pairs_dev, (int64_t)n_pairs, ranges, L.n_tiles, s);
-    launch_raster_fwd(b, o, opts->batch_depth, ranges, tv, rec, out_rgb, T_final, n_contrib,
+    launch_tile_ranges(tk, n_pairs_dev, (int64_t)n_pairs, ranges, L.n_tiles, sb, s);
+    launch_raster_fwd(b, o, opts->batch_depth, ranges, tk, tv, rec, out_rgb, T_final, n_contrib,
                       nullptr, s);
     PBR_CUDA(cudaGetLastError());
+    // the kernels' status word (pair overflow, inconsistent counts): one
+    // read-back into a host variable after the pass
+    uint32_t dev_status = 0;
+    PBR_CUDA(cudaMemcpyAsync(&dev_status, status, sizeof dev_status, cudaMemcpyDeviceToHost, s));
+    PBR_CUDA(cudaStreamSynchronize(s));
+    if (dev_status)
+        return set_error(PBR_ERR_DEVICE_STATUS,
+                         "pbr_render_forward_noalloc: device status 0x%x", dev_status);
     return PBR_OK;
 }

@@ -188,14 +188,16 @@ void enqueue_forward(pbr_graph *g, cudaStream_t s)
                       g->cap_pairs, status, g->temp, s);
     int key_bits = bit_width(L.n_tiles > 0 ? L.n_tiles - 1 : 0);
     if (key_bits < 1) key_bits = 1;
-    radix_sort_pairs(tk, tv, tk2, tv2, n_pairs_dev, g->cap_pairs, key_bits, g->temp, s);
+    const int sb = block_bits(o.tile_w, o.tile_h);
+    radix_sort_pairs(tk, tv, tk2, tv2, n_pairs_dev, g->cap_pairs, key_bits, g->temp, s, 0,
+                     0xffffffffu, false, sb);
     g->keys_final = tk;
     g->vals_final = tv;
     cudaMemsetAsync(g->ranges, 0, sizeof(uint2) * L.n_tiles, s);
-    launch_tile_ranges(tk, n_pairs_dev, g->cap_pairs, g->ranges, L.n_tiles, s);
+    launch_tile_ranges(tk, n_pairs_dev, g->cap_pairs, g->ranges, L.n_tiles, sb, s);
     const bool persist = g->opts.persistent && g->opts.batch_depth == 0;
     if (persist) launch_tile_order(b, g->ranges, L.n_tiles, g->order, g->work, s);
-    launch_raster_fwd(b, o, g->opts.batch_depth, g->ranges, tv, g->rec, g->out_rgb, g->T_final,
+    launch_raster_fwd(b, o, g->opts.batch_depth, g->ranges, tk, tv, g->rec, g->out_rgb, g->T_final,
                       g->n_contrib, nullptr, s, persist ? g->order : nullptr, g->work);
 }
 
@@ -206,7 +208,8 @@ void enqueue_backward(pbr_graph *g, const float *grad_rgb, cudaStream_t s)
     cudaMemsetAsync(g->g2d, 0, sizeof(float4) * 2 * L.n_pv, s);
     const bool persist = g->opts.persistent && g->opts.batch_depth == 0;
     if (persist) reset_work_counters(g->work, s);
-    launch_raster_bwd(b, g->dopts, g->opts.batch_depth, g->ranges, g->vals_final, g->rec,
+    launch_raster_bwd(b, g->dopts, g->opts.batch_depth, g->ranges, g->keys_final, g->vals_final,
+                      g->rec,
                       g->T_final, g->n_contrib, grad_rgb, g->g2d, nullptr, s,
                       persist ? g->order : nullptr, g->work);
     launch_preprocess_bwd(b, g->dopts, g->g2d, g->grad_pos, g->grad_sh, g->grad_opacity, s);

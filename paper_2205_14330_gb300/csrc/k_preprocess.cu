@@ -16,9 +16,9 @@
 //   s  = (fx r) / X2  (radius_mode 0)  or  (r min(W,H)) 0.5  (mode 1)
 //   rc = cutoff_k s,  rc2 = rc rc
 //   pixel box: [floor(px - rc) - 1, ceil(px + rc)] clamped to the image;
-//   listed tiles of the box: all when it spans more than 32 tiles, else
-//   those whose rectangle of pixel centres (clipped to the image) is within
-//   rc of (px, py) by the same fp32 test.
+//   listed tiles: those holding a pixel (inside the image) whose centre
+//   passes the per-pixel test d2 <= rc2 -- decided at the tile's pixel
+//   centre nearest the splat centre (rect_reached).
 //
 // preprocess_bwd (Sec. 3.3): one thread per point; per view it chains the
 // screen-space adjoint {dpx, dpy, dq, do, dr, dg, db} (q = 1/s^2) through the
@@ -114,50 +114,47 @@ __device__ void pre_fwd_point(const Batch &b, const DevOpts &o, const DevScene &
                 sg = __fmul_rn(__fmul_rn(r, (float)min(V.W, V.H)), 0.5f);
             const float rc = __fmul_rn(o.cutoff_k, sg);
             const float rc2 = __fmul_rn(rc, rc);
-            float xlo = __fsub_rn(floorf(__fsub_rn(px, rc)), 1.0f);
-            float xhi = ceilf(__fadd_rn(px, rc));
-            float ylo = __fsub_rn(floorf(__fsub_rn(py, rc)), 1.0f);
-            float yhi = ceilf(__fadd_rn(py, rc));
-            const float W1 = (float)(V.W - 1), H1 = (float)(V.H - 1);
-            if (sg > 0.0f && xhi >= 0.0f && xlo <= W1 && yhi >= 0.0f && ylo <= H1) do {
-                xlo = xlo < 0.0f ? 0.0f : xlo;
-                ylo = ylo < 0.0f ? 0.0f : ylo;
-                xhi = xhi > W1 ? W1 : xhi;
-                yhi = yhi > H1 ? H1 : yhi;
+            int x0, x1, y0, y1;
+            if (sg > 0.0f && pixel_box(px, py, rc, V.W, V.H, x0, x1, y0, y1)) do {
                 // tile sizes are powers of two and the box is non-negative
-                const int tx0 = (int)xlo >> tws, tx1 = (int)xhi >> tws;
-                const int ty0 = (int)ylo >> ths, ty1 = (int)yhi >> ths;
+                const int tx0 = x0 >> tws, tx1 = x1 >> tws;
+                const int ty0 = y0 >> ths, ty1 = y1 >> ths;
                 const int wx = tx1 - tx0 + 1, wy = ty1 - ty0 + 1;
-                // listed tiles: all of a box wider than 32 tiles, else those
-                // whose clipped rectangle of pixel centres is within the
-                // cutoff (fp32 distance from the nearest rectangle point)
-                uint32_t mask = 0;
-                if (wx * wy > 32) {
-                    nt = (uint32_t)(wx * wy);
-                } else {
-                    // tile bounds are integer-valued floats (exact), stepped
-                    // by the tile size; the last tile is clipped to the image
-                    const float tw = (float)o.tile_w, th = (float)o.tile_h;
-                    const float Wm = (float)V.W - 0.5f, Hm = (float)V.H - 0.5f;
-                    const float xl0 = (float)(tx0 * o.tile_w) + 0.5f;
-                    float yl = (float)(ty0 * o.tile_h) + 0.5f;
+                // listed tiles: those holding a pixel that passes the cutoff
+                // test (rect_reached on the tile's pixels inside the image)
+                uint32_t w = 0;
+                if (wx * wy <= 32) {
                     int bit = 0;
-                    for (int ty = ty0; ty <= ty1; ++ty, yl += th) {
-                        const float yh = fminf(yl + (th - 1.0f), Hm);
-                        const float cyr = py < yl ? yl : (py > yh ? yh : py);
-                        const float ey = __fsub_rn(cyr, py);
-                        const float ey2 = __fmul_rn(ey, ey);
-                        float xl = xl0;
-                        for (int tx = tx0; tx <= tx1; ++tx, xl += tw, ++bit) {
-                            const float xh = fminf(xl + (tw - 1.0f), Wm);
-                            const float cxr = px < xl ? xl : (px > xh ? xh : px);
-                            const float ex = __fsub_rn(cxr, px);
-                            if (__fadd_rn(__fmul_rn(ex, ex), ey2) <= rc2) mask |= 1u << bit;
+                    for (int ty = ty0; ty <= ty1; ++ty) {
+                        const int ya = ty << ths, yb = min(ya + o.tile_h, V.H) - 1;
+                        for (int tx = tx0; tx <= tx1; ++tx, ++bit) {
+                            const int xa = tx << tws, xb = min(xa + o.tile_w, V.W) - 1;
+                            if (rect_reached(px, py, rc2, xa, xb, ya, yb)) w |= 1u << bit;
                         }
                     }
-                    nt = (uint32_t)__popc(mask);
-                    if (nt == 0) break; // no pixel centre within reach: not visible
+                    nt = (uint32_t)__popc(w);
+                } else {
+                    // wide box: per tile row, the listed tiles are one run
+                    // around the column nearest the splat centre (the nearest
+                    // pixel's distance grows away from it); walk it out
+                    const int xn = (int)fminf(fmaxf(floorf(px), (float)x0), (float)x1);
+                    const int tc = xn >> tws;
+                    for (int ty = ty0; ty <= ty1; ++ty) {
+                        const int ya = ty << ths, yb = min(ya + o.tile_h, V.H) - 1;
+                        auto reached = [&](int tx) {
+                            const int xa = tx << tws;
+                            return rect_reached(px, py, rc2, xa, min(xa + o.tile_w, V.W) - 1, ya,
+                                                yb);
+                        };
+                        if (!reached(tc)) continue;
+                        int lo = tc, hi = tc;
+                        while (lo > tx0 && reached(lo - 1)) --lo;
+                        while (hi < tx1 && reached(hi + 1)) ++hi;
+                        nt += (uint32_t)(hi - lo + 1);
+                    }
+                    w = nt;
                 }
+                if (nt == 0) break; // no pixel within reach: not visible
                 // view direction (Eq. 3) and colour (Eq. 4)
                 const float inv = rsqrtf(X[0] * X[0] + X[1] * X[1] + z * z);
                 float dx = X[0] * inv, dy = X[1] * inv, dz = z * inv;
@@ -182,8 +179,8 @@ __device__ void pre_fwd_point(const Batch &b, const DevOpts &o, const DevScene &
                 rec[2 * pv] = make_float4(px, py, rc2, qp);
                 rec[2 * pv + 1] = make_float4(op, c0, c1, c2);
                 zbits[pv] = __float_as_uint(z);
-                rect[pv] = make_uint4((uint32_t)tx0 | ((uint32_t)ty0 << 16),
-                                      (uint32_t)tx1 | ((uint32_t)ty1 << 16), mask, 0u);
+                rect[pv] = make_uint4(__float_as_uint(px), __float_as_uint(py),
+                                      __float_as_uint(rc), w);
                 ++vis_cnt;
                 pair_cnt += nt;
                 zlo = min(zlo, __float_as_uint(z));

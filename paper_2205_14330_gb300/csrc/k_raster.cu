@@ -223,6 +223,89 @@ __device__ __forceinline__ void warp_add_terms(const float v[8], int lane, float
     }
 }
 
+// ------------------------------------------------------ block-mask queues
+// The pair keys carry the mask of the 8 x 8 pixel blocks of the tile that
+// hold a pixel including the point (pair key = tile << B | mask), so a warp
+// working on one block takes from its tile's list only the entries with its
+// block's bit: the queue below holds their list positions (relative to the
+// tile's first entry) and point-view ids, in compositing order, and the
+// compositing loops consume it 32 entries at a time.  bit == 0 (tiles of
+// one block) takes every entry.
+struct WarpQueue {
+    uint32_t pos[64]; // list positions, relative to the tile's first entry
+    uint32_t pv[64];  // point-view ids
+};
+
+// Front to back: scans the list from position p (absolute, < e) 32 entries
+// at a time, appending the entries with `bit`, until the queue holds 32 or
+// the list ends.  Warp-uniform.
+__device__ __forceinline__ void queue_fill_front(const uint32_t *__restrict__ keys,
+                                                 const uint32_t *__restrict__ pv_list, uint32_t s,
+                                                 uint32_t e, uint32_t bit, uint32_t &p, int &qn,
+                                                 WarpQueue &q, int lane)
+{
+    const uint32_t lt = lanemask_lt_r();
+    while (qn < 32 && p < e) {
+        const uint32_t i = p + lane;
+        bool take = i < e;
+        if (take && bit) take = (__ldg(keys + i) & bit) != 0;
+        const uint32_t m = __ballot_sync(0xffffffffu, take);
+        if (take) {
+            const int slot = qn + __popc(m & lt);
+            q.pos[slot] = i - s;
+            q.pv[slot] = __ldg(pv_list + i);
+        }
+        qn += __popc(m);
+        p += 32;
+    }
+    __syncwarp();
+}
+
+// Back to front: scans the relative positions [0, c + 32) downwards from
+// the aligned chunk c (c < 0: nothing left), entries below `lim` only, 32
+// at a time, appending the entries with `bit` in descending position order.
+__device__ __forceinline__ void queue_fill_back(const uint32_t *__restrict__ keys,
+                                                const uint32_t *__restrict__ pv_list, uint32_t s,
+                                                uint32_t lim, uint32_t bit, int64_t &c, int &qn,
+                                                WarpQueue &q, int lane)
+{
+    const uint32_t gt = ~(lanemask_lt_r() | (1u << lane));
+    while (qn < 32 && c >= 0) {
+        const uint32_t i = (uint32_t)c + lane;
+        bool take = i < lim;
+        if (take && bit) take = (__ldg(keys + s + i) & bit) != 0;
+        const uint32_t m = __ballot_sync(0xffffffffu, take);
+        if (take) {
+            const int slot = qn + __popc(m & gt);
+            q.pos[slot] = i;
+            q.pv[slot] = __ldg(pv_list + s + i);
+        }
+        qn += __popc(m);
+        c -= 32;
+    }
+    __syncwarp();
+}
+
+// Takes the next min(qn, 32) queued entries: lane l < the count receives
+// entry l (its relative position and point-view); the rest move to the
+// front.  Returns the count.
+__device__ __forceinline__ int queue_take(WarpQueue &q, int &qn, int lane, uint32_t &pos,
+                                          uint32_t &pv)
+{
+    const int take = qn < 32 ? qn : 32;
+    if (lane < take) {
+        pos = q.pos[lane];
+        pv = q.pv[lane];
+    }
+    if (lane + 32 < qn) { // each lane moves the entry 32 places behind its own
+        q.pos[lane] = q.pos[lane + 32];
+        q.pv[lane] = q.pv[lane + 32];
+    }
+    qn -= take;
+    __syncwarp();
+    return take;
+}
+
 // One composited point, front to back.  Returns true when the pixel stops.
 __device__ __forceinline__ bool pixel_blend(float d2, const float4 a, const float4 c,
                                             const DevOpts &o, float &T, float &C0, float &C1,
@@ -340,10 +423,10 @@ __device__ __forceinline__ void add_stats(unsigned long long *stats, uint32_t a,
 }
 
 // ======================================================= warp-streamed
-// One warp composites sub-block `sub` of tile `tile`.
-// Warp-streamed items.  Each step takes 32 list entries (one per lane),
-// culls them against the warp's rectangle with one ballot and stages the
-// hits in the warp's shared buffer; then
+// One warp composites its 8 x 4 sub-block of a tile.  Each step takes 32
+// entries of the warp's 8 x 8 block from its queue, culls them against the
+// warp's rectangle with one ballot and stages the hits in the warp's shared
+// buffer; then
 //   phase 1 (warp-uniform): for every hit, every lane runs its exact fp32
 //            cutoff test and records the hit in its own bitmask;
 //   phase 2 (per lane): each lane walks only its own included entries.
@@ -351,173 +434,183 @@ __device__ __forceinline__ void add_stats(unsigned long long *stats, uint32_t a,
 // g: the lane's pixel and the warp's rectangle; [s, e): the tile's list.
 template <bool STATS = true>
 __device__ __forceinline__ void fwd_stream_item(const PixelGeom &g, uint32_t s, uint32_t e,
-                                                const DevOpts &o, int lane,
+                                                uint32_t bit, const DevOpts &o, int lane,
+                                                const uint32_t *__restrict__ keys,
                                                 const uint32_t *__restrict__ pv_list,
                                                 const float4 *__restrict__ rec,
                                                 float *__restrict__ out_rgb,
                                                 float *__restrict__ T_final,
                                                 uint32_t *__restrict__ n_contrib,
                                                 uint32_t &examined_acc, uint32_t &composited_acc,
-                                                float4 *wbuf)
+                                                float4 *wbuf, uint32_t *wpos, WarpQueue &q)
 {
     float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     uint32_t cnt = 0, last = 0, examined = 0;
     bool done = !g.inside;
-    if (!__all_sync(0xffffffffu, done)) {
-        // software pipeline: point ids two steps ahead, records one step
-        // ahead, so the id -> record load chain is hidden behind a step
-        uint32_t pv_n = 0, pv_nn = 0;
-        float4 a_n = make_float4(0.f, 0.f, -1.f, 0.f);
-        if (s + lane < e) {
-            pv_n = __ldg(pv_list + s + lane);
-            a_n = __ldg(rec + 2 * (size_t)pv_n);
+    uint32_t p = s;
+    int qn = 0;
+    while (!__all_sync(0xffffffffu, done)) {
+        queue_fill_front(keys, pv_list, s, e, bit, p, qn, q, lane);
+        if (qn == 0) break;
+        uint32_t rel = 0, pv = 0;
+        const int take = queue_take(q, qn, lane, rel, pv);
+        const bool valid = lane < take;
+        float4 a = make_float4(0.f, 0.f, -1.f, 0.f);
+        if (valid) a = __ldg(rec + 2 * (size_t)pv);
+        // every lane takes part in the reductions, whatever its entry
+        const PixelGeom ar = active_rect(g, !done);
+        const bool hit = valid && disc_meets_rect(a, ar);
+        const bool covers = hit && disc_covers_rect(a, ar);
+        uint32_t m = __ballot_sync(0xffffffffu, hit);
+        // entries whose disc holds every active pixel need no per-pixel test
+        uint32_t mine = __ballot_sync(0xffffffffu, covers);
+        if (hit) {
+            wbuf[lane] = a;
+            wbuf[32 + lane] = __ldg(rec + 2 * (size_t)pv + 1);
+            wpos[lane] = rel;
         }
-        if (s + 32 + lane < e) pv_nn = __ldg(pv_list + s + 32 + lane);
-        for (uint32_t c = s; c < e; c += 32) {
-            const uint32_t pv = pv_n;
-            const float4 a = a_n;
-            const bool valid = c + lane < e;
-            if (c + 32 + lane < e) {
-                pv_n = pv_nn;
-                a_n = __ldg(rec + 2 * (size_t)pv_n);
-            }
-            if (c + 64 + lane < e) pv_nn = __ldg(pv_list + c + 64 + lane);
-            // every lane takes part in the reductions, whatever its entry
-            const PixelGeom ar = active_rect(g, !done);
-            const bool hit = valid && disc_meets_rect(a, ar);
-            const bool covers = hit && disc_covers_rect(a, ar);
-            uint32_t m = __ballot_sync(0xffffffffu, hit);
-            // entries whose disc holds every active pixel need no per-pixel test
-            uint32_t mine = __ballot_sync(0xffffffffu, covers);
-            if (hit) {
-                wbuf[lane] = a;
-                wbuf[32 + lane] = __ldg(rec + 2 * (size_t)pv + 1);
-            }
-            __syncwarp();
-            if (STATS && !done) examined += (uint32_t)__popc(m);
-            m &= ~mine;
-            while (m) {
-                const int j = __ffs(m) - 1;
-                m &= m - 1;
-                const float4 aj = wbuf[j];
-                float dx, dy;
-                if (pixel_d2(g.ux, g.uy, aj.x, aj.y, dx, dy) <= aj.z) mine |= 1u << j;
-            }
-            if (done) mine = 0;
-            while (mine) {
-                const int j = __ffs(mine) - 1;
-                mine &= mine - 1;
-                const float4 aj = wbuf[j];
-                float dx, dy;
-                const float d2 = pixel_d2(g.ux, g.uy, aj.x, aj.y, dx, dy);
-                last = c + j - s + 1;
-                if (pixel_blend(d2, aj, wbuf[32 + j], o, T, C0, C1, C2, cnt)) {
-                    done = true;
-                    break;
-                }
-            }
-            __syncwarp(); // chunk consumed before the buffer is refilled
-            if (__all_sync(0xffffffffu, done)) break;
+        __syncwarp();
+        if (STATS && !done) examined += (uint32_t)__popc(m);
+        m &= ~mine;
+        while (m) {
+            const int j = __ffs(m) - 1;
+            m &= m - 1;
+            const float4 aj = wbuf[j];
+            float dx, dy;
+            if (pixel_d2(g.ux, g.uy, aj.x, aj.y, dx, dy) <= aj.z) mine |= 1u << j;
         }
+        if (done) mine = 0;
+        while (mine) {
+            const int j = __ffs(mine) - 1;
+            mine &= mine - 1;
+            const float4 aj = wbuf[j];
+            float dx, dy;
+            const float d2 = pixel_d2(g.ux, g.uy, aj.x, aj.y, dx, dy);
+            last = wpos[j] + 1;
+            if (pixel_blend(d2, aj, wbuf[32 + j], o, T, C0, C1, C2, cnt)) {
+                done = true;
+                break;
+            }
+        }
+        __syncwarp(); // chunk consumed before the buffers are refilled
     }
     examined_acc += examined;
     composited_acc += cnt;
     write_pixel(g, o, T, C0, C1, C2, last, out_rgb, T_final, n_contrib);
 }
 
-// Forward of one 8 x 8 sub-block by one warp, for the persistent schedule:
+// ------------------------------------------------- packed two-pixel math
+// A lane of the 8 x 8-pixel warps owns two pixels of one column, rows 4
+// apart (A above B); their per-point arithmetic runs in packed fp32x2
+// operations (.x pixel A, .y pixel B), one instruction for both pixels.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Squared fp32 distances from the lane's two pixel centres (ux, uy.x) and
+// (ux, uy.y) to the splat centre, with the rounding of pixel_d2: dx =
+// ux - px (shared), dy = uy - py, d2 = dx dx + dy dy, each operation rounded
+// to nearest (no contraction).
+__device__ __forceinline__ float2 pair_d2(float ux, float2 uy, float px, float py, float &dx,
+                                          float2 &dy)
+{
+    dx = __fsub_rn(ux, px);
+    dy = add2(uy, f2(-py));
+    const float dx2 = __fmul_rn(dx, dx);
+    return add2(f2(dx2), mul2(dy, dy));
+}
+
+// Forward of one 8 x 8 block by one warp, for the persistent schedule:
 // lane l owns the pixels (l & 7, l >> 3) and (l & 7, 4 + (l >> 3)), gA and
-// gB.  The per-chunk staging, culling and ballots serve 64 pixels; every
-// lane tests each hit at both of its pixels, then walks the first pixel's
-// included entries and the second's.  Each pixel's blend sequence is the
-// one-pixel walk's.
+// gB.  The warp takes the tile list's entries with its block's bit (`bit`)
+// 32 at a time from its queue; the per-chunk staging, culling and ballots
+// serve 64 pixels; every lane tests each hit at both of its pixels, then
+// walks the first pixel's included entries and the second's.  Each pixel's
+// blend sequence is the one-pixel walk's.
 template <bool STATS>
 __device__ __forceinline__ void fwd_pair_item(const PixelGeom &gA, const PixelGeom &gB,
-                                              uint32_t s, uint32_t e, const DevOpts &o, int lane,
+                                              uint32_t s, uint32_t e, uint32_t bit,
+                                              const DevOpts &o, int lane,
+                                              const uint32_t *__restrict__ keys,
                                               const uint32_t *__restrict__ pv_list,
                                               const float4 *__restrict__ rec,
                                               float *__restrict__ out_rgb,
                                               float *__restrict__ T_final,
                                               uint32_t *__restrict__ n_contrib,
                                               uint32_t &examined_acc, uint32_t &composited_acc,
-                                              float4 *wbuf)
+                                              float4 *wbuf, uint32_t *wpos, WarpQueue &q)
 {
     float TA = 1.0f, A0 = 0.f, A1 = 0.f, A2 = 0.f;
     float TB = 1.0f, B0 = 0.f, B1 = 0.f, B2 = 0.f;
     uint32_t cntA = 0, cntB = 0, lastA = 0, lastB = 0, examined = 0;
     bool doneA = !gA.inside, doneB = !gB.inside;
-    if (!__all_sync(0xffffffffu, doneA && doneB)) {
-        // software pipeline as in fwd_stream_item
-        uint32_t pv_n = 0, pv_nn = 0;
-        float4 a_n = make_float4(0.f, 0.f, -1.f, 0.f);
-        if (s + lane < e) {
-            pv_n = __ldg(pv_list + s + lane);
-            a_n = __ldg(rec + 2 * (size_t)pv_n);
+    const PixelGeom g2[2] = {gA, gB};
+    const float2 uy2 = make_float2(gA.uy, gB.uy);
+    uint32_t p = s;
+    int qn = 0;
+    while (!__all_sync(0xffffffffu, doneA && doneB)) {
+        queue_fill_front(keys, pv_list, s, e, bit, p, qn, q, lane);
+        if (qn == 0) break;
+        uint32_t rel = 0, pv = 0;
+        const int take = queue_take(q, qn, lane, rel, pv);
+        const bool valid = lane < take;
+        float4 a = make_float4(0.f, 0.f, -1.f, 0.f);
+        if (valid) a = __ldg(rec + 2 * (size_t)pv);
+        // every lane takes part in the reductions, whatever its entry
+        const bool act[2] = {!doneA, !doneB};
+        const PixelGeom ar = active_rect_rows<2>(g2, act);
+        const bool hit = valid && disc_meets_rect(a, ar);
+        const bool covers = hit && disc_covers_rect(a, ar);
+        uint32_t m = __ballot_sync(0xffffffffu, hit);
+        // entries whose disc holds every active pixel need no per-pixel test
+        const uint32_t full = __ballot_sync(0xffffffffu, covers);
+        if (hit) {
+            wbuf[lane] = a;
+            wbuf[32 + lane] = __ldg(rec + 2 * (size_t)pv + 1);
+            wpos[lane] = rel;
         }
-        if (s + 32 + lane < e) pv_nn = __ldg(pv_list + s + 32 + lane);
-        const PixelGeom g2[2] = {gA, gB};
-        for (uint32_t c = s; c < e; c += 32) {
-            const uint32_t pv = pv_n;
-            const float4 a = a_n;
-            const bool valid = c + lane < e;
-            if (c + 32 + lane < e) {
-                pv_n = pv_nn;
-                a_n = __ldg(rec + 2 * (size_t)pv_n);
-            }
-            if (c + 64 + lane < e) pv_nn = __ldg(pv_list + c + 64 + lane);
-            // every lane takes part in the reductions, whatever its entry
-            const bool act[2] = {!doneA, !doneB};
-            const PixelGeom ar = active_rect_rows<2>(g2, act);
-            const bool hit = valid && disc_meets_rect(a, ar);
-            const bool covers = hit && disc_covers_rect(a, ar);
-            uint32_t m = __ballot_sync(0xffffffffu, hit);
-            // entries whose disc holds every active pixel need no per-pixel test
-            const uint32_t full = __ballot_sync(0xffffffffu, covers);
-            if (hit) {
-                wbuf[lane] = a;
-                wbuf[32 + lane] = __ldg(rec + 2 * (size_t)pv + 1);
-            }
-            __syncwarp();
-            if (STATS) examined += (uint32_t)__popc(m) * ((uint32_t)!doneA + (uint32_t)!doneB);
-            uint32_t mA = full, mB = full;
-            m &= ~full;
-            while (m) {
-                const int j = __ffs(m) - 1;
-                m &= m - 1;
-                const float4 aj = wbuf[j];
-                float dx, dy;
-                if (pixel_d2(gA.ux, gA.uy, aj.x, aj.y, dx, dy) <= aj.z) mA |= 1u << j;
-                if (pixel_d2(gB.ux, gB.uy, aj.x, aj.y, dx, dy) <= aj.z) mB |= 1u << j;
-            }
-            if (doneA) mA = 0;
-            if (doneB) mB = 0;
-            while (mA) {
-                const int j = __ffs(mA) - 1;
-                mA &= mA - 1;
-                const float4 aj = wbuf[j];
-                float dx, dy;
-                const float d2 = pixel_d2(gA.ux, gA.uy, aj.x, aj.y, dx, dy);
-                lastA = c + j - s + 1;
-                if (pixel_blend(d2, aj, wbuf[32 + j], o, TA, A0, A1, A2, cntA)) {
-                    doneA = true;
-                    break;
-                }
-            }
-            while (mB) {
-                const int j = __ffs(mB) - 1;
-                mB &= mB - 1;
-                const float4 aj = wbuf[j];
-                float dx, dy;
-                const float d2 = pixel_d2(gB.ux, gB.uy, aj.x, aj.y, dx, dy);
-                lastB = c + j - s + 1;
-                if (pixel_blend(d2, aj, wbuf[32 + j], o, TB, B0, B1, B2, cntB)) {
-                    doneB = true;
-                    break;
-                }
-            }
-            __syncwarp(); // chunk consumed before the buffer is refilled
-            if (__all_sync(0xffffffffu, doneA && doneB)) break;
+        __syncwarp();
+        if (STATS) examined += (uint32_t)__popc(m) * ((uint32_t)!doneA + (uint32_t)!doneB);
+        uint32_t mA = full, mB = full;
+        m &= ~full;
+        while (m) {
+            const int j = __ffs(m) - 1;
+            m &= m - 1;
+            const float4 aj = wbuf[j];
+            float dx;
+            float2 dy;
+            const float2 d2 = pair_d2(gA.ux, uy2, aj.x, aj.y, dx, dy);
+            if (d2.x <= aj.z) mA |= 1u << j;
+            if (d2.y <= aj.z) mB |= 1u << j;
         }
+        if (doneA) mA = 0;
+        if (doneB) mB = 0;
+        while (mA) {
+            const int j = __ffs(mA) - 1;
+            mA &= mA - 1;
+            const float4 aj = wbuf[j];
+            float dx, dy;
+            const float d2 = pixel_d2(gA.ux, gA.uy, aj.x, aj.y, dx, dy);
+            lastA = wpos[j] + 1;
+            if (pixel_blend(d2, aj, wbuf[32 + j], o, TA, A0, A1, A2, cntA)) {
+                doneA = true;
+                break;
+            }
+        }
+        while (mB) {
+            const int j = __ffs(mB) - 1;
+            mB &= mB - 1;
+            const float4 aj = wbuf[j];
+            float dx, dy;
+            const float d2 = pixel_d2(gB.ux, gB.uy, aj.x, aj.y, dx, dy);
+            lastB = wpos[j] + 1;
+            if (pixel_blend(d2, aj, wbuf[32 + j], o, TB, B0, B1, B2, cntB)) {
+                doneB = true;
+                break;
+            }
+        }
+        __syncwarp(); // chunk consumed before the buffers are refilled
     }
     examined_acc += examined;
     composited_acc += cntA + cntB;
@@ -536,22 +629,25 @@ constexpr int BWD_DIRECT_MAX = 16;
 // of both their pixels: fastest at 24 (11.1 ms; 11.4 ms at 16, 11.9 ms at
 // 8, 15.8 ms with atomics only) on the same workload.
 constexpr int BWD_PAIR_DIRECT_MAX = 24;
-// Pixel rows (of 8 x 4) per warp in the persistent backward: 2 (8 x 8
-// pixels).  4 rows examine 41% more pairs through the coarser cull and
-// need 80 registers; the step's backward then takes 13.4 ms against 11.1.
-constexpr int BWD_ROWS = 2;
+// The persistent backward runs 8 x 8-pixel warps (two pixels per lane):
+// 8 x 16 (four pixels per lane) examined 41% more pairs through the coarser
+// cull and needed 80 registers (13.4 ms against 11.1).
 
-// One warp back-propagates through sub-block `sub` of tile `tile`.
+// One warp back-propagates through sub-block `sub` of tile `tile`, taking
+// the entries of its 8 x 8 block (`bit`) from its queue, back to front.
 template <int TW, int TH>
 __device__ __forceinline__ void bwd_stream_item(const Batch &b, const DevOpts &o, uint32_t tile,
-                                                int sub, int lane, const uint2 *__restrict__ ranges,
+                                                int sub, uint32_t bit, int lane,
+                                                const uint2 *__restrict__ ranges,
+                                                const uint32_t *__restrict__ keys,
                                                 const uint32_t *__restrict__ pv_list,
                                                 const float4 *__restrict__ rec,
                                                 const float *__restrict__ T_final,
                                                 const uint32_t *__restrict__ n_contrib,
                                                 const float *__restrict__ grad_rgb,
                                                 float *__restrict__ g2d, uint32_t &examined,
-                                                uint32_t &used, float4 *wbuf, uint32_t *wpv)
+                                                uint32_t &used, float4 *wbuf, uint32_t *wpv,
+                                                uint32_t *wpos, WarpQueue &q)
 {
     const PixelGeom g = pixel_geom<TW, TH>(b, tile, sub, lane);
     const uint32_t s = ranges[tile].x;
@@ -569,39 +665,34 @@ __device__ __forceinline__ void bwd_stream_item(const Batch &b, const DevOpts &o
     const uint32_t wmax = __reduce_max_sync(0xffffffffu, L);
     if (wmax == 0) return;
     int64_t c = (int64_t)((wmax - 1) & ~31u);
-    uint32_t pv_n = 0, pv_nn = 0;
-    float4 a_n = make_float4(0.f, 0.f, -1.f, 0.f);
-    if ((uint32_t)c + lane < wmax) {
-        pv_n = __ldg(pv_list + s + (uint32_t)c + lane);
-        a_n = __ldg(rec + 2 * (size_t)pv_n);
-    }
-    if (c >= 32) pv_nn = __ldg(pv_list + s + (uint32_t)c - 32 + lane);
-    for (; c >= 0; c -= 32) {
-        const uint32_t pv = pv_n;
-        const float4 a = a_n;
-        const bool valid = (uint32_t)c + lane < wmax;
-        if (c >= 32) {
-            pv_n = pv_nn;
-            a_n = __ldg(rec + 2 * (size_t)pv_n);
-        }
-        if (c >= 64) pv_nn = __ldg(pv_list + s + (uint32_t)c - 64 + lane);
-        // lanes whose composited list reaches into this chunk; every lane
-        // takes part in the reductions, whatever its entry
-        const PixelGeom ar = active_rect(g, (int64_t)L > c);
+    int qn = 0;
+    while (true) {
+        queue_fill_back(keys, pv_list, s, wmax, bit, c, qn, q, lane);
+        if (qn == 0) break;
+        uint32_t rel = 0, pv = 0;
+        const int take = queue_take(q, qn, lane, rel, pv);
+        const bool valid = lane < take;
+        float4 a = make_float4(0.f, 0.f, -1.f, 0.f);
+        if (valid) a = __ldg(rec + 2 * (size_t)pv);
+        // lanes whose composited list reaches the chunk's nearest entry; every
+        // lane takes part in the reductions, whatever its entry
+        const uint32_t lowest = __shfl_sync(0xffffffffu, rel, take - 1);
+        const PixelGeom ar = active_rect(g, L > lowest);
         const bool hit = valid && disc_meets_rect(a, ar);
         uint32_t m = __ballot_sync(0xffffffffu, hit);
         if (hit) {
             wbuf[lane] = a;
             wbuf[32 + lane] = __ldg(rec + 2 * (size_t)pv + 1);
             wpv[lane] = pv;
+            wpos[lane] = rel;
         }
         __syncwarp();
         while (m) {
-            const int j = 31 - __clz(m); // back to front
-            m &= ~(1u << j);
+            const int j = __ffs(m) - 1; // back to front: queue order
+            m &= m - 1;
             const float4 aj = wbuf[j];
             const float4 cj = wbuf[32 + j];
-            const bool before = (uint32_t)c + j < L;
+            const bool before = wpos[j] < L;
             float dx, dy;
             const float d2 = pixel_d2(g.ux, g.uy, aj.x, aj.y, dx, dy);
             const bool contrib = before && d2 <= aj.z;
@@ -621,7 +712,7 @@ __device__ __forceinline__ void bwd_stream_item(const Batch &b, const DevOpts &o
                 }
             }
         }
-        __syncwarp(); // chunk consumed before the buffer is refilled
+        __syncwarp(); // chunk consumed before the buffers are refilled
     }
 }
 
@@ -650,103 +741,133 @@ __device__ __forceinline__ BwdPixel bwd_pixel(const PixelGeom &g, const DevOpts 
     return p;
 }
 
-// Backward of one 8 x 4P sub-block (sub-blocks numbered row-major, TW/8 per
-// row) by one warp, for the persistent schedule: lane l owns the P pixels
-// (l & 7, 4q + (l >> 3)), q < P.  Per listed point the lane forms the
-// adjoint at each of its pixels and adds the term vectors, so the
-// per-point warp work (staging, cull, reduction or atomics) serves 32P
-// pixels instead of 32.  Each pixel's T and S recursions are the same
-// operations as in the one-pixel walk.
+// Adjoint state of a lane's two pixels (see BwdPixel), packed.
+struct BwdPair {
+    float2 T, S, g0, g1, g2;
+    uint32_t LA, LB;
+};
+
+// The adjoint of one composited point at both pixels of a lane (the
+// operations of pixel_adjoint_masked, packed): take.x / take.y (0 or 1) say
+// whether the point was composited at pixel A / B (0: its terms are 0 and
+// T, S stay).  Returns the sum over the two pixels of the terms {dpx, dpy,
+// dq, do, dr, dg, db} in v[0..6].
+__device__ __forceinline__ void pair_adjoint(float2 take, float2 d2, float dx, float2 dy,
+                                             const float4 a, const float4 c, float amax,
+                                             BwdPair &p, float v[8])
+{
+    const float2 e = mul2(d2, f2(a.w));
+    const float2 G = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+    const float2 raw = mul2(f2(c.x), G);
+    const float2 alpha = mul2(make_float2(fminf(amax, raw.x), fminf(amax, raw.y)), take);
+    const float2 om = fma2(alpha, f2(-1.0f), f2(1.0f));
+    const float2 rom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
+    const float2 Tb = mul2(p.T, rom);
+    const float2 wgt = mul2(alpha, Tb);
+    const float2 cg = fma2(f2(c.w), p.g2, fma2(f2(c.z), p.g1, mul2(f2(c.y), p.g0)));
+    const float2 t4 = mul2(wgt, p.g0), t5 = mul2(wgt, p.g1), t6 = mul2(wgt, p.g2);
+    v[4] = t4.x + t4.y;
+    v[5] = t5.x + t5.y;
+    v[6] = t6.x + t6.y;
+    const float2 dalpha = mul2(fma2(Tb, cg, mul2(p.S, mul2(rom, f2(-1.0f)))), take);
+    p.S = fma2(wgt, cg, p.S);
+    p.T = Tb;
+    // clamped alpha: no geometry terms
+    const float2 ca0 = mul2(dalpha, alpha), dg0 = mul2(dalpha, G);
+    const float2 ca = make_float2(raw.x < amax ? ca0.x : 0.0f, raw.y < amax ? ca0.y : 0.0f);
+    const float2 caq = mul2(ca, f2(a.w * QP_TO_Q));
+    const float2 t1 = mul2(caq, dy), t2 = mul2(ca, d2);
+    v[0] = (caq.x + caq.y) * dx;
+    v[1] = t1.x + t1.y;
+    v[2] = -0.5f * (t2.x + t2.y);
+    v[3] = (raw.x < amax ? dg0.x : 0.0f) + (raw.y < amax ? dg0.y : 0.0f);
+    v[7] = 0.0f;
+}
+
+// Backward of one 8 x 8 block (blocks numbered row-major, TW/8 per row) by
+// one warp, for the persistent schedule: lane l owns the pixels A = (l & 7,
+// l >> 3) and B = (l & 7, 4 + (l >> 3)).  The warp takes the tile list's
+// entries with its block's bit (`bit`) from its queue, back to front.  Per
+// listed point the lane forms the adjoint at both pixels (packed fp32x2)
+// and adds the two term vectors, so the per-point warp work (staging, cull,
+// reduction or atomics) serves 64 pixels.  Each pixel's T and S recursions
+// are the one-pixel walk's operations.
 // V, (tx, ty): the tile's view and position; s: the start of its list.
-template <int TW, int TH, int P, bool STATS>
-__device__ __forceinline__ void bwd_rows_item(const DevView *V, int tx, int ty, uint32_t s,
-                                              const DevOpts &o, int sub, int lane,
+template <int TW, int TH, bool STATS>
+__device__ __forceinline__ void bwd_pair_item(const DevView *V, int tx, int ty, uint32_t s,
+                                              uint32_t bit, const DevOpts &o, int sub, int lane,
+                                              const uint32_t *__restrict__ keys,
                                               const uint32_t *__restrict__ pv_list,
                                               const float4 *__restrict__ rec,
                                               const float *__restrict__ T_final,
                                               const uint32_t *__restrict__ n_contrib,
                                               const float *__restrict__ grad_rgb,
                                               float *__restrict__ g2d, uint32_t &examined,
-                                              uint32_t &used, float4 *wbuf, uint32_t *wpv)
+                                              uint32_t &used, float4 *wbuf, uint32_t *wpv,
+                                              uint32_t *wpos, WarpQueue &q)
 {
-    static_assert(TH % (4 * P) == 0, "sub-block rows must tile the tile");
-    const int sx0 = tx * TW + (sub % (TW / 8)) * 8, sy0 = ty * TH + (sub / (TW / 8)) * (4 * P);
-    PixelGeom g[P];
-    BwdPixel px[P];
-    uint32_t lmax = 0;
-#pragma unroll
-    for (int q = 0; q < P; ++q) {
-        g[q] = pixel_geom_at(V, sx0, sy0 + 4 * q, lane);
-        px[q] = bwd_pixel(g[q], o, T_final, n_contrib, grad_rgb);
-        lmax = px[q].L > lmax ? px[q].L : lmax;
-    }
-    const uint32_t wmax = __reduce_max_sync(0xffffffffu, lmax);
+    const int sx0 = tx * TW + (sub % (TW / 8)) * 8, sy0 = ty * TH + (sub / (TW / 8)) * 8;
+    PixelGeom g[2];
+    g[0] = pixel_geom_at(V, sx0, sy0, lane);
+    g[1] = pixel_geom_at(V, sx0, sy0 + 4, lane);
+    const BwdPixel pa = bwd_pixel(g[0], o, T_final, n_contrib, grad_rgb);
+    const BwdPixel pb = bwd_pixel(g[1], o, T_final, n_contrib, grad_rgb);
+    BwdPair p;
+    p.T = make_float2(pa.T, pb.T);
+    p.S = make_float2(pa.S, pb.S);
+    p.g0 = make_float2(pa.g0, pb.g0);
+    p.g1 = make_float2(pa.g1, pb.g1);
+    p.g2 = make_float2(pa.g2, pb.g2);
+    p.LA = pa.L;
+    p.LB = pb.L;
+    const float ux = g[0].ux;
+    const float2 uy = make_float2(g[0].uy, g[1].uy);
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, max(pa.L, pb.L));
     if (wmax == 0) return;
     int64_t c = (int64_t)((wmax - 1) & ~31u);
-    uint32_t pv_n = 0, pv_nn = 0;
-    float4 a_n = make_float4(0.f, 0.f, -1.f, 0.f);
-    if ((uint32_t)c + lane < wmax) {
-        pv_n = __ldg(pv_list + s + (uint32_t)c + lane);
-        a_n = __ldg(rec + 2 * (size_t)pv_n);
-    }
-    if (c >= 32) pv_nn = __ldg(pv_list + s + (uint32_t)c - 32 + lane);
-    for (; c >= 0; c -= 32) {
-        const uint32_t pv = pv_n;
-        const float4 a = a_n;
-        const bool valid = (uint32_t)c + lane < wmax;
-        if (c >= 32) {
-            pv_n = pv_nn;
-            a_n = __ldg(rec + 2 * (size_t)pv_n);
-        }
-        if (c >= 64) pv_nn = __ldg(pv_list + s + (uint32_t)c - 64 + lane);
-        // every lane takes part in the reductions, whatever its entry
-        bool act[P];
-#pragma unroll
-        for (int q = 0; q < P; ++q) act[q] = (int64_t)px[q].L > c;
-        const PixelGeom ar = active_rect_rows<P>(g, act);
+    int qn = 0;
+    while (true) {
+        queue_fill_back(keys, pv_list, s, wmax, bit, c, qn, q, lane);
+        if (qn == 0) break;
+        uint32_t rel = 0, pv = 0;
+        const int take = queue_take(q, qn, lane, rel, pv);
+        const bool valid = lane < take;
+        float4 a = make_float4(0.f, 0.f, -1.f, 0.f);
+        if (valid) a = __ldg(rec + 2 * (size_t)pv);
+        // pixels whose composited list reaches the chunk's nearest entry; every
+        // lane takes part in the reductions, whatever its entry
+        const uint32_t lowest = __shfl_sync(0xffffffffu, rel, take - 1);
+        const bool act[2] = {p.LA > lowest, p.LB > lowest};
+        const PixelGeom ar = active_rect_rows<2>(g, act);
         const bool hit = valid && disc_meets_rect(a, ar);
         uint32_t m = __ballot_sync(0xffffffffu, hit);
         if (hit) {
             wbuf[lane] = a;
             wbuf[32 + lane] = __ldg(rec + 2 * (size_t)pv + 1);
             wpv[lane] = pv;
+            wpos[lane] = rel;
         }
         __syncwarp();
         while (m) {
-            const int j = 31 - __clz(m); // back to front
-            m &= ~(1u << j);
+            const int j = __ffs(m) - 1; // back to front: queue order
+            m &= m - 1;
             const float4 aj = wbuf[j];
-            const float4 cj = wbuf[32 + j];
-            const uint32_t idx = (uint32_t)c + j;
-            float d2[P], dx[P], dy[P];
-            bool ct[P];
-            bool any = false;
-#pragma unroll
-            for (int q = 0; q < P; ++q) {
-                const bool bq = idx < px[q].L;
-                d2[q] = pixel_d2(g[q].ux, g[q].uy, aj.x, aj.y, dx[q], dy[q]);
-                ct[q] = bq && d2[q] <= aj.z;
-                if (STATS) {
-                    examined += (uint32_t)bq;
-                    used += (uint32_t)ct[q];
-                }
-                any = any || ct[q];
+            const uint32_t idx = wpos[j];
+            float dx;
+            float2 dy;
+            const float2 d2 = pair_d2(ux, uy, aj.x, aj.y, dx, dy);
+            const bool bA = idx < p.LA, bB = idx < p.LB;
+            const bool cA = bA && d2.x <= aj.z, cB = bB && d2.y <= aj.z;
+            if (STATS) {
+                examined += (uint32_t)bA + (uint32_t)bB;
+                used += (uint32_t)cA + (uint32_t)cB;
             }
+            const bool any = cA || cB;
             const uint32_t cm = __ballot_sync(0xffffffffu, any);
             if (cm) {
                 float v[8];
-                pixel_adjoint_masked(ct[0] ? 1.0f : 0.0f, d2[0], dx[0], dy[0], aj, cj,
-                                     o.alpha_max, px[0].g0, px[0].g1, px[0].g2, px[0].T,
-                                     px[0].S, v);
-#pragma unroll
-                for (int q = 1; q < P; ++q) {
-                    float u[8];
-                    pixel_adjoint_masked(ct[q] ? 1.0f : 0.0f, d2[q], dx[q], dy[q], aj, cj,
-                                         o.alpha_max, px[q].g0, px[q].g1, px[q].g2, px[q].T,
-                                         px[q].S, u);
-#pragma unroll
-                    for (int k = 0; k < 7; ++k) v[k] += u[k];
-                }
+                pair_adjoint(make_float2(cA ? 1.0f : 0.0f, cB ? 1.0f : 0.0f), d2, dx, dy, aj,
+                             wbuf[32 + j], o.alpha_max, p, v);
                 if (__popc(cm) > BWD_PAIR_DIRECT_MAX) {
                     warp_add_terms(v, lane, g2d, wpv[j]);
                 } else if (any) { // few lanes: each adds its own terms
@@ -756,42 +877,58 @@ __device__ __forceinline__ void bwd_rows_item(const DevView *V, int tx, int ty, 
                 }
             }
         }
-        __syncwarp(); // chunk consumed before the buffer is refilled
+        __syncwarp(); // chunk consumed before the buffers are refilled
     }
+}
+
+// Bit of the 8 x 8 block holding the 8 x 4 sub-block w of a TW-wide tile
+// in the pair keys' block masks (0 when a tile is a single block).
+template <int TW, int TH>
+__device__ __forceinline__ uint32_t stream_block_bit(int w)
+{
+    constexpr int BPR = TW / 8;
+    return block_bits(TW, TH) ? 1u << (((w / BPR) >> 1) * BPR + w % BPR) : 0u;
 }
 
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW * TH)
 raster_fwd_stream_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
-                         const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
-                         float *__restrict__ out_rgb, float *__restrict__ T_final,
-                         uint32_t *__restrict__ n_contrib, unsigned long long *__restrict__ stats)
+                         const uint32_t *__restrict__ keys, const uint32_t *__restrict__ pv_list,
+                         const float4 *__restrict__ rec, float *__restrict__ out_rgb,
+                         float *__restrict__ T_final, uint32_t *__restrict__ n_contrib,
+                         unsigned long long *__restrict__ stats)
 {
-    __shared__ float4 s_buf[TW * TH / 32][64];
-    const int lane = threadIdx.x & 31;
+    constexpr int NW = TW * TH / 32;
+    __shared__ float4 s_buf[NW][64];
+    __shared__ uint32_t s_pos[NW][32];
+    __shared__ WarpQueue s_q[NW];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t ex = 0, co = 0;
     const uint2 rg = ranges[blockIdx.x];
-    fwd_stream_item(pixel_geom<TW, TH>(b, blockIdx.x, threadIdx.x >> 5, lane), rg.x,
-                    rg.y > rg.x ? rg.y : rg.x, o, lane, pv_list, rec, out_rgb, T_final, n_contrib,
-                    ex, co, s_buf[threadIdx.x >> 5]);
+    fwd_stream_item(pixel_geom<TW, TH>(b, blockIdx.x, w, lane), rg.x, rg.y > rg.x ? rg.y : rg.x,
+                    stream_block_bit<TW, TH>(w), o, lane, keys, pv_list, rec, out_rgb, T_final,
+                    n_contrib, ex, co, s_buf[w], s_pos[w], s_q[w]);
     add_stats(stats, ex, co, lane);
 }
 
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW * TH)
 raster_bwd_stream_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
-                         const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
-                         const float *__restrict__ T_final, const uint32_t *__restrict__ n_contrib,
-                         const float *__restrict__ grad_rgb, float *__restrict__ g2d,
-                         unsigned long long *__restrict__ stats)
+                         const uint32_t *__restrict__ keys, const uint32_t *__restrict__ pv_list,
+                         const float4 *__restrict__ rec, const float *__restrict__ T_final,
+                         const uint32_t *__restrict__ n_contrib, const float *__restrict__ grad_rgb,
+                         float *__restrict__ g2d, unsigned long long *__restrict__ stats)
 {
-    __shared__ float4 s_buf[TW * TH / 32][64];
-    __shared__ uint32_t s_pv[TW * TH / 32][32];
-    const int lane = threadIdx.x & 31;
+    constexpr int NW = TW * TH / 32;
+    __shared__ float4 s_buf[NW][64];
+    __shared__ uint32_t s_pv[NW][32];
+    __shared__ uint32_t s_pos[NW][32];
+    __shared__ WarpQueue s_q[NW];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t ex = 0, us = 0;
-    bwd_stream_item<TW, TH>(b, o, blockIdx.x, threadIdx.x >> 5, lane, ranges, pv_list, rec,
-                            T_final, n_contrib, grad_rgb, g2d, ex, us, s_buf[threadIdx.x >> 5],
-                            s_pv[threadIdx.x >> 5]);
+    bwd_stream_item<TW, TH>(b, o, blockIdx.x, w, stream_block_bit<TW, TH>(w), lane, ranges, keys,
+                            pv_list, rec, T_final, n_contrib, grad_rgb, g2d, ex, us, s_buf[w],
+                            s_pv[w], s_pos[w], s_q[w]);
     add_stats(stats ? stats + 2 : nullptr, ex, us, lane);
 }
 
@@ -830,14 +967,18 @@ __device__ __forceinline__ uint4 tile_desc(const Batch &b, const uint2 *ranges, 
 template <int TW, int TH, bool STATS>
 __global__ void __launch_bounds__(PERSIST_THREADS, FWD_PERSIST_BLOCKS)
 raster_fwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
-                          const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
-                          float *__restrict__ out_rgb, float *__restrict__ T_final,
-                          uint32_t *__restrict__ n_contrib, unsigned long long *__restrict__ stats,
-                          const uint4 *__restrict__ order, uint32_t *work)
+                          const uint32_t *__restrict__ keys, const uint32_t *__restrict__ pv_list,
+                          const float4 *__restrict__ rec, float *__restrict__ out_rgb,
+                          float *__restrict__ T_final, uint32_t *__restrict__ n_contrib,
+                          unsigned long long *__restrict__ stats, const uint4 *__restrict__ order,
+                          uint32_t *work)
 {
     constexpr uint32_t SUBS = (TW / 8) * (TH / 8);
-    __shared__ float4 s_buf[PERSIST_THREADS / 32][64];
-    const int lane = threadIdx.x & 31;
+    constexpr int NW = PERSIST_THREADS / 32;
+    __shared__ float4 s_buf[NW][64];
+    __shared__ uint32_t s_pos[NW][32];
+    __shared__ WarpQueue s_q[NW];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t n_items = b.n_tiles * SUBS;
     uint32_t ex = 0, co = 0;
     for (uint32_t it = next_item(work, lane); it < n_items; it = next_item(work, lane)) {
@@ -846,9 +987,10 @@ raster_fwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
         const DevView *V = &b.views[d.x];
         const int sx0 = (int)(d.y & 0xffffu) * TW + (sub % (TW / 8)) * 8;
         const int sy0 = (int)(d.y >> 16) * TH + (sub / (TW / 8)) * 8;
+        const uint32_t bit = block_bits(TW, TH) ? 1u << sub : 0u;
         fwd_pair_item<STATS>(pixel_geom_at(V, sx0, sy0, lane), pixel_geom_at(V, sx0, sy0 + 4, lane),
-                             d.z, d.w, o, lane, pv_list, rec, out_rgb, T_final, n_contrib, ex, co,
-                             s_buf[threadIdx.x >> 5]);
+                             d.z, d.w, bit, o, lane, keys, pv_list, rec, out_rgb, T_final,
+                             n_contrib, ex, co, s_buf[w], s_pos[w], s_q[w]);
     }
     if (STATS) add_stats(stats, ex, co, lane);
 }
@@ -856,25 +998,30 @@ raster_fwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
 template <int TW, int TH, bool STATS>
 __global__ void __launch_bounds__(PERSIST_THREADS)
 raster_bwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
-                          const uint32_t *__restrict__ pv_list, const float4 *__restrict__ rec,
-                          const float *__restrict__ T_final, const uint32_t *__restrict__ n_contrib,
+                          const uint32_t *__restrict__ keys, const uint32_t *__restrict__ pv_list,
+                          const float4 *__restrict__ rec, const float *__restrict__ T_final,
+                          const uint32_t *__restrict__ n_contrib,
                           const float *__restrict__ grad_rgb, float *__restrict__ g2d,
                           unsigned long long *__restrict__ stats, const uint4 *__restrict__ order,
                           uint32_t *work)
 {
-    constexpr int P = (TH % (4 * BWD_ROWS) == 0) ? BWD_ROWS : 2;
-    constexpr uint32_t SUBS = (TW / 8) * (TH / (4 * P));
-    __shared__ float4 s_buf[PERSIST_THREADS / 32][64];
-    __shared__ uint32_t s_pv[PERSIST_THREADS / 32][32];
-    const int lane = threadIdx.x & 31;
+    // 8 x 8 blocks, numbered like the key masks
+    constexpr uint32_t SUBS = (TW / 8) * (TH / 8);
+    constexpr int NW = PERSIST_THREADS / 32;
+    __shared__ float4 s_buf[NW][64];
+    __shared__ uint32_t s_pv[NW][32];
+    __shared__ uint32_t s_pos[NW][32];
+    __shared__ WarpQueue s_q[NW];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t n_items = b.n_tiles * SUBS;
     uint32_t ex = 0, us = 0;
     for (uint32_t it = next_item(work, lane); it < n_items; it = next_item(work, lane)) {
         const uint4 d = order[it / SUBS];
-        bwd_rows_item<TW, TH, P, STATS>(&b.views[d.x], (int)(d.y & 0xffffu), (int)(d.y >> 16),
-                                        d.z, o, (int)(it % SUBS), lane, pv_list, rec, T_final,
-                                        n_contrib, grad_rgb, g2d, ex, us, s_buf[threadIdx.x >> 5],
-                                        s_pv[threadIdx.x >> 5]);
+        const int sub = (int)(it % SUBS);
+        const uint32_t bit = block_bits(TW, TH) ? 1u << sub : 0u;
+        bwd_pair_item<TW, TH, STATS>(&b.views[d.x], (int)(d.y & 0xffffu), (int)(d.y >> 16), d.z,
+                                     bit, o, sub, lane, keys, pv_list, rec, T_final, n_contrib,
+                                     grad_rgb, g2d, ex, us, s_buf[w], s_pv[w], s_pos[w], s_q[w]);
     }
     if (STATS) add_stats(stats + 2, ex, us, lane);
 }
@@ -1122,7 +1269,8 @@ int persist_grid(const void *kernel)
 
 template <int TW, int TH>
 void fwd_dispatch(const Batch &b, const DevOpts &o, int depth, const uint2 *ranges,
-                  const uint32_t *pv_list, const float4 *rec, float *out_rgb, float *T_final,
+                  const uint32_t *keys, const uint32_t *pv_list, const float4 *rec,
+                  float *out_rgb, float *T_final,
                   uint32_t *n_contrib, unsigned long long *stats, const uint4 *order,
                   uint32_t *work, cudaStream_t s)
 {
@@ -1131,16 +1279,16 @@ void fwd_dispatch(const Batch &b, const DevOpts &o, int depth, const uint2 *rang
             static const int grid =
                 persist_grid((const void *)raster_fwd_persist_kernel<TW, TH, true>);
             raster_fwd_persist_kernel<TW, TH, true><<<grid, PERSIST_THREADS, 0, s>>>(
-                b, o, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats, order, work);
+                b, o, ranges, keys, pv_list, rec, out_rgb, T_final, n_contrib, stats, order, work);
         } else {
             static const int grid =
                 persist_grid((const void *)raster_fwd_persist_kernel<TW, TH, false>);
             raster_fwd_persist_kernel<TW, TH, false><<<grid, PERSIST_THREADS, 0, s>>>(
-                b, o, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats, order, work);
+                b, o, ranges, keys, pv_list, rec, out_rgb, T_final, n_contrib, stats, order, work);
         }
     } else if (depth == 0) {
         raster_fwd_stream_kernel<TW, TH><<<b.n_tiles, TW * TH, 0, s>>>(
-            b, o, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats);
+            b, o, ranges, keys, pv_list, rec, out_rgb, T_final, n_contrib, stats);
     } else {
         const size_t smem =
             (size_t)depth * (2 * sizeof(float4) + (TW * TH / 32) * sizeof(uint16_t));
@@ -1156,7 +1304,8 @@ void fwd_dispatch(const Batch &b, const DevOpts &o, int depth, const uint2 *rang
 
 template <int TW, int TH>
 void bwd_dispatch(const Batch &b, const DevOpts &o, int depth, const uint2 *ranges,
-                  const uint32_t *pv_list, const float4 *rec, const float *T_final,
+                  const uint32_t *keys, const uint32_t *pv_list, const float4 *rec,
+                  const float *T_final,
                   const uint32_t *n_contrib, const float *grad_rgb, float4 *g2d,
                   unsigned long long *stats, const uint4 *order, uint32_t *work,
                   cudaStream_t s)
@@ -1166,18 +1315,18 @@ void bwd_dispatch(const Batch &b, const DevOpts &o, int depth, const uint2 *rang
             static const int grid =
                 persist_grid((const void *)raster_bwd_persist_kernel<TW, TH, true>);
             raster_bwd_persist_kernel<TW, TH, true><<<grid, PERSIST_THREADS, 0, s>>>(
-                b, o, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d, stats,
-                order, work + 1);
+                b, o, ranges, keys, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d,
+                stats, order, work + 1);
         } else {
             static const int grid =
                 persist_grid((const void *)raster_bwd_persist_kernel<TW, TH, false>);
             raster_bwd_persist_kernel<TW, TH, false><<<grid, PERSIST_THREADS, 0, s>>>(
-                b, o, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d, stats,
-                order, work + 1);
+                b, o, ranges, keys, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d,
+                stats, order, work + 1);
         }
     } else if (depth == 0) {
         raster_bwd_stream_kernel<TW, TH><<<b.n_tiles, TW * TH, 0, s>>>(
-            b, o, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d, stats);
+            b, o, ranges, keys, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d, stats);
     } else {
         const size_t smem = (size_t)depth * (4 * sizeof(float4) + sizeof(uint32_t) +
                                              (TW * TH / 32) * sizeof(uint16_t));
@@ -1211,39 +1360,39 @@ void reset_work_counters(uint32_t *work, cudaStream_t s)
 }
 
 void launch_raster_fwd(const Batch &b, const DevOpts &o, int depth, const uint2 *ranges,
-                       const uint32_t *pv_list, const float4 *rec, float *out_rgb,
-                       float *T_final, uint32_t *n_contrib, unsigned long long *stats,
-                       cudaStream_t s, const uint4 *order, uint32_t *work)
-{
-    if (b.n_tiles == 0) return;
-    if (o.tile_w == 8 && o.tile_h == 8)
-        fwd_dispatch<8, 8>(b, o, depth, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats,
-                           order, work, s);
-    else if (o.tile_w == 16 && o.tile_h == 32)
-        fwd_dispatch<16, 32>(b, o, depth, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats,
-                             order, work, s);
-    else
-        fwd_dispatch<16, 16>(b, o, depth, ranges, pv_list, rec, out_rgb, T_final, n_contrib, stats,
-                             order, work, s);
-}
-
-void launch_raster_bwd(const Batch &b, const DevOpts &o, int depth, const uint2 *ranges,
-                       const uint32_t *pv_list, const float4 *rec, const float *T_final,
-                       const uint32_t *n_contrib, const float *grad_rgb, float4 *g2d,
+                       const uint32_t *keys, const uint32_t *pv_list, const float4 *rec,
+                       float *out_rgb, float *T_final, uint32_t *n_contrib,
                        unsigned long long *stats, cudaStream_t s, const uint4 *order,
                        uint32_t *work)
 {
     if (b.n_tiles == 0) return;
-
     if (o.tile_w == 8 && o.tile_h == 8)
-        bwd_dispatch<8, 8>(b, o, depth, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, g2d,
+        fwd_dispatch<8, 8>(b, o, depth, ranges, keys, pv_list, rec, out_rgb, T_final, n_contrib,
                            stats, order, work, s);
     else if (o.tile_w == 16 && o.tile_h == 32)
-        bwd_dispatch<16, 32>(b, o, depth, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, g2d,
-                             stats, order, work, s);
+        fwd_dispatch<16, 32>(b, o, depth, ranges, keys, pv_list, rec, out_rgb, T_final,
+                             n_contrib, stats, order, work, s);
     else
-        bwd_dispatch<16, 16>(b, o, depth, ranges, pv_list, rec, T_final, n_contrib, grad_rgb, g2d,
-                             stats, order, work, s);
+        fwd_dispatch<16, 16>(b, o, depth, ranges, keys, pv_list, rec, out_rgb, T_final,
+                             n_contrib, stats, order, work, s);
+}
+
+void launch_raster_bwd(const Batch &b, const DevOpts &o, int depth, const uint2 *ranges,
+                       const uint32_t *keys, const uint32_t *pv_list, const float4 *rec,
+                       const float *T_final, const uint32_t *n_contrib, const float *grad_rgb,
+                       float4 *g2d, unsigned long long *stats, cudaStream_t s,
+                       const uint4 *order, uint32_t *work)
+{
+    if (b.n_tiles == 0) return;
+    if (o.tile_w == 8 && o.tile_h == 8)
+        bwd_dispatch<8, 8>(b, o, depth, ranges, keys, pv_list, rec, T_final, n_contrib, grad_rgb,
+                           g2d, stats, order, work, s);
+    else if (o.tile_w == 16 && o.tile_h == 32)
+        bwd_dispatch<16, 32>(b, o, depth, ranges, keys, pv_list, rec, T_final, n_contrib,
+                             grad_rgb, g2d, stats, order, work, s);
+    else
+        bwd_dispatch<16, 16>(b, o, depth, ranges, keys, pv_list, rec, T_final, n_contrib,
+                             grad_rgb, g2d, stats, order, work, s);
 }
 
 } // namespace pbr

@@ -403,35 +403,15 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
 }
 
 // ------------------------------------------------------------ emission
-// One gather per depth-sorted point-view: its tile rectangle (the only
-// random access of the emission), turned into the tile count, the global id
-// of the rectangle's first tile and the rectangle width / tiles per row.
-__global__ void gather_rects_kernel(const DevView *__restrict__ views, int32_t n_views,
-                                    const uint32_t *__restrict__ sorted_pv,
-                                    const uint4 *__restrict__ rect, const uint32_t *n_dev,
-                                    int64_t cap, uint32_t *__restrict__ nt_sorted,
-                                    uint32_t *__restrict__ tb_sorted,
-                                    uint32_t *__restrict__ wx_sorted,
-                                    uint32_t *__restrict__ mask_sorted)
+// Tile counts in depth order (the scan that places each point-view's run of
+// pairs reads them).
+__global__ void gather_counts_kernel(const uint32_t *__restrict__ sorted_pv,
+                                     const uint32_t *__restrict__ ntiles, const uint32_t *n_dev,
+                                     int64_t cap, uint32_t *__restrict__ nt_sorted)
 {
     const int64_t n = dev_count(n_dev, cap);
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const uint32_t pv = sorted_pv[j];
-    int lo = 0, hi = n_views - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (views[mid].pv_base <= (int64_t)pv) lo = mid; else hi = mid - 1;
-    }
-    const uint4 rc = rect[pv];
-    const uint32_t tx0 = rc.x & 0xffff, ty0 = rc.x >> 16, tx1 = rc.y & 0xffff, ty1 = rc.y >> 16;
-    const uint32_t tpx = (uint32_t)views[lo].tiles_x;
-    const uint32_t wx = tx1 - tx0 + 1, wy = ty1 - ty0 + 1;
-    const uint32_t m = wx * wy > 32 ? 0u : rc.z; // 0: every tile of the box
-    nt_sorted[j] = m ? (uint32_t)__popc(m) : wx * wy;
-    tb_sorted[j] = views[lo].tile_base + ty0 * tpx + tx0;
-    wx_sorted[j] = wx | (tpx << 16);
-    mask_sorted[j] = m;
+    if (j < n) nt_sorted[j] = ntiles[sorted_pv[j]];
 }
 
 // Position of the (t+1)-th set bit of m (t < popc(m)), by halving.
@@ -452,32 +432,63 @@ __device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t t)
 
 // Each warp owns 32 consecutive depth-sorted point-views; their pair runs
 // are contiguous in the output, so the warp writes them together: output q
-// belongs to the last lane whose run starts at or before q.
+// belongs to the last lane whose run starts at or before q.  The run of a
+// box wider than 32 tiles (no listed-tile mask) is written afterwards by the
+// whole warp, 32 tiles of the box at a time.  Key of a pair: global tile <<
+// sb | the 8 x 8 block mask of the pair (sb = block_bits; 0: no mask).
+template <int TW, int TH>
 __global__ void __launch_bounds__(256)
-emit_pairs_kernel(const uint32_t *__restrict__ sorted_pv, const uint32_t *__restrict__ nt_sorted,
-                  const uint32_t *__restrict__ offs, const uint32_t *__restrict__ tb_sorted,
-                  const uint32_t *__restrict__ wx_sorted, const uint32_t *__restrict__ mask_sorted,
+emit_pairs_kernel(const DevView *__restrict__ views, int32_t n_views,
+                  const uint32_t *__restrict__ sorted_pv, const uint32_t *__restrict__ nt_sorted,
+                  const uint32_t *__restrict__ offs, const uint4 *__restrict__ rect,
                   const uint32_t *n_dev, int64_t cap_vis, uint32_t *__restrict__ keys,
                   uint32_t *__restrict__ vals, int64_t cap_pairs, uint32_t *status)
 {
+    constexpr uint32_t FULL = 0xffffffffu;
+    constexpr int sb = block_bits(TW, TH);
+    constexpr int tws = TW == 8 ? 3 : 4, ths = TH == 8 ? 3 : (TH == 16 ? 4 : 5);
+    static_assert((1 << tws) == TW && (1 << ths) == TH, "tile sizes are powers of two");
     const int64_t n = dev_count(n_dev, cap_vis);
     const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31;
     if (j0 >= n) return; // whole warp past the end
     const int lane = threadIdx.x & 31;
     const int64_t j = j0 + lane;
     const bool ok = j < n;
-    uint32_t pre = 0xffffffffu, nt = 0, pv = 0, tb = 0, wxt = 1, msk = 0; // invalid lanes own no output
+    // the lane's point-view (invalid lanes own no output)
+    uint32_t pre = 0xffffffffu, nt = 0, pv = 0, tb = 0, wxt = 1, mask = 0, box = 0, wh = 0;
+    uint32_t wy = 1;
+    float px = 0.f, py = 0.f, rc2 = 0.f;
+    bool big = false;
     if (ok) {
         pre = offs[j];
         nt = nt_sorted[j];
         pv = sorted_pv[j];
-        tb = tb_sorted[j];
-        wxt = wx_sorted[j];
-        msk = mask_sorted[j];
+        int lo = 0, hi = n_views - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (views[mid].pv_base <= (int64_t)pv) lo = mid; else hi = mid - 1;
+        }
+        const DevView &V = views[lo];
+        const uint4 r4 = rect[pv];
+        px = __uint_as_float(r4.x);
+        py = __uint_as_float(r4.y);
+        const float rc = __uint_as_float(r4.z);
+        rc2 = __fmul_rn(rc, rc);
+        int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+        pixel_box(px, py, rc, V.W, V.H, x0, x1, y0, y1); // meets the image: the pv is listed
+        const uint32_t tx0 = (uint32_t)x0 >> tws, ty0 = (uint32_t)y0 >> ths;
+        const uint32_t wx = ((uint32_t)x1 >> tws) - tx0 + 1;
+        wy = ((uint32_t)y1 >> ths) - ty0 + 1;
+        big = wx * wy > 32;
+        mask = big ? 0u : r4.w;
+        tb = V.tile_base + ty0 * (uint32_t)V.tiles_x + tx0;
+        wxt = wx | ((uint32_t)V.tiles_x << 16);
+        box = (tx0 << tws) | ((ty0 << ths) << 16);
+        wh = (uint32_t)V.W | ((uint32_t)V.H << 16);
     }
-    const uint32_t start = __shfl_sync(0xffffffffu, pre, 0);
+    const uint32_t start = __shfl_sync(FULL, pre, 0);
     const uint32_t last_lane = (uint32_t)(n - 1 - j0 < 31 ? n - 1 - j0 : 31);
-    const uint32_t end = __shfl_sync(0xffffffffu, pre + nt, last_lane);
+    const uint32_t end = __shfl_sync(FULL, pre + nt, last_lane);
     if (lane == 0 && (int64_t)end > cap_pairs) atomicOr(status, ST_PAIR_OVERFLOW);
     // Owner of output q: the last lane whose run starts at or before q.  Every
     // valid lane's run is non-empty (a listed point-view covers a tile), so
@@ -489,49 +500,107 @@ emit_pairs_kernel(const uint32_t *__restrict__ sorted_pv, const uint32_t *__rest
     for (uint32_t q0 = start; q0 < end; q0 += 32) {
         const uint32_t q = q0 + lane;
         const uint32_t rel = pre - q0; // valid lanes: pre >= q0 once their run is due
-        const uint32_t starts = __reduce_or_sync(0xffffffffu, rel < 32u ? 1u << rel : 0u);
+        const uint32_t starts = __reduce_or_sync(FULL, rel < 32u ? 1u << rel : 0u);
         const int ow = before + __popc(starts & le);
         before += __popc(starts);
-        const uint32_t opre = __shfl_sync(0xffffffffu, pre, ow);
-        const uint32_t otb = __shfl_sync(0xffffffffu, tb, ow);
-        const uint32_t owxt = __shfl_sync(0xffffffffu, wxt, ow);
-        const uint32_t opv = __shfl_sync(0xffffffffu, pv, ow);
-        uint32_t omask = __shfl_sync(0xffffffffu, msk, ow);
-        if (q < end && (int64_t)q < cap_pairs) {
-            uint32_t t = q - opre;
-            if (omask) t = nth_set_bit(omask, t); // position of the t-th listed tile
+        const uint32_t opre = __shfl_sync(FULL, pre, ow);
+        const uint32_t otb = __shfl_sync(FULL, tb, ow);
+        const uint32_t owxt = __shfl_sync(FULL, wxt, ow);
+        const uint32_t opv = __shfl_sync(FULL, pv, ow);
+        const uint32_t omask = __shfl_sync(FULL, mask, ow);
+        uint32_t obox = 0, owh = 0;
+        float opx = 0.f, opy = 0.f, orc2 = 0.f;
+        if (sb) {
+            obox = __shfl_sync(FULL, box, ow);
+            owh = __shfl_sync(FULL, wh, ow);
+            opx = __shfl_sync(FULL, px, ow);
+            opy = __shfl_sync(FULL, py, ow);
+            orc2 = __shfl_sync(FULL, rc2, ow);
+        }
+        // omask == 0: a wide box, written below
+        if (q < end && (int64_t)q < cap_pairs && omask) {
+            const uint32_t t = nth_set_bit(omask, q - opre); // position of the listed tile
             const uint32_t owx = owxt & 0xffff;
             // row = floor(t / owx), exactly: (t + 0.5) / owx is at least
             // 0.5 / owx away from an integer and the two roundings move it
-            // by less than 2^-23 of itself, which is smaller for t < 2^22
-            // (a box has fewer tiles)
+            // by less than 2^-23 of itself (t < 32)
             const uint32_t row =
                 (uint32_t)__fmul_rn((float)t + 0.5f, __frcp_rn((float)owx));
-            keys[q] = otb + row * (owxt >> 16) + (t - row * owx);
+            const uint32_t col = t - row * owx;
+            uint32_t key = otb + row * (owxt >> 16) + col;
+            if (sb) {
+                const int ox = (int)(obox & 0xffff) + ((int)col << tws);
+                const int oy = (int)(obox >> 16) + ((int)row << ths);
+                key = (key << sb) | tile_block_mask<TW, TH>(opx, opy, orc2, ox, oy,
+                                                            (int)(owh & 0xffff), (int)(owh >> 16));
+            }
+            keys[q] = key;
             vals[q] = opv;
         }
     }
+    // wide boxes: the warp tests 32 tiles of the box at a time and writes the
+    // listed ones in row-major order (the same test the count came from)
+    uint32_t wide = __ballot_sync(FULL, ok && big);
+    while (wide) {
+        const int bl = __ffs(wide) - 1;
+        wide &= wide - 1;
+        const uint32_t bpre = __shfl_sync(FULL, pre, bl), bnt = __shfl_sync(FULL, nt, bl);
+        const uint32_t btb = __shfl_sync(FULL, tb, bl), bwxt = __shfl_sync(FULL, wxt, bl);
+        const uint32_t bwy = __shfl_sync(FULL, wy, bl), bpv = __shfl_sync(FULL, pv, bl);
+        const uint32_t bbox = __shfl_sync(FULL, box, bl), bwh = __shfl_sync(FULL, wh, bl);
+        const float bpx = __shfl_sync(FULL, px, bl), bpy = __shfl_sync(FULL, py, bl);
+        const float brc2 = __shfl_sync(FULL, rc2, bl);
+        const uint32_t bwx = bwxt & 0xffff, total = bwx * bwy;
+        const int W = (int)(bwh & 0xffff), H = (int)(bwh >> 16);
+        uint32_t written = 0;
+        for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+            const uint32_t k = k0 + lane;
+            bool listed = false;
+            uint32_t key = 0;
+            if (k < total) {
+                const uint32_t row = k / bwx, col = k - row * bwx;
+                const int xa = (int)(bbox & 0xffff) + ((int)col << tws);
+                const int ya = (int)(bbox >> 16) + ((int)row << ths);
+                listed = rect_reached(bpx, bpy, brc2, xa, min(xa + TW, W) - 1, ya,
+                                      min(ya + TH, H) - 1);
+                key = btb + row * (bwxt >> 16) + col;
+                if (listed && sb)
+                    key = (key << sb) | tile_block_mask<TW, TH>(bpx, bpy, brc2, xa, ya, W, H);
+            }
+            const uint32_t m = __ballot_sync(FULL, listed);
+            const uint32_t rank = written + (uint32_t)__popc(m & lanemask_lt());
+            const uint32_t q = bpre + rank;
+            if (listed && rank < bnt && (int64_t)q < cap_pairs) {
+                keys[q] = key;
+                vals[q] = bpv;
+            }
+            written += (uint32_t)__popc(m);
+        }
+        if (lane == 0 && written != bnt) atomicOr(status, ST_BAD_RANGE);
+    }
 }
 
-// [start, end) of every tile in the sorted key list; four keys per thread.
+// [start, end) of every tile (key >> shift) in the sorted key list; four
+// keys per thread.
 __global__ void tile_ranges_kernel(const uint32_t *__restrict__ keys, const uint32_t *n_dev,
-                                   int64_t cap, uint2 *__restrict__ ranges, uint32_t n_tiles)
+                                   int64_t cap, uint2 *__restrict__ ranges, uint32_t n_tiles,
+                                   int shift)
 {
     const int64_t n = dev_count(n_dev, cap);
     const int64_t j4 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
     if (j4 >= n) return;
-    uint32_t k[6]; // k[0] = key before the group, k[5] = key after it
+    uint32_t k[6]; // k[0] = tile before the group, k[5] = tile after it
     if (j4 + 3 < n) {
         const uint4 q = *reinterpret_cast<const uint4 *>(keys + j4);
-        k[1] = q.x;
-        k[2] = q.y;
-        k[3] = q.z;
-        k[4] = q.w;
+        k[1] = q.x >> shift;
+        k[2] = q.y >> shift;
+        k[3] = q.z >> shift;
+        k[4] = q.w >> shift;
     } else {
-        for (int i = 0; i < 4; ++i) k[1 + i] = j4 + i < n ? keys[j4 + i] : 0xffffffffu;
+        for (int i = 0; i < 4; ++i) k[1 + i] = j4 + i < n ? keys[j4 + i] >> shift : 0xffffffffu;
     }
-    k[0] = j4 > 0 ? keys[j4 - 1] : 0xffffffffu;
-    k[5] = j4 + 4 < n ? keys[j4 + 4] : 0xffffffffu;
+    k[0] = j4 > 0 ? keys[j4 - 1] >> shift : 0xffffffffu;
+    k[5] = j4 + 4 < n ? keys[j4 + 4] >> shift : 0xffffffffu;
 #pragma unroll
     for (int i = 1; i <= 4; ++i) {
         const int64_t j = j4 + i - 1;
@@ -580,7 +649,8 @@ int radix_passes(int key_bits)
 
 void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *&keys_alt, uint32_t *&vals_alt,
                       const uint32_t *n_dev, int64_t cap, int key_bits, void *temp,
-                      cudaStream_t s, uint32_t key_lo, uint32_t key_max, bool index_vals)
+                      cudaStream_t s, uint32_t key_lo, uint32_t key_max, bool index_vals,
+                      int bit_lo)
 {
     if (cap <= 0) return;
     if (key_bits <= 0) {
@@ -596,14 +666,14 @@ void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *&keys_alt, uin
     void *scan_tmp = hist + nb * RBINS;
     const int passes = radix_passes(key_bits);
     const int width = (key_bits + passes - 1) / passes;
-    for (int shift = 0; shift < key_bits; shift += width) {
-        const int wd = key_bits - shift < width ? key_bits - shift : width;
+    for (int shift = bit_lo; shift < bit_lo + key_bits; shift += width) {
+        const int wd = bit_lo + key_bits - shift < width ? bit_lo + key_bits - shift : width;
         radix_hist_kernel<<<(unsigned)nb, SORT_THREADS, 0, s>>>(keys, n_dev, cap, key_lo, key_max,
                                                                 shift, wd, hist, nb);
         run_scan(LoadU32{hist}, ActStore{hist}, nullptr, nb << wd, scan_tmp, nullptr, nullptr, s);
         radix_scatter_kernel<<<(unsigned)nb, SORT_THREADS, SCATTER_SMEM, s>>>(
             keys, vals, keys_alt, vals_alt, n_dev, cap, key_lo, key_max, shift, wd, hist, nb,
-            index_vals && shift == 0);
+            index_vals && shift == bit_lo);
         count_launches(2);
         uint32_t *tk = keys, *tv = vals;
         keys = keys_alt;
@@ -615,7 +685,7 @@ void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *&keys_alt, uin
 
 size_t emit_temp_bytes(int64_t cap_vis)
 {
-    return (size_t)(cap_vis > 0 ? cap_vis : 1) * 5 * sizeof(uint32_t) + scan_temp_bytes(cap_vis);
+    return (size_t)(cap_vis > 0 ? cap_vis : 1) * 2 * sizeof(uint32_t) + scan_temp_bytes(cap_vis);
 }
 
 void launch_emit_pairs(const Batch &b, const DevOpts &o, const uint32_t *sorted_pv,
@@ -623,32 +693,29 @@ void launch_emit_pairs(const Batch &b, const DevOpts &o, const uint32_t *sorted_
                        const uint4 *rect, uint32_t *keys, uint32_t *vals, int64_t cap_pairs,
                        uint32_t *status, void *temp, cudaStream_t s)
 {
-    (void)o;
     if (cap_vis <= 0) return;
-    (void)ntiles;
     uint32_t *nt_sorted = (uint32_t *)temp;
     uint32_t *offs = nt_sorted + cap_vis;
-    uint32_t *tb_sorted = offs + cap_vis;
-    uint32_t *wx_sorted = tb_sorted + cap_vis;
-    uint32_t *mask_sorted = wx_sorted + cap_vis;
-    void *scan_tmp = mask_sorted + cap_vis;
+    void *scan_tmp = offs + cap_vis;
     const unsigned nb = (unsigned)((cap_vis + 255) / 256);
-    gather_rects_kernel<<<nb, 256, 0, s>>>(b.views, b.n_views, sorted_pv, rect, n_vis, cap_vis,
-                                           nt_sorted, tb_sorted, wx_sorted, mask_sorted);
+    gather_counts_kernel<<<nb, 256, 0, s>>>(sorted_pv, ntiles, n_vis, cap_vis, nt_sorted);
     run_scan(LoadU32{nt_sorted}, ActStore{offs}, n_vis, cap_vis, scan_tmp, nullptr, status, s);
-    emit_pairs_kernel<<<nb, 256, 0, s>>>(sorted_pv, nt_sorted, offs, tb_sorted, wx_sorted,
-                                         mask_sorted, n_vis, cap_vis, keys, vals, cap_pairs,
-                                         status);
+    auto emit = emit_pairs_kernel<16, 16>;
+    if (o.tile_w == 8 && o.tile_h == 8) emit = emit_pairs_kernel<8, 8>;
+    else if (o.tile_w == 16 && o.tile_h == 32) emit = emit_pairs_kernel<16, 32>;
+    emit<<<nb, 256, 0, s>>>(b.views, b.n_views, sorted_pv, nt_sorted, offs, rect, n_vis,
+                            cap_vis, keys, vals, cap_pairs, status);
     count_launches(2);
 }
 
 void launch_tile_ranges(const uint32_t *keys, const uint32_t *n_pairs, int64_t cap_pairs,
-                        uint2 *ranges, uint32_t n_tiles, cudaStream_t s)
+                        uint2 *ranges, uint32_t n_tiles, int shift, cudaStream_t s)
 {
     if (cap_pairs <= 0) return;
     const int th = 256;
     const int64_t nb = ((cap_pairs + 3) / 4 + th - 1) / th;
-    tile_ranges_kernel<<<(unsigned)nb, th, 0, s>>>(keys, n_pairs, cap_pairs, ranges, n_tiles);
+    tile_ranges_kernel<<<(unsigned)nb, th, 0, s>>>(keys, n_pairs, cap_pairs, ranges, n_tiles,
+                                                   shift);
     count_launches(1);
 }
 

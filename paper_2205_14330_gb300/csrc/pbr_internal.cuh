@@ -93,15 +93,102 @@ unsigned long long launches_total();
 constexpr float LOG2E = 1.4426950408889634f;
 constexpr float QP_TO_Q = -2.0f / 1.4426950408889634f;
 
+// ---- binning rule (Sec. 3.2 cutoff), shared by the per-point stage and the
+// pair emission.  A tile lists a point-view iff some pixel of the tile
+// (inside the image) passes the per-pixel fp32 cutoff test; each listed
+// pair carries the mask of the tile's 8 x 8 pixel blocks holding such a
+// pixel (bit by * (tile_w / 8) + bx, row-major inside the tile), stored in
+// the low block_bits() bits of its sort key: key = tile << block_bits | mask.
+
+// Mask bits per key: one per 8 x 8 block when a tile holds more than one.
+__host__ __device__ constexpr int block_bits(int tile_w, int tile_h)
+{
+    return (tile_w / 8) * (tile_h / 8) > 1 ? (tile_w / 8) * (tile_h / 8) : 0;
+}
+
+// Whether some pixel centre of the pixel rectangle [x0, x1] x [y0, y1]
+// (inclusive, non-empty) passes the cutoff test d2 <= rc2 (fp32
+// round-to-nearest, d2 = (ux - px)^2 + (uy - py)^2).  Rounding is monotone,
+// so the centre nearest the splat centre per axis -- floor(p) + 0.5 clamped
+// into the rectangle -- has the smallest fp32 d2: testing it decides for the
+// whole rectangle.
+__device__ __forceinline__ bool rect_reached(float px, float py, float rc2, int x0, int x1,
+                                             int y0, int y1)
+{
+    const float cx = fminf(fmaxf(__fadd_rn(floorf(px), 0.5f), __fadd_rn((float)x0, 0.5f)),
+                           __fadd_rn((float)x1, 0.5f));
+    const float cy = fminf(fmaxf(__fadd_rn(floorf(py), 0.5f), __fadd_rn((float)y0, 0.5f)),
+                           __fadd_rn((float)y1, 0.5f));
+    const float ex = __fsub_rn(cx, px), ey = __fsub_rn(cy, py);
+    return __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)) <= rc2;
+}
+
+// Mask of the 8 x 8 blocks of the TW x TH tile with top-left pixel (ox,
+// oy) that hold a pixel passing the cutoff test (blocks clipped to the W x H
+// image): rect_reached per block, with the squared x distance computed once
+// per block column and the squared y distance once per block row (the same
+// operations, so the same decisions).
+template <int TW, int TH>
+__device__ __forceinline__ uint32_t tile_block_mask(float px, float py, float rc2, int ox, int oy,
+                                                    int W, int H)
+{
+    constexpr int BX = TW / 8, BY = TH / 8;
+    const float fx = __fadd_rn(floorf(px), 0.5f), fy = __fadd_rn(floorf(py), 0.5f);
+    float ex2[BX], ey2[BY];
+#pragma unroll
+    for (int bx = 0; bx < BX; ++bx) {
+        const int x0 = ox + 8 * bx;
+        const float c = fminf(fmaxf(fx, __fadd_rn((float)x0, 0.5f)),
+                              __fadd_rn((float)min(x0 + 7, W - 1), 0.5f));
+        const float e = __fsub_rn(c, px);
+        ex2[bx] = x0 < W ? __fmul_rn(e, e) : __int_as_float(0x7f800000); // +inf: outside
+    }
+#pragma unroll
+    for (int by = 0; by < BY; ++by) {
+        const int y0 = oy + 8 * by;
+        const float c = fminf(fmaxf(fy, __fadd_rn((float)y0, 0.5f)),
+                              __fadd_rn((float)min(y0 + 7, H - 1), 0.5f));
+        const float e = __fsub_rn(c, py);
+        ey2[by] = y0 < H ? __fmul_rn(e, e) : __int_as_float(0x7f800000);
+    }
+    uint32_t m = 0;
+#pragma unroll
+    for (int by = 0; by < BY; ++by)
+#pragma unroll
+        for (int bx = 0; bx < BX; ++bx)
+            if (__fadd_rn(ex2[bx], ey2[by]) <= rc2) m |= 1u << (by * BX + bx);
+    return m;
+}
+
+// The clamped pixel box of a splat: [floor(px - rc) - 1, ceil(px + rc)] x
+// (the same in y), clamped to the image; false when it misses the image.
+// Every pixel passing the cutoff test lies inside.
+__device__ __forceinline__ bool pixel_box(float px, float py, float rc, int W, int H, int &x0,
+                                          int &x1, int &y0, int &y1)
+{
+    float xlo = __fsub_rn(floorf(__fsub_rn(px, rc)), 1.0f);
+    float xhi = ceilf(__fadd_rn(px, rc));
+    float ylo = __fsub_rn(floorf(__fsub_rn(py, rc)), 1.0f);
+    float yhi = ceilf(__fadd_rn(py, rc));
+    const float W1 = (float)(W - 1), H1 = (float)(H - 1);
+    if (!(xhi >= 0.0f && xlo <= W1 && yhi >= 0.0f && ylo <= H1)) return false;
+    x0 = (int)(xlo < 0.0f ? 0.0f : xlo);
+    y0 = (int)(ylo < 0.0f ? 0.0f : ylo);
+    x1 = (int)(xhi > W1 ? W1 : xhi);
+    y1 = (int)(yhi > H1 ? H1 : yhi);
+    return true;
+}
+
 // ---- preprocess (k_preprocess.cu)
 // counters[0] += (tile, point-view) pairs, counters[1] += visible point-views;
 // 32-bit words 12 / 13 of counters: min / max depth bits of visible
 // point-views (word 12 must start at 0xffffffff, word 13 at 0).
 // zbits[pv] = fp32 bits of the depth, 0xffffffff for a point-view listing no
 // tile (every finite depth's bits are smaller).
-// rect[pv] = {tx0 | ty0 << 16, tx1 | ty1 << 16, mask, 0}: the tile box and,
-// for a box of at most 32 tiles, bit (ty - ty0) * wx + (tx - tx0) set for
-// each listed tile (wider boxes list every tile).
+// rect[pv] = {px, py, rc (fp32 bits), w}: the splat centre and cutoff
+// radius (the pixel box follows from them by pixel_box), w = the mask of
+// the listed tiles of the box (bit (ty - ty0) * wx + (tx - tx0)) when the
+// box spans at most 32 tiles, else the number of listed tiles.
 void launch_preprocess_fwd(const Batch &b, const DevOpts &o, float4 *rec, uint32_t *zbits,
                            uint32_t *ntiles, uint4 *rect, unsigned long long *counters,
                            cudaStream_t s);
@@ -122,25 +209,28 @@ void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n,
 // Radix sort of (key, value) pairs, stable; n read from device *n_dev,
 // capacity cap.  key_bits: number of low key bits that can be non-zero.
 // Sorted result ends in (keys, vals) (buffers are ping-ponged internally).
-// Keys are ordered by min(key - key_lo, key_max); key_bits = bits of the
-// largest such value.  Digits of up to 9 bits, ceil(key_bits / 9) passes.
-// index_vals: the input values are not read; value i is taken to be i.
+// Keys are ordered by min(key - key_lo, key_max) >> bit_lo; key_bits = bits
+// of the largest such value.  Digits of up to 9 bits, ceil(key_bits / 9)
+// passes.  index_vals: the input values are not read; value i is taken to
+// be i.  bit_lo > 0 needs key_lo = 0 and key_max = 0xffffffff.
 size_t radix_temp_bytes(int64_t cap);
 int radix_passes(int key_bits);
 void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *&keys_alt, uint32_t *&vals_alt,
                       const uint32_t *n_dev, int64_t cap, int key_bits, void *temp,
                       cudaStream_t s, uint32_t key_lo = 0, uint32_t key_max = 0xffffffffu,
-                      bool index_vals = false);
+                      bool index_vals = false, int bit_lo = 0);
 // Scratch of launch_emit_pairs (depth-ordered counts, offsets, scan).
 size_t emit_temp_bytes(int64_t cap_vis);
 // Emits (tile, pv) pairs in depth order: gathers the tile counts in depth
 // order, scans them, then writes each warp's runs cooperatively.
+// Keys are tile << block_bits(tile size) | block mask.
 void launch_emit_pairs(const Batch &b, const DevOpts &o, const uint32_t *sorted_pv,
                        const uint32_t *n_vis, int64_t cap_vis, const uint32_t *ntiles,
                        const uint4 *rect, uint32_t *keys, uint32_t *vals, int64_t cap_pairs,
                        uint32_t *status, void *temp, cudaStream_t s);
+// Ranges of the tiles key >> shift of the sorted keys.
 void launch_tile_ranges(const uint32_t *keys, const uint32_t *n_pairs, int64_t cap_pairs,
-                        uint2 *ranges, uint32_t n_tiles, cudaStream_t s);
+                        uint2 *ranges, uint32_t n_tiles, int shift, cudaStream_t s);
 
 // ---- coarse-to-fine update and kNN (k_refine.cu)
 // Cube grid over a point set: origin lo, cell side h (0 when all points
@@ -247,12 +337,16 @@ void launch_sh_normals(uint64_t seed, int64_t c0, int64_t count, float *out, cud
 // batch_depth 0 = warp-streamed, > 0 = block-staged.  With order/work set
 // (warp-streamed only) the launch is persistent: warps pull (tile,
 // sub-block) items from work[0] (forward) / work[1] (backward) over `order`.
+// keys: the sorted pair keys (their block masks let a warp skip the entries
+// none of its pixels can include); pv_list: the sorted point-view ids.
 void launch_raster_fwd(const Batch &b, const DevOpts &o, int batch_depth, const uint2 *ranges,
-                       const uint32_t *pv_list, const float4 *rec, float *out_rgb,
+                       const uint32_t *keys, const uint32_t *pv_list, const float4 *rec,
+                       float *out_rgb,
                        float *T_final, uint32_t *n_contrib, unsigned long long *stats,
                        cudaStream_t s, const uint4 *order = nullptr, uint32_t *work = nullptr);
 void launch_raster_bwd(const Batch &b, const DevOpts &o, int batch_depth, const uint2 *ranges,
-                       const uint32_t *pv_list, const float4 *rec, const float *T_final,
+                       const uint32_t *keys, const uint32_t *pv_list, const float4 *rec,
+                       const float *T_final,
                        const uint32_t *n_contrib, const float *grad_rgb, float4 *g2d,
                        unsigned long long *stats, cudaStream_t s,
                        const uint4 *order = nullptr, uint32_t *work = nullptr);

@@ -52,6 +52,23 @@ def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30))
 
 
+def _block_bits(tile):
+    n = (tile[0] // 8) * (tile[1] // 8)
+    return n if n > 1 else 0
+
+
+def _check_lists(st, keys, vals, masks, ranges, tile):
+    """The GPU's sorted pair keys (tile << B | 8 x 8 block mask), point-view
+    ids and ranges against the oracle's lists, bit for bit."""
+    sb = _block_bits(tile)
+    gk = st.read("tile_keys")
+    assert np.array_equal(gk >> np.uint32(sb), keys)
+    if sb:
+        assert np.array_equal(gk & np.uint32((1 << sb) - 1), masks.astype(np.uint32))
+    assert np.array_equal(st.read("tile_vals"), vals)
+    assert np.array_equal(st.read("ranges"), ranges)
+
+
 def _small_scene(seed, n=300, deg=2, spread=0.8, r=(0.02, 0.06)):
     rng = np.random.default_rng(seed)
     return dict(pos=rng.uniform(-spread, spread, (n, 3)).astype(np.float32),
@@ -82,11 +99,9 @@ def test_bins_and_records_bit_exact(R, tile):
     cams = [scenes.camera((0.3, 0.2, 2.2), 70, 45), scenes.camera((-1.8, 0.4, 1.5), 33, 57),
             scenes.camera((0.0, 2.0, 0.3), 16, 16)]
     img, st, _ = _gpu_render(R, sc, cams, tile=tile)
-    keys, vals, ranges, recs = O.bin_tiles(sc["pos"], sc["sh"], sc["radius"], sc["deg"], cams,
-                                           tile_w=tile[0], tile_h=tile[1])
-    assert np.array_equal(st.read("tile_keys"), keys)
-    assert np.array_equal(st.read("tile_vals"), vals)
-    assert np.array_equal(st.read("ranges"), ranges)
+    keys, vals, masks, ranges, recs = O.bin_tiles(sc["pos"], sc["sh"], sc["radius"], sc["deg"],
+                                                  cams, tile_w=tile[0], tile_h=tile[1])
+    _check_lists(st, keys, vals, masks, ranges, tile)
     flat = recs.reshape(-1)
     vis = flat["visible"] == 1
     nt = st.read("ntiles")
@@ -102,6 +117,42 @@ def test_bins_and_records_bit_exact(R, tile):
     err = np.abs(img.cpu().numpy() - ref).max()
     print(f"tile {tile}: {len(keys)} pairs bit-exact; image max abs err {err:.3e}")
     assert err <= IMG_TOL
+    st.close()
+
+
+@pytest.mark.parametrize("tile", [(8, 8), (16, 16), (16, 32)])
+@pytest.mark.parametrize("schedule", [dict(), dict(persistent=1), dict(batch_depth=128)],
+                         ids=["streamed", "persistent", "staged"])
+def test_wide_splats_lists_and_image(R, tile, schedule):
+    """Splats whose pixel box spans more than 32 tiles (listed by the
+    per-row walk and emitted by whole warps), some cut by the image border,
+    among small ones: lists and masks bit-exact, image and gradients against
+    the oracle in every compositing schedule."""
+    sc = _small_scene(4, n=250)
+    sc["radius"][:6] = [0.5, 0.35, 0.7, 0.3, 0.45, 0.25]
+    sc["pos"][2] = [0.9, -0.7, 0.2]
+    sc["opacity"][:6] = 0.3
+    cams = [scenes.camera((0.3, 0.2, 2.2), 200, 150), scenes.camera((-1.5, 0.4, 1.5), 151, 117)]
+    img, st, scene = _gpu_render(R, sc, cams, tile=tile, **schedule)
+    keys, vals, masks, ranges, recs = O.bin_tiles(sc["pos"], sc["sh"], sc["radius"], sc["deg"],
+                                                  cams, tile_w=tile[0], tile_h=tile[1])
+    wide = [(r["tx_hi"] - r["tx_lo"] + 1) * (r["ty_hi"] - r["ty_lo"] + 1)
+            for r in recs.reshape(-1) if r["visible"]]
+    assert max(wide) > 32
+    _check_lists(st, keys, vals, masks, ranges, tile)
+    ref, _, _ = O.render(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], cams)
+    err = np.abs(img.cpu().numpy() - ref).max()
+    rng = np.random.default_rng(3)
+    g = rng.normal(size=ref.shape)
+    import torch
+    gpos, gsh, gop = R.backward(st, torch.from_numpy(g.astype(np.float32)).cuda())
+    dpos, dsh, dop = O.backward(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], cams, g)
+    e = (_rel(gpos.cpu().numpy(), dpos), _rel(gsh.cpu().numpy().reshape(dsh.shape), dsh),
+         _rel(gop.cpu().numpy(), dop))
+    print(f"wide splats {tile} {schedule}: {len(keys)} pairs, max box {max(wide)} tiles; image "
+          f"err {err:.3e}; grad rel L2 {e[0]:.2e} {e[1]:.2e} {e[2]:.2e}")
+    assert err <= IMG_TOL
+    assert max(e) <= GRAD_TOL
     st.close()
 
 
@@ -125,12 +176,11 @@ def test_bins_exact_in_both_depth_orderings(R, hidden):
     cams = [scenes.camera((0.2, 0.1, 2.4), 80, 60, fov_deg=60.0),
             scenes.camera((-2.0, 0.5, 1.2), 64, 64, fov_deg=60.0)]
     img, st, scene = _gpu_render(R, sc, cams)
-    keys, vals, ranges, recs = O.bin_tiles(sc["pos"], sc["sh"], sc["radius"], sc["deg"], cams)
+    keys, vals, masks, ranges, recs = O.bin_tiles(sc["pos"], sc["sh"], sc["radius"], sc["deg"],
+                                                  cams)
     vis_frac = float((recs.reshape(-1)["visible"] == 1).mean())
     assert (vis_frac >= 0.75) == (hidden == 0.0), vis_frac
-    assert np.array_equal(st.read("tile_keys"), keys)
-    assert np.array_equal(st.read("tile_vals"), vals)
-    assert np.array_equal(st.read("ranges"), ranges)
+    _check_lists(st, keys, vals, masks, ranges, (16, 16))
     G = pbr.Graph(R, [scene], cams, pbr.default_opts(), backward=False)
     G.launch(pbr.Graph.FORWARD)
     assert G.check()[0]
