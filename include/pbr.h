@@ -84,7 +84,9 @@ typedef struct {
                               Sec. 3.1 Eq. 3; 1: world-frame direction R^T v */
     float cutoff_k;        /* cutoff radius = cutoff_k * s (default 3) */
     float alpha_max;       /* alpha = min(alpha_max, o * G), default 0.99, < 1 */
-    float t_eps;           /* stop once transmittance < t_eps (default 1e-5) */
+    float t_eps;           /* stop once transmittance < t_eps (default 1e-5); values
+                              below 1e-30 act as 1e-30 (T stays a normal fp32 number
+                              for the backward's recovery of T) */
     int32_t max_per_pixel; /* composite at most this many points (0 = no cap) */
     float bg[3];           /* background colour (default 0) */
     float z_near;          /* points with z <= z_near are culled (default 0.01) */
@@ -338,6 +340,15 @@ int pbr_wait(pbr_ctx *ctx, uint64_t req_id, int32_t timeout_ms, int32_t *status)
 int pbr_serve_stats(pbr_ctx *ctx, pbr_serve_stats_t *stats, int32_t reset);
 /* The serving loop's steady clock (seconds), for arrival times. */
 double pbr_now(void);
+/* Device intervals of the batches completed since the loop started (or the
+ * last reset): batch i ran on the GPU from start_ms[i] to end_ms[i]
+ * (milliseconds after the loop's start, measured with CUDA events recorded
+ * on the batch's stream before its first kernel and after its last), with
+ * views[i] views.  Two intervals that intersect are batches whose work was on
+ * the device at the same time.  Fills min(cap, *n) entries of each non-NULL
+ * array; *n receives the number recorded; reset != 0 clears them. */
+int pbr_serve_trace(pbr_ctx *ctx, double *start_ms, double *end_ms, int32_t *views, int32_t cap,
+                    int32_t *n, int32_t reset);
 
 /* --------------------------------------------------- measurement support */
 /* Number of CUDA kernels this library has launched in this process. */

@@ -192,7 +192,12 @@ DevOpts pbr::dev_opts(const pbr_render_opts *o)
     d.dir_frame = o->dir_frame;
     d.cutoff_k = o->cutoff_k;
     d.alpha_max = o->alpha_max;
-    d.t_eps = o->t_eps;
+    // Compositing stops once T falls below t_eps, and never lets T leave the
+    // normal fp32 range: the backward recovers T before each point by
+    // dividing by (1 - alpha), which fails once T has been flushed to zero
+    // (after a few thousand faint layers at t_eps = 0).  What is left behind
+    // T < 1e-30 weighs less than 1e-30 of the colour scale.
+    d.t_eps = o->t_eps > T_EPS_FLOOR ? o->t_eps : T_EPS_FLOOR;
     d.max_per_pixel = o->max_per_pixel;
     for (int i = 0; i < 3; ++i) d.bg[i] = o->bg[i];
     d.z_near = o->z_near;

@@ -67,6 +67,9 @@ struct Batch {
 
 constexpr int PRE_THREADS = 128;
 
+// Smallest transmittance the compositing continues below (see dev_opts).
+constexpr float T_EPS_FLOOR = 1e-30f;
+
 // Stages of a pass, for the optional per-stage CUDA-event timing.
 enum Stage : int {
     STG_PREPROCESS_FWD = 0,

@@ -58,7 +58,8 @@ struct InFlight {
     std::vector<uint64_t> ids;
     std::vector<int32_t> scenes;
     int slot = 0;
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev = nullptr;       // completion (timing) event
+    cudaEvent_t ev_start = nullptr; // recorded on the slot's stream before the batch
     size_t bytes = 0;
 };
 
@@ -90,6 +91,10 @@ struct ServeState {
     std::vector<cudaStream_t> streams;
     std::vector<bool> busy;
     std::vector<InFlight> inflight;
+    // device intervals of completed batches: [start, end) in ms after t0_ev
+    cudaEvent_t t0_ev = nullptr;
+    std::vector<double> trace_start, trace_end;
+    std::vector<int32_t> trace_views;
     // statistics
     std::vector<double> lat_ms;
     int64_t submitted = 0, completed = 0, rejected = 0, batches = 0, views = 0, max_batch = 0;
@@ -124,8 +129,17 @@ void ServeState::finish_ready()
             t_last = t;
         }
         for (int32_t s : b.scenes) scenes[s].refs--;
+        float ms0 = 0.f, ms1 = 0.f;
+        if (t0_ev && b.ev_start && q == cudaSuccess &&
+            cudaEventElapsedTime(&ms0, t0_ev, b.ev_start) == cudaSuccess &&
+            cudaEventElapsedTime(&ms1, t0_ev, b.ev) == cudaSuccess) {
+            trace_start.push_back(ms0);
+            trace_end.push_back(ms1);
+            trace_views.push_back((int32_t)b.ids.size());
+        }
         cudaGetLastError();
         cudaEventDestroy(b.ev);
+        if (b.ev_start) cudaEventDestroy(b.ev_start);
         busy[b.slot] = false;
         in_use -= b.bytes;
         inflight.erase(inflight.begin() + (long)i);
@@ -183,6 +197,12 @@ bool ServeState::launch_one()
         outs.push_back(r.out);
     }
     cudaStream_t s = streams[slot];
+    cudaEvent_t ev_start = nullptr;
+    if (cudaEventCreate(&ev_start) != cudaSuccess || cudaEventRecord(ev_start, s) != cudaSuccess) {
+        if (ev_start) cudaEventDestroy(ev_start);
+        ev_start = nullptr;
+        cudaGetLastError();
+    }
     pbr_state st;
     st.stream = s;
     st.opts = opts;
@@ -200,13 +220,13 @@ bool ServeState::launch_one()
     }
     st.release();
     cudaEvent_t ev = nullptr;
-    if (rc == PBR_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess &&
-        cudaEventRecord(ev, s) == cudaSuccess) {
+    if (rc == PBR_OK && cudaEventCreate(&ev) == cudaSuccess && cudaEventRecord(ev, s) == cudaSuccess) {
         InFlight b;
         b.ids = ids;
         for (uint64_t id : ids) b.scenes.push_back(reqs[id].scene);
         b.slot = slot;
         b.ev = ev;
+        b.ev_start = ev_start;
         b.bytes = bytes;
         busy[slot] = true;
         in_use += bytes;
@@ -217,6 +237,8 @@ bool ServeState::launch_one()
         return true;
     }
     cudaGetLastError();
+    if (ev) cudaEventDestroy(ev);
+    if (ev_start) cudaEventDestroy(ev_start);
     for (uint64_t id : ids) {
         Request &r = reqs[id];
         r.done = true;
@@ -261,6 +283,7 @@ void serve_shutdown(pbr_ctx *c)
     cudaSetDevice(c->device);
     for (auto &kv : S->scenes) cudaFree(kv.second.mem);
     for (cudaStream_t s : S->streams) cudaStreamDestroy(s);
+    if (S->t0_ev) cudaEventDestroy(S->t0_ev);
     delete S;
     c->serve = nullptr;
 }
@@ -289,6 +312,12 @@ extern "C" int pbr_serve_start(pbr_ctx *c, const pbr_render_opts *opts, int32_t 
         }
         S->streams.push_back(s);
         S->busy.push_back(false);
+    }
+    // reference point of the batch trace (pbr_serve_trace)
+    if (cudaEventCreate(&S->t0_ev) != cudaSuccess || cudaEventRecord(S->t0_ev, S->streams[0]) != cudaSuccess) {
+        cudaGetLastError();
+        if (S->t0_ev) cudaEventDestroy(S->t0_ev);
+        S->t0_ev = nullptr;
     }
     c->serve = S;
     S->th = std::thread([S] { S->loop(); });
@@ -483,6 +512,27 @@ extern "C" int pbr_serve_set_budget(pbr_ctx *c, size_t hbm_budget_bytes)
     if (c->serve) {
         std::lock_guard<std::mutex> g(c->serve->mu);
         c->serve->budget = hbm_budget_bytes;
+    }
+    return PBR_OK;
+}
+
+extern "C" int pbr_serve_trace(pbr_ctx *c, double *start_ms, double *end_ms, int32_t *views,
+                               int32_t cap, int32_t *n, int32_t reset)
+{
+    if (!c || !c->serve || !n || cap < 0) return set_error(PBR_ERR_INVALID_ARG, "bad arguments");
+    ServeState *S = c->serve;
+    std::lock_guard<std::mutex> g(S->mu);
+    const int32_t m = (int32_t)S->trace_start.size();
+    *n = m;
+    for (int32_t i = 0; i < m && i < cap; ++i) {
+        if (start_ms) start_ms[i] = S->trace_start[i];
+        if (end_ms) end_ms[i] = S->trace_end[i];
+        if (views) views[i] = S->trace_views[i];
+    }
+    if (reset) {
+        S->trace_start.clear();
+        S->trace_end.clear();
+        S->trace_views.clear();
     }
     return PBR_OK;
 }

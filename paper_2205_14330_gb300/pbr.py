@@ -144,6 +144,8 @@ def lib():
             L.pbr_serve_stats.argtypes = [vp, C.POINTER(ServeStats), i32]
             L.pbr_now.restype = C.c_double
             L.pbr_now.argtypes = []
+            L.pbr_serve_trace.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                          C.POINTER(i32), i32, C.POINTER(i32), i32]
             L.pbr_default_optimizer.argtypes = [C.POINTER(OptimizerCfg)]
             L.pbr_default_optimizer.restype = None
             L.pbr_image_loss_tv.argtypes = [C.POINTER(Camera), i32, vp, vp, i32, C.c_float, vp, vp,
@@ -515,6 +517,17 @@ class Server:
         s = ServeStats()
         check(lib().pbr_serve_stats(self.ctx, C.byref(s), 1 if reset else 0))
         return {k: getattr(s, k) for k, _ in ServeStats._fields_}
+
+    def trace(self, reset=False):
+        """Device intervals of the completed batches: a list of (start_ms,
+        end_ms, views), milliseconds after the loop started."""
+        n = C.c_int32()
+        check(lib().pbr_serve_trace(self.ctx, None, None, None, 0, C.byref(n), 0))
+        m = n.value
+        a, b, v = (C.c_double * max(m, 1))(), (C.c_double * max(m, 1))(), (C.c_int32 * max(m, 1))()
+        check(lib().pbr_serve_trace(self.ctx, a, b, v, m, C.byref(n), 1 if reset else 0))
+        m = min(m, n.value)
+        return [(a[i], b[i], v[i]) for i in range(m)]
 
     def stop(self):
         if self.running:

@@ -1,11 +1,18 @@
 """Batching form: a whole batch of views (several scenes / frames, uneven
 resolutions) captured as CUDA graphs, and the schedule autotuner.  Graph
-replays must reproduce the eager path: the forward bit for bit, gradients
-to the backward's atomic-order tolerance."""
+replays must match the FP64 oracle per frame (images max abs 1e-4,
+gradients and one training update rel L2 1e-3) and reproduce the eager
+path: the forward bit for bit, gradients to the backward's atomic-order
+tolerance."""
 import numpy as np
 import pytest
 
+from oracle import oracle as O
+from oracle import train_ref as TR
 from paper_2205_14330_gb300 import scenes
+
+IMG_TOL = 1e-4
+GRAD_TOL = 1e-3
 
 pytestmark = pytest.mark.gpu
 
@@ -38,6 +45,84 @@ def _rel(a, b):
     a = a.double().cpu().numpy()
     b = b.double().cpu().numpy()
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def _frames(seed=0, n=1500, frames=3):
+    """A small batch shaped like the dynamic-video workload: `frames` frames
+    of one deforming cloud (each a scene), seen by 4 cameras of uneven size
+    (the same cameras in every frame), SH degree 2."""
+    d = scenes.dynamic_video(seed, n=n, frames=frames, n_cams=4, width=64, height=48)
+    rng = np.random.default_rng(seed + 5)
+    rad = scenes.log_uniform(rng, n, 0.02, 0.05)
+    sizes = [(96, 64), (64, 64), (80, 48), (48, 72)]
+    eyes = [(0.0, 0.4, 3.2), (2.6, 0.8, 1.6), (-2.4, 1.2, 1.8), (0.5, 2.8, 1.5)]
+    cams = [scenes.camera(e, w, h) for e, (w, h) in zip(eyes, sizes)]
+    return d["frames"], d["sh"], d["opacity"], rad, d["deg"], cams
+
+
+def _rel_np(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30))
+
+
+@pytest.mark.parametrize("sched", [dict(), dict(persistent=1), dict(tile=(16, 32), persistent=1)],
+                         ids=["streamed", "persistent", "persistent-16x32"])
+def test_graph_frames_match_oracle(env, sched):
+    """FORWARD, STEP (L2 loss + backward) and TRAIN (Eq. 8 objective and an
+    SGD update) replays of a multi-frame batch (frames as scenes,
+    scene_of_view) against the FP64 oracle, frame by frame."""
+    import torch
+    pbr, R = env
+    frames, sh, op, rad, deg, cams = _frames()
+    nf, nc, n, K = len(frames), len(cams), len(rad), (deg + 1) ** 2
+    views = [c for _ in frames for c in cams]
+    sov = [f for f in range(nf) for _ in cams]
+    sc = [pbr.Scene(p, sh, op, rad, deg) for p in frames]
+    rng = np.random.default_rng(9)
+    sh_t = (sh + rng.normal(0, 0.1, sh.shape)).astype(np.float32)
+    tgt = np.concatenate([O.render(p, sh_t, op, rad, deg, cams)[0] for p in frames])
+    G = pbr.Graph(R, sc, views, pbr.default_opts(**sched), scene_of_view=sov,
+                  target=torch.from_numpy(tgt.astype(np.float32)).cuda(), loss="l2")
+    npx = sum(c["width"] * c["height"] for c in cams)  # pixels of one frame
+    refs = [O.render(p, sh, op, rad, deg, cams)[0] for p in frames]
+    G.launch(pbr.Graph.FORWARD)
+    assert G.check()[0]
+    out = G.out.cpu().numpy()
+    err = max(float(np.abs(out[f * npx:(f + 1) * npx] - refs[f]).max()) for f in range(nf))
+    # STEP: dL/dI = 2 (I - target) per frame, adjoint per frame
+    G.launch(pbr.Graph.STEP)
+    assert G.check()[0]
+    gp, gs, go = (G.grad_pos.cpu().numpy(), G.grad_sh.cpu().numpy(),
+                  G.grad_opacity.cpu().numpy())
+    e_step = []
+    for f in range(nf):
+        g_img = 2.0 * (refs[f] - tgt[f * npx:(f + 1) * npx])
+        dpos, dsh, dop = O.backward(frames[f], sh, op, rad, deg, cams, g_img)
+        e_step.append((_rel_np(gp[f * n:(f + 1) * n], dpos),
+                       _rel_np(gs[f * n * K * 3:(f + 1) * n * K * 3].reshape(dsh.shape), dsh),
+                       _rel_np(go[f * n:(f + 1) * n], dop)))
+    # TRAIN: Eq. 8 objective (squared error + 0.01 anisotropic TV per view),
+    # one SGD step moves each frame's parameters by -lr times its gradient
+    lr_pos, lr_sh = 1e-3, 2e-3
+    G.set_optimizer(kind="sgd", lr_pos=lr_pos, lr_sh=lr_sh, lambda_tv=0.01)
+    p0 = [s.pos.clone() for s in sc]
+    h0 = [s.sh.clone() for s in sc]
+    G.launch(pbr.Graph.TRAIN)
+    assert G.check()[0]
+    _, g_all = TR.batch_loss_and_grad(np.concatenate(refs), tgt,
+                                      [(c["width"], c["height"]) for c in views], 0.01, "l2")
+    e_train = []
+    for f in range(nf):
+        dpos, dsh, _ = O.backward(frames[f], sh, op, rad, deg, cams,
+                                  g_all[f * npx:(f + 1) * npx])
+        e_train.append((_rel_np((sc[f].pos - p0[f]).cpu().numpy(), -lr_pos * dpos),
+                        _rel_np((sc[f].sh - h0[f]).cpu().numpy().reshape(dsh.shape),
+                                -lr_sh * dsh)))
+    print(f"graph frames {sched}: image max abs err {err:.3e}; step grad rel L2 (worst frame) "
+          f"{np.max(e_step, 0)}; train update rel L2 {np.max(e_train, 0)}")
+    assert err <= IMG_TOL
+    assert np.max(e_step) <= GRAD_TOL
+    assert np.max(e_train) <= GRAD_TOL
+    G.close()
 
 
 @pytest.mark.parametrize("sched", [dict(), dict(persistent=1), dict(batch_depth=256),

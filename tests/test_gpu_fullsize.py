@@ -1,10 +1,12 @@
-"""Full-size workloads, rendered by the GPU in the launch configuration the
-benchmark times (whole batch in one call, 16x16 tiles, batch depth 256),
-checked against the FP64 oracle on sampled pixels: random pixels plus full
-tiles (one at the ragged bottom-right corner) of a few views.  Gradients
-use a loss masked to the sampled pixels, so the oracle computes the exact
-same gradient; it is compared over every point and over the 64 points with
-the largest gradients."""
+"""Full-size workloads, rendered by the GPU in the launch configurations the
+benchmark's autotuner chooses between (whole batch in one call; 16x16
+tiles one block per tile, and the persistent schedule with 16x16 and 16x32
+tiles), checked against the FP64 oracle on sampled pixels: random pixels
+plus full tiles (one at the ragged bottom-right corner) of a few views.
+Gradients use a loss masked to the sampled pixels, so the oracle computes
+the exact same gradient; it is compared over every point and over the 64
+points with the largest gradients.  The static training workload also gets
+a central finite-difference check of the GPU gradient on 64 points."""
 import numpy as np
 import pytest
 
@@ -31,26 +33,27 @@ def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30))
 
 
+SCHEDULES = [dict(), dict(persistent=1), dict(persistent=1, tile=(16, 32))]
+
+
 def _check(R, scene_list, cams, sov, loss, views, n_random, n_tiles, target_rng=1):
-    """Renders the full batch; compares the sampled pixels of `views` (and
-    the gradients of a loss masked to them) with the oracle."""
+    """Renders the full batch in every schedule of SCHEDULES; compares the
+    sampled pixels of `views` (and the gradients of a loss masked to them)
+    with the oracle."""
     import torch
     from paper_2205_14330_gb300 import pbr
-    opts = pbr.default_opts()
     dscenes = [pbr.Scene(s["pos"], s["sh"], s["opacity"], s["radius"], s["deg"]) for s in scene_list]
-    img, st = R.forward(dscenes, cams, opts, scene_of_view=sov)
     offs = np.cumsum([0] + [c["width"] * c["height"] for c in cams])
     pix = scenes.sample_pixels(cams, n_random=n_random, n_tiles=n_tiles, views=views)
     _, first = np.unique(pix, axis=0, return_index=True)  # each pixel once
     pix = pix[np.sort(first)]
     flat = offs[pix[:, 0]] + pix[:, 2].astype(np.int64) * np.array(
         [cams[v]["width"] for v in pix[:, 0]]) + pix[:, 1]
-    got = img.cpu().numpy()[flat]
     # target: the same pixels rendered by the oracle from perturbed SH
     rng = np.random.default_rng(target_rng)
     g_full = np.zeros((offs[-1], 3), np.float32)
     total_grad = {}
-    max_err = 0.0
+    refs = {}
     for si, sc in enumerate(scene_list):
         sel = [k for k in range(len(pix)) if (sov[pix[k, 0]] if sov else 0) == si]
         if not sel:
@@ -62,34 +65,38 @@ def _check(R, scene_list, cams, sov, loss, views, n_random, n_tiles, target_rng=
         vcams = [cams[v] for v in vlist]
         ref, _, _ = O.render(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], vcams,
                              pix=p)
-        err = float(np.abs(got[sel] - ref).max())
-        max_err = max(max_err, err)
+        refs[si] = (sel, ref)
         tgt = ref + rng.normal(0, 0.05, ref.shape)
         # dL/dI from the oracle's image, fed identically to both backward passes
         g = (np.sign(ref - tgt) if loss == "l1" else 2.0 * (ref - tgt)).astype(np.float32)
         g_full[flat[sel]] = g
         total_grad[si] = O.backward(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"],
                                     vcams, g.astype(np.float64), pix=p)
-    print(f"image max abs err on {len(pix)} sampled pixels: {max_err:.3e}")
-    assert max_err <= IMG_TOL
-    gpos, gsh, gop = R.backward(st, torch.from_numpy(g_full).cuda())
-    gpos, gsh, gop = gpos.cpu().numpy(), gsh.cpu().numpy(), gop.cpu().numpy()
-    pbase = shbase = 0
-    for si, sc in enumerate(scene_list):
-        n, K = len(sc["pos"]), (sc["deg"] + 1) ** 2
-        if si in total_grad:
-            dpos, dsh, dop = total_grad[si]
-            a_pos = gpos[pbase:pbase + n]
-            a_sh = gsh[shbase:shbase + n * K * 3].reshape(n, K, 3)
-            a_op = gop[pbase:pbase + n]
-            top = np.argsort(-np.linalg.norm(dpos, axis=1))[:64]
-            e = dict(pos=_rel(a_pos, dpos), sh=_rel(a_sh, dsh), op=_rel(a_op, dop),
-                     pos64=_rel(a_pos[top], dpos[top]), sh64=_rel(a_sh[top], dsh[top]))
-            print(f"scene {si}: grad rel L2 " + " ".join(f"{k} {v:.2e}" for k, v in e.items()))
-            assert max(e.values()) <= GRAD_TOL
-        pbase += n
-        shbase += n * K * 3
-    st.close()
+    for sched in SCHEDULES:
+        img, st = R.forward(dscenes, cams, pbr.default_opts(**sched), scene_of_view=sov)
+        got = img.cpu().numpy()[flat]
+        max_err = max(float(np.abs(got[sel] - ref).max()) for sel, ref in refs.values())
+        print(f"{sched}: image max abs err on {len(pix)} sampled pixels: {max_err:.3e}")
+        assert max_err <= IMG_TOL
+        gpos, gsh, gop = R.backward(st, torch.from_numpy(g_full).cuda())
+        gpos, gsh, gop = gpos.cpu().numpy(), gsh.cpu().numpy(), gop.cpu().numpy()
+        pbase = shbase = 0
+        for si, sc in enumerate(scene_list):
+            n, K = len(sc["pos"]), (sc["deg"] + 1) ** 2
+            if si in total_grad:
+                dpos, dsh, dop = total_grad[si]
+                a_pos = gpos[pbase:pbase + n]
+                a_sh = gsh[shbase:shbase + n * K * 3].reshape(n, K, 3)
+                a_op = gop[pbase:pbase + n]
+                top = np.argsort(-np.linalg.norm(dpos, axis=1))[:64]
+                e = dict(pos=_rel(a_pos, dpos), sh=_rel(a_sh, dsh), op=_rel(a_op, dop),
+                         pos64=_rel(a_pos[top], dpos[top]), sh64=_rel(a_sh[top], dsh[top]))
+                print(f"{sched} scene {si}: grad rel L2 " +
+                      " ".join(f"{k} {v:.2e}" for k, v in e.items()))
+                assert max(e.values()) <= GRAD_TOL
+            pbase += n
+            shbase += n * K * 3
+        st.close()
 
 
 def test_static_training_step_500k_4x800(R):
@@ -112,3 +119,92 @@ def test_dynamic_30_frames_480_views(R):
     nc = len(d["cams"])
     views = [0 * nc + 3, 17 * nc + 8, 29 * nc + 15]  # three frames, three cameras
     _check(R, frames, cams, sov, "l2", views=views, n_random=384, n_tiles=1)
+
+
+def test_static_finite_differences_64_points(R):
+    """Finite differences of the GPU renderer's own loss on the 500k-point,
+    4 x 800^2 training workload, over the positions of 64 points, against its
+    hand-written gradient (rel L2 1e-3).  Each coordinate a gets a loss of
+    its own: a fixed random weighting of the pixels within 3 sigma of the 64
+    points in the views whose viewing axis has no a component (moving a point
+    along a leaves its depth there unchanged, so the step cannot reorder
+    overlapping splats -- which would be a genuine jump of the image -- and
+    can be large enough for fp32 rounding of the image to stay small against
+    the difference).  Cutoff 8 sigma, no early termination, a 4-point
+    central stencil (error O(h^4)).  The oracle's adjoint of the same losses
+    is compared beside it."""
+    import torch
+    from paper_2205_14330_gb300 import pbr
+    sc = scenes.static_train()
+    cams = sc["cams"]
+    kw = dict(cutoff_k=8.0, t_eps=0.0)
+    opts = pbr.default_opts(persistent=1, **kw)
+    h = np.float32(4e-4)
+    recs, _ = O.preprocess(sc["pos"], sc["sh"], sc["radius"], sc["deg"], cams, **kw)
+    rng = np.random.default_rng(5)
+    inside = np.flatnonzero((recs[0]["visible"] == 1) & (recs[0]["px32"] > 20) &
+                            (recs[0]["px32"] < 780) & (recs[0]["py32"] > 20) &
+                            (recs[0]["py32"] < 780))
+    idx = np.sort(rng.choice(inside, 64, replace=False))
+    offs = np.cumsum([0] + [c["width"] * c["height"] for c in cams])
+    scene = pbr.Scene(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"])
+    grad = np.zeros((len(idx), 3))
+    fd = np.zeros((len(idx), 3))
+    orc = np.zeros((len(idx), 3))
+    n_pix = []
+    for a in range(3):
+        views = [v for v, c in enumerate(cams) if abs(np.asarray(c["R"]).reshape(9)[6 + a]) < 1e-6]
+        assert views
+        pix = set()
+        for v in views:
+            c = cams[v]
+            for i in idx:
+                r = recs[v, i]
+                if not r["visible"]:
+                    continue
+                rad = 3.0 * float(r["s32"])
+                x0, x1 = int(max(0, np.floor(r["px32"] - rad))), int(min(c["width"] - 1, r["px32"] + rad))
+                y0, y1 = int(max(0, np.floor(r["py32"] - rad))), int(min(c["height"] - 1, r["py32"] + rad))
+                for y in range(y0, y1 + 1):
+                    for x in range(x0, x1 + 1):
+                        if (x + 0.5 - r["px32"]) ** 2 + (y + 0.5 - r["py32"]) ** 2 <= rad * rad:
+                            pix.add((v, x, y))
+        pix = np.array(sorted(pix), np.int32)
+        n_pix.append(len(pix))
+        flat = offs[pix[:, 0]] + pix[:, 2].astype(np.int64) * cams[0]["width"] + pix[:, 1]
+        w = rng.normal(size=(len(pix), 3))
+        w_dev = torch.from_numpy(w).cuda()
+        flat_dev = torch.from_numpy(flat).cuda()
+
+        def loss():
+            img, _ = R.forward([scene], cams, opts, keep_state=False)
+            return float((img[flat_dev].double() * w_dev).sum())
+
+        img, st = R.forward([scene], cams, opts)
+        g = torch.zeros((int(offs[-1]), 3), dtype=torch.float32, device="cuda")
+        g[flat_dev] = w_dev.float()
+        gpos, _, _ = R.backward(st, g)
+        st.close()
+        grad[:, a] = gpos.cpu().numpy()[idx, a]
+        with torch.no_grad():
+            for k, i in enumerate(idx):
+                p0 = scene.pos[i, a].item()
+                xs = [np.float32(p0) + m * h for m in (-2, -1, 1, 2)]
+                ls = []
+                for x in xs:
+                    scene.pos[i, a] = float(x)
+                    ls.append(loss())
+                scene.pos[i, a] = p0
+                # the stencil on the fp32 positions the renderer saw
+                step = (float(xs[3]) - float(xs[0])) / 4.0
+                fd[k, a] = (ls[0] - 8.0 * ls[1] + 8.0 * ls[2] - ls[3]) / (12.0 * step)
+        dpos, _, _ = O.backward(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"],
+                                cams, w, pix=pix, **kw)
+        orc[:, a] = dpos[idx, a]
+    e_fd, e_or = _rel(grad, fd), _rel(grad, orc)
+    per = [_rel(grad[:, a], fd[:, a]) for a in range(3)]
+    print(f"static 500k, 64 points, {n_pix} loss pixels (x, y, z): GPU gradient vs 4-point "
+          f"differences rel L2 {e_fd:.2e} (per axis {per[0]:.1e} {per[1]:.1e} {per[2]:.1e}); vs "
+          f"FP64 oracle adjoint {e_or:.2e}; oracle vs differences {_rel(orc, fd):.2e}")
+    assert e_fd <= GRAD_TOL
+    assert e_or <= GRAD_TOL

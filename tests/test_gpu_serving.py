@@ -1,11 +1,14 @@
 """Serving form: resident scenes, continuous batching of mixed-size views,
-admission by HBM budget.  Every request's image must be the same whether it
-is rendered alone (pbr_render_forward) or inside a mixed batch."""
+admission by HBM budget.  Every request's image must match the FP64 oracle
+(max abs 1e-4) and be the same whether it is rendered alone
+(pbr_render_forward) or inside a mixed batch; batches admitted while others
+run must overlap them on the device."""
 import time
 
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_2205_14330_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -48,6 +51,11 @@ def _alone(pbr, R, sc, cam):
     return img
 
 
+def _oracle(sc, cam):
+    rgb, _, _ = O.render(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], [cam])
+    return rgb
+
+
 def test_mixed_batch_equals_alone(env):
     pbr = env
     R = pbr.Renderer(0)
@@ -61,21 +69,37 @@ def test_mixed_batch_equals_alone(env):
     st = sv.stats()
     assert st["completed"] == 24 and st["rejected"] == 0
     assert st["max_batch_views"] > 1  # requests really were batched together
+    worst = 0.0
     for (s, cam), (_, out) in zip(reqs, subs):
         ref = _alone(pbr, R, data[s], cam)
         err = float((out - ref).abs().max())
         assert err <= IMG_TOL, err
+        err_o = float(np.abs(out.cpu().numpy() - _oracle(data[s], cam)).max())
+        assert err_o <= IMG_TOL, err_o
+        worst = max(worst, err_o)
+    print(f"served images (24 requests, batches of up to 16 views): max abs err vs FP64 "
+          f"oracle {worst:.3e}")
     sv.stop()
     R.close()
 
 
 def test_arrivals_while_busy_overlap_and_complete(env):
+    """Requests arriving while batches run are admitted into later batches on
+    the other stream slot: their device intervals (CUDA events around each
+    batch) intersect those of batches still running, every request completes,
+    and its image matches the oracle."""
     pbr = env
     R = pbr.Renderer(0)
     sv = pbr.Server(R, max_batch_views=8, n_streams=2)
     data = _scenes(2)
     ids = [sv.upload(d) for d in data]
-    reqs = _requests(40, seed=3)
+    rng = np.random.default_rng(3)
+    reqs = []
+    for _ in range(40):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        W, H = int(rng.integers(8, 41)) * 16, int(rng.integers(8, 31)) * 16
+        reqs.append((int(rng.integers(0, 3)), scenes.camera(d * rng.uniform(2.5, 4.0), W, H)))
     subs = []
     for k, (s, cam) in enumerate(reqs):
         subs.append(sv.submit(ids[s], cam, arrival=pbr.now()))
@@ -86,8 +110,17 @@ def test_arrivals_while_busy_overlap_and_complete(env):
     st = sv.stats(reset=True)
     assert st["completed"] == 40 and st["batches"] >= 5
     assert st["p99_ms"] >= st["p50_ms"] > 0
+    tr = sv.trace(reset=True)
+    assert len(tr) == st["batches"]
+    overlaps = [(i, j) for i in range(len(tr)) for j in range(i + 1, len(tr))
+                if tr[j][0] < tr[i][1] and tr[i][0] < tr[j][1]]
+    print(f"{len(tr)} batches, {len(overlaps)} pairs overlapping on the device; first "
+          f"intervals (ms) {[(round(a, 3), round(b, 3), v) for a, b, v in tr[:4]]}")
+    assert overlaps, "no two batches were on the device at the same time"
     for (s, cam), (_, out) in list(zip(reqs, subs))[::7]:
-        assert float((out - _alone(pbr, R, data[s], cam)).abs().max()) <= IMG_TOL
+        got = out.cpu().numpy()
+        assert float(np.abs(got - _alone(pbr, R, data[s], cam).cpu().numpy()).max()) <= IMG_TOL
+        assert float(np.abs(got - _oracle(data[s], cam)).max()) <= IMG_TOL
     sv.stop()
     R.close()
 
