@@ -428,81 +428,88 @@ def hull_report(pbr, R, hbm_peak, hbm_src, with_cpu, n_target=200_000, reps=5):
     return out
 
 
+# ------------------------------------------------------------------ roofline
+def stage_roofline(stage_ms, sizes, pairs, param_bytes, grad_bytes, hbm_gbs, fp32_tflops,
+                   ex2_gops, step_ms):
+    """Per-stage roofline of one training step (forward, loss, backward) over
+    the algorithmic work of each stage: bytes the definition must move
+    (one read and one write of every array a stage consumes or produces;
+    sort passes beyond one read and one write are overhead), FP32 flops and
+    MUFU ex2 operations of the compositing stages (composited / contributing
+    pairs x flops per pair).  Roofline time of a stage = max(bytes / HBM,
+    flops / FP32, ex2 / MUFU); step_frac = the stages' roofline times summed
+    over the measured step."""
+    n_pv, n_vis, D, npix = (sizes["n_point_views"], sizes["n_visible"], sizes["n_pairs"],
+                            sizes["n_pixels"])
+    comp, contrib = pairs["fwd_composited"], pairs["bwd_contributing"]
+    work = {
+        # params read once; visible records (32 B) written; depth key and
+        # tile count of every point-view written
+        "preprocess_fwd": (param_bytes + 32 * n_vis + 8 * n_pv, 0, 0),
+        "depth_sort": (16 * n_vis, 0, 0),              # (key, value) read + written
+        "emit_pairs": (8 * D + 12 * n_vis, 0, 0),      # pairs written; counts and ids read
+        "tile_sort": (16 * D, 0, 0),                   # (key, value) read + written
+        "tile_ranges": (4 * D + 8 * sizes["n_tiles"], 0, 0),
+        # records and lists read, image, T and list position written
+        "raster_fwd": (32 * n_vis + 4 * D + 20 * npix, (FLOP_TEST + FLOP_FWD) * comp, comp),
+        # records, lists, grad image, T and positions read, 2D terms written;
+        # ex2 and the reciprocal per contributing pair
+        "raster_bwd": (32 * n_vis + 4 * D + 20 * npix + 28 * n_pv,
+                       (FLOP_TEST + FLOP_BWD) * contrib, 2 * contrib),
+        # 2D terms read, parameter gradients written
+        "preprocess_bwd": (28 * n_pv + grad_bytes, 0, 0),
+    }
+    rows, total = {}, 0.0
+    for k, ms in stage_ms.items():
+        if k not in work:
+            continue
+        b, f, x = work[k]
+        t_b = b / (hbm_gbs * 1e9) * 1e3
+        t_f = f / (fp32_tflops * 1e12) * 1e3 if f else 0.0
+        t_x = x / (ex2_gops * 1e9) * 1e3 if x else 0.0
+        t = max(t_b, t_f, t_x)
+        bound = ["hbm", "fp32", "ex2"][int(np.argmax([t_b, t_f, t_x]))]
+        rows[k] = {"ms": ms, "bytes": int(b), "flops": int(f), "ex2": int(x), "bound": bound,
+                   "roofline_ms": t, "frac": t / ms if ms else None,
+                   "achieved": (b / (ms * 1e-3) / 1e9 if bound == "hbm" else
+                                f / (ms * 1e-3) / 1e12 if bound == "fp32" else
+                                x / (ms * 1e-3) / 1e9),
+                   "unit": {"hbm": "GB/s", "fp32": "TFLOP/s", "ex2": "Gop/s"}[bound]}
+        total += t
+    return {"stages": rows, "roofline_ms": total, "step_ms": step_ms,
+            "step_frac": total / step_ms if step_ms else None,
+            "peaks": {"hbm_gbs": hbm_gbs, "fp32_tflops": fp32_tflops, "ex2_gops": ex2_gops}}
+
+
 # ------------------------------------------------------------------ GPU arm
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batched",
-                    choices=["batched", "static", "tiny", "dynamic"])
-    ap.add_argument("--tile", default="16x16")
-    ap.add_argument("--batch-depth", type=int, default=0,
-                    help="0 = warp-streamed compositing, else block-staged batch size")
-    ap.add_argument("--persistent", type=int, default=0)
-    ap.add_argument("--ref-pixels", type=int, default=2048)
-    ap.add_argument("--cpu-pixels", type=int, default=2048)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
-    ap.add_argument("--no-train", action="store_true")
-    ap.add_argument("--no-refine", action="store_true")
-    ap.add_argument("--no-frame-init", action="store_true")
-    ap.add_argument("--no-hull", action="store_true")
-    ap.add_argument("--refine-points", type=int, default=1_000_000,
-                    help="points of the coarse-to-fine update leg")
-    ap.add_argument("--views", type=int, default=0,
-                    help="use only the first N cameras (a smaller case for profiling)")
-    ap.add_argument("--serve-rates", default="500",
-                    help="comma-separated Poisson arrival rates (req/s); empty = no serving run")
-    ap.add_argument("--serve-seconds", type=float, default=3.0)
-    args = ap.parse_args()
-
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-
-    sc, desc = workload(args.workload)
-    if args.views and "cams" in sc and args.views < len(sc["cams"]):
-        # a smaller case of the same workload (profiling captures)
-        sc["cams"] = sc["cams"][:args.views]
-        desc += f"; first {args.views} cameras only"
-    if args.impl == "reference":
-        if rank == 0:
-            run_reference(args, sc, desc)
-        return
-
-    import torch
-    from paper_2205_14330_gb300 import pbr
-    import __graft_entry__
-    __graft_entry__.build()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:  # independent replicas: every rank renders its own copy of the batch
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-
-    tw, th = (int(x) for x in args.tile.split("x"))
-    opts = pbr.default_opts(tile=(tw, th), batch_depth=args.batch_depth,
-                            persistent=args.persistent)
-    R = pbr.Renderer(local)
-    dev = f"cuda:{local}"
-
+def build_scenes(pbr, torch, sc, dev):
     if "frames" in sc:
         scene_list = [pbr.Scene(p, sc["sh"], sc["opacity"], sc["radius"], sc["deg"], dev)
                       for p in sc["frames"]]
         cams = [c for _ in sc["frames"] for c in sc["cams"]]
         sov = [f for f in range(len(sc["frames"])) for _ in sc["cams"]]
-        n_points = sum(s.n for s in scene_list)
     else:
         scene_list = [pbr.Scene(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], dev)]
         cams, sov = sc["cams"], None
-        n_points = scene_list[0].n
+    return scene_list, cams, sov
+
+
+def measure_workload(args, pbr, torch, R, sc, desc, dist, world, local, headline, alu):
+    """Times the training step of one workload: CUDA-graph replays of the
+    whole step (the value), forward only, the same steps launched eagerly
+    with per-stage CUDA events (stage_ms, roofline), the plain
+    one-view-per-launch renderer and, for the headline workload, the full
+    training iteration and the end-to-end pipeline from host buffers."""
+    dev = f"cuda:{local}"
+    tw, th = (int(x) for x in args.tile.split("x"))
+    opts = pbr.default_opts(tile=(tw, th), batch_depth=args.batch_depth,
+                            persistent=args.persistent)
+    scene_list, cams, sov = build_scenes(pbr, torch, sc, dev)
+    n_points = sum(s.n for s in scene_list)
     npix = pbr.n_pixels(cams)
     mp = npix / 1e6
     loss_kind = "l1" if sc.get("loss") == "l1" else "l2"
+    steps = args.steps if headline else max(2, args.steps // 2)
 
     # target image: the same cameras with perturbed SH coefficients
     rng = np.random.default_rng(1)
@@ -550,26 +557,28 @@ def main():
     G = pbr.Graph(R, scene_list, cams, opts, scene_of_view=sov, target=target, loss=loss_kind)
     for _ in range(max(args.warmup, 0)):
         G.launch(pbr.Graph.STEP)
-    ok, n_pairs_replay, cap_pairs = G.check()
+    ok, _, _ = G.check()
     if not ok:
         G.replan()
+        for _ in range(max(args.warmup, 1)):
+            G.launch(pbr.Graph.STEP)
     clocks = ClockSampler(local)
     launches0 = pbr.kernel_launches()
     clocks.start()
-    ms = timed(lambda: G.launch(pbr.Graph.STEP), args.steps)
+    ms = timed(lambda: G.launch(pbr.Graph.STEP), steps)
     clk = clocks.stop()
     launches = pbr.kernel_launches() - launches0
     ok, _, _ = G.check()
     assert ok, "graph replay outgrew its plan during the timed region"
     value = world * mp / (ms * 1e-3)
-    fwd_ms = timed(lambda: G.launch(pbr.Graph.FORWARD), max(1, args.steps // 2))
+    fwd_ms = timed(lambda: G.launch(pbr.Graph.FORWARD), max(1, steps // 2))
 
     # ---- the paper's full training iteration (Sec. 3.3): forward, squared
     # error + 0.01 anisotropic TV, backward, Adam on positions (8e-4) and SH
     # (3e-3), as one graph replay; it updates the scene in place, so it runs
     # on a copy of the point arrays
     train = None
-    if not args.no_train:
+    if headline and not args.no_train:
         tr_scenes = [pbr.Scene(s.pos.clone(), s.sh.clone(), s.opacity, s.radius, s.deg, dev)
                      for s in scene_list]
         GT = pbr.Graph(R, tr_scenes, cams, opts, scene_of_view=sov, target=target,
@@ -577,7 +586,7 @@ def main():
         GT.set_optimizer(kind="adam", lr_pos=8e-4, lr_sh=3e-3, lambda_tv=0.01)
         for _ in range(max(args.warmup, 1)):
             GT.launch(pbr.Graph.TRAIN)
-        tr_ms = timed(lambda: GT.launch(pbr.Graph.TRAIN), max(1, args.steps // 2))
+        tr_ms = timed(lambda: GT.launch(pbr.Graph.TRAIN), max(1, steps // 2))
         ok_t, _, _ = GT.check()
         train = {"ms_per_step": tr_ms, "mp_s": world * mp / (tr_ms * 1e-3), "valid": bool(ok_t),
                  "objective": "sum of squared errors + 0.01 anisotropic TV (Eq. 8)",
@@ -600,7 +609,7 @@ def main():
         st, _, _ = step()
         states.append(st)
 
-    k_eager = max(2, args.steps // 2)
+    k_eager = max(2, steps // 2)
     eager_ms = timed(train_step, k_eager)
     stage = R.stage_times()
     R.set_stage_timing(False)
@@ -616,10 +625,9 @@ def main():
     opts.no_pair_stats = 1  # the legs below time the uncounted kernels too
 
     # ---- plain single-view renderer: same kernels, one view per launch chain
+    # (a multi-frame batch renders each view from its own frame's scene)
     plain = None
     if not args.no_plain:
-        # one view per launch chain; a multi-frame batch renders each view from
-        # its own frame's scene
         pix_off = np.concatenate([[0], np.cumsum([pbr.n_pixels([c]) for c in cams])])
 
         def scene_for(v):
@@ -633,12 +641,13 @@ def main():
                 _, g = pbr.image_loss(out_v, tgt_v, loss_kind)
                 R.backward(st, g)
                 st.close()
+
         def plain_fwd():
             for v in range(len(cams)):
                 out_v = torch.empty((pbr.n_pixels([cams[v]]), 3), dtype=torch.float32, device=dev)
                 R.forward(scene_for(v), [cams[v]], opts, out=out_v, keep_state=False)
         plain_step()
-        k = max(1, min(3, args.steps // 3))
+        k = max(1, min(3, steps // 3))
         p_ms = timed(plain_step, k)
         pf_ms = timed(plain_fwd, k)
         plain = {"fwd_bwd_mp_s": mp / (p_ms * 1e-3), "fwd_mp_s": mp / (pf_ms * 1e-3),
@@ -646,7 +655,7 @@ def main():
 
     # ---- end to end through the public API with host buffers (graph step)
     e2e = None
-    if not args.no_e2e:
+    if headline and not args.no_e2e:
         host = [[t.detach().cpu().pin_memory() for t in (s.pos, s.sh, s.opacity, s.radius)]
                 for s in scene_list]
         host_tgt = target.cpu().pin_memory()
@@ -667,7 +676,7 @@ def main():
         Gb = pbr.Graph(R, scenes_b, cams, opts, scene_of_view=sov, target=target_b,
                        loss=loss_kind)
         slots = [(G, scene_list, target), (Gb, scenes_b, target_b)]
-        main = torch.cuda.current_stream()
+        main_s = torch.cuda.current_stream()
         cs = torch.cuda.Stream()
 
         def upload(slot, ev):
@@ -692,29 +701,29 @@ def main():
             ev_done = [torch.cuda.Event(), torch.cuda.Event()]
             barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(main)
-            cs.wait_stream(main)
+            e0.record(main_s)
+            cs.wait_stream(main_s)
             upload(0, ev_in[0])
             for it in range(k):
                 s_ = it % 2
-                main.wait_event(ev_in[s_])
+                main_s.wait_event(ev_in[s_])
                 slots[s_][0].launch(pbr.Graph.STEP)
-                ev_done[s_].record(main)
+                ev_done[s_].record(main_s)
                 if it + 1 < k:
                     if it >= 1:
                         cs.wait_event(ev_done[1 - s_])  # step it-1 used the other slot
                     upload(1 - s_, ev_in[1 - s_])
                 cs.wait_event(ev_done[s_])
                 download(s_)
-            main.wait_stream(cs)
-            e1.record(main)
+            main_s.wait_stream(cs)
+            e1.record(main_s)
             barrier()
             return e0.elapsed_time(e1) / k
 
         e2e_run(2)
         # as many steps as the device-resident timed region: the pipeline's
         # fill (first upload) and drain (last download) count once per run
-        e_ms = max_over_ranks(e2e_run(max(2, args.steps)), dist, dev)
+        e_ms = max_over_ranks(e2e_run(max(2, steps)), dist, dev)
         Gb.close()
         e2e = {"value": world * mp / (e_ms * 1e-3), "unit": "MP/s", "ms_per_step": e_ms,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
@@ -724,8 +733,8 @@ def main():
                        "k's download run on a copy stream while step k computes"}
     G.close()
 
-    # ---- roofline of the dominant kernel
-    hbm_peak, hbm_src, peaks = measured_peaks()
+    # ---- roofline of the dominant kernel and of every stage
+    hbm_peak, hbm_src, _ = measured_peaks()
     stage_ms = {k: v[0] / k_eager for k, v in stage.items() if v[1]}
     dom = max(stage_ms, key=stage_ms.get)
     sm_mhz = (clk or {}).get("sm_mhz") or 1500.0
@@ -743,13 +752,120 @@ def main():
                 "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                 "traffic": captured_traffic(dom, sched),
                 "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (sampled)",
+                "peak_measured": alu["fp32_tflops"],
+                "frac_of_measured": achieved / alu["fp32_tflops"],
                 "work": {k: int(v) for k, v in pair_stats.items()}}
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm_peak, "unit": "GB/s",
                 "frac": None, "traffic": None, "peak_source": hbm_src}
+    param_bytes = sum(s.n * (12 + 12 * (s.deg + 1) ** 2 + 8) for s in scene_list)
+    grad_bytes = sum(s.n * (12 + 12 * (s.deg + 1) ** 2 + 4) for s in scene_list)
+    roof["stages"] = stage_roofline(stage_ms, sizes, pair_stats, param_bytes, grad_bytes,
+                                    hbm_peak, alu["fp32_tflops"], alu["ex2_gops"], ms)
+    return dict(desc=desc, value=value, ms=ms, fwd_ms=fwd_ms, eager_ms=eager_ms, mp=mp,
+                n_points=n_points, views=len(cams), sched=sched, tune=tune, train=train,
+                plain=plain, e2e=e2e, stage_ms=stage_ms, roof=roof, clk=clk, launches=launches,
+                steps=steps, pairs={k: int(v) for k, v in pair_stats.items()}, sizes=sizes,
+                loss=loss_kind, img=img, cams=cams, scene_list=scene_list,
+                hbm_peak=hbm_peak, hbm_src=hbm_src)
 
-    # ---- CPU oracle on a bounded sample
-    cpu = None
+
+def image_parity(res, sc, n_pix=256, seed=3):
+    """The bench's own last rendered image against the FP64 oracle on random
+    pixels of view 0: default mode (fp32 screen positions) and all-double."""
+    from oracle import oracle as O
+    cam = res["cams"][0]
+    rng = np.random.default_rng(seed)
+    xs, ys = rng.integers(0, cam["width"], n_pix), rng.integers(0, cam["height"], n_pix)
+    pix = np.stack([np.zeros(n_pix, np.int64), xs, ys], 1).astype(np.int32)
+    got = res["img"][:cam["width"] * cam["height"]].cpu().numpy()[ys * cam["width"] + xs]
+    pos = sc["pos"] if "pos" in sc else sc["frames"][0]
+    out = {"pixels": f"{n_pix} random pixels of view 0"}
+    for key, mode in (("max_abs_err_vs_oracle", 1), ("max_abs_err_vs_all_double", 0)):
+        ref, _, _ = O.render(pos, sc["sh"], sc["opacity"], sc["radius"], sc["deg"], [cam],
+                             pix=pix, screen_fp32=mode)
+        out[key] = float(np.abs(got - ref).max())
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched",
+                    choices=["batched", "static", "tiny", "dynamic"])
+    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--batch-depth", type=int, default=0,
+                    help="0 = warp-streamed compositing, else block-staged batch size")
+    ap.add_argument("--persistent", type=int, default=0)
+    ap.add_argument("--ref-pixels", type=int, default=2048)
+    ap.add_argument("--cpu-pixels", type=int, default=2048)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--no-dynamic", action="store_true",
+                    help="skip the multi-frame video leg (30 frames x 16 views in one batch)")
+    ap.add_argument("--no-refine", action="store_true")
+    ap.add_argument("--no-frame-init", action="store_true")
+    ap.add_argument("--no-hull", action="store_true")
+    ap.add_argument("--refine-points", type=int, default=1_000_000,
+                    help="points of the coarse-to-fine update leg")
+    ap.add_argument("--views", type=int, default=0,
+                    help="use only the first N cameras (a smaller case for profiling)")
+    ap.add_argument("--serve-rates", default="200,500,1000,2000",
+                    help="comma-separated Poisson arrival rates (req/s); empty = no serving run")
+    ap.add_argument("--serve-seconds", type=float, default=4.0)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    sc, desc = workload(args.workload)
+    if args.views and "cams" in sc and args.views < len(sc["cams"]):
+        # a smaller case of the same workload (profiling captures)
+        sc["cams"] = sc["cams"][:args.views]
+        desc += f"; first {args.views} cameras only"
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, sc, desc)
+        return
+
+    import torch
+    from paper_2205_14330_gb300 import pbr
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:  # independent replicas: every rank renders its own copy of the batch
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    R = pbr.Renderer(local)
+    # FP32 and MUFU ex2 rates of this GPU, from the library's own kernels
+    fp32_flops, ex2_ops = pbr.measure_alu_peaks(local)
+    alu = {"fp32_tflops": fp32_flops / 1e12, "ex2_gops": ex2_ops / 1e9}
+
+    res = measure_workload(args, pbr, torch, R, sc, desc, dist, world, local, True, alu)
+
+    dynamic = None
+    if args.workload == "batched" and not args.no_dynamic and not args.views:
+        dsc, ddesc = workload("dynamic")
+        d = measure_workload(args, pbr, torch, R, dsc, ddesc, dist, world, local, False, alu)
+        dynamic = {"workload": ddesc, "views": d["views"], "points": d["n_points"],
+                   "megapixels_per_step": d["mp"], "mp_s": d["value"], "ms_per_step": d["ms"],
+                   "fwd_mp_s": world * d["mp"] / (d["fwd_ms"] * 1e-3), "fwd_ms": d["fwd_ms"],
+                   "plain": d["plain"], "schedule": d["sched"], "stage_ms": d["stage_ms"],
+                   "roofline": d["roof"], "pairs": d["pairs"], "sizes": d["sizes"],
+                   "clocks": d["clk"], "timing": "CUDA-graph replays of the whole step "
+                   "(all 480 views, per-frame gradients) and forward alone"}
+        del d
+
+    # ---- CPU oracle on a bounded sample, and the image's parity against it
+    cpu = parity = None
     if rank == 0 and not args.no_cpu_baseline:
         osc = sc if "frames" not in sc else dict(pos=sc["frames"][0], sh=sc["sh"],
                                                  opacity=sc["opacity"], radius=sc["radius"],
@@ -758,12 +874,14 @@ def main():
         cpu = {"value": px / secs / 1e6, "unit": "MP/s", "cores": threads, "kind": "oracle",
                "sample": f"{px} random pixels of view 0, forward + backward, FP64 brute force "
                          f"over all {osc['pos'].shape[0]} points ({secs:.1f} s)"}
+        parity = image_parity(res, osc)
 
     serving = None
     if rank == 0 and args.serve_rates:
         serving = serving_report(pbr, R, [float(x) for x in args.serve_rates.split(",")],
                                  args.serve_seconds)
 
+    hbm_peak, hbm_src = res["hbm_peak"], res["hbm_src"]
     refine = None
     if rank == 0 and not args.no_refine:
         refine = refine_report(pbr, R, hbm_peak, hbm_src, not args.no_cpu_baseline,
@@ -776,30 +894,32 @@ def main():
         hull = hull_report(pbr, R, hbm_peak, hbm_src, not args.no_cpu_baseline)
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "MP/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        mp, ms, scene_list = res["mp"], res["ms"], res["scene_list"]
+        line = {"metric": METRIC, "value": res["value"], "unit": "MP/s", "n_gpus": world,
+                "steps": res["steps"], "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": desc, "points": n_points, "views": len(cams),
-                           "megapixels_per_step": mp, "schedule": sched, "loss": loss_kind,
+                "config": {"workload": res["desc"], "points": res["n_points"],
+                           "views": res["views"], "megapixels_per_step": mp,
+                           "schedule": res["sched"], "loss": res["loss"],
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2_policy": "inputs larger than L2 (params "
                                         f"{sum(s.pos.numel()+s.sh.numel()+2*s.n for s in scene_list)*4/1e6:.0f} MB, "
-                                        f"images {npix*12/1e6:.0f} MB per step)"},
-                "fwd_mp_s": world * mp / (fwd_ms * 1e-3), "fwd_ms": fwd_ms,
-                "eager_ms_per_step": eager_ms, "eager_mp_s": world * mp / (eager_ms * 1e-3),
-                "schedule": sched, "autotune_ms": tune,
+                                        f"images {mp*12:.0f} MB per step)"},
+                "fwd_mp_s": world * mp / (res["fwd_ms"] * 1e-3), "fwd_ms": res["fwd_ms"],
+                "eager_ms_per_step": res["eager_ms"],
+                "eager_mp_s": world * mp / (res["eager_ms"] * 1e-3),
+                "schedule": res["sched"], "autotune_ms": res["tune"],
                 "timing": "value/fwd: CUDA-graph replays of the whole step; stage_ms and the "
                           "roofline: the same steps launched eagerly with per-stage CUDA events",
-                "train_iteration": train,
-                "plain": plain, "serving": serving, "refine": refine, "frame_init": frame,
-                "visual_hull": hull,
-                "stage_ms": stage_ms,
-                "roofline": roof,
-                "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(launches // max(1, args.steps)),
-                "gpu_launches_timed_region": int(launches), "clocks": clk,
-                "pairs": {k: int(v) for k, v in pair_stats.items()}, "sizes": sizes,
+                "train_iteration": res["train"], "plain": res["plain"], "dynamic": dynamic,
+                "serving": serving, "refine": refine, "frame_init": frame, "visual_hull": hull,
+                "stage_ms": res["stage_ms"], "roofline": res["roof"], "parity": parity,
+                "alu_peaks_measured": alu,
+                "cpu_baseline": cpu, "e2e": res["e2e"],
+                "gpu_launches": int(res["launches"] // max(1, res["steps"])),
+                "gpu_launches_timed_region": int(res["launches"]), "clocks": res["clk"],
+                "pairs": res["pairs"], "sizes": res["sizes"],
                 "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src}
         print(json.dumps(line))
     if dist is not None:
