@@ -306,17 +306,29 @@ __device__ __forceinline__ int queue_take(WarpQueue &q, int &qn, int lane, uint3
     return take;
 }
 
+// Keeps the compiler from fusing the product that produced v into a later
+// add (a product feeding an add can be merged into one fused multiply-add
+// even across __fmul_rn, which changes the rounding of a distance and with
+// it the exact cutoff decision).
+__device__ __forceinline__ float unfused1(float v)
+{
+    asm volatile("" : "+f"(v));
+    return v;
+}
+
 // One composited point, front to back.  Returns true when the pixel stops.
+// Every rounding is explicit: alpha = min(alpha_max, o 2^(q' d2)), weight
+// alpha T, C += weight c (fused), T -= weight.
 __device__ __forceinline__ bool pixel_blend(float d2, const float4 a, const float4 c,
                                             const DevOpts &o, float &T, float &C0, float &C1,
                                             float &C2, uint32_t &cnt)
 {
-    const float alpha = fminf(o.alpha_max, c.x * ex2_approx(d2 * a.w));
-    const float wgt = alpha * T;
+    const float alpha = fminf(o.alpha_max, __fmul_rn(c.x, ex2_approx(__fmul_rn(d2, a.w))));
+    const float wgt = __fmul_rn(alpha, T);
     C0 = fmaf(wgt, c.y, C0);
     C1 = fmaf(wgt, c.z, C1);
     C2 = fmaf(wgt, c.w, C2);
-    T = T - wgt;
+    T = __fsub_rn(T, wgt);
     ++cnt;
     return T < o.t_eps || cnt == (uint32_t)o.max_per_pixel;
 }
@@ -392,7 +404,7 @@ __device__ __forceinline__ float pixel_d2(float ux, float uy, float px, float py
 {
     dx = __fsub_rn(ux, px);
     dy = __fsub_rn(uy, py);
-    return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    return __fadd_rn(unfused1(__fmul_rn(dx, dx)), unfused1(__fmul_rn(dy, dy)));
 }
 
 __device__ __forceinline__ void write_pixel(const PixelGeom &g, const DevOpts &o, float T,
@@ -508,6 +520,19 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
+// Keeps the compiler from fusing the product that produced v into a later
+// packed add (it merges a product feeding a packed add into one packed FMA,
+// even across __fmul_rn, which changes the rounding of a distance and with it
+// the exact cutoff decision).
+__device__ __forceinline__ float2 unfused(float2 v)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+    asm volatile("" : "+l"(r));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+
 // Squared fp32 distances from the lane's two pixel centres (ux, uy.x) and
 // (ux, uy.y) to the splat centre, with the rounding of pixel_d2: dx =
 // ux - px (shared), dy = uy - py, d2 = dx dx + dy dy, each operation rounded
@@ -518,7 +543,7 @@ __device__ __forceinline__ float2 pair_d2(float ux, float2 uy, float px, float p
     dx = __fsub_rn(ux, px);
     dy = add2(uy, f2(-py));
     const float dx2 = __fmul_rn(dx, dx);
-    return add2(f2(dx2), mul2(dy, dy));
+    return add2(unfused(f2(dx2)), unfused(mul2(dy, dy)));
 }
 
 // Forward of one 8 x 8 block by one warp, for the persistent schedule:

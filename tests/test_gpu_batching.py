@@ -2,8 +2,9 @@
 resolutions) captured as CUDA graphs, and the schedule autotuner.  Graph
 replays must match the FP64 oracle per frame (images max abs 1e-4,
 gradients and one training update rel L2 1e-3) and reproduce the eager
-path: the forward bit for bit, gradients to the backward's atomic-order
-tolerance."""
+path of the same schedule: the forward bit for bit, gradients to the
+backward's atomic-order tolerance.  Different schedules composite the same
+points and agree to fp32 rounding (1e-6)."""
 import numpy as np
 import pytest
 
@@ -158,8 +159,11 @@ def test_graph_replay_matches_eager(env, sched):
 @pytest.mark.parametrize("tile", [(16, 16), (8, 8), (16, 32)])
 def test_persistent_matches_streamed_on_a_batch(env, tile):
     """The persistent schedule (tile descriptors over several views and
-    scenes of uneven sizes) against the one-block-per-tile schedule: the
-    same image bit for bit, the same gradients to atomic-order rounding."""
+    scenes of uneven sizes) against the one-block-per-tile schedule: the same
+    composited points at every pixel (identical list positions after the
+    last one), the same image to fp32 rounding (the persistent forward blends
+    a lane's two pixels with packed instructions), the same gradients to
+    atomic-order rounding."""
     import torch
     pbr, R = env
     sc, cams, sov = _batch(pbr, seed=7)
@@ -169,9 +173,10 @@ def test_persistent_matches_streamed_on_a_batch(env, tile):
         img, st = R.forward(sc, cams, pbr.default_opts(tile=tile, persistent=per),
                             scene_of_view=sov)
         _, g = pbr.image_loss(img, target, "l2")
-        out.append((img, R.backward(st, g)))
+        out.append((img, R.backward(st, g), st.read("n_contrib")))
         st.close()
-    assert torch.equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][2], out[1][2])
+    assert float((out[0][0] - out[1][0]).abs().max()) <= 1e-6
     for a, b in zip(out[0][1], out[1][1]):
         assert _rel(b, a) <= 1e-5
 
@@ -228,8 +233,7 @@ def test_autotuner_picks_a_timed_candidate(env):
     again, t2 = pbr.autotune(R, sc, cams, scene_of_view=sov, backward=True, report=False)
     assert (again.tile_w, again.tile_h, again.batch_depth, again.persistent) == \
         (best.tile_w, best.tile_h, best.batch_depth, best.persistent) and t2 == {}
-    # every candidate renders the same image
+    # every candidate renders the same image (to fp32 rounding)
     ref, _ = R.forward(sc, cams, pbr.default_opts(), scene_of_view=sov, keep_state=False)
     img, _ = R.forward(sc, cams, best, scene_of_view=sov, keep_state=False)
-    import torch
-    assert torch.equal(img, ref)
+    assert float((img - ref).abs().max()) <= 1e-6

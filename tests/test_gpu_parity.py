@@ -200,8 +200,10 @@ def test_image_independent_of_tile_size_and_batch_depth(R):
         img, st, _ = _gpu_render(R, sc, cams, tile=tile, batch_depth=depth, persistent=per)
         imgs.append(img.cpu().numpy())
         st.close()
+    # the same composited points everywhere; the persistent forward blends a
+    # lane's two pixels with packed instructions, which agree to fp32 rounding
     for im in imgs[1:]:
-        assert np.array_equal(im, imgs[0])
+        assert np.abs(im - imgs[0]).max() <= 1e-6
 
 
 @pytest.mark.parametrize("per", [0, 1])
