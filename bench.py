@@ -598,24 +598,53 @@ def measure_workload(args, pbr, torch, R, sc, desc, dist, world, local, headline
     # running the kernels the graph replays run (no pair counting); one more
     # eager step counts the pairs
     opts.no_pair_stats = 1
+    opts.bwd_mode = 1  # recompute, as the graphs do
     for _ in range(2):
         st, _, _ = step()
         st.close()
-    R.set_stage_timing(True)
-    R.stage_times()  # reset
     states = []
 
     def train_step():
         st, _, _ = step()
         states.append(st)
 
+    def stage_region():
+        R.set_stage_timing(True)
+        R.stage_times()  # reset
+        t = timed(train_step, k_eager)
+        out = R.stage_times()
+        R.set_stage_timing(False)
+        for s_ in states:
+            s_.close()
+        states.clear()
+        return t, out
+
     k_eager = max(2, steps // 2)
-    eager_ms = timed(train_step, k_eager)
-    stage = R.stage_times()
-    R.set_stage_timing(False)
-    for s_ in states:
-        s_.close()
-    states.clear()
+    eager_ms, stage = stage_region()
+    # the same steps with the backward in store mode: the forward keeps each
+    # pixel's transmittance before its first points instead of the backward
+    # recovering it by division
+    bwd_modes = None
+    if headline:
+        ws_bytes, store_bytes = R.workspace_size(scene_list, cams, opts, scene_of_view=sov)
+        opts.bwd_mode = 2
+        st, _, _ = step()
+        st.close()
+        store_ms, store_stage = stage_region()
+        opts.bwd_mode = 1
+        ws_store, store_list = R.workspace_size(
+            scene_list, cams, pbr.default_opts(tile=(opts.tile_w, opts.tile_h),
+                                               persistent=opts.persistent, bwd_mode=2),
+            scene_of_view=sov)
+        pick = ("raster_fwd", "raster_bwd")
+        bwd_modes = {
+            "recompute": {"ms_per_step": eager_ms, "forward_workspace_bytes": ws_bytes,
+                          **{k: stage[k][0] / k_eager for k in pick if k in stage}},
+            "store": {"ms_per_step": store_ms, "forward_workspace_bytes": ws_store,
+                      "stored_list_bytes": store_list, "store_depth": 32,
+                      **{k: store_stage[k][0] / k_eager for k in pick if k in store_stage}},
+            "timing": "eager steps with per-stage CUDA events (raster_fwd includes writing "
+                      "the list in store mode)"}
     opts.no_pair_stats = 0
     st, _, _ = step()
     pair_stats = st.stats()
@@ -763,6 +792,7 @@ def measure_workload(args, pbr, torch, R, sc, desc, dist, world, local, headline
     roof["stages"] = stage_roofline(stage_ms, sizes, pair_stats, param_bytes, grad_bytes,
                                     hbm_peak, alu["fp32_tflops"], alu["ex2_gops"], ms)
     return dict(desc=desc, value=value, ms=ms, fwd_ms=fwd_ms, eager_ms=eager_ms, mp=mp,
+                bwd_modes=bwd_modes,
                 n_points=n_points, views=len(cams), sched=sched, tune=tune, train=train,
                 plain=plain, e2e=e2e, stage_ms=stage_ms, roof=roof, clk=clk, launches=launches,
                 steps=steps, pairs={k: int(v) for k, v in pair_stats.items()}, sizes=sizes,
@@ -912,7 +942,8 @@ def main():
                 "schedule": res["sched"], "autotune_ms": res["tune"],
                 "timing": "value/fwd: CUDA-graph replays of the whole step; stage_ms and the "
                           "roofline: the same steps launched eagerly with per-stage CUDA events",
-                "train_iteration": res["train"], "plain": res["plain"], "dynamic": dynamic,
+                "train_iteration": res["train"], "plain": res["plain"],
+                "bwd_modes": res["bwd_modes"], "dynamic": dynamic,
                 "serving": serving, "refine": refine, "frame_init": frame, "visual_hull": hull,
                 "stage_ms": res["stage_ms"], "roofline": res["roof"], "parity": parity,
                 "alu_peaks_measured": alu,

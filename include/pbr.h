@@ -102,7 +102,22 @@ typedef struct {
     int32_t no_pair_stats; /* 1: the compositing kernels skip the pair counting
                               that pbr_state_stats reports (as captured graphs
                               always do); 0 (default): count */
-    int32_t reserved[2];
+    int32_t bwd_mode;      /* how the backward pass gets the transmittance T each
+                              pixel had before each composited point (Sec. 3.3
+                              end-to-end gradients need it):
+                              1 recompute: from T after the last point, dividing
+                                by (1 - alpha) back to front (no memory beyond
+                                T_final and the list position per pixel);
+                              2 store: the forward keeps T before each of the
+                                first store_depth composited points of every
+                                pixel (4 store_depth + 4 bytes per pixel; deeper
+                                points fall back to recomputation);
+                              0 auto (default): store when that list takes at
+                                most an eighth of the context's HBM budget, else
+                                recompute.  The block-staged schedule and
+                                captured graphs always recompute. */
+    int32_t store_depth;   /* composited points per pixel whose T is kept in store
+                              mode (0 = default 32; at most 255) */
 } pbr_render_opts;
 
 /* One scene: n points with position [n,3], SH coefficients [n,K,3]
@@ -167,6 +182,24 @@ int pbr_render_forward(pbr_ctx *ctx, const pbr_points *scenes, int32_t n_scenes,
                        const pbr_render_opts *opts, float *out_rgb, pbr_state **state_out,
                        pbr_stream_t stream);
 
+/* Device memory a pbr_render_forward call with these arguments would
+ * allocate, at its peak (the forward state and the call's temporaries), so
+ * that a caller (or the serving loop's admission) can plan by memory.  Runs
+ * the per-point stage once, counting only (it writes no per-point record), to
+ * learn the number of visible point-views and (tile, point-view) pairs of
+ * Sec. 3.2's binning, and synchronises the stream.
+ *   keep_state : 1 = the caller will ask for the state (state_out non-NULL),
+ *                which adds the stored transmittance list when opts->bwd_mode
+ *                resolves to store; 0 = a forward-only call.
+ *   bytes      : receives the peak bytes.
+ *   store_bytes: (nullable) receives the bytes of the stored transmittance
+ *                list alone (0 when the mode resolves to recompute).
+ * Errors as pbr_render_forward. */
+int pbr_forward_workspace_size(pbr_ctx *ctx, const pbr_points *scenes, int32_t n_scenes,
+                               const int32_t *scene_of_view, const pbr_camera *cams,
+                               int32_t n_cams, const pbr_render_opts *opts, int32_t keep_state,
+                               size_t *bytes, size_t *store_bytes, pbr_stream_t stream);
+
 /* Backward pass (Sec. 3.3) for L with dL/dI = grad_rgb (device, packed like
  * out_rgb).  Gradients are OVERWRITTEN, packed over scenes in scene order:
  * grad_pos [sum_s n_s, 3], grad_sh [sum_s n_s K_s 3], grad_opacity [sum_s n_s]
@@ -180,8 +213,10 @@ int pbr_state_info(pbr_state *state, pbr_state_info_t *info);
 
 /* Copies one array of a forward state into host memory (inspection and
  * tests).  which: 0 tile keys (as in pbr_state_info_t), 1 tile values
- * (point-view ids), 2 ranges,
- * 3 records, 4 tile counts, 5 T_final, 6 n_contrib.  Copies
+ * (point-view ids), 2 ranges, 3 records, 4 tile counts, 5 T_final,
+ * 6 n_contrib, 7 the stored transmittances (store mode: [store_depth][n_pixels]
+ * fp32, T before the k-th composited point of each pixel), 8 the number of
+ * points composited per pixel (store mode, u32).  Copies
  * min(cap_bytes, size) bytes; *size_bytes receives the full size.
  * Synchronises the state's stream. */
 int pbr_state_read(pbr_state *state, int32_t which, void *host_dst, size_t cap_bytes,

@@ -182,6 +182,8 @@ int pbr::check_opts(const pbr_render_opts *o)
         return set_error(PBR_ERR_INVALID_ARG, "radius_mode and dir_frame are 0 or 1");
     if (o->no_pair_stats < 0 || o->no_pair_stats > 1)
         return set_error(PBR_ERR_INVALID_ARG, "no_pair_stats is 0 or 1");
+    if (o->bwd_mode < 0 || o->bwd_mode > 2 || o->store_depth < 0 || o->store_depth > 255)
+        return set_error(PBR_ERR_INVALID_ARG, "bwd_mode in 0..2, store_depth in 0..255");
     return PBR_OK;
 }
 
@@ -325,12 +327,27 @@ static int key_bits_for(uint32_t n_keys)
     return b < 1 ? 1 : b;
 }
 
+int32_t pbr::resolve_store_depth(const pbr_ctx *c, const pbr_render_opts *o, int64_t n_pix,
+                                 bool keep_state)
+{
+    if (!keep_state || o->bwd_mode == 1 || o->batch_depth != 0) return 0;
+    const int32_t depth = o->store_depth > 0 ? o->store_depth : 32;
+    if (o->bwd_mode == 2) return depth;
+    return store_bytes(depth, n_pix) <= c->hbm_budget / 8 ? depth : 0;
+}
+
+size_t pbr::store_bytes(int32_t store_depth, int64_t n_pix)
+{
+    return store_depth > 0 ? (size_t)(4 * (int64_t)store_depth + 4) * (size_t)n_pix : 0;
+}
+
 void pbr_state::release()
 {
     void **all[] = {(void **)&d_views, (void **)&d_scenes, (void **)&d_view_list, (void **)&rec,
                     (void **)&ntiles, (void **)&counters, (void **)&tile_keys,
                     (void **)&tile_vals, (void **)&ranges, (void **)&T_final,
-                    (void **)&n_contrib, (void **)&tile_order, (void **)&work};
+                    (void **)&n_contrib, (void **)&tile_order, (void **)&work,
+                    (void **)&T_store, (void **)&n_comp};
     for (void **p : all) {
         dfree(*p, stream);
         *p = nullptr;
@@ -465,6 +482,11 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
         PBR_TRY(dalloc((void **)&st->tile_order, sizeof(uint4) * L.n_tiles, s));
         PBR_TRY(dalloc((void **)&st->work, 64 * sizeof(uint32_t), s));
     }
+    if (st->store_depth > 0) {
+        PBR_TRY(dalloc((void **)&st->T_store,
+                       sizeof(float) * (size_t)st->store_depth * (size_t)L.n_pix, s));
+        PBR_TRY(dalloc((void **)&st->n_comp, sizeof(uint32_t) * L.n_pix, s));
+    }
     {
         StageScope t(c, STG_RASTER_FWD, s);
         if (persist) launch_tile_order(b, st->ranges, L.n_tiles, st->tile_order, st->work, s);
@@ -472,9 +494,87 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
                           st->rec, out_rgb,
                           st->T_final, st->n_contrib,
                           st->opts.no_pair_stats ? nullptr : st->counters + 2, s, st->tile_order,
-                          st->work);
+                          st->work, st->store());
     }
     PBR_CUDA(cudaGetLastError());
+    return PBR_OK;
+}
+
+// The bytes forward_eager allocates (each allocation at least 16 bytes), all
+// alive at its end: the state's buffers, the call's temporaries and, in store
+// mode, the transmittance list.
+static size_t forward_bytes(const HostLayout &L, int64_t n_vis, int64_t n_pairs,
+                            const pbr_render_opts *o, int32_t store_depth)
+{
+    auto al = [](size_t b) { return b ? b : (size_t)16; };
+    const int64_t npv = L.n_pv;
+    const bool direct = n_vis > 0 && 4 * n_vis >= 3 * npv;
+    const int64_t n_sort = direct ? npv : n_vis;
+    const int64_t cap_sort = std::max<int64_t>(n_sort, n_pairs);
+    const size_t temp = std::max(std::max(scan_temp_bytes(npv), radix_temp_bytes(cap_sort)),
+                                 emit_temp_bytes(n_vis));
+    size_t b = al(sizeof(DevView) * L.views.size()) + al(sizeof(DevScene) * L.scenes.size()) +
+               al(sizeof(int32_t) * L.view_list.size());
+    b += al(32 * (size_t)npv) + al(4 * (size_t)npv) + 128;         // records, tile counts, counters
+    b += al(4 * (size_t)npv) + al(16 * (size_t)npv);              // depth bits, rectangles
+    b += (direct ? 0 : al(4 * (size_t)n_sort)) + 3 * al(4 * (size_t)n_sort); // depth sort
+    b += 4 * al(4 * (size_t)n_pairs);                              // pair lists, sort buffers
+    b += al(8 * (size_t)L.n_tiles) + 2 * al(4 * (size_t)L.n_pix);  // ranges, T_final, n_contrib
+    b += al(temp);
+    if (o->persistent && o->batch_depth == 0) b += al(16 * (size_t)L.n_tiles) + 256;
+    if (store_depth > 0)
+        b += al(4 * (size_t)store_depth * (size_t)L.n_pix) + al(4 * (size_t)L.n_pix);
+    return b;
+}
+
+extern "C" int pbr_forward_workspace_size(pbr_ctx *c, const pbr_points *scenes, int32_t n_scenes,
+                                          const int32_t *scene_of_view, const pbr_camera *cams,
+                                          int32_t n_cams, const pbr_render_opts *opts,
+                                          int32_t keep_state, size_t *bytes, size_t *store_out,
+                                          pbr_stream_t stream)
+{
+    if (!c || !bytes) return set_error(PBR_ERR_INVALID_ARG, "ctx or bytes is NULL");
+    PBR_TRY(check_opts(opts));
+    PBR_CUDA(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    HostLayout L;
+    PBR_TRY(build_layout(scenes, n_scenes, scene_of_view, cams, n_cams, opts, L));
+    // the per-point stage, counting only: visible point-views and pairs
+    TempBufs tmp(s);
+    DevView *dv = nullptr;
+    DevScene *ds = nullptr;
+    int32_t *dl = nullptr;
+    unsigned long long *counters = nullptr;
+    PBR_TRY(tmp.alloc(&dv, sizeof(DevView) * L.views.size()));
+    PBR_TRY(tmp.alloc(&ds, sizeof(DevScene) * L.scenes.size()));
+    PBR_TRY(tmp.alloc(&dl, sizeof(int32_t) * L.view_list.size()));
+    PBR_TRY(tmp.alloc(&counters, 128));
+    PBR_CUDA(cudaMemcpyAsync(dv, L.views.data(), sizeof(DevView) * L.views.size(),
+                             cudaMemcpyHostToDevice, s));
+    PBR_CUDA(cudaMemcpyAsync(ds, L.scenes.data(), sizeof(DevScene) * L.scenes.size(),
+                             cudaMemcpyHostToDevice, s));
+    PBR_CUDA(cudaMemcpyAsync(dl, L.view_list.data(), sizeof(int32_t) * L.view_list.size(),
+                             cudaMemcpyHostToDevice, s));
+    PBR_CUDA(cudaMemsetAsync(counters, 0, 128, s));
+    PBR_CUDA(cudaMemsetAsync((char *)counters + 48, 0xff, 4, s));
+    Batch b;
+    b.views = dv;
+    b.scenes = ds;
+    b.view_list = dl;
+    b.n_views = (int32_t)L.views.size();
+    b.n_scenes = (int32_t)L.scenes.size();
+    b.n_pv = L.n_pv;
+    b.n_tiles = L.n_tiles;
+    b.n_pix = L.n_pix;
+    b.n_point_blocks = L.n_point_blocks;
+    launch_preprocess_fwd(b, dev_opts(opts), nullptr, nullptr, nullptr, nullptr, counters, s);
+    PBR_CUDA(cudaGetLastError());
+    unsigned long long host[2] = {0, 0};
+    PBR_CUDA(cudaMemcpyAsync(host, counters, sizeof host, cudaMemcpyDeviceToHost, s));
+    PBR_CUDA(cudaStreamSynchronize(s));
+    const int32_t depth = resolve_store_depth(c, opts, L.n_pix, keep_state != 0);
+    *bytes = forward_bytes(L, (int64_t)host[1], (int64_t)host[0], opts, depth);
+    if (store_out) *store_out = store_bytes(depth, L.n_pix);
     return PBR_OK;
 }
 
@@ -495,6 +595,7 @@ extern "C" int pbr_render_forward(pbr_ctx *c, const pbr_points *scenes, int32_t 
     st->dopts = dev_opts(opts);
     st->batch_depth = opts->batch_depth;
     int rc = build_layout(scenes, n_scenes, scene_of_view, cams, n_cams, opts, st->layout);
+    st->store_depth = resolve_store_depth(c, opts, st->layout.n_pix, state_out != nullptr);
     if (rc == PBR_OK) rc = forward_eager(c, st, out_rgb, s);
     if (rc != PBR_OK || !state_out) {
         st->release();
@@ -526,7 +627,7 @@ extern "C" int pbr_render_backward(pbr_ctx *c, pbr_state *st, const float *grad_
                           st->tile_vals, st->rec,
                           st->T_final, st->n_contrib, grad_rgb, g2d,
                           st->opts.no_pair_stats ? nullptr : st->counters + 2, s,
-                          st->tile_order, st->work);
+                          st->tile_order, st->work, st->store());
     }
     {
         StageScope t(c, STG_PREPROCESS_BWD, s);
@@ -586,6 +687,8 @@ extern "C" int pbr_state_read(pbr_state *st, int32_t which, void *host_dst, size
     case 4: src = st->ntiles; n = 4 * (size_t)L.n_pv; break;
     case 5: src = st->T_final; n = 4 * (size_t)L.n_pix; break;
     case 6: src = st->n_contrib; n = 4 * (size_t)L.n_pix; break;
+    case 7: src = st->T_store; n = 4 * (size_t)st->store_depth * (size_t)L.n_pix; break;
+    case 8: src = st->n_comp; n = st->n_comp ? 4 * (size_t)L.n_pix : 0; break;
     default: return set_error(PBR_ERR_INVALID_ARG, "pbr_state_read: unknown array %d", which);
     }
     if (size_bytes) *size_bytes = n;

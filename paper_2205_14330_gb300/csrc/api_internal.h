@@ -79,6 +79,21 @@ struct pbr_state {
     uint32_t *n_contrib = nullptr;
     uint4 *tile_order = nullptr; // persistent raster: tile descriptors, longest list first
     uint32_t *work = nullptr;       // persistent raster: item counters + buckets
+    // store mode (bwd_mode): T before the first store_depth composited points
+    // of every pixel, and the points composited per pixel
+    int32_t store_depth = 0;
+    float *T_store = nullptr;
+    uint32_t *n_comp = nullptr;
+
+    pbr::StoreBuf store() const
+    {
+        pbr::StoreBuf b;
+        b.T = T_store;
+        b.n = n_comp;
+        b.depth = store_depth;
+        b.n_pix = layout.n_pix;
+        return b;
+    }
 
     pbr::Batch batch() const
     {
@@ -147,6 +162,13 @@ int run_knn(TempBufs &tb, const float *q, int64_t nq, const float *ref, int64_t 
             cudaStream_t s);
 
 int forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s);
+// Composited points per pixel whose T the forward keeps for the backward:
+// 0 = recompute (bwd_mode 1, the block-staged schedule, forward-only calls,
+// or auto when the list would take more than an eighth of the HBM budget).
+int32_t resolve_store_depth(const pbr_ctx *c, const pbr_render_opts *o, int64_t n_pix,
+                            bool keep_state);
+// Bytes of the stored transmittance list for store_depth points per pixel.
+size_t store_bytes(int32_t store_depth, int64_t n_pix);
 
 // Records CUDA events around one stage on stream s when the context has
 // stage timing switched on (pbr_set_stage_timing); otherwise does nothing.

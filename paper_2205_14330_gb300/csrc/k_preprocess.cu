@@ -155,6 +155,11 @@ __device__ void pre_fwd_point(const Batch &b, const DevOpts &o, const DevScene &
                     w = nt;
                 }
                 if (nt == 0) break; // no pixel within reach: not visible
+                ++vis_cnt;
+                pair_cnt += nt;
+                zlo = min(zlo, __float_as_uint(z));
+                zhi = max(zhi, __float_as_uint(z));
+                if (!rec) break; // counting only
                 // view direction (Eq. 3) and colour (Eq. 4)
                 const float inv = rsqrtf(X[0] * X[0] + X[1] * X[1] + z * z);
                 float dx = X[0] * inv, dy = X[1] * inv, dz = z * inv;
@@ -181,12 +186,9 @@ __device__ void pre_fwd_point(const Batch &b, const DevOpts &o, const DevScene &
                 zbits[pv] = __float_as_uint(z);
                 rect[pv] = make_uint4(__float_as_uint(px), __float_as_uint(py),
                                       __float_as_uint(rc), w);
-                ++vis_cnt;
-                pair_cnt += nt;
-                zlo = min(zlo, __float_as_uint(z));
-                zhi = max(zhi, __float_as_uint(z));
             } while (0);
         }
+        if (!rec) continue; // counting only: nothing is written
         ntiles[pv] = nt;
         if (nt == 0) zbits[pv] = 0xffffffffu; // not visible: sorts behind every depth
     }

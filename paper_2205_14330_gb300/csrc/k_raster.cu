@@ -343,16 +343,19 @@ __device__ __forceinline__ float rcp_approx(float x)
 // Branch-free adjoint for a warp-uniform loop: `take` (0 or 1) says whether
 // the point was composited at this pixel; with take = 0 every term is 0 and
 // T, S are unchanged.
+// With has_tb, tb is the stored transmittance before the point (store mode)
+// instead of the one recovered by division.
 __device__ __forceinline__ void pixel_adjoint_masked(float take, float d2, float dx, float dy,
                                                      const float4 a, const float4 c, float amax,
                                                      float g0, float g1, float g2, float &T,
-                                                     float &S, float v[8])
+                                                     float &S, float v[8], bool has_tb = false,
+                                                     float tb = 0.0f)
 {
     const float G = ex2_approx(d2 * a.w);
     const float raw = c.x * G;
     const float alpha = fminf(amax, raw) * take;
     const float rom = rcp_approx(1.0f - alpha);
-    const float Tb = T * rom;
+    const float Tb = has_tb ? tb : T * rom;
     const float wgt = alpha * Tb;
     const float cg = c.y * g0 + c.z * g1 + c.w * g2;
     v[4] = wgt * g0;
@@ -407,6 +410,18 @@ __device__ __forceinline__ float pixel_d2(float ux, float uy, float px, float py
     return __fadd_rn(unfused1(__fmul_rn(dx, dx)), unfused1(__fmul_rn(dy, dy)));
 }
 
+// Index of the pixel in the packed per-pixel arrays (valid when inside).
+__device__ __forceinline__ int64_t pixel_index(const PixelGeom &g)
+{
+    return g.V->pix_base + (int64_t)g.y * g.V->W + g.x;
+}
+
+// Store mode: T before the cnt-th composited point of pixel pix.
+__device__ __forceinline__ void store_T(const StoreBuf &sto, int64_t pix, uint32_t cnt, float T)
+{
+    if (sto.T && cnt < (uint32_t)sto.depth) sto.T[(int64_t)cnt * sto.n_pix + pix] = T;
+}
+
 __device__ __forceinline__ void write_pixel(const PixelGeom &g, const DevOpts &o, float T,
                                             float C0, float C1, float C2, uint32_t last,
                                             float *out_rgb, float *T_final, uint32_t *n_contrib)
@@ -444,7 +459,7 @@ __device__ __forceinline__ void add_stats(unsigned long long *stats, uint32_t a,
 //   phase 2 (per lane): each lane walks only its own included entries.
 // wbuf: this warp's 64 float4 (a-parts, then b-parts of the chunk).
 // g: the lane's pixel and the warp's rectangle; [s, e): the tile's list.
-template <bool STATS = true>
+template <bool STATS, bool STORE>
 __device__ __forceinline__ void fwd_stream_item(const PixelGeom &g, uint32_t s, uint32_t e,
                                                 uint32_t bit, const DevOpts &o, int lane,
                                                 const uint32_t *__restrict__ keys,
@@ -454,11 +469,13 @@ __device__ __forceinline__ void fwd_stream_item(const PixelGeom &g, uint32_t s, 
                                                 float *__restrict__ T_final,
                                                 uint32_t *__restrict__ n_contrib,
                                                 uint32_t &examined_acc, uint32_t &composited_acc,
-                                                float4 *wbuf, uint32_t *wpos, WarpQueue &q)
+                                                float4 *wbuf, uint32_t *wpos, WarpQueue &q,
+                                                const StoreBuf &sto)
 {
     float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     uint32_t cnt = 0, last = 0, examined = 0;
     bool done = !g.inside;
+    const int64_t pix = STORE && g.inside ? pixel_index(g) : 0;
     uint32_t p = s;
     int qn = 0;
     while (!__all_sync(0xffffffffu, done)) {
@@ -499,6 +516,7 @@ __device__ __forceinline__ void fwd_stream_item(const PixelGeom &g, uint32_t s, 
             float dx, dy;
             const float d2 = pixel_d2(g.ux, g.uy, aj.x, aj.y, dx, dy);
             last = wpos[j] + 1;
+            if (STORE) store_T(sto, pix, cnt, T);
             if (pixel_blend(d2, aj, wbuf[32 + j], o, T, C0, C1, C2, cnt)) {
                 done = true;
                 break;
@@ -508,6 +526,7 @@ __device__ __forceinline__ void fwd_stream_item(const PixelGeom &g, uint32_t s, 
     }
     examined_acc += examined;
     composited_acc += cnt;
+    if (STORE && g.inside) sto.n[pix] = cnt;
     write_pixel(g, o, T, C0, C1, C2, last, out_rgb, T_final, n_contrib);
 }
 
@@ -553,7 +572,7 @@ __device__ __forceinline__ float2 pair_d2(float ux, float2 uy, float px, float p
 // serve 64 pixels; every lane tests each hit at both of its pixels, then
 // walks the first pixel's included entries and the second's.  Each pixel's
 // blend sequence is the one-pixel walk's.
-template <bool STATS>
+template <bool STATS, bool STORE>
 __device__ __forceinline__ void fwd_pair_item(const PixelGeom &gA, const PixelGeom &gB,
                                               uint32_t s, uint32_t e, uint32_t bit,
                                               const DevOpts &o, int lane,
@@ -564,8 +583,11 @@ __device__ __forceinline__ void fwd_pair_item(const PixelGeom &gA, const PixelGe
                                               float *__restrict__ T_final,
                                               uint32_t *__restrict__ n_contrib,
                                               uint32_t &examined_acc, uint32_t &composited_acc,
-                                              float4 *wbuf, uint32_t *wpos, WarpQueue &q)
+                                              float4 *wbuf, uint32_t *wpos, WarpQueue &q,
+                                              const StoreBuf &sto)
 {
+    const int64_t pixA = STORE && gA.inside ? pixel_index(gA) : 0;
+    const int64_t pixB = STORE && gB.inside ? pixel_index(gB) : 0;
     float TA = 1.0f, A0 = 0.f, A1 = 0.f, A2 = 0.f;
     float TB = 1.0f, B0 = 0.f, B1 = 0.f, B2 = 0.f;
     uint32_t cntA = 0, cntB = 0, lastA = 0, lastB = 0, examined = 0;
@@ -618,6 +640,7 @@ __device__ __forceinline__ void fwd_pair_item(const PixelGeom &gA, const PixelGe
             float dx, dy;
             const float d2 = pixel_d2(gA.ux, gA.uy, aj.x, aj.y, dx, dy);
             lastA = wpos[j] + 1;
+            if (STORE) store_T(sto, pixA, cntA, TA);
             if (pixel_blend(d2, aj, wbuf[32 + j], o, TA, A0, A1, A2, cntA)) {
                 doneA = true;
                 break;
@@ -630,6 +653,7 @@ __device__ __forceinline__ void fwd_pair_item(const PixelGeom &gA, const PixelGe
             float dx, dy;
             const float d2 = pixel_d2(gB.ux, gB.uy, aj.x, aj.y, dx, dy);
             lastB = wpos[j] + 1;
+            if (STORE) store_T(sto, pixB, cntB, TB);
             if (pixel_blend(d2, aj, wbuf[32 + j], o, TB, B0, B1, B2, cntB)) {
                 doneB = true;
                 break;
@@ -639,6 +663,10 @@ __device__ __forceinline__ void fwd_pair_item(const PixelGeom &gA, const PixelGe
     }
     examined_acc += examined;
     composited_acc += cntA + cntB;
+    if (STORE) {
+        if (gA.inside) sto.n[pixA] = cntA;
+        if (gB.inside) sto.n[pixB] = cntB;
+    }
     write_pixel(gA, o, TA, A0, A1, A2, lastA, out_rgb, T_final, n_contrib);
     write_pixel(gB, o, TB, B0, B1, B2, lastB, out_rgb, T_final, n_contrib);
 }
@@ -660,7 +688,7 @@ constexpr int BWD_PAIR_DIRECT_MAX = 24;
 
 // One warp back-propagates through sub-block `sub` of tile `tile`, taking
 // the entries of its 8 x 8 block (`bit`) from its queue, back to front.
-template <int TW, int TH>
+template <int TW, int TH, bool STORE>
 __device__ __forceinline__ void bwd_stream_item(const Batch &b, const DevOpts &o, uint32_t tile,
                                                 int sub, uint32_t bit, int lane,
                                                 const uint2 *__restrict__ ranges,
@@ -672,14 +700,16 @@ __device__ __forceinline__ void bwd_stream_item(const Batch &b, const DevOpts &o
                                                 const float *__restrict__ grad_rgb,
                                                 float *__restrict__ g2d, uint32_t &examined,
                                                 uint32_t &used, float4 *wbuf, uint32_t *wpv,
-                                                uint32_t *wpos, WarpQueue &q)
+                                                uint32_t *wpos, WarpQueue &q, const StoreBuf &sto)
 {
     const PixelGeom g = pixel_geom<TW, TH>(b, tile, sub, lane);
     const uint32_t s = ranges[tile].x;
     float T = 1.0f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    uint32_t L = 0;
+    uint32_t L = 0, k = 0; // k: composited points not yet visited (store mode)
+    int64_t pix = 0;
     if (g.inside) {
-        const int64_t pix = g.V->pix_base + (int64_t)g.y * g.V->W + g.x;
+        pix = g.V->pix_base + (int64_t)g.y * g.V->W + g.x;
+        if (STORE) k = sto.n[pix];
         T = T_final[pix];
         L = n_contrib[pix];
         g0 = grad_rgb[3 * pix];
@@ -726,8 +756,14 @@ __device__ __forceinline__ void bwd_stream_item(const Batch &b, const DevOpts &o
             const uint32_t cm = __ballot_sync(0xffffffffu, contrib);
             if (cm) {
                 float v[8];
+                bool has_tb = false;
+                float tb = 0.0f;
+                if (STORE && contrib && --k < (uint32_t)sto.depth) {
+                    has_tb = true;
+                    tb = sto.T[(int64_t)k * sto.n_pix + pix];
+                }
                 pixel_adjoint_masked(contrib ? 1.0f : 0.0f, d2, dx, dy, aj, cj, o.alpha_max, g0,
-                                     g1, g2, T, S, v);
+                                     g1, g2, T, S, v, has_tb, tb);
                 if (__popc(cm) > BWD_DIRECT_MAX) {
                     warp_add_terms(v, lane, g2d, wpv[j]);
                 } else if (contrib) { // few pixels: each adds its own terms
@@ -777,9 +813,13 @@ struct BwdPair {
 // whether the point was composited at pixel A / B (0: its terms are 0 and
 // T, S stay).  Returns the sum over the two pixels of the terms {dpx, dpy,
 // dq, do, dr, dg, db} in v[0..6].
+// Bit 0 / 1 of has_tb: tb.x / .y is the stored transmittance before the
+// point at pixel A / B (store mode) instead of the one recovered by
+// division.
 __device__ __forceinline__ void pair_adjoint(float2 take, float2 d2, float dx, float2 dy,
                                              const float4 a, const float4 c, float amax,
-                                             BwdPair &p, float v[8])
+                                             BwdPair &p, float v[8], uint32_t has_tb = 0u,
+                                             float2 tb = {0.0f, 0.0f})
 {
     const float2 e = mul2(d2, f2(a.w));
     const float2 G = make_float2(ex2_approx(e.x), ex2_approx(e.y));
@@ -787,7 +827,9 @@ __device__ __forceinline__ void pair_adjoint(float2 take, float2 d2, float dx, f
     const float2 alpha = mul2(make_float2(fminf(amax, raw.x), fminf(amax, raw.y)), take);
     const float2 om = fma2(alpha, f2(-1.0f), f2(1.0f));
     const float2 rom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
-    const float2 Tb = mul2(p.T, rom);
+    float2 Tb = mul2(p.T, rom);
+    if (has_tb & 1u) Tb.x = tb.x;
+    if (has_tb & 2u) Tb.y = tb.y;
     const float2 wgt = mul2(alpha, Tb);
     const float2 cg = fma2(f2(c.w), p.g2, fma2(f2(c.z), p.g1, mul2(f2(c.y), p.g0)));
     const float2 t4 = mul2(wgt, p.g0), t5 = mul2(wgt, p.g1), t6 = mul2(wgt, p.g2);
@@ -818,7 +860,7 @@ __device__ __forceinline__ void pair_adjoint(float2 take, float2 d2, float dx, f
 // reduction or atomics) serves 64 pixels.  Each pixel's T and S recursions
 // are the one-pixel walk's operations.
 // V, (tx, ty): the tile's view and position; s: the start of its list.
-template <int TW, int TH, bool STATS>
+template <int TW, int TH, bool STATS, bool STORE>
 __device__ __forceinline__ void bwd_pair_item(const DevView *V, int tx, int ty, uint32_t s,
                                               uint32_t bit, const DevOpts &o, int sub, int lane,
                                               const uint32_t *__restrict__ keys,
@@ -829,7 +871,7 @@ __device__ __forceinline__ void bwd_pair_item(const DevView *V, int tx, int ty, 
                                               const float *__restrict__ grad_rgb,
                                               float *__restrict__ g2d, uint32_t &examined,
                                               uint32_t &used, float4 *wbuf, uint32_t *wpv,
-                                              uint32_t *wpos, WarpQueue &q)
+                                              uint32_t *wpos, WarpQueue &q, const StoreBuf &sto)
 {
     const int sx0 = tx * TW + (sub % (TW / 8)) * 8, sy0 = ty * TH + (sub / (TW / 8)) * 8;
     PixelGeom g[2];
@@ -845,6 +887,14 @@ __device__ __forceinline__ void bwd_pair_item(const DevView *V, int tx, int ty, 
     p.g2 = make_float2(pa.g2, pb.g2);
     p.LA = pa.L;
     p.LB = pb.L;
+    // store mode: composited points not yet visited, per pixel
+    const int64_t pixA = STORE && g[0].inside ? pixel_index(g[0]) : 0;
+    const int64_t pixB = STORE && g[1].inside ? pixel_index(g[1]) : 0;
+    uint32_t kA = 0, kB = 0;
+    if (STORE) {
+        if (g[0].inside) kA = sto.n[pixA];
+        if (g[1].inside) kB = sto.n[pixB];
+    }
     const float ux = g[0].ux;
     const float2 uy = make_float2(g[0].uy, g[1].uy);
     const uint32_t wmax = __reduce_max_sync(0xffffffffu, max(pa.L, pb.L));
@@ -891,8 +941,20 @@ __device__ __forceinline__ void bwd_pair_item(const DevView *V, int tx, int ty, 
             const uint32_t cm = __ballot_sync(0xffffffffu, any);
             if (cm) {
                 float v[8];
+                uint32_t has_tb = 0u;
+                float2 tb = make_float2(0.0f, 0.0f);
+                if (STORE) {
+                    if (cA && --kA < (uint32_t)sto.depth) {
+                        has_tb |= 1u;
+                        tb.x = sto.T[(int64_t)kA * sto.n_pix + pixA];
+                    }
+                    if (cB && --kB < (uint32_t)sto.depth) {
+                        has_tb |= 2u;
+                        tb.y = sto.T[(int64_t)kB * sto.n_pix + pixB];
+                    }
+                }
                 pair_adjoint(make_float2(cA ? 1.0f : 0.0f, cB ? 1.0f : 0.0f), d2, dx, dy, aj,
-                             wbuf[32 + j], o.alpha_max, p, v);
+                             wbuf[32 + j], o.alpha_max, p, v, has_tb, tb);
                 if (__popc(cm) > BWD_PAIR_DIRECT_MAX) {
                     warp_add_terms(v, lane, g2d, wpv[j]);
                 } else if (any) { // few lanes: each adds its own terms
@@ -915,13 +977,13 @@ __device__ __forceinline__ uint32_t stream_block_bit(int w)
     return block_bits(TW, TH) ? 1u << (((w / BPR) >> 1) * BPR + w % BPR) : 0u;
 }
 
-template <int TW, int TH>
+template <int TW, int TH, bool STORE>
 __global__ void __launch_bounds__(TW * TH)
 raster_fwd_stream_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
                          const uint32_t *__restrict__ keys, const uint32_t *__restrict__ pv_list,
                          const float4 *__restrict__ rec, float *__restrict__ out_rgb,
                          float *__restrict__ T_final, uint32_t *__restrict__ n_contrib,
-                         unsigned long long *__restrict__ stats)
+                         unsigned long long *__restrict__ stats, StoreBuf sto)
 {
     constexpr int NW = TW * TH / 32;
     __shared__ float4 s_buf[NW][64];
@@ -930,19 +992,21 @@ raster_fwd_stream_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t ex = 0, co = 0;
     const uint2 rg = ranges[blockIdx.x];
-    fwd_stream_item(pixel_geom<TW, TH>(b, blockIdx.x, w, lane), rg.x, rg.y > rg.x ? rg.y : rg.x,
+    fwd_stream_item<true, STORE>(pixel_geom<TW, TH>(b, blockIdx.x, w, lane), rg.x,
+                    rg.y > rg.x ? rg.y : rg.x,
                     stream_block_bit<TW, TH>(w), o, lane, keys, pv_list, rec, out_rgb, T_final,
-                    n_contrib, ex, co, s_buf[w], s_pos[w], s_q[w]);
+                    n_contrib, ex, co, s_buf[w], s_pos[w], s_q[w], sto);
     add_stats(stats, ex, co, lane);
 }
 
-template <int TW, int TH>
+template <int TW, int TH, bool STORE>
 __global__ void __launch_bounds__(TW * TH)
 raster_bwd_stream_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
                          const uint32_t *__restrict__ keys, const uint32_t *__restrict__ pv_list,
                          const float4 *__restrict__ rec, const float *__restrict__ T_final,
                          const uint32_t *__restrict__ n_contrib, const float *__restrict__ grad_rgb,
-                         float *__restrict__ g2d, unsigned long long *__restrict__ stats)
+                         float *__restrict__ g2d, unsigned long long *__restrict__ stats,
+                         StoreBuf sto)
 {
     constexpr int NW = TW * TH / 32;
     __shared__ float4 s_buf[NW][64];
@@ -951,9 +1015,10 @@ raster_bwd_stream_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
     __shared__ WarpQueue s_q[NW];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t ex = 0, us = 0;
-    bwd_stream_item<TW, TH>(b, o, blockIdx.x, w, stream_block_bit<TW, TH>(w), lane, ranges, keys,
+    bwd_stream_item<TW, TH, STORE>(b, o, blockIdx.x, w, stream_block_bit<TW, TH>(w), lane,
+                                   ranges, keys,
                             pv_list, rec, T_final, n_contrib, grad_rgb, g2d, ex, us, s_buf[w],
-                            s_pv[w], s_pos[w], s_q[w]);
+                            s_pv[w], s_pos[w], s_q[w], sto);
     add_stats(stats ? stats + 2 : nullptr, ex, us, lane);
 }
 
@@ -989,14 +1054,14 @@ __device__ __forceinline__ uint4 tile_desc(const Batch &b, const uint2 *ranges, 
 // warps run five blocks per SM (48 registers): 5.84 ms on the 1M-point,
 // 64-view step against 6.05 at four and 6.10 at six.  The backward runs
 // best at its natural four blocks (five: 11.1 -> 11.9 ms).
-template <int TW, int TH, bool STATS>
+template <int TW, int TH, bool STATS, bool STORE>
 __global__ void __launch_bounds__(PERSIST_THREADS, FWD_PERSIST_BLOCKS)
 raster_fwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
                           const uint32_t *__restrict__ keys, const uint32_t *__restrict__ pv_list,
                           const float4 *__restrict__ rec, float *__restrict__ out_rgb,
                           float *__restrict__ T_final, uint32_t *__restrict__ n_contrib,
                           unsigned long long *__restrict__ stats, const uint4 *__restrict__ order,
-                          uint32_t *work)
+                          uint32_t *work, StoreBuf sto)
 {
     constexpr uint32_t SUBS = (TW / 8) * (TH / 8);
     constexpr int NW = PERSIST_THREADS / 32;
@@ -1013,14 +1078,15 @@ raster_fwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
         const int sx0 = (int)(d.y & 0xffffu) * TW + (sub % (TW / 8)) * 8;
         const int sy0 = (int)(d.y >> 16) * TH + (sub / (TW / 8)) * 8;
         const uint32_t bit = block_bits(TW, TH) ? 1u << sub : 0u;
-        fwd_pair_item<STATS>(pixel_geom_at(V, sx0, sy0, lane), pixel_geom_at(V, sx0, sy0 + 4, lane),
+        fwd_pair_item<STATS, STORE>(pixel_geom_at(V, sx0, sy0, lane),
+                                    pixel_geom_at(V, sx0, sy0 + 4, lane),
                              d.z, d.w, bit, o, lane, keys, pv_list, rec, out_rgb, T_final,
-                             n_contrib, ex, co, s_buf[w], s_pos[w], s_q[w]);
+                             n_contrib, ex, co, s_buf[w], s_pos[w], s_q[w], sto);
     }
     if (STATS) add_stats(stats, ex, co, lane);
 }
 
-template <int TW, int TH, bool STATS>
+template <int TW, int TH, bool STATS, bool STORE>
 __global__ void __launch_bounds__(PERSIST_THREADS)
 raster_bwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
                           const uint32_t *__restrict__ keys, const uint32_t *__restrict__ pv_list,
@@ -1028,7 +1094,7 @@ raster_bwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
                           const uint32_t *__restrict__ n_contrib,
                           const float *__restrict__ grad_rgb, float *__restrict__ g2d,
                           unsigned long long *__restrict__ stats, const uint4 *__restrict__ order,
-                          uint32_t *work)
+                          uint32_t *work, StoreBuf sto)
 {
     // 8 x 8 blocks, numbered like the key masks
     constexpr uint32_t SUBS = (TW / 8) * (TH / 8);
@@ -1044,9 +1110,11 @@ raster_bwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
         const uint4 d = order[it / SUBS];
         const int sub = (int)(it % SUBS);
         const uint32_t bit = block_bits(TW, TH) ? 1u << sub : 0u;
-        bwd_pair_item<TW, TH, STATS>(&b.views[d.x], (int)(d.y & 0xffffu), (int)(d.y >> 16), d.z,
+        bwd_pair_item<TW, TH, STATS, STORE>(&b.views[d.x], (int)(d.y & 0xffffu), (int)(d.y >> 16),
+                                            d.z,
                                      bit, o, sub, lane, keys, pv_list, rec, T_final, n_contrib,
-                                     grad_rgb, g2d, ex, us, s_buf[w], s_pv[w], s_pos[w], s_q[w]);
+                                     grad_rgb, g2d, ex, us, s_buf[w], s_pv[w], s_pos[w], s_q[w],
+                                     sto);
     }
     if (STATS) add_stats(stats + 2, ex, us, lane);
 }
@@ -1292,28 +1360,55 @@ int persist_grid(const void *kernel)
     return sms * (per_sm > 0 ? per_sm : 1);
 }
 
+template <int TW, int TH, bool STATS, bool STORE>
+void fwd_persist_launch(const Batch &b, const DevOpts &o, const uint2 *ranges,
+                        const uint32_t *keys, const uint32_t *pv_list, const float4 *rec,
+                        float *out_rgb, float *T_final, uint32_t *n_contrib,
+                        unsigned long long *stats, const uint4 *order, uint32_t *work,
+                        cudaStream_t s, const StoreBuf &sto)
+{
+    static const int grid =
+        persist_grid((const void *)raster_fwd_persist_kernel<TW, TH, STATS, STORE>);
+    raster_fwd_persist_kernel<TW, TH, STATS, STORE><<<grid, PERSIST_THREADS, 0, s>>>(
+        b, o, ranges, keys, pv_list, rec, out_rgb, T_final, n_contrib, stats, order, work, sto);
+}
+
+template <int TW, int TH, bool STATS, bool STORE>
+void bwd_persist_launch(const Batch &b, const DevOpts &o, const uint2 *ranges,
+                        const uint32_t *keys, const uint32_t *pv_list, const float4 *rec,
+                        const float *T_final, const uint32_t *n_contrib, const float *grad_rgb,
+                        float4 *g2d, unsigned long long *stats, const uint4 *order, uint32_t *work,
+                        cudaStream_t s, const StoreBuf &sto)
+{
+    static const int grid =
+        persist_grid((const void *)raster_bwd_persist_kernel<TW, TH, STATS, STORE>);
+    raster_bwd_persist_kernel<TW, TH, STATS, STORE><<<grid, PERSIST_THREADS, 0, s>>>(
+        b, o, ranges, keys, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d, stats,
+        order, work + 1, sto);
+}
+
+// The kernels are instantiated with and without pair counting (STATS) and
+// store mode (STORE), so that the variants the graphs run carry neither.
 template <int TW, int TH>
 void fwd_dispatch(const Batch &b, const DevOpts &o, int depth, const uint2 *ranges,
                   const uint32_t *keys, const uint32_t *pv_list, const float4 *rec,
                   float *out_rgb, float *T_final,
                   uint32_t *n_contrib, unsigned long long *stats, const uint4 *order,
-                  uint32_t *work, cudaStream_t s)
+                  uint32_t *work, cudaStream_t s, const StoreBuf &sto)
 {
+    const bool store = sto.T != nullptr;
     if (depth == 0 && order) {
-        if (stats) {
-            static const int grid =
-                persist_grid((const void *)raster_fwd_persist_kernel<TW, TH, true>);
-            raster_fwd_persist_kernel<TW, TH, true><<<grid, PERSIST_THREADS, 0, s>>>(
-                b, o, ranges, keys, pv_list, rec, out_rgb, T_final, n_contrib, stats, order, work);
-        } else {
-            static const int grid =
-                persist_grid((const void *)raster_fwd_persist_kernel<TW, TH, false>);
-            raster_fwd_persist_kernel<TW, TH, false><<<grid, PERSIST_THREADS, 0, s>>>(
-                b, o, ranges, keys, pv_list, rec, out_rgb, T_final, n_contrib, stats, order, work);
-        }
+        auto f = stats ? (store ? fwd_persist_launch<TW, TH, true, true>
+                                : fwd_persist_launch<TW, TH, true, false>)
+                       : (store ? fwd_persist_launch<TW, TH, false, true>
+                                : fwd_persist_launch<TW, TH, false, false>);
+        f(b, o, ranges, keys, pv_list, rec, out_rgb, T_final, n_contrib, stats, order, work, s,
+          sto);
     } else if (depth == 0) {
-        raster_fwd_stream_kernel<TW, TH><<<b.n_tiles, TW * TH, 0, s>>>(
-            b, o, ranges, keys, pv_list, rec, out_rgb, T_final, n_contrib, stats);
+        auto k = store ? raster_fwd_stream_kernel<TW, TH, true>
+                       : raster_fwd_stream_kernel<TW, TH, false>;
+        k<<<b.n_tiles, TW * TH, 0, s>>>(b, o, ranges, keys, pv_list, rec, out_rgb, T_final,
+                                        n_contrib, stats, sto);
     } else {
         const size_t smem =
             (size_t)depth * (2 * sizeof(float4) + (TW * TH / 32) * sizeof(uint16_t));
@@ -1333,25 +1428,21 @@ void bwd_dispatch(const Batch &b, const DevOpts &o, int depth, const uint2 *rang
                   const float *T_final,
                   const uint32_t *n_contrib, const float *grad_rgb, float4 *g2d,
                   unsigned long long *stats, const uint4 *order, uint32_t *work,
-                  cudaStream_t s)
+                  cudaStream_t s, const StoreBuf &sto)
 {
+    const bool store = sto.T != nullptr;
     if (depth == 0 && order) {
-        if (stats) {
-            static const int grid =
-                persist_grid((const void *)raster_bwd_persist_kernel<TW, TH, true>);
-            raster_bwd_persist_kernel<TW, TH, true><<<grid, PERSIST_THREADS, 0, s>>>(
-                b, o, ranges, keys, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d,
-                stats, order, work + 1);
-        } else {
-            static const int grid =
-                persist_grid((const void *)raster_bwd_persist_kernel<TW, TH, false>);
-            raster_bwd_persist_kernel<TW, TH, false><<<grid, PERSIST_THREADS, 0, s>>>(
-                b, o, ranges, keys, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d,
-                stats, order, work + 1);
-        }
+        auto f = stats ? (store ? bwd_persist_launch<TW, TH, true, true>
+                                : bwd_persist_launch<TW, TH, true, false>)
+                       : (store ? bwd_persist_launch<TW, TH, false, true>
+                                : bwd_persist_launch<TW, TH, false, false>);
+        f(b, o, ranges, keys, pv_list, rec, T_final, n_contrib, grad_rgb, g2d, stats, order, work,
+          s, sto);
     } else if (depth == 0) {
-        raster_bwd_stream_kernel<TW, TH><<<b.n_tiles, TW * TH, 0, s>>>(
-            b, o, ranges, keys, pv_list, rec, T_final, n_contrib, grad_rgb, (float *)g2d, stats);
+        auto k = store ? raster_bwd_stream_kernel<TW, TH, true>
+                       : raster_bwd_stream_kernel<TW, TH, false>;
+        k<<<b.n_tiles, TW * TH, 0, s>>>(b, o, ranges, keys, pv_list, rec, T_final, n_contrib,
+                                        grad_rgb, (float *)g2d, stats, sto);
     } else {
         const size_t smem = (size_t)depth * (4 * sizeof(float4) + sizeof(uint32_t) +
                                              (TW * TH / 32) * sizeof(uint16_t));
@@ -1388,36 +1479,36 @@ void launch_raster_fwd(const Batch &b, const DevOpts &o, int depth, const uint2 
                        const uint32_t *keys, const uint32_t *pv_list, const float4 *rec,
                        float *out_rgb, float *T_final, uint32_t *n_contrib,
                        unsigned long long *stats, cudaStream_t s, const uint4 *order,
-                       uint32_t *work)
+                       uint32_t *work, const StoreBuf &sto)
 {
     if (b.n_tiles == 0) return;
     if (o.tile_w == 8 && o.tile_h == 8)
         fwd_dispatch<8, 8>(b, o, depth, ranges, keys, pv_list, rec, out_rgb, T_final, n_contrib,
-                           stats, order, work, s);
+                           stats, order, work, s, sto);
     else if (o.tile_w == 16 && o.tile_h == 32)
         fwd_dispatch<16, 32>(b, o, depth, ranges, keys, pv_list, rec, out_rgb, T_final,
-                             n_contrib, stats, order, work, s);
+                             n_contrib, stats, order, work, s, sto);
     else
         fwd_dispatch<16, 16>(b, o, depth, ranges, keys, pv_list, rec, out_rgb, T_final,
-                             n_contrib, stats, order, work, s);
+                             n_contrib, stats, order, work, s, sto);
 }
 
 void launch_raster_bwd(const Batch &b, const DevOpts &o, int depth, const uint2 *ranges,
                        const uint32_t *keys, const uint32_t *pv_list, const float4 *rec,
                        const float *T_final, const uint32_t *n_contrib, const float *grad_rgb,
                        float4 *g2d, unsigned long long *stats, cudaStream_t s,
-                       const uint4 *order, uint32_t *work)
+                       const uint4 *order, uint32_t *work, const StoreBuf &sto)
 {
     if (b.n_tiles == 0) return;
     if (o.tile_w == 8 && o.tile_h == 8)
         bwd_dispatch<8, 8>(b, o, depth, ranges, keys, pv_list, rec, T_final, n_contrib, grad_rgb,
-                           g2d, stats, order, work, s);
+                           g2d, stats, order, work, s, sto);
     else if (o.tile_w == 16 && o.tile_h == 32)
         bwd_dispatch<16, 32>(b, o, depth, ranges, keys, pv_list, rec, T_final, n_contrib,
-                             grad_rgb, g2d, stats, order, work, s);
+                             grad_rgb, g2d, stats, order, work, s, sto);
     else
         bwd_dispatch<16, 16>(b, o, depth, ranges, keys, pv_list, rec, T_final, n_contrib,
-                             grad_rgb, g2d, stats, order, work, s);
+                             grad_rgb, g2d, stats, order, work, s, sto);
 }
 
 } // namespace pbr

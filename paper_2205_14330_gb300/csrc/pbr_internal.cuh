@@ -192,6 +192,7 @@ __device__ __forceinline__ bool pixel_box(float px, float py, float rc, int W, i
 // radius (the pixel box follows from them by pixel_box), w = the mask of
 // the listed tiles of the box (bit (ty - ty0) * wx + (tx - tx0)) when the
 // box spans at most 32 tiles, else the number of listed tiles.
+// rec == nullptr: counting only (the counters; nothing else is written).
 void launch_preprocess_fwd(const Batch &b, const DevOpts &o, float4 *rec, uint32_t *zbits,
                            uint32_t *ntiles, uint4 *rect, unsigned long long *counters,
                            cudaStream_t s);
@@ -337,22 +338,37 @@ void launch_hull_take(const float *cand, const uint32_t *flags, const uint32_t *
 void launch_sh_normals(uint64_t seed, int64_t c0, int64_t count, float *out, cudaStream_t s);
 
 // ---- raster (k_raster.cu)
+// Store mode (bwd_mode 2): T[k * n_pix + pix] = the transmittance pixel pix
+// had before its k-th composited point (k < depth), n[pix] = the points it
+// composited.  T == nullptr: recompute mode (the backward recovers T by
+// dividing by 1 - alpha back to front).
+struct StoreBuf {
+    float *T = nullptr;
+    uint32_t *n = nullptr;
+    int32_t depth = 0;
+    int64_t n_pix = 0;
+};
+
 // batch_depth 0 = warp-streamed, > 0 = block-staged.  With order/work set
 // (warp-streamed only) the launch is persistent: warps pull (tile,
 // sub-block) items from work[0] (forward) / work[1] (backward) over `order`.
 // keys: the sorted pair keys (their block masks let a warp skip the entries
 // none of its pixels can include); pv_list: the sorted point-view ids.
+// sto: store mode's buffers (the warp-streamed and persistent schedules;
+// the block-staged one always recomputes).
 void launch_raster_fwd(const Batch &b, const DevOpts &o, int batch_depth, const uint2 *ranges,
                        const uint32_t *keys, const uint32_t *pv_list, const float4 *rec,
                        float *out_rgb,
                        float *T_final, uint32_t *n_contrib, unsigned long long *stats,
-                       cudaStream_t s, const uint4 *order = nullptr, uint32_t *work = nullptr);
+                       cudaStream_t s, const uint4 *order = nullptr, uint32_t *work = nullptr,
+                       const StoreBuf &sto = StoreBuf());
 void launch_raster_bwd(const Batch &b, const DevOpts &o, int batch_depth, const uint2 *ranges,
                        const uint32_t *keys, const uint32_t *pv_list, const float4 *rec,
                        const float *T_final,
                        const uint32_t *n_contrib, const float *grad_rgb, float4 *g2d,
                        unsigned long long *stats, cudaStream_t s,
-                       const uint4 *order = nullptr, uint32_t *work = nullptr);
+                       const uint4 *order = nullptr, uint32_t *work = nullptr,
+                       const StoreBuf &sto = StoreBuf());
 // Longest-first tile order for the persistent raster, as tile descriptors
 // {view, tx | ty << 16, list start, list end}; work: 34 u32 words.
 void launch_tile_order(const Batch &b, const uint2 *ranges, uint32_t n_tiles, uint4 *order,

@@ -43,7 +43,8 @@ class Opts(C.Structure):
                 ("alpha_max", C.c_float), ("t_eps", C.c_float), ("max_per_pixel", C.c_int32),
                 ("bg", C.c_float * 3), ("z_near", C.c_float), ("tile_w", C.c_int32),
                 ("tile_h", C.c_int32), ("batch_depth", C.c_int32), ("persistent", C.c_int32),
-                ("no_pair_stats", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("no_pair_stats", C.c_int32), ("bwd_mode", C.c_int32),
+                ("store_depth", C.c_int32)]
 
 
 class Points(C.Structure):
@@ -114,6 +115,10 @@ def lib():
             L.pbr_render_forward.argtypes = [vp, C.POINTER(Points), i32, vp, C.POINTER(Camera),
                                              i32, C.POINTER(Opts), vp, C.POINTER(vp), vp]
             L.pbr_render_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+            L.pbr_forward_workspace_size.argtypes = [vp, C.POINTER(Points), i32, vp,
+                                                     C.POINTER(Camera), i32, C.POINTER(Opts), i32,
+                                                     C.POINTER(C.c_size_t), C.POINTER(C.c_size_t),
+                                                     vp]
             L.pbr_state_free.argtypes = [vp, vp]
             L.pbr_state_info.argtypes = [vp, C.POINTER(StateInfo)]
             L.pbr_state_read.argtypes = [vp, i32, vp, C.c_size_t, C.POINTER(C.c_size_t)]
@@ -264,7 +269,7 @@ class State:
 
     ARRAYS = {"tile_keys": (0, np.uint32), "tile_vals": (1, np.uint32), "ranges": (2, np.uint32),
               "records": (3, np.float32), "ntiles": (4, np.uint32), "T_final": (5, np.float32),
-              "n_contrib": (6, np.uint32)}
+              "n_contrib": (6, np.uint32), "T_store": (7, np.float32), "n_comp": (8, np.uint32)}
 
     def read(self, name: str) -> np.ndarray:
         """Host copy of one state array (see pbr_state_read)."""
@@ -345,6 +350,21 @@ class Renderer:
                                        C.byref(opts), _ptr(out), C.byref(h) if keep_state else None,
                                        _stream()))
         return out, (State(self, h, scenes) if keep_state else None)
+
+    def workspace_size(self, scenes, cams, opts=None, scene_of_view=None, keep_state=True):
+        """(peak device bytes of forward(...) with these arguments, bytes of its
+        stored transmittance list) -- pbr_forward_workspace_size."""
+        scenes = scenes if isinstance(scenes, (list, tuple)) else [scenes]
+        opts = opts or default_opts()
+        pts = (Points * len(scenes))(*[s.points() for s in scenes])
+        sov = None
+        if scene_of_view is not None:
+            sov = (C.c_int32 * len(cams))(*[int(x) for x in scene_of_view])
+        b, sb = C.c_size_t(), C.c_size_t()
+        check(lib().pbr_forward_workspace_size(self.ctx, pts, len(scenes), sov, make_cameras(cams),
+                                               len(cams), C.byref(opts), 1 if keep_state else 0,
+                                               C.byref(b), C.byref(sb), _stream()))
+        return b.value, sb.value
 
     def backward(self, state: State, grad_rgb, want_opacity=True):
         """Gradients (packed over the state's scenes) for dL/dimage = grad_rgb."""
