@@ -214,7 +214,7 @@ int pbr_state_info(pbr_state *state, pbr_state_info_t *info);
 /* Copies one array of a forward state into host memory (inspection and
  * tests).  which: 0 tile keys (as in pbr_state_info_t), 1 tile values
  * (point-view ids), 2 ranges, 3 records, 4 tile counts, 5 T_final,
- * 6 n_contrib, 7 the stored transmittances (store mode: [store_depth][n_pixels]
+ * 6 n_contrib, 7 the stored transmittances (store mode: [n_pixels][store_depth]
  * fp32, T before the k-th composited point of each pixel), 8 the number of
  * points composited per pixel (store mode, u32).  Copies
  * min(cap_bytes, size) bytes; *size_bytes receives the full size.

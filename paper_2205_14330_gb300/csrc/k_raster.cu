@@ -419,7 +419,7 @@ __device__ __forceinline__ int64_t pixel_index(const PixelGeom &g)
 // Store mode: T before the cnt-th composited point of pixel pix.
 __device__ __forceinline__ void store_T(const StoreBuf &sto, int64_t pix, uint32_t cnt, float T)
 {
-    if (sto.T && cnt < (uint32_t)sto.depth) sto.T[(int64_t)cnt * sto.n_pix + pix] = T;
+    if (sto.T && cnt < (uint32_t)sto.depth) sto.T[pix * sto.depth + cnt] = T;
 }
 
 __device__ __forceinline__ void write_pixel(const PixelGeom &g, const DevOpts &o, float T,
@@ -568,10 +568,12 @@ __device__ __forceinline__ float2 pair_d2(float ux, float2 uy, float px, float p
 // Forward of one 8 x 8 block by one warp, for the persistent schedule:
 // lane l owns the pixels (l & 7, l >> 3) and (l & 7, 4 + (l >> 3)), gA and
 // gB.  The warp takes the tile list's entries with its block's bit (`bit`)
-// 32 at a time from its queue; the per-chunk staging, culling and ballots
-// serve 64 pixels; every lane tests each hit at both of its pixels, then
-// walks the first pixel's included entries and the second's.  Each pixel's
-// blend sequence is the one-pixel walk's.
+// 32 at a time from its queue, culls them against the rectangle of its
+// active pixels and stages the hits; then it steps through the hits in list
+// order, every lane testing and blending the point at both of its pixels at
+// once (packed fp32x2, .x pixel A, .y pixel B), with the blend of a pixel
+// the point does not include (or that has stopped) masked to zero weight.
+// Each pixel's blend sequence and roundings are the one-pixel walk's.
 template <bool STATS, bool STORE>
 __device__ __forceinline__ void fwd_pair_item(const PixelGeom &gA, const PixelGeom &gB,
                                               uint32_t s, uint32_t e, uint32_t bit,
@@ -588,12 +590,12 @@ __device__ __forceinline__ void fwd_pair_item(const PixelGeom &gA, const PixelGe
 {
     const int64_t pixA = STORE && gA.inside ? pixel_index(gA) : 0;
     const int64_t pixB = STORE && gB.inside ? pixel_index(gB) : 0;
-    float TA = 1.0f, A0 = 0.f, A1 = 0.f, A2 = 0.f;
-    float TB = 1.0f, B0 = 0.f, B1 = 0.f, B2 = 0.f;
+    float2 T = f2(1.0f), C0 = f2(0.0f), C1 = f2(0.0f), C2 = f2(0.0f);
     uint32_t cntA = 0, cntB = 0, lastA = 0, lastB = 0, examined = 0;
     bool doneA = !gA.inside, doneB = !gB.inside;
     const PixelGeom g2[2] = {gA, gB};
     const float2 uy2 = make_float2(gA.uy, gB.uy);
+    const uint32_t cmax = (uint32_t)o.max_per_pixel;
     uint32_t p = s;
     int qn = 0;
     while (!__all_sync(0xffffffffu, doneA && doneB)) {
@@ -608,10 +610,7 @@ __device__ __forceinline__ void fwd_pair_item(const PixelGeom &gA, const PixelGe
         const bool act[2] = {!doneA, !doneB};
         const PixelGeom ar = active_rect_rows<2>(g2, act);
         const bool hit = valid && disc_meets_rect(a, ar);
-        const bool covers = hit && disc_covers_rect(a, ar);
         uint32_t m = __ballot_sync(0xffffffffu, hit);
-        // entries whose disc holds every active pixel need no per-pixel test
-        const uint32_t full = __ballot_sync(0xffffffffu, covers);
         if (hit) {
             wbuf[lane] = a;
             wbuf[32 + lane] = __ldg(rec + 2 * (size_t)pv + 1);
@@ -619,8 +618,6 @@ __device__ __forceinline__ void fwd_pair_item(const PixelGeom &gA, const PixelGe
         }
         __syncwarp();
         if (STATS) examined += (uint32_t)__popc(m) * ((uint32_t)!doneA + (uint32_t)!doneB);
-        uint32_t mA = full, mB = full;
-        m &= ~full;
         while (m) {
             const int j = __ffs(m) - 1;
             m &= m - 1;
@@ -628,35 +625,32 @@ __device__ __forceinline__ void fwd_pair_item(const PixelGeom &gA, const PixelGe
             float dx;
             float2 dy;
             const float2 d2 = pair_d2(gA.ux, uy2, aj.x, aj.y, dx, dy);
-            if (d2.x <= aj.z) mA |= 1u << j;
-            if (d2.y <= aj.z) mB |= 1u << j;
-        }
-        if (doneA) mA = 0;
-        if (doneB) mB = 0;
-        while (mA) {
-            const int j = __ffs(mA) - 1;
-            mA &= mA - 1;
-            const float4 aj = wbuf[j];
-            float dx, dy;
-            const float d2 = pixel_d2(gA.ux, gA.uy, aj.x, aj.y, dx, dy);
-            lastA = wpos[j] + 1;
-            if (STORE) store_T(sto, pixA, cntA, TA);
-            if (pixel_blend(d2, aj, wbuf[32 + j], o, TA, A0, A1, A2, cntA)) {
-                doneA = true;
-                break;
+            const bool inA = !doneA && d2.x <= aj.z, inB = !doneB && d2.y <= aj.z;
+            if (!__any_sync(0xffffffffu, inA || inB)) continue;
+            const float4 cj = wbuf[32 + j];
+            const float2 ea = mul2(d2, f2(aj.w));
+            const float2 raw = mul2(f2(cj.x), make_float2(ex2_approx(ea.x), ex2_approx(ea.y)));
+            const float2 alpha = make_float2(inA ? fminf(o.alpha_max, raw.x) : 0.0f,
+                                             inB ? fminf(o.alpha_max, raw.y) : 0.0f);
+            if (STORE) {
+                if (inA) store_T(sto, pixA, cntA, T.x);
+                if (inB) store_T(sto, pixB, cntB, T.y);
             }
-        }
-        while (mB) {
-            const int j = __ffs(mB) - 1;
-            mB &= mB - 1;
-            const float4 aj = wbuf[j];
-            float dx, dy;
-            const float d2 = pixel_d2(gB.ux, gB.uy, aj.x, aj.y, dx, dy);
-            lastB = wpos[j] + 1;
-            if (STORE) store_T(sto, pixB, cntB, TB);
-            if (pixel_blend(d2, aj, wbuf[32 + j], o, TB, B0, B1, B2, cntB)) {
-                doneB = true;
-                break;
+            const float2 wgt = mul2(alpha, T);
+            C0 = fma2(wgt, f2(cj.y), C0);
+            C1 = fma2(wgt, f2(cj.z), C1);
+            C2 = fma2(wgt, f2(cj.w), C2);
+            T = add2(T, make_float2(-wgt.x, -wgt.y));
+            const uint32_t pos1 = wpos[j] + 1;
+            if (inA) {
+                lastA = pos1;
+                ++cntA;
+                doneA = T.x < o.t_eps || cntA == cmax;
+            }
+            if (inB) {
+                lastB = pos1;
+                ++cntB;
+                doneB = T.y < o.t_eps || cntB == cmax;
             }
         }
         __syncwarp(); // chunk consumed before the buffers are refilled
@@ -667,8 +661,8 @@ __device__ __forceinline__ void fwd_pair_item(const PixelGeom &gA, const PixelGe
         if (gA.inside) sto.n[pixA] = cntA;
         if (gB.inside) sto.n[pixB] = cntB;
     }
-    write_pixel(gA, o, TA, A0, A1, A2, lastA, out_rgb, T_final, n_contrib);
-    write_pixel(gB, o, TB, B0, B1, B2, lastB, out_rgb, T_final, n_contrib);
+    write_pixel(gA, o, T.x, C0.x, C1.x, C2.x, lastA, out_rgb, T_final, n_contrib);
+    write_pixel(gB, o, T.y, C0.y, C1.y, C2.y, lastB, out_rgb, T_final, n_contrib);
 }
 
 // Up to this many contributing pixels of a warp add their terms with their
@@ -760,7 +754,7 @@ __device__ __forceinline__ void bwd_stream_item(const Batch &b, const DevOpts &o
                 float tb = 0.0f;
                 if (STORE && contrib && --k < (uint32_t)sto.depth) {
                     has_tb = true;
-                    tb = sto.T[(int64_t)k * sto.n_pix + pix];
+                    tb = sto.T[pix * sto.depth + k];
                 }
                 pixel_adjoint_masked(contrib ? 1.0f : 0.0f, d2, dx, dy, aj, cj, o.alpha_max, g0,
                                      g1, g2, T, S, v, has_tb, tb);
@@ -946,11 +940,11 @@ __device__ __forceinline__ void bwd_pair_item(const DevView *V, int tx, int ty, 
                 if (STORE) {
                     if (cA && --kA < (uint32_t)sto.depth) {
                         has_tb |= 1u;
-                        tb.x = sto.T[(int64_t)kA * sto.n_pix + pixA];
+                        tb.x = sto.T[pixA * sto.depth + kA];
                     }
                     if (cB && --kB < (uint32_t)sto.depth) {
                         has_tb |= 2u;
-                        tb.y = sto.T[(int64_t)kB * sto.n_pix + pixB];
+                        tb.y = sto.T[pixB * sto.depth + kB];
                     }
                 }
                 pair_adjoint(make_float2(cA ? 1.0f : 0.0f, cB ? 1.0f : 0.0f), d2, dx, dy, aj,

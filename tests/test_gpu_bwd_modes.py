@@ -65,8 +65,8 @@ def test_store_and_recompute_match_the_oracle(env, sched):
     st = res[2]
     assert res[1]["n_comp"].size == 0 and st["n_comp"].size == cnt.size
     assert np.array_equal(st["n_comp"], cnt.astype(np.uint32))
-    T = st["T_store"].reshape(depth, -1)
-    assert np.all(T[0][cnt > 0] == 1.0)
+    T = st["T_store"].reshape(-1, depth)
+    assert np.all(T[:, 0][cnt > 0] == 1.0)
     errs = {}
     for m in (1, 2):
         r = res[m]
