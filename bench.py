@@ -42,25 +42,19 @@ FALLBACK_HBM_GBS = 6800.0
 FLOP_TEST, FLOP_FWD, FLOP_BWD = 6, 11, 31
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture of the kernel on the full-size batched workload; valid only for
-# the kernel source it was taken on (sha256 of the file), else reported null.
+# ncu capture of the kernel on the first 16 of the batched workload's 64 views,
+# scaled to the full launch by its contributing pairs (1.727 G / 0.575 G = 3.00);
+# valid only for the kernel source it was taken on (sha256 of the file), else
+# reported null.
 CAPTURED_TRAFFIC = {
-    ("raster_bwd", "16x16", 0, 1): {
-        "bytes": 12.99e9 + 1.19e9, "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
-        "sha256": "87ed8ddee71f0edca08834adbd624566c60fbab93c60fe8f022b66f5b58267f8",
-        "profile": "profiles/raster_persist_dram_batched_1M_64views.md"},
-    ("raster_fwd", "16x16", 0, 1): {
-        "bytes": 9.19e9 + 1.20e9, "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
-        "sha256": "87ed8ddee71f0edca08834adbd624566c60fbab93c60fe8f022b66f5b58267f8",
-        "profile": "profiles/raster_persist_dram_batched_1M_64views.md"},
     ("raster_bwd", "16x32", 0, 1): {
-        "bytes": 15.54e9 + 1.14e9, "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
-        "sha256": "87ed8ddee71f0edca08834adbd624566c60fbab93c60fe8f022b66f5b58267f8",
-        "profile": "profiles/raster_persist_dram_batched_1M_64views.md"},
+        "bytes": 3.00 * (2.252e9 + 0.247e9), "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
+        "sha256": "d704b7885f86678cbae5524e1d159277f1babeb8d68fe2d4debc36da39df427e",
+        "profile": "profiles/raster_persist_16x32_16views.md"},
     ("raster_fwd", "16x32", 0, 1): {
-        "bytes": 11.49e9 + 1.20e9, "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
-        "sha256": "87ed8ddee71f0edca08834adbd624566c60fbab93c60fe8f022b66f5b58267f8",
-        "profile": "profiles/raster_persist_dram_batched_1M_64views.md"},
+        "bytes": 3.00 * (1.240e9 + 0.365e9), "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
+        "sha256": "d704b7885f86678cbae5524e1d159277f1babeb8d68fe2d4debc36da39df427e",
+        "profile": "profiles/raster_persist_16x32_16views.md"},
 }
 
 
