@@ -842,7 +842,7 @@ def main():
                     help="use only the first N cameras (a smaller case for profiling)")
     ap.add_argument("--serve-rates", default="200,500,1000,2000",
                     help="comma-separated Poisson arrival rates (req/s); empty = no serving run")
-    ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))

@@ -1,7 +1,8 @@
 """Full-size workloads, rendered by the GPU in the launch configurations the
 benchmark's autotuner chooses between (whole batch in one call; 16x16
 tiles one block per tile, and the persistent schedule with 16x16 and 16x32
-tiles), checked against the FP64 oracle on sampled pixels: random pixels
+tiles), with the backward in store mode and in recompute mode, checked
+against the FP64 oracle on sampled pixels: random pixels
 plus full tiles (one at the ragged bottom-right corner) of a few views.
 Gradients use a loss masked to the sampled pixels, so the oracle computes
 the exact same gradient; it is compared over every point and over the 64
@@ -33,7 +34,10 @@ def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30))
 
 
-SCHEDULES = [dict(), dict(persistent=1), dict(persistent=1, tile=(16, 32))]
+# bwd_mode 0 (auto) keeps the per-pixel transmittances at these sizes (store
+# mode); the last schedule recomputes them in the backward
+SCHEDULES = [dict(), dict(persistent=1), dict(persistent=1, tile=(16, 32)),
+             dict(persistent=1, tile=(16, 32), bwd_mode=1)]
 
 
 def _check(R, scene_list, cams, sov, loss, views, n_random, n_tiles, target_rng=1):
