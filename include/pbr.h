@@ -20,7 +20,7 @@
  *
  * Conventions shared by every entry point
  *   - Every function returns an int status: PBR_OK (0) or a negative
- *     PBR_ERR_* code; pbr_last_error() returns a message for the calling
+ *     PBR_ERR_* code; pbr_last_error(ctx) returns a message for the calling
  *     thread.  No C++ exception crosses this boundary.
  *   - Point arrays, images and gradient buffers are DEVICE pointers owned by
  *     the caller (fp32, C-contiguous); cameras and options are HOST structs.
@@ -161,8 +161,10 @@ typedef struct {
  * device memory at creation). */
 int pbr_create(pbr_ctx **out, int device, size_t hbm_budget_bytes);
 int pbr_destroy(pbr_ctx *ctx);
-/* Message for the last error on the calling thread ("" if none). */
-const char *pbr_last_error(void);
+/* Message for the last error of a pbr_* call on the calling thread ("" if
+ * none).  The message is kept per thread, not per context: ctx may be NULL
+ * (e.g. after a failed pbr_create) and is not dereferenced. */
+const char *pbr_last_error(const pbr_ctx *ctx);
 void pbr_default_opts(pbr_render_opts *opts);
 /* Library version string and the compiled SM architecture. */
 const char *pbr_version(void);

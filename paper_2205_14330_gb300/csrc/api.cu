@@ -99,7 +99,7 @@ int pbr::set_error(int code, const char *fmt, ...)
     return code;
 }
 
-extern "C" const char *pbr_last_error(void) { return g_err.c_str(); }
+extern "C" const char *pbr_last_error(const pbr_ctx *) { return g_err.c_str(); }
 
 extern "C" const char *pbr_version(void) { return "pbr 0.1 (sm_103a)"; }
 

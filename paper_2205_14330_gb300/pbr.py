@@ -109,6 +109,7 @@ def lib():
             L.pbr_create.argtypes = [C.POINTER(vp), C.c_int, C.c_size_t]
             L.pbr_destroy.argtypes = [vp]
             L.pbr_last_error.restype = C.c_char_p
+            L.pbr_last_error.argtypes = [C.c_void_p]
             L.pbr_version.restype = C.c_char_p
             L.pbr_default_opts.argtypes = [C.POINTER(Opts)]
             L.pbr_default_opts.restype = None
@@ -192,7 +193,7 @@ def lib():
 
 def check(rc):
     if rc != PBR_OK:
-        raise PBRError(rc, lib().pbr_last_error().decode(errors="replace"))
+        raise PBRError(rc, lib().pbr_last_error(None).decode(errors="replace"))
     return rc
 
 
