@@ -231,76 +231,97 @@ __device__ __forceinline__ void warp_add_terms(const float v[8], int lane, float
 // tile's first entry) and point-view ids, in compositing order, and the
 // compositing loops consume it 32 entries at a time.  bit == 0 (tiles of
 // one block) takes every entry.
+// The queue is a ring of QCAP entries read from `head`; a fill scans
+// FILL_GROUPS groups of 32 list entries per step, their loads in flight
+// together (a warp's block takes a fraction of its tile's entries, so a
+// refill scans several groups).
+constexpr int QCAP = 128;
+constexpr int FILL_GROUPS = 3; // 32 + 3 x 32 entries fit the ring
 struct WarpQueue {
-    uint32_t pos[64]; // list positions, relative to the tile's first entry
-    uint32_t pv[64];  // point-view ids
+    uint32_t pos[QCAP]; // list positions, relative to the tile's first entry
+    uint32_t pv[QCAP];  // point-view ids
 };
 
-// Front to back: scans the list from position p (absolute, < e) 32 entries
-// at a time, appending the entries with `bit`, until the queue holds 32 or
-// the list ends.  Warp-uniform.
+// Front to back: scans the list from position p (absolute, < e), appending
+// the entries with `bit`, until the queue holds 32 or the list ends.
+// Warp-uniform.
 __device__ __forceinline__ void queue_fill_front(const uint32_t *__restrict__ keys,
                                                  const uint32_t *__restrict__ pv_list, uint32_t s,
                                                  uint32_t e, uint32_t bit, uint32_t &p, int &qn,
-                                                 WarpQueue &q, int lane)
+                                                 uint32_t qh, WarpQueue &q, int lane)
 {
     const uint32_t lt = lanemask_lt_r();
     while (qn < 32 && p < e) {
-        const uint32_t i = p + lane;
-        bool take = i < e;
-        if (take && bit) take = (__ldg(keys + i) & bit) != 0;
-        const uint32_t m = __ballot_sync(0xffffffffu, take);
-        if (take) {
-            const int slot = qn + __popc(m & lt);
-            q.pos[slot] = i - s;
-            q.pv[slot] = __ldg(pv_list + i);
+        uint32_t k[FILL_GROUPS];
+#pragma unroll
+        for (int g = 0; g < FILL_GROUPS; ++g) {
+            const uint32_t i = p + 32 * g + lane;
+            k[g] = bit && i < e ? __ldg(keys + i) : 0u;
         }
-        qn += __popc(m);
-        p += 32;
+#pragma unroll
+        for (int g = 0; g < FILL_GROUPS; ++g) {
+            const uint32_t i = p + 32 * g + lane;
+            const bool take = i < e && (bit == 0 || (k[g] & bit) != 0);
+            const uint32_t m = __ballot_sync(0xffffffffu, take);
+            if (take) {
+                const uint32_t slot = (qh + (uint32_t)qn + __popc(m & lt)) & (QCAP - 1);
+                q.pos[slot] = i - s;
+                q.pv[slot] = __ldg(pv_list + i);
+            }
+            qn += __popc(m);
+        }
+        p = e - p > 32u * FILL_GROUPS ? p + 32u * FILL_GROUPS : e;
     }
     __syncwarp();
 }
 
 // Back to front: scans the relative positions [0, c + 32) downwards from
-// the aligned chunk c (c < 0: nothing left), entries below `lim` only, 32
-// at a time, appending the entries with `bit` in descending position order.
+// the aligned chunk c (c < 0: nothing left), entries below `lim` only,
+// appending the entries with `bit` in descending position order.
 __device__ __forceinline__ void queue_fill_back(const uint32_t *__restrict__ keys,
                                                 const uint32_t *__restrict__ pv_list, uint32_t s,
                                                 uint32_t lim, uint32_t bit, int64_t &c, int &qn,
-                                                WarpQueue &q, int lane)
+                                                uint32_t qh, WarpQueue &q, int lane)
 {
     const uint32_t gt = ~(lanemask_lt_r() | (1u << lane));
     while (qn < 32 && c >= 0) {
-        const uint32_t i = (uint32_t)c + lane;
-        bool take = i < lim;
-        if (take && bit) take = (__ldg(keys + s + i) & bit) != 0;
-        const uint32_t m = __ballot_sync(0xffffffffu, take);
-        if (take) {
-            const int slot = qn + __popc(m & gt);
-            q.pos[slot] = i;
-            q.pv[slot] = __ldg(pv_list + s + i);
+        uint32_t k[FILL_GROUPS];
+#pragma unroll
+        for (int g = 0; g < FILL_GROUPS; ++g) {
+            const int64_t cg = c - 32 * g;
+            const uint32_t i = (uint32_t)cg + lane;
+            k[g] = bit && cg >= 0 && i < lim ? __ldg(keys + s + i) : 0u;
         }
-        qn += __popc(m);
-        c -= 32;
+#pragma unroll
+        for (int g = 0; g < FILL_GROUPS; ++g) {
+            const int64_t cg = c - 32 * g;
+            const uint32_t i = (uint32_t)cg + lane;
+            const bool take = cg >= 0 && i < lim && (bit == 0 || (k[g] & bit) != 0);
+            const uint32_t m = __ballot_sync(0xffffffffu, take);
+            if (take) {
+                const uint32_t slot = (qh + (uint32_t)qn + __popc(m & gt)) & (QCAP - 1);
+                q.pos[slot] = i;
+                q.pv[slot] = __ldg(pv_list + s + i);
+            }
+            qn += __popc(m);
+        }
+        c -= 32 * FILL_GROUPS;
     }
     __syncwarp();
 }
 
 // Takes the next min(qn, 32) queued entries: lane l < the count receives
-// entry l (its relative position and point-view); the rest move to the
-// front.  Returns the count.
-__device__ __forceinline__ int queue_take(WarpQueue &q, int &qn, int lane, uint32_t &pos,
-                                          uint32_t &pv)
+// entry l (its relative position and point-view).  Returns the count.
+__device__ __forceinline__ int queue_take(WarpQueue &q, int &qn, uint32_t &qh, int lane,
+                                          uint32_t &pos, uint32_t &pv)
 {
     const int take = qn < 32 ? qn : 32;
     if (lane < take) {
-        pos = q.pos[lane];
-        pv = q.pv[lane];
+        const uint32_t slot = (qh + (uint32_t)lane) & (QCAP - 1);
+        pos = q.pos[slot];
+        pv = q.pv[slot];
     }
-    if (lane + 32 < qn) { // each lane moves the entry 32 places behind its own
-        q.pos[lane] = q.pos[lane + 32];
-        q.pv[lane] = q.pv[lane + 32];
-    }
+    qh += (uint32_t)take;
     qn -= take;
     __syncwarp();
     return take;
@@ -478,11 +499,12 @@ __device__ __forceinline__ void fwd_stream_item(const PixelGeom &g, uint32_t s, 
     const int64_t pix = STORE && g.inside ? pixel_index(g) : 0;
     uint32_t p = s;
     int qn = 0;
+    uint32_t qh = 0;
     while (!__all_sync(0xffffffffu, done)) {
-        queue_fill_front(keys, pv_list, s, e, bit, p, qn, q, lane);
+        queue_fill_front(keys, pv_list, s, e, bit, p, qn, qh, q, lane);
         if (qn == 0) break;
         uint32_t rel = 0, pv = 0;
-        const int take = queue_take(q, qn, lane, rel, pv);
+        const int take = queue_take(q, qn, qh, lane, rel, pv);
         const bool valid = lane < take;
         float4 a = make_float4(0.f, 0.f, -1.f, 0.f);
         if (valid) a = __ldg(rec + 2 * (size_t)pv);
@@ -598,11 +620,12 @@ __device__ __forceinline__ void fwd_pair_item(const PixelGeom &gA, const PixelGe
     const uint32_t cmax = (uint32_t)o.max_per_pixel;
     uint32_t p = s;
     int qn = 0;
+    uint32_t qh = 0;
     while (!__all_sync(0xffffffffu, doneA && doneB)) {
-        queue_fill_front(keys, pv_list, s, e, bit, p, qn, q, lane);
+        queue_fill_front(keys, pv_list, s, e, bit, p, qn, qh, q, lane);
         if (qn == 0) break;
         uint32_t rel = 0, pv = 0;
-        const int take = queue_take(q, qn, lane, rel, pv);
+        const int take = queue_take(q, qn, qh, lane, rel, pv);
         const bool valid = lane < take;
         float4 a = make_float4(0.f, 0.f, -1.f, 0.f);
         if (valid) a = __ldg(rec + 2 * (size_t)pv);
@@ -715,11 +738,12 @@ __device__ __forceinline__ void bwd_stream_item(const Batch &b, const DevOpts &o
     if (wmax == 0) return;
     int64_t c = (int64_t)((wmax - 1) & ~31u);
     int qn = 0;
+    uint32_t qh = 0;
     while (true) {
-        queue_fill_back(keys, pv_list, s, wmax, bit, c, qn, q, lane);
+        queue_fill_back(keys, pv_list, s, wmax, bit, c, qn, qh, q, lane);
         if (qn == 0) break;
         uint32_t rel = 0, pv = 0;
-        const int take = queue_take(q, qn, lane, rel, pv);
+        const int take = queue_take(q, qn, qh, lane, rel, pv);
         const bool valid = lane < take;
         float4 a = make_float4(0.f, 0.f, -1.f, 0.f);
         if (valid) a = __ldg(rec + 2 * (size_t)pv);
@@ -895,11 +919,12 @@ __device__ __forceinline__ void bwd_pair_item(const DevView *V, int tx, int ty, 
     if (wmax == 0) return;
     int64_t c = (int64_t)((wmax - 1) & ~31u);
     int qn = 0;
+    uint32_t qh = 0;
     while (true) {
-        queue_fill_back(keys, pv_list, s, wmax, bit, c, qn, q, lane);
+        queue_fill_back(keys, pv_list, s, wmax, bit, c, qn, qh, q, lane);
         if (qn == 0) break;
         uint32_t rel = 0, pv = 0;
-        const int take = queue_take(q, qn, lane, rel, pv);
+        const int take = queue_take(q, qn, qh, lane, rel, pv);
         const bool valid = lane < take;
         float4 a = make_float4(0.f, 0.f, -1.f, 0.f);
         if (valid) a = __ldg(rec + 2 * (size_t)pv);
