@@ -888,8 +888,8 @@ __device__ __forceinline__ void bwd_pair_item(const DevView *V, int tx, int ty, 
                                               const uint32_t *__restrict__ n_contrib,
                                               const float *__restrict__ grad_rgb,
                                               float *__restrict__ g2d, uint32_t &examined,
-                                              uint32_t &used, float4 *wbuf, uint32_t *wpv,
-                                              uint32_t *wpos, WarpQueue &q, const StoreBuf &sto)
+                                              uint32_t &used, float4 *wbuf, uint2 *wpp,
+                                              WarpQueue &q, const StoreBuf &sto)
 {
     const int sx0 = tx * TW + (sub % (TW / 8)) * 8, sy0 = ty * TH + (sub / (TW / 8)) * 8;
     PixelGeom g[2];
@@ -938,15 +938,15 @@ __device__ __forceinline__ void bwd_pair_item(const DevView *V, int tx, int ty, 
         if (hit) {
             wbuf[lane] = a;
             wbuf[32 + lane] = __ldg(rec + 2 * (size_t)pv + 1);
-            wpv[lane] = pv;
-            wpos[lane] = rel;
+            wpp[lane] = make_uint2(rel, pv);
         }
         __syncwarp();
         while (m) {
             const int j = __ffs(m) - 1; // back to front: queue order
             m &= m - 1;
             const float4 aj = wbuf[j];
-            const uint32_t idx = wpos[j];
+            const uint2 pp = wpp[j]; // list position, point-view
+            const uint32_t idx = pp.x;
             float dx;
             float2 dy;
             const float2 d2 = pair_d2(ux, uy, aj.x, aj.y, dx, dy);
@@ -975,9 +975,9 @@ __device__ __forceinline__ void bwd_pair_item(const DevView *V, int tx, int ty, 
                 pair_adjoint(make_float2(cA ? 1.0f : 0.0f, cB ? 1.0f : 0.0f), d2, dx, dy, aj,
                              wbuf[32 + j], o.alpha_max, p, v, has_tb, tb);
                 if (__popc(cm) > BWD_PAIR_DIRECT_MAX) {
-                    warp_add_terms(v, lane, g2d, wpv[j]);
+                    warp_add_terms(v, lane, g2d, pp.y);
                 } else if (any) { // few lanes: each adds its own terms
-                    float4 *dst = reinterpret_cast<float4 *>(g2d) + 2 * (size_t)wpv[j];
+                    float4 *dst = reinterpret_cast<float4 *>(g2d) + 2 * (size_t)pp.y;
                     atomicAdd(dst, make_float4(v[0], v[1], v[2], v[3]));
                     atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], 0.f));
                 }
@@ -1119,8 +1119,7 @@ raster_bwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
     constexpr uint32_t SUBS = (TW / 8) * (TH / 8);
     constexpr int NW = PERSIST_THREADS / 32;
     __shared__ float4 s_buf[NW][64];
-    __shared__ uint32_t s_pv[NW][32];
-    __shared__ uint32_t s_pos[NW][32];
+    __shared__ uint2 s_pp[NW][32];
     __shared__ WarpQueue s_q[NW];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t n_items = b.n_tiles * SUBS;
@@ -1132,7 +1131,7 @@ raster_bwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
         bwd_pair_item<TW, TH, STATS, STORE>(&b.views[d.x], (int)(d.y & 0xffffu), (int)(d.y >> 16),
                                             d.z,
                                      bit, o, sub, lane, keys, pv_list, rec, T_final, n_contrib,
-                                     grad_rgb, g2d, ex, us, s_buf[w], s_pv[w], s_pos[w], s_q[w],
+                                     grad_rgb, g2d, ex, us, s_buf[w], s_pp[w], s_q[w],
                                      sto);
     }
     if (STATS) add_stats(stats + 2, ex, us, lane);
