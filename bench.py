@@ -833,6 +833,8 @@ def main():
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-dynamic", action="store_true",
                     help="skip the multi-frame video leg (30 frames x 16 views in one batch)")
+    ap.add_argument("--no-static", action="store_true",
+                    help="skip the static training-step leg (500k points, 4 views at 800^2)")
     ap.add_argument("--no-refine", action="store_true")
     ap.add_argument("--no-frame-init", action="store_true")
     ap.add_argument("--no-hull", action="store_true")
@@ -875,18 +877,26 @@ def main():
 
     res = measure_workload(args, pbr, torch, R, sc, desc, dist, world, local, True, alu)
 
-    dynamic = None
-    if args.workload == "batched" and not args.no_dynamic and not args.views:
-        dsc, ddesc = workload("dynamic")
-        d = measure_workload(args, pbr, torch, R, dsc, ddesc, dist, world, local, False, alu)
-        dynamic = {"workload": ddesc, "views": d["views"], "points": d["n_points"],
-                   "megapixels_per_step": d["mp"], "mp_s": d["value"], "ms_per_step": d["ms"],
-                   "fwd_mp_s": world * d["mp"] / (d["fwd_ms"] * 1e-3), "fwd_ms": d["fwd_ms"],
-                   "plain": d["plain"], "schedule": d["sched"], "stage_ms": d["stage_ms"],
-                   "roofline": d["roof"], "pairs": d["pairs"], "sizes": d["sizes"],
-                   "clocks": d["clk"], "timing": "CUDA-graph replays of the whole step "
-                   "(all 480 views, per-frame gradients) and forward alone"}
-        del d
+    def side_leg(name, timing):
+        """Another workload's training step measured like the headline (graph
+        replays, eager per-stage events, roofline, plain renderer)."""
+        wsc, wdesc = workload(name)
+        d = measure_workload(args, pbr, torch, R, wsc, wdesc, dist, world, local, False, alu)
+        return {"workload": wdesc, "views": d["views"], "points": d["n_points"],
+                "megapixels_per_step": d["mp"], "mp_s": d["value"], "ms_per_step": d["ms"],
+                "fwd_mp_s": world * d["mp"] / (d["fwd_ms"] * 1e-3), "fwd_ms": d["fwd_ms"],
+                "plain": d["plain"], "schedule": d["sched"], "stage_ms": d["stage_ms"],
+                "roofline": d["roof"], "pairs": d["pairs"], "sizes": d["sizes"],
+                "clocks": d["clk"], "timing": timing}
+
+    side = args.workload == "batched" and not args.views
+    dynamic = static = None
+    if side and not args.no_dynamic:
+        dynamic = side_leg("dynamic", "CUDA-graph replays of the whole step (all 480 views, "
+                                      "per-frame gradients) and forward alone")
+    if side and not args.no_static:
+        static = side_leg("static", "CUDA-graph replays of the whole step (4 views) and "
+                                    "forward alone")
 
     # ---- CPU oracle on a bounded sample, and the image's parity against it
     cpu = parity = None
@@ -937,7 +947,7 @@ def main():
                 "timing": "value/fwd: CUDA-graph replays of the whole step; stage_ms and the "
                           "roofline: the same steps launched eagerly with per-stage CUDA events",
                 "train_iteration": res["train"], "plain": res["plain"],
-                "bwd_modes": res["bwd_modes"], "dynamic": dynamic,
+                "bwd_modes": res["bwd_modes"], "dynamic": dynamic, "static": static,
                 "serving": serving, "refine": refine, "frame_init": frame, "visual_hull": hull,
                 "stage_ms": res["stage_ms"], "roofline": res["roof"], "parity": parity,
                 "alu_peaks_measured": alu,

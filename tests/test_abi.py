@@ -29,7 +29,9 @@ def libpath():
 def test_header_declares_the_boundary():
     names = _declared()
     for required in ("pbr_render_forward", "pbr_render_backward", "pbr_create", "pbr_destroy",
-                     "pbr_state_free", "pbr_last_error"):
+                     "pbr_state_free", "pbr_last_error", "pbr_forward_workspace_size",
+                     "pbr_upload_scene", "pbr_evict_scene", "pbr_submit_request", "pbr_poll",
+                     "pbr_serve_stats"):
         assert required in names
 
 
