@@ -49,11 +49,11 @@ FLOP_TEST, FLOP_FWD, FLOP_BWD = 6, 11, 31
 CAPTURED_TRAFFIC = {
     ("raster_bwd", "16x32", 0, 1): {
         "bytes": 3.00 * (2.247e9 + 0.247e9), "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
-        "sha256": "3dfdb2fd07f95f8b5765a160577c758aa8a7f7130a13ca2b6bf74aafa015f5cd",
+        "sha256": "469a7bdac4602e8c21b387c4a21e63f24af6dc9a0ac358b4152867ac73b19565",
         "profile": "profiles/raster_persist_16x32_16views.md"},
     ("raster_fwd", "16x32", 0, 1): {
         "bytes": 3.00 * (1.323e9 + 0.365e9), "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
-        "sha256": "3dfdb2fd07f95f8b5765a160577c758aa8a7f7130a13ca2b6bf74aafa015f5cd",
+        "sha256": "469a7bdac4602e8c21b387c4a21e63f24af6dc9a0ac358b4152867ac73b19565",
         "profile": "profiles/raster_persist_16x32_16views.md"},
 }
 

@@ -22,17 +22,25 @@
 // contribute, else summed first with a transposed shuffle reduction (two
 // atomics per warp and point) in the warp-streamed schedules.
 //
-// A block covers one TW x TH screen tile; each warp owns an 8 x 4 sub-block
-// of it (an 8 x 8 one, two pixels per lane, in the persistent schedule) and
-// skips list entries whose cutoff disc misses its still active pixels.  Two
-// schedules:
-//   - warp-streamed (batch depth 0, default): every warp walks the tile list
-//     by itself, 32 entries per step (loads shared through L1), culls them
-//     with one ballot and stops as soon as its own pixels have saturated.
-//     No block barriers.
+// The pair keys carry the mask of the tile's 8 x 8 pixel blocks that hold a
+// pixel including the point, so a warp takes from its tile's list only the
+// entries of its own block, and it skips those whose cutoff disc misses its
+// still active pixels.  Three schedules:
+//   - warp-streamed (batch depth 0, default): a block covers one TW x TH
+//     screen tile, each warp an 8 x 4 sub-block of it; every warp walks its
+//     entries by itself, 32 per step, culls them with one ballot and stops
+//     as soon as its own pixels have saturated.  No block barriers.
+//   - persistent (batch depth 0, persistent): one launch; warps take (tile,
+//     8 x 8 block) items longest list first from an atomic counter; a lane
+//     owns two pixels of a column, four rows apart, and their arithmetic
+//     runs packed (fp32x2).  The forward steps through each chunk's hits in
+//     lockstep; the backward forms the adjoint at both pixels per hit.
 //   - block-staged (batch depth > 0): the block stages `depth` records in
 //     shared memory and each warp culls the batch into its own list; block
 //     barriers between batches, per-block shared-memory gradient sums.
+// Store mode (STORE): the forward also keeps T before each of a pixel's
+// first store_depth composited points, and the backward reads it there
+// instead of dividing.
 #include "pbr_internal.cuh"
 
 namespace pbr {
