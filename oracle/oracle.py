@@ -99,12 +99,18 @@ def lib():
                                        C.POINTER(Camera), C.POINTER(Opts), C.c_int64, C.c_void_p,
                                        dp, dp, dp, dp, C.c_void_p]
             L.orc_num_threads.restype = C.c_int
+            L.orc_set_num_threads.argtypes = [C.c_int]
             _lib = L
     return _lib
 
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's later parallel regions (timing only)."""
+    lib().orc_set_num_threads(int(n))
 
 
 # ---------------------------------------------------------------- marshalling

@@ -703,6 +703,17 @@ int orc_backward(int64_t n, const double *pos, const double *sh, const double *o
     return 0;
 }
 
+/* Threads of the following OpenMP regions (timing on one core); n <= 0
+ * leaves the default. */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int orc_num_threads(void)
 {
     int nt = 1;
