@@ -21,7 +21,9 @@
 //   centre nearest the splat centre (rect_reached).
 //
 // preprocess_bwd (Sec. 3.3): one thread per point; per view it chains the
-// screen-space adjoint {dpx, dpy, dq, do, dr, dg, db} (q = 1/s^2) through the
+// screen-space adjoint {dpx, dpy, dq, do, dr, dg, db} (q = 1/s^2; the
+// compositing kernels leave dpx = q t0, dpy = q t1 and dq = -t2 / 2 to this
+// stage, which applies the factors once per point-view) through the
 // kernel width, the projection, the direction normalisation and the SH basis
 // back to the point position, SH coefficients and opacity.  Views are
 // visited in a fixed order, so the result does not depend on scheduling.
@@ -300,7 +302,7 @@ __device__ void pre_bwd_point(const Batch &b, const DevOpts &o, const DevScene &
         const DevView &V = b.views[v];
         cp_async_wait<BWD_AHEAD - 1>(); // the copies of views 0..vv have landed
         const float4 *slot = sg + (vv % BWD_SLOTS) * 2 * PRE_THREADS;
-        const float4 ga = slot[0];           // dpx, dpy, dq, do
+        const float4 ga = slot[0];           // t0, t1, t2, do
         const float4 gb = slot[PRE_THREADS]; // dr, dg, db, -
         if (vv + BWD_AHEAD < nv) fetch_view_terms(b, sc, i, vv + BWD_AHEAD, g2d, sg);
         cp_async_commit();
@@ -313,17 +315,18 @@ __device__ void pre_bwd_point(const Batch &b, const DevOpts &o, const DevScene &
             X[a] = V.R[3 * a] * P0 + V.R[3 * a + 1] * P1 + V.R[3 * a + 2] * P2 + V.t[a];
         const float z = X[2];
         const float iz = 1.0f / z;
+        // the kernel width of this point-view and q = 1/s^2
+        const float s = o.radius_mode == 0 ? V.fx * r * iz : r * (float)min(V.W, V.H) * 0.5f;
+        const float q = 1.0f / (s * s);
+        const float gpx = ga.x * q, gpy = ga.y * q, gq = -0.5f * ga.z;
         float dX0 = 0.f, dX1 = 0.f, dX2 = 0.f;
         // p = (fx X0/z + cx, fy X1/z + cy)
-        dX0 += ga.x * V.fx * iz;
-        dX2 -= ga.x * V.fx * X[0] * iz * iz;
-        dX1 += ga.y * V.fy * iz;
-        dX2 -= ga.y * V.fy * X[1] * iz * iz;
+        dX0 += gpx * V.fx * iz;
+        dX2 -= gpx * V.fx * X[0] * iz * iz;
+        dX1 += gpy * V.fy * iz;
+        dX2 -= gpy * V.fy * X[1] * iz * iz;
         // q = 1/s^2 = z^2 / (fx r)^2  =>  dq/dz = 2 q / z  (radius_mode 0)
-        if (o.radius_mode == 0) {
-            const float s = V.fx * r * iz;
-            dX2 += ga.z * 2.0f * iz / (s * s);
-        }
+        if (o.radius_mode == 0) dX2 += gq * 2.0f * iz * q;
         dop += ga.w;
         // colour: c = sum_k h_k Y_k(v)
         const float nrm2 = X[0] * X[0] + X[1] * X[1] + z * z;

@@ -17,6 +17,9 @@
 // and, below the alpha_max clamp,
 //   dL/do = dL/dalpha G,  dL/dp = dL/dalpha alpha q (u - p),
 //   dL/dq = -dL/dalpha alpha d2 / 2          (q = 1/s^2).
+// The kernels sum {ca (u - p), ca d2} with ca = dL/dalpha alpha, without
+// the per-point factors q and -1/2, which the point stage applies once per
+// point-view: the terms are {ca dx, ca dy, ca d2, do, dr, dg, db}.
 // The 7 per-point terms of a warp go to the per-(view, point) buffer with
 // 16-byte atomics: straight from each contributing lane when few lanes
 // contribute, else summed first with a transposed shuffle reduction (two
@@ -394,16 +397,16 @@ __device__ __forceinline__ void pixel_adjoint_masked(float take, float d2, float
     S = fmaf(wgt, cg, S);
     T = Tb;
     const float ca = raw < amax ? dalpha * alpha : 0.0f; // clamped: no geometry terms
-    const float q = a.w * QP_TO_Q;
-    v[0] = ca * q * dx;
-    v[1] = ca * q * dy;
-    v[2] = -0.5f * ca * d2;
+    v[0] = ca * dx;
+    v[1] = ca * dy;
+    v[2] = ca * d2;
     v[3] = raw < amax ? dalpha * G : 0.0f;
     v[7] = 0.0f;
 }
 
 // Per-pixel adjoint of one composited point (see the file comment).  On
-// return v[0..6] = {dpx, dpy, dq, do, dr, dg, db}; T and S are updated.
+// return v[0..6] = {ca dx, ca dy, ca d2, do, dr, dg, db}; T and S are
+// updated.
 __device__ __forceinline__ void pixel_adjoint(float d2, float dx, float dy, const float4 a,
                                               const float4 c, float amax, float g0, float g1,
                                               float g2, float &T, float &S, float v[8])
@@ -422,11 +425,10 @@ __device__ __forceinline__ void pixel_adjoint(float d2, float dx, float dy, cons
     S = fmaf(wgt, cg, S);
     T = Tb;
     if (raw < amax) {
-        const float q = a.w * QP_TO_Q;
         const float ca = dalpha * alpha;
-        v[0] = ca * q * dx;
-        v[1] = ca * q * dy;
-        v[2] = -0.5f * ca * d2;
+        v[0] = ca * dx;
+        v[1] = ca * dy;
+        v[2] = ca * d2;
         v[3] = dalpha * G;
     }
 }
@@ -837,8 +839,8 @@ struct BwdPair {
 // The adjoint of one composited point at both pixels of a lane (the
 // operations of pixel_adjoint_masked, packed): take.x / take.y (0 or 1) say
 // whether the point was composited at pixel A / B (0: its terms are 0 and
-// T, S stay).  Returns the sum over the two pixels of the terms {dpx, dpy,
-// dq, do, dr, dg, db} in v[0..6].
+// T, S stay).  Returns the sum over the two pixels of the terms {ca dx,
+// ca dy, ca d2, do, dr, dg, db} in v[0..6].
 // Bit 0 / 1 of has_tb: tb.x / .y is the stored transmittance before the
 // point at pixel A / B (store mode) instead of the one recovered by
 // division.
@@ -868,11 +870,10 @@ __device__ __forceinline__ void pair_adjoint(float2 take, float2 d2, float dx, f
     // clamped alpha: no geometry terms
     const float2 ca0 = mul2(dalpha, alpha), dg0 = mul2(dalpha, G);
     const float2 ca = make_float2(raw.x < amax ? ca0.x : 0.0f, raw.y < amax ? ca0.y : 0.0f);
-    const float2 caq = mul2(ca, f2(a.w * QP_TO_Q));
-    const float2 t1 = mul2(caq, dy), t2 = mul2(ca, d2);
-    v[0] = (caq.x + caq.y) * dx;
+    const float2 t1 = mul2(ca, dy), t2 = mul2(ca, d2);
+    v[0] = (ca.x + ca.y) * dx;
     v[1] = t1.x + t1.y;
-    v[2] = -0.5f * (t2.x + t2.y);
+    v[2] = t2.x + t2.y;
     v[3] = (raw.x < amax ? dg0.x : 0.0f) + (raw.y < amax ? dg0.y : 0.0f);
     v[7] = 0.0f;
 }

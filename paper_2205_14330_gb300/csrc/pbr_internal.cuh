@@ -92,9 +92,8 @@ enum Stage : int {
 void count_launches(int n);
 unsigned long long launches_total();
 
-// log2(e) and the factor that turns q' = -log2(e) / (2 s^2) into q = 1 / s^2
+// log2(e) (the kernel exponent is taken base 2: q' = -log2(e) / (2 s^2))
 constexpr float LOG2E = 1.4426950408889634f;
-constexpr float QP_TO_Q = -2.0f / 1.4426950408889634f;
 
 // ---- binning rule (Sec. 3.2 cutoff), shared by the per-point stage and the
 // pair emission.  A tile lists a point-view iff some pixel of the tile
