@@ -651,6 +651,9 @@ __device__ __forceinline__ void fwd_pair_item(const PixelGeom &gA, const PixelGe
         }
         __syncwarp();
         if (STATS) examined += (uint32_t)__popc(m) * ((uint32_t)!doneA + (uint32_t)!doneB);
+        // the chunk's composited entries of each pixel, as bits of the chunk
+        // (counts and the last position follow after the chunk)
+        uint32_t incA = 0u, incB = 0u;
         while (m) {
             const int j = __ffs(m) - 1;
             m &= m - 1;
@@ -666,25 +669,35 @@ __device__ __forceinline__ void fwd_pair_item(const PixelGeom &gA, const PixelGe
             const float2 alpha = make_float2(inA ? fminf(o.alpha_max, raw.x) : 0.0f,
                                              inB ? fminf(o.alpha_max, raw.y) : 0.0f);
             if (STORE) {
-                if (inA) store_T(sto, pixA, cntA, T.x);
-                if (inB) store_T(sto, pixB, cntB, T.y);
+                if (inA) store_T(sto, pixA, cntA + __popc(incA), T.x);
+                if (inB) store_T(sto, pixB, cntB + __popc(incB), T.y);
             }
             const float2 wgt = mul2(alpha, T);
             C0 = fma2(wgt, f2(cj.y), C0);
             C1 = fma2(wgt, f2(cj.z), C1);
             C2 = fma2(wgt, f2(cj.w), C2);
             T = add2(T, make_float2(-wgt.x, -wgt.y));
-            const uint32_t pos1 = wpos[j] + 1;
+            const uint32_t bit_j = 1u << j;
             if (inA) {
-                lastA = pos1;
-                ++cntA;
-                doneA = T.x < o.t_eps || cntA == cmax;
+                incA |= bit_j;
+                doneA = T.x < o.t_eps;
             }
             if (inB) {
-                lastB = pos1;
-                ++cntB;
-                doneB = T.y < o.t_eps || cntB == cmax;
+                incB |= bit_j;
+                doneB = T.y < o.t_eps;
             }
+            if (cmax) { // count cap (warp-uniform branch)
+                doneA = doneA || (inA && cntA + __popc(incA) == cmax);
+                doneB = doneB || (inB && cntB + __popc(incB) == cmax);
+            }
+        }
+        if (incA) {
+            cntA += __popc(incA);
+            lastA = wpos[31 - __clz(incA)] + 1;
+        }
+        if (incB) {
+            cntB += __popc(incB);
+            lastB = wpos[31 - __clz(incB)] + 1;
         }
         __syncwarp(); // chunk consumed before the buffers are refilled
     }
