@@ -314,10 +314,12 @@ __device__ void pre_bwd_point(const Batch &b, const DevOpts &o, const DevScene &
         for (int a = 0; a < 3; ++a)
             X[a] = V.R[3 * a] * P0 + V.R[3 * a + 1] * P1 + V.R[3 * a + 2] * P2 + V.t[a];
         const float z = X[2];
-        const float iz = 1.0f / z;
+        float iz; // 1/z, approximate (gradient factors only)
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(iz) : "f"(z));
         // the kernel width of this point-view and q = 1/s^2
         const float s = o.radius_mode == 0 ? V.fx * r * iz : r * (float)min(V.W, V.H) * 0.5f;
-        const float q = 1.0f / (s * s);
+        float q; // 1/s^2, approximate as well
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(q) : "f"(s * s));
         const float gpx = ga.x * q, gpy = ga.y * q, gq = -0.5f * ga.z;
         float dX0 = 0.f, dX1 = 0.f, dX2 = 0.f;
         // p = (fx X0/z + cx, fy X1/z + cy)
