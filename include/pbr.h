@@ -387,6 +387,15 @@ double pbr_now(void);
 int pbr_serve_trace(pbr_ctx *ctx, double *start_ms, double *end_ms, int32_t *views, int32_t cap,
                     int32_t *n, int32_t reset);
 
+/* What a request for resident scene scene_id from cam reserves from the
+ * HBM budget while it is in flight (bytes): the forward pass's allocations
+ * with every point-view visible and listed in as many tiles as the scene's
+ * largest splat can reach from this camera (largest radius at the nearest
+ * depth of the scene's bounding box), an upper bound of what
+ * pbr_forward_workspace_size reports for the same view.  Errors:
+ * INVALID_ARG, NOT_FOUND (no such scene). */
+int pbr_serve_estimate(pbr_ctx *ctx, int32_t scene_id, const pbr_camera *cam, size_t *bytes);
+
 /* --------------------------------------------------- measurement support */
 /* Number of CUDA kernels this library has launched in this process. */
 unsigned long long pbr_kernel_launches(void);

@@ -503,8 +503,8 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
 // The bytes forward_eager allocates (each allocation at least 16 bytes), all
 // alive at its end: the state's buffers, the call's temporaries and, in store
 // mode, the transmittance list.
-static size_t forward_bytes(const HostLayout &L, int64_t n_vis, int64_t n_pairs,
-                            const pbr_render_opts *o, int32_t store_depth)
+size_t pbr::forward_bytes(const HostLayout &L, int64_t n_vis, int64_t n_pairs,
+                          const pbr_render_opts *o, int32_t store_depth)
 {
     auto al = [](size_t b) { return b ? b : (size_t)16; };
     const int64_t npv = L.n_pv;

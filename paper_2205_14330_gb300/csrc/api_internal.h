@@ -51,6 +51,11 @@ int check_opts(const pbr_render_opts *o);
 DevOpts dev_opts(const pbr_render_opts *o);
 int build_layout(const pbr_points *scenes, int32_t n_scenes, const int32_t *scene_of_view,
                  const pbr_camera *cams, int32_t n_cams, const pbr_render_opts *o, HostLayout &L);
+// Device bytes a forward pass allocates for a layout with n_vis visible
+// point-views and n_pairs (tile, point-view) pairs (store_depth > 0: with
+// the stored transmittance list).
+size_t forward_bytes(const HostLayout &L, int64_t n_vis, int64_t n_pairs,
+                     const pbr_render_opts *o, int32_t store_depth);
 int dalloc(void **p, size_t bytes, cudaStream_t s);
 void dfree(void *p, cudaStream_t s);
 void serve_shutdown(pbr_ctx *c);

@@ -16,6 +16,7 @@
 // is completion minus arrival on the host's steady clock.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -41,6 +42,10 @@ struct SceneRes {
     pbr_points pts{}; // device pointers owned by the library
     void *mem = nullptr;
     int refs = 0; // queued or in-flight requests
+    // bounds for the admission estimate: a sphere holding every point and
+    // the largest radius
+    double centre[3] = {0.0, 0.0, 0.0};
+    double extent = 0.0, r_max = 0.0;
 };
 
 struct Request {
@@ -63,13 +68,33 @@ struct InFlight {
     size_t bytes = 0;
 };
 
-// Workspace estimate of one view of a scene with n points: per point-view
-// the 32-byte record, tile count, depth bits, rectangle and sort buffers
-// (64 B), about four (tile, point-view) pairs at 16 B with their sort
-// buffers, and per pixel T and the list position.
-size_t estimate_bytes(int64_t n, const pbr_camera &c)
+// Admission reservation of one view of a resident scene: the bytes its
+// forward pass allocates (pbr::forward_bytes) with every point-view visible
+// and every point-view listed in as many tiles as the largest splat can
+// reach.  The largest splat is the largest radius at the smallest depth of
+// the scene's bounding sphere along the camera's axis (no nearer than
+// z_near), so the bound holds for every camera; it is loose for splats
+// below the largest.  Returns 0 when the layout is invalid.
+size_t admission_bytes(const SceneRes &sc, const pbr_camera &cam, const pbr_render_opts &o)
 {
-    return (size_t)n * (64 + 4 * 16) + (size_t)c.width * c.height * 8 + (1u << 20);
+    HostLayout L;
+    if (build_layout(&sc.pts, 1, nullptr, &cam, 1, &o, L) != PBR_OK) return 0;
+    // camera centre C = -R^T t, optical axis a = R^T e_z
+    double C[3], a[3];
+    for (int k = 0; k < 3; ++k) {
+        C[k] = -(cam.R[k] * cam.t[0] + cam.R[3 + k] * cam.t[1] + cam.R[6 + k] * cam.t[2]);
+        a[k] = cam.R[6 + k];
+    }
+    const double along = a[0] * (sc.centre[0] - C[0]) + a[1] * (sc.centre[1] - C[1]) +
+                         a[2] * (sc.centre[2] - C[2]);
+    const double z_min = std::max((double)o.z_near, along - sc.extent);
+    const double sigma = o.radius_mode == 0 ? cam.fx * sc.r_max / z_min
+                                            : sc.r_max * std::min(cam.width, cam.height) * 0.5;
+    const double side = 2.0 * o.cutoff_k * sigma + 3.0; // pixel box of the splat
+    const double tx = std::ceil(side / o.tile_w) + 1.0, ty = std::ceil(side / o.tile_h) + 1.0;
+    const double tiles = std::min((double)L.n_tiles, tx * ty);
+    const double pairs = std::min((double)L.n_pv * tiles, 4.0e18);
+    return forward_bytes(L, L.n_pv, (int64_t)pairs, &o, 0);
 }
 
 } // namespace
@@ -371,10 +396,33 @@ extern "C" int pbr_upload_scene(pbr_ctx *c, const pbr_points *p, int32_t *scene_
             return set_error(PBR_ERR_CUDA, "scene upload: %s", cudaGetErrorString(e));
         }
     }
-    std::lock_guard<std::mutex> g(S->mu);
     SceneRes r;
     r.pts = d;
     r.mem = mem;
+    if (n > 0) { // bounds of the admission estimate, from a host copy
+        std::vector<float> hp(3 * (size_t)n), hr((size_t)n);
+        if (cudaMemcpy(hp.data(), d.pos, b_pos, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(hr.data(), d.radius, b_s, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(mem);
+            return set_error(PBR_ERR_CUDA, "scene upload: reading the bounds back failed");
+        }
+        double lo[3] = {hp[0], hp[1], hp[2]}, hi[3] = {hp[0], hp[1], hp[2]};
+        for (int64_t i = 0; i < n; ++i) {
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = std::min(lo[k], (double)hp[3 * i + k]);
+                hi[k] = std::max(hi[k], (double)hp[3 * i + k]);
+            }
+            r.r_max = std::max(r.r_max, (double)hr[i]);
+        }
+        double e2 = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            r.centre[k] = 0.5 * (lo[k] + hi[k]);
+            e2 += 0.25 * (hi[k] - lo[k]) * (hi[k] - lo[k]);
+        }
+        r.extent = std::sqrt(e2) * (1.0 + 1e-6) + 1e-6; // the box's half diagonal
+    }
+    std::lock_guard<std::mutex> g(S->mu);
     *scene_id = S->next_scene++;
     S->scenes[*scene_id] = r;
     return PBR_OK;
@@ -413,7 +461,8 @@ extern "C" int pbr_submit_request(pbr_ctx *c, int32_t scene_id, const pbr_camera
         r.cam = *cam;
         r.out = out_rgb_device;
         r.t_arrival = arrival_time > 0.0 ? arrival_time : now_s();
-        r.bytes = estimate_bytes(it->second.pts.n, *cam);
+        r.bytes = admission_bytes(it->second, *cam, S->opts);
+        if (r.bytes == 0) return set_error(PBR_ERR_INVALID_ARG, "request camera is invalid");
         it->second.refs++;
         S->reqs[r.id] = r;
         S->queue.push_back(r.id);
@@ -534,5 +583,19 @@ extern "C" int pbr_serve_trace(pbr_ctx *c, double *start_ms, double *end_ms, int
         S->trace_end.clear();
         S->trace_views.clear();
     }
+    return PBR_OK;
+}
+
+extern "C" int pbr_serve_estimate(pbr_ctx *c, int32_t scene_id, const pbr_camera *cam,
+                                  size_t *bytes)
+{
+    if (!c || !c->serve || !cam || !bytes)
+        return set_error(PBR_ERR_INVALID_ARG, "pbr_serve_estimate: bad arguments");
+    ServeState *S = c->serve;
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->scenes.find(scene_id);
+    if (it == S->scenes.end()) return set_error(PBR_ERR_NOT_FOUND, "no scene %d", scene_id);
+    *bytes = admission_bytes(it->second, *cam, S->opts);
+    if (*bytes == 0) return set_error(PBR_ERR_INVALID_ARG, "camera is invalid");
     return PBR_OK;
 }

@@ -150,6 +150,8 @@ def lib():
             L.pbr_serve_stats.argtypes = [vp, C.POINTER(ServeStats), i32]
             L.pbr_now.restype = C.c_double
             L.pbr_now.argtypes = []
+            L.pbr_serve_estimate.argtypes = [vp, C.c_int32, C.POINTER(Camera),
+                                             C.POINTER(C.c_size_t)]
             L.pbr_serve_trace.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(i32), i32, C.POINTER(i32), i32]
             L.pbr_default_optimizer.argtypes = [C.POINTER(OptimizerCfg)]
@@ -538,6 +540,14 @@ class Server:
         s = ServeStats()
         check(lib().pbr_serve_stats(self.ctx, C.byref(s), 1 if reset else 0))
         return {k: getattr(s, k) for k, _ in ServeStats._fields_}
+
+    def estimate(self, scene_id, cam):
+        """Bytes a request for scene_id from cam reserves from the HBM budget
+        (pbr_serve_estimate)."""
+        b = C.c_size_t()
+        check(lib().pbr_serve_estimate(self.ctx, int(scene_id), make_cameras([cam]),
+                                       C.byref(b)))
+        return b.value
 
     def trace(self, reset=False):
         """Device intervals of the completed batches: a list of (start_ms,

@@ -129,10 +129,12 @@ def test_admission_by_hbm_budget(env):
     pbr = env
     R = pbr.Renderer(0)
     data = _scenes(4)
-    # budget that fits about one request: batches of one, all complete
-    sv = pbr.Server(R, max_batch_views=16, n_streams=2, hbm_budget=3_000_000)
+    # a budget that fits one request's reservation but not two: batches of
+    # one, all complete
+    sv = pbr.Server(R, max_batch_views=16, n_streams=2, hbm_budget=1 << 34)
     ids = [sv.upload(d) for d in data]
     reqs = [(1, scenes.camera((0.0, 0.5, 3.0), 64, 48))] * 6
+    sv.set_budget(int(1.5 * sv.estimate(ids[1], reqs[0][1])))
     subs = [sv.submit(ids[s], cam) for s, cam in reqs]
     for rid, _ in subs:
         assert sv.wait(rid) == 0
@@ -153,5 +155,31 @@ def test_admission_by_hbm_budget(env):
     with pytest.raises(pbr.PBRError) as e:
         sv.submit(ids[0], reqs[0][1])
     assert e.value.code == -7
+    sv.stop()
+    R.close()
+
+
+def test_admission_estimate_covers_the_workspace(env):
+    """The reservation of a request (pbr_serve_estimate) is not below what
+    the forward of that view allocates (pbr_forward_workspace_size, forward
+    only), on the serving scenes from near cameras at the largest size (the
+    most tile pairs per point), at the smallest size, and from far."""
+    pbr = env
+    R = pbr.Renderer(0)
+    data = scenes.serving_scenes()
+    opts = pbr.default_opts()
+    sv = pbr.Server(R, opts=opts, max_batch_views=4, n_streams=2)
+    ratios = []
+    for k, d in enumerate(data):
+        sid = sv.upload(d)
+        scene = pbr.Scene(d["pos"], d["sh"], d["opacity"], d["radius"], d["deg"])
+        for dist, (W, H) in ((3.0, (1920, 1072)), (3.0, (256, 256)), (5.0, (1920, 1072))):
+            cam = scenes.camera((0.3 * dist, 0.4 * dist, 0.866 * dist), W, H)
+            exact, _ = R.workspace_size([scene], [cam], opts, keep_state=False)
+            est = sv.estimate(sid, cam)
+            ratios.append(est / exact)
+            assert est >= exact, (k, dist, W, H, exact, est)
+        sv.evict(sid)
+    print(f"admission reservation / workspace: {min(ratios):.2f} .. {max(ratios):.2f}")
     sv.stop()
     R.close()
