@@ -919,6 +919,17 @@ def main():
         # the oracle's cost per pixel does not depend on the image, so the
         # sampled rate extrapolates linearly in pixels to the whole step
         cpu["full_step_s_extrapolated"] = res["mp"] / cpu["value"]
+        # the tiny scene (4096 points, one 128^2 view) in full, all cores
+        tiny = scenes.tiny()
+        t0 = time.perf_counter()
+        rgb, _, _ = O.render(tiny["pos"], tiny["sh"], tiny["opacity"], tiny["radius"],
+                             tiny["deg"], tiny["cams"])
+        O.backward(tiny["pos"], tiny["sh"], tiny["opacity"], tiny["radius"], tiny["deg"],
+                   tiny["cams"], 2.0 * (rgb - 0.5))
+        t_tiny = time.perf_counter() - t0
+        cpu["tiny_full"] = {"seconds": t_tiny, "mp_s": 128 * 128 / t_tiny / 1e6,
+                            "sample": "the whole tiny scene: 4096 points, one 128^2 view, "
+                                      "forward + backward"}
         parity = image_parity(res, osc)
 
     serving = None
