@@ -45,8 +45,10 @@ def _grads(pbr, R, sc, cams, g, **kw):
 
 
 @pytest.mark.parametrize("sched", [dict(), dict(persistent=1), dict(persistent=1, tile=(16, 32)),
-                                   dict(persistent=1, store_depth=3)],
-                         ids=["streamed", "persistent", "persistent-16x32", "depth-3"])
+                                   dict(persistent=1, store_depth=3),
+                                   dict(persistent=1, tile=(16, 32), max_per_pixel=5)],
+                         ids=["streamed", "persistent", "persistent-16x32", "depth-3",
+                              "persistent-n5"])
 def test_store_and_recompute_match_the_oracle(env, sched):
     """The tiny workload (4096 points, 128^2): both modes against the oracle's
     adjoint and against each other; store mode's per-pixel point counts equal
@@ -56,10 +58,12 @@ def test_store_and_recompute_match_the_oracle(env, sched):
     sc = scenes.tiny()
     cams = sc["cams"]
     rng = np.random.default_rng(2)
-    ref, _, cnt = O.render(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], cams)
+    okw = {k: v for k, v in sched.items() if k == "max_per_pixel"}
+    ref, _, cnt = O.render(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], cams,
+                           **okw)
     g = rng.normal(size=ref.shape)
     dpos, dsh, dop = O.backward(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"],
-                                cams, g)
+                                cams, g, **okw)
     res = {m: _grads(pbr, R, sc, cams, g, bwd_mode=m, **sched) for m in (1, 2)}
     depth = sched.get("store_depth", 32)
     st = res[2]

@@ -241,9 +241,14 @@ def test_forward_is_deterministic(R):
 @pytest.mark.parametrize("kw", [dict(), dict(dir_frame=1), dict(radius_mode=1),
                                 dict(max_per_pixel=15), dict(bg=(0.2, 0.5, 0.9)),
                                 dict(t_eps=0.0, cutoff_k=4.0), dict(alpha_max=0.5),
-                                dict(batch_depth=256), dict(max_per_pixel=15, batch_depth=64)],
+                                dict(batch_depth=256), dict(max_per_pixel=15, batch_depth=64),
+                                dict(persistent=1, max_per_pixel=15),
+                                dict(persistent=1, tile=(16, 32), max_per_pixel=3),
+                                dict(persistent=1, t_eps=0.0, cutoff_k=4.0),
+                                dict(persistent=1, tile=(8, 8), bg=(0.2, 0.5, 0.9))],
                          ids=["default", "world-dir", "ndc-radius", "n15", "bg", "no-stop",
-                              "amax", "staged", "staged-n15"])
+                              "amax", "staged", "staged-n15", "persistent-n15",
+                              "persistent-16x32-n3", "persistent-no-stop", "persistent-8x8-bg"])
 def test_option_variants(R, kw):
     sc = _small_scene(4, n=600)
     if kw.get("radius_mode") == 1:
