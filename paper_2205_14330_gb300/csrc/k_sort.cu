@@ -239,33 +239,41 @@ __device__ __forceinline__ uint32_t peers_by_ballot(uint32_t d, bool full)
     return peers;
 }
 
-// Per-block digit histogram: shared-memory atomics into one block counter
-// per digit.
+// Digit histograms of HIST_TILES consecutive scatter tiles (SORT_TILE keys
+// each) per block: shared-memory atomics into one counter per (tile,
+// digit), written out as hist[digit][tile].
+constexpr int HIST_TILES = 4;
+
 __global__ void __launch_bounds__(SORT_THREADS)
 radix_hist_kernel(const uint32_t *__restrict__ keys, const uint32_t *n_dev, int64_t cap,
                   uint32_t key_lo, uint32_t key_max, int shift, int width,
                   uint32_t *__restrict__ hist, int64_t nb)
 {
-    __shared__ uint32_t s_h[RBINS];
+    __shared__ uint32_t s_h[HIST_TILES][RBINS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int j = threadIdx.x; j < RBINS; j += SORT_THREADS) s_h[j] = 0;
+    for (int j = threadIdx.x; j < HIST_TILES * RBINS; j += SORT_THREADS) (&s_h[0][0])[j] = 0;
     const int64_t n = dev_count(n_dev, cap);
-    const int64_t base = (int64_t)blockIdx.x * SORT_TILE + (int64_t)w * 32 * SORT_ITEMS;
     const uint32_t mask = (1u << width) - 1u;
-    uint32_t d[SORT_ITEMS];
+    const int64_t t0 = (int64_t)blockIdx.x * HIST_TILES;
+    __syncthreads();
 #pragma unroll
-    for (int r = 0; r < SORT_ITEMS; ++r) {
-        const int64_t i = base + r * 32 + lane;
-        d[r] = i < n ? digit_of(keys[i], key_lo, key_max, shift, mask) : (uint32_t)RBINS;
+    for (int k = 0; k < HIST_TILES; ++k) {
+        const int64_t base = (t0 + k) * SORT_TILE + (int64_t)w * 32 * SORT_ITEMS;
+        uint32_t d[SORT_ITEMS];
+#pragma unroll
+        for (int r = 0; r < SORT_ITEMS; ++r) {
+            const int64_t i = base + r * 32 + lane;
+            d[r] = i < n ? digit_of(keys[i], key_lo, key_max, shift, mask) : (uint32_t)RBINS;
+        }
+#pragma unroll
+        for (int r = 0; r < SORT_ITEMS; ++r)
+            if (d[r] < RBINS) atomicAdd(&s_h[k][d[r]], 1u);
     }
     __syncthreads();
-#pragma unroll
-    for (int r = 0; r < SORT_ITEMS; ++r)
-        if (d[r] < RBINS) atomicAdd(&s_h[d[r]], 1u);
-    __syncthreads();
     const int bins = 1 << width;
-    for (int dd = threadIdx.x; dd < bins; dd += SORT_THREADS)
-        hist[(int64_t)dd * nb + blockIdx.x] = s_h[dd];
+    for (int k = 0; k < HIST_TILES && t0 + k < nb; ++k)
+        for (int dd = threadIdx.x; dd < bins; dd += SORT_THREADS)
+            hist[(int64_t)dd * nb + t0 + k] = s_h[k][dd];
 }
 
 constexpr size_t SCATTER_SMEM = sizeof(uint32_t) * (3 * SORT_TILE + SORT_WARPS * RBINS + 3 * RBINS +
@@ -668,8 +676,8 @@ void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *&keys_alt, uin
     const int width = (key_bits + passes - 1) / passes;
     for (int shift = bit_lo; shift < bit_lo + key_bits; shift += width) {
         const int wd = bit_lo + key_bits - shift < width ? bit_lo + key_bits - shift : width;
-        radix_hist_kernel<<<(unsigned)nb, SORT_THREADS, 0, s>>>(keys, n_dev, cap, key_lo, key_max,
-                                                                shift, wd, hist, nb);
+        radix_hist_kernel<<<(unsigned)((nb + HIST_TILES - 1) / HIST_TILES), SORT_THREADS, 0, s>>>(
+            keys, n_dev, cap, key_lo, key_max, shift, wd, hist, nb);
         run_scan(LoadU32{hist}, ActStore{hist}, nullptr, nb << wd, scan_tmp, nullptr, nullptr, s);
         radix_scatter_kernel<<<(unsigned)nb, SORT_THREADS, SCATTER_SMEM, s>>>(
             keys, vals, keys_alt, vals_alt, n_dev, cap, key_lo, key_max, shift, wd, hist, nb,
