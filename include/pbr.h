@@ -392,7 +392,9 @@ int pbr_serve_trace(pbr_ctx *ctx, double *start_ms, double *end_ms, int32_t *vie
  * with every point-view visible and listed in as many tiles as the scene's
  * largest splat can reach from this camera (largest radius at the nearest
  * depth of the scene's bounding box), an upper bound of what
- * pbr_forward_workspace_size reports for the same view.  Errors:
+ * pbr_forward_workspace_size reports for the same view; when that bound is
+ * above 1/64 of the budget (a camera near or inside the scene), the exact
+ * workspace from a counting pass on the device instead.  Errors:
  * INVALID_ARG, NOT_FOUND (no such scene). */
 int pbr_serve_estimate(pbr_ctx *ctx, int32_t scene_id, const pbr_camera *cam, size_t *bytes);
 

@@ -115,6 +115,9 @@ struct ServeState {
     uint64_t next_id = 1;
     std::vector<cudaStream_t> streams;
     std::vector<bool> busy;
+    // exact workspace queries of admission (reserve_bytes)
+    cudaStream_t admit_stream = nullptr;
+    std::mutex admit_mu;
     std::vector<InFlight> inflight;
     // device intervals of completed batches: [start, end) in ms after t0_ev
     cudaEvent_t t0_ev = nullptr;
@@ -308,6 +311,7 @@ void serve_shutdown(pbr_ctx *c)
     cudaSetDevice(c->device);
     for (auto &kv : S->scenes) cudaFree(kv.second.mem);
     for (cudaStream_t s : S->streams) cudaStreamDestroy(s);
+    if (S->admit_stream) cudaStreamDestroy(S->admit_stream);
     if (S->t0_ev) cudaEventDestroy(S->t0_ev);
     delete S;
     c->serve = nullptr;
@@ -337,6 +341,11 @@ extern "C" int pbr_serve_start(pbr_ctx *c, const pbr_render_opts *opts, int32_t 
         }
         S->streams.push_back(s);
         S->busy.push_back(false);
+    }
+    if (cudaStreamCreateWithFlags(&S->admit_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        for (cudaStream_t t : S->streams) cudaStreamDestroy(t);
+        delete S;
+        return set_error(PBR_ERR_CUDA, "stream creation failed");
     }
     // reference point of the batch trace (pbr_serve_trace)
     if (cudaEventCreate(&S->t0_ev) != cudaSuccess || cudaEventRecord(S->t0_ev, S->streams[0]) != cudaSuccess) {
@@ -443,6 +452,25 @@ extern "C" int pbr_evict_scene(pbr_ctx *c, int32_t scene_id)
     return PBR_OK;
 }
 
+// The bytes a request reserves: the host bound of admission_bytes, or, when
+// that bound would take more than 1/64 of the budget (a camera close to or
+// inside the scene's bounding box makes it loose), the exact workspace of
+// the view from a counting pass on the device (pbr_forward_workspace_size),
+// so that loose bounds do not hold back other requests.  The scene must be
+// pinned (refs > 0) by the caller; mu is not held.
+static int reserve_bytes(pbr_ctx *c, ServeState *S, const pbr_points &pts, size_t bound,
+                         size_t budget, const pbr_camera &cam, size_t *bytes)
+{
+    *bytes = bound;
+    if (bound <= budget / 64) return PBR_OK;
+    std::lock_guard<std::mutex> ga(S->admit_mu);
+    size_t exact = 0;
+    PBR_TRY(pbr_forward_workspace_size(c, &pts, 1, nullptr, &cam, 1, &S->opts, 0, &exact, nullptr,
+                                       (pbr_stream_t)S->admit_stream));
+    *bytes = std::min(bound, exact);
+    return PBR_OK;
+}
+
 extern "C" int pbr_submit_request(pbr_ctx *c, int32_t scene_id, const pbr_camera *cam,
                                   float *out_rgb_device, double arrival_time, uint64_t *req_id)
 {
@@ -451,19 +479,33 @@ extern "C" int pbr_submit_request(pbr_ctx *c, int32_t scene_id, const pbr_camera
     if (cam->width <= 0 || cam->height <= 0 || cam->width > 32768 || cam->height > 32768)
         return set_error(PBR_ERR_INVALID_ARG, "camera size %dx%d", cam->width, cam->height);
     ServeState *S = c->serve;
+    pbr_points pts{};
+    size_t bound = 0, budget = 0;
     {
         std::lock_guard<std::mutex> g(S->mu);
         auto it = S->scenes.find(scene_id);
         if (it == S->scenes.end()) return set_error(PBR_ERR_NOT_FOUND, "no scene %d", scene_id);
+        bound = admission_bytes(it->second, *cam, S->opts);
+        if (bound == 0) return set_error(PBR_ERR_INVALID_ARG, "request camera is invalid");
+        pts = it->second.pts;
+        budget = S->budget;
+        it->second.refs++; // pinned from here on (queued requests hold a reference)
+    }
+    size_t bytes = 0;
+    const int rc = reserve_bytes(c, S, pts, bound, budget, *cam, &bytes);
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        if (rc != PBR_OK) {
+            S->scenes[scene_id].refs--;
+            return rc;
+        }
         Request r;
         r.id = S->next_id++;
         r.scene = scene_id;
         r.cam = *cam;
         r.out = out_rgb_device;
         r.t_arrival = arrival_time > 0.0 ? arrival_time : now_s();
-        r.bytes = admission_bytes(it->second, *cam, S->opts);
-        if (r.bytes == 0) return set_error(PBR_ERR_INVALID_ARG, "request camera is invalid");
-        it->second.refs++;
+        r.bytes = bytes;
         S->reqs[r.id] = r;
         S->queue.push_back(r.id);
         ++S->submitted;
@@ -592,10 +634,20 @@ extern "C" int pbr_serve_estimate(pbr_ctx *c, int32_t scene_id, const pbr_camera
     if (!c || !c->serve || !cam || !bytes)
         return set_error(PBR_ERR_INVALID_ARG, "pbr_serve_estimate: bad arguments");
     ServeState *S = c->serve;
+    pbr_points pts{};
+    size_t bound = 0, budget = 0;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        auto it = S->scenes.find(scene_id);
+        if (it == S->scenes.end()) return set_error(PBR_ERR_NOT_FOUND, "no scene %d", scene_id);
+        bound = admission_bytes(it->second, *cam, S->opts);
+        if (bound == 0) return set_error(PBR_ERR_INVALID_ARG, "camera is invalid");
+        pts = it->second.pts;
+        budget = S->budget;
+        it->second.refs++;
+    }
+    const int rc = reserve_bytes(c, S, pts, bound, budget, *cam, bytes);
     std::lock_guard<std::mutex> g(S->mu);
-    auto it = S->scenes.find(scene_id);
-    if (it == S->scenes.end()) return set_error(PBR_ERR_NOT_FOUND, "no scene %d", scene_id);
-    *bytes = admission_bytes(it->second, *cam, S->opts);
-    if (*bytes == 0) return set_error(PBR_ERR_INVALID_ARG, "camera is invalid");
-    return PBR_OK;
+    S->scenes[scene_id].refs--;
+    return rc;
 }

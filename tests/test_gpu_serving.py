@@ -173,12 +173,16 @@ def test_admission_estimate_covers_the_workspace(env):
     for k, d in enumerate(data):
         sid = sv.upload(d)
         scene = pbr.Scene(d["pos"], d["sh"], d["opacity"], d["radius"], d["deg"])
-        for dist, (W, H) in ((3.0, (1920, 1072)), (3.0, (256, 256)), (5.0, (1920, 1072))):
+        for dist, (W, H) in ((3.0, (1920, 1072)), (3.0, (256, 256)), (5.0, (1920, 1072)),
+                             (0.5, (1280, 720))):  # the last camera is inside the scene
             cam = scenes.camera((0.3 * dist, 0.4 * dist, 0.866 * dist), W, H)
             exact, _ = R.workspace_size([scene], [cam], opts, keep_state=False)
             est = sv.estimate(sid, cam)
             ratios.append(est / exact)
             assert est >= exact, (k, dist, W, H, exact, est)
+        # a request from inside the scene is admitted and completes
+        rid, out = sv.submit(sid, scenes.camera((0.15, 0.2, 0.43), 320, 240))
+        assert sv.wait(rid) == 0
         sv.evict(sid)
     print(f"admission reservation / workspace: {min(ratios):.2f} .. {max(ratios):.2f}")
     sv.stop()
