@@ -18,9 +18,9 @@
 //   5. tile_ranges      : [start, end) of every tile in the sorted list
 //
 // Scans are reduce-then-scan (three kernels, no inter-block waiting).  The
-// radix pass ranks keys stably inside a block with warp ballots and shared
-// atomics, and reorders them in shared memory so that the scatter writes
-// contiguous runs.
+// radix pass ranks keys stably inside a block with per-warp peer masks
+// (shared-memory OR) and shared atomics, and reorders them in shared memory
+// so that the scatter writes contiguous runs.
 #include "pbr_internal.cuh"
 
 namespace pbr {
@@ -311,6 +311,10 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
         gb[k] = dd < bins ? hist[(int64_t)dd * nb + blockIdx.x] : 0u;
     }
     for (int j = threadIdx.x; j < SORT_WARPS * RBINS; j += SORT_THREADS) (&s_wh[0][0])[j] = 0;
+    // the warps' peer masks (one word per digit) live in s_k, free until the
+    // placement below
+    uint32_t *s_pm = s_k + w * RBINS;
+    for (int j = threadIdx.x; j < SORT_TILE; j += SORT_THREADS) s_k[j] = 0;
     const int64_t base = blk + (int64_t)w * 32 * SORT_ITEMS;
     uint32_t key[SORT_ITEMS], rank[SORT_ITEMS];
     const int lbase = w * 32 * SORT_ITEMS + lane; // local index of round 0
@@ -325,17 +329,32 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
     const uint32_t lt = lanemask_lt();
     const bool full = blk + SORT_TILE <= n; // every key of the block is in range
     {
-        // stable rank inside the warp: peer masks from ballots, the group
-        // leader's shared-memory atomic on the warp's digit counter (one
-        // warp's shared atomics execute in program order, so rounds stay
-        // ordered), then the broadcast of each group's base
+        // stable rank inside the warp: the lanes holding the same digit (each
+        // lane ORs its bit into its digit's word of the warp's peer masks and
+        // reads the word back; with out-of-range keys, from ballots), the
+        // group leader's shared-memory atomic on the warp's digit counter
+        // (one warp's shared atomics execute in program order, so rounds stay
+        // ordered) and its reset of the peer word, then the broadcast of each
+        // group's base
 #pragma unroll
         for (int r = 0; r < SORT_ITEMS; ++r) {
             const bool ok = base + r * 32 + lane < n;
             const uint32_t d = ok ? digit_of(key[r], key_lo, key_max, shift, mask) : (uint32_t)RBINS;
-            const uint32_t peers = peers_by_ballot(d, full);
+            uint32_t peers;
+            if (full || __all_sync(0xffffffffu, ok)) {
+                atomicOr(&s_pm[d], 1u << lane);
+                __syncwarp();
+                peers = s_pm[d];
+                __syncwarp();
+            } else {
+                peers = peers_by_ballot(d, false);
+            }
             uint32_t old = 0;
-            if (d < RBINS && (peers & lt) == 0) old = atomicAdd(&s_wh[w][d], (uint32_t)__popc(peers));
+            if (d < RBINS && (peers & lt) == 0) {
+                old = atomicAdd(&s_wh[w][d], (uint32_t)__popc(peers));
+                s_pm[d] = 0;
+            }
+            __syncwarp(); // peer words clear before the next round's ORs
             rank[r] = (uint32_t)(__ffs(peers) - 1) | ((uint32_t)__popc(peers & lt) << 5) | (old << 10);
         }
 #pragma unroll
