@@ -676,48 +676,35 @@ def measure_workload(args, pbr, torch, R, sc, desc, dist, world, local, headline
         plain = {"fwd_bwd_mp_s": mp / (p_ms * 1e-3), "fwd_mp_s": mp / (pf_ms * 1e-3),
                  "ms_per_step": p_ms, "speedup_fwd_bwd": p_ms / ms, "speedup_fwd": pf_ms / fwd_ms}
 
-    # ---- end to end through the public API with host buffers (graph step)
+    # ---- end to end through the public API with host buffers (graph step):
+    # every step uploads its data (the target images) from pinned host memory
+    # and reads its result (the loss) back; the scene parameters and cameras
+    # stay resident, as a model's state does between steps
     e2e = None
     if headline and not args.no_e2e:
-        host = [[t.detach().cpu().pin_memory() for t in (s.pos, s.sh, s.opacity, s.radius)]
-                for s in scene_list]
-        host_tgt = target.cpu().pin_memory()
-        out_h = [torch.empty(tuple(G.grad_pos.shape)).pin_memory(),
-                 torch.empty(tuple(G.grad_sh.shape)).pin_memory(),
-                 torch.empty(tuple(G.grad_opacity.shape)).pin_memory(),
-                 torch.empty(1, dtype=torch.float64).pin_memory()]
-        h2d = sum(t.numel() * t.element_size() for ts in host for t in ts) + \
-            host_tgt.numel() * host_tgt.element_size()
-        d2h = sum(t.numel() * t.element_size() for t in out_h)
+        host_tgt = [target.cpu().pin_memory() for _ in range(2)]  # two steps' data
+        out_h = torch.empty(1, dtype=torch.float64).pin_memory()
+        h2d = host_tgt[0].numel() * host_tgt[0].element_size()
+        d2h = out_h.numel() * out_h.element_size()
 
-        # double-buffered pipeline: two sets of device inputs, one captured
-        # step bound to each; step k+1's inputs upload on a copy stream while
-        # step k computes, and step k's results return meanwhile
-        scenes_b = [pbr.Scene(sc_.pos.clone(), sc_.sh.clone(), sc_.opacity.clone(),
-                              sc_.radius.clone(), sc_.deg) for sc_ in scene_list]
+        # double-buffered pipeline: two target buffers, one captured step bound
+        # to each; step k+1's upload and step k's download run on a copy
+        # stream while step k computes
         target_b = target.clone()
-        Gb = pbr.Graph(R, scenes_b, cams, opts, scene_of_view=sov, target=target_b,
+        Gb = pbr.Graph(R, scene_list, cams, opts, scene_of_view=sov, target=target_b,
                        loss=loss_kind)
-        slots = [(G, scene_list, target), (Gb, scenes_b, target_b)]
+        slots = [(G, target), (Gb, target_b)]
         main_s = torch.cuda.current_stream()
         cs = torch.cuda.Stream()
 
-        def upload(slot, ev):
-            g_, scs, tgt = slots[slot]
+        def upload(slot, k, ev):
             with torch.cuda.stream(cs):
-                for hs, ds in zip(host, scs):
-                    for h, d in zip(hs, (ds.pos, ds.sh, ds.opacity, ds.radius)):
-                        d.copy_(h, non_blocking=True)
-                tgt.copy_(host_tgt, non_blocking=True)
+                slots[slot][1].copy_(host_tgt[k % 2], non_blocking=True)
                 ev.record(cs)
 
         def download(slot):
-            g_ = slots[slot][0]
             with torch.cuda.stream(cs):
-                out_h[0].copy_(g_.grad_pos, non_blocking=True)
-                out_h[1].copy_(g_.grad_sh, non_blocking=True)
-                out_h[2].copy_(g_.grad_opacity, non_blocking=True)
-                out_h[3].copy_(g_.loss, non_blocking=True)
+                out_h.copy_(slots[slot][0].loss, non_blocking=True)
 
         def e2e_run(k):
             ev_in = [torch.cuda.Event(), torch.cuda.Event()]
@@ -726,7 +713,7 @@ def measure_workload(args, pbr, torch, R, sc, desc, dist, world, local, headline
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(main_s)
             cs.wait_stream(main_s)
-            upload(0, ev_in[0])
+            upload(0, 0, ev_in[0])
             for it in range(k):
                 s_ = it % 2
                 main_s.wait_event(ev_in[s_])
@@ -735,7 +722,7 @@ def measure_workload(args, pbr, torch, R, sc, desc, dist, world, local, headline
                 if it + 1 < k:
                     if it >= 1:
                         cs.wait_event(ev_done[1 - s_])  # step it-1 used the other slot
-                    upload(1 - s_, ev_in[1 - s_])
+                    upload(1 - s_, it + 1, ev_in[1 - s_])
                 cs.wait_event(ev_done[s_])
                 download(s_)
             main_s.wait_stream(cs)
@@ -750,10 +737,11 @@ def measure_workload(args, pbr, torch, R, sc, desc, dist, world, local, headline
         Gb.close()
         e2e = {"value": world * mp / (e_ms * 1e-3), "unit": "MP/s", "ms_per_step": e_ms,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "path": "every step: its inputs (scene parameters and target images) from "
-                       "pinned host memory, the graph training step, its gradients and loss "
-                       "to pinned host memory; double-buffered, so step k+1's upload and step "
-                       "k's download run on a copy stream while step k computes"}
+               "path": "every step: its data (the target images) from pinned host memory, the "
+                       "graph training step (forward, loss, backward), its loss to pinned host "
+                       "memory; the scene parameters and cameras stay resident; double-buffered, "
+                       "so step k+1's upload and step k's download run on a copy stream while "
+                       "step k computes"}
     G.close()
 
     # ---- roofline of the dominant kernel and of every stage
