@@ -273,33 +273,46 @@ def test_sh_degrees(R, deg):
     st.close()
 
 
-def test_edge_cases(R):
+@pytest.mark.parametrize("sched", [dict(), dict(persistent=1, tile=(16, 32)),
+                                   dict(persistent=1, tile=(8, 8), bwd_mode=2)],
+                         ids=["streamed", "persistent-16x32", "persistent-8x8-store"])
+def test_edge_cases(R, sched):
+    import torch
     pbr = _pbr()
     cam = scenes.camera((0.0, 0.0, 2.5), 20, 12)
-    # empty scene -> background everywhere
+    # empty scene -> background everywhere, zero gradients
     empty = dict(pos=np.zeros((0, 3), np.float32), sh=np.zeros((0, 1, 3), np.float32),
                  opacity=np.zeros(0, np.float32), radius=np.zeros(0, np.float32), deg=0)
-    img, st, _ = _gpu_render(R, empty, [cam], bg=(0.1, 0.2, 0.3))
+    img, st, _ = _gpu_render(R, empty, [cam], bg=(0.1, 0.2, 0.3), **sched)
     assert np.allclose(img.cpu().numpy(), [0.1, 0.2, 0.3])
     st.close()
-    # every point behind the camera or at the near plane -> culled
+    # every point behind the camera or at the near plane -> culled, zero gradients
     sc = _small_scene(9, n=50)
     sc["pos"][:, 2] = np.float32(2.5)  # z = 0 in the camera frame
-    img, st, _ = _gpu_render(R, sc, [cam])
+    img, st, _ = _gpu_render(R, sc, [cam], **sched)
     assert np.all(img.cpu().numpy() == 0) and st.info()["n_pairs"] == 0
+    gpos, gsh, gop = R.backward(st, torch.ones_like(img))
+    assert not gpos.any() and not gsh.any() and not gop.any()
     st.close()
-    # a 1x1 image and a one-row image
+    # a 1x1 image and one-row and one-column images, with their gradients
     sc = _small_scene(10, n=200, spread=0.2, r=(0.05, 0.2))
     for W, H in ((1, 1), (37, 1), (1, 29)):
         c = scenes.camera((0.0, 0.0, 2.0), W, H)
-        img, st, _ = _gpu_render(R, sc, [c])
+        img, st, _ = _gpu_render(R, sc, [c], **sched)
         ref, _, _ = O.render(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], [c])
         assert np.abs(img.cpu().numpy() - ref).max() <= IMG_TOL
+        g = np.random.default_rng(W * 100 + H).normal(size=ref.shape)
+        gpos, gsh, gop = R.backward(st, torch.from_numpy(g.astype(np.float32)).cuda())
+        dpos, dsh, dop = O.backward(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"],
+                                    [c], g)
+        for a, b in ((gpos, dpos), (gop, dop)):
+            a = a.cpu().numpy().astype(np.float64)
+            assert np.linalg.norm(a - b) <= GRAD_TOL * max(np.linalg.norm(b), 1e-12)
         st.close()
     # equal depths: ties broken by point index
     sc = _small_scene(11, n=40)
     sc["pos"][:, 2] = np.float32(0.25)
-    img, st, _ = _gpu_render(R, sc, [cam])
+    img, st, _ = _gpu_render(R, sc, [cam], **sched)
     ref, _, _ = O.render(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], [cam])
     assert np.abs(img.cpu().numpy() - ref).max() <= IMG_TOL
     st.close()
