@@ -49,11 +49,11 @@ FLOP_TEST, FLOP_FWD, FLOP_BWD = 6, 11, 31
 CAPTURED_TRAFFIC = {
     ("raster_bwd", "16x32", 0, 1): {
         "bytes": 3.00 * (2.244e9 + 0.247e9), "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
-        "sha256": "0de7b8b7e3681e0653fdab7d65c64a4120f2f0e71b194a5461a259b16bd85bd0",
+        "sha256": "bf867d3cc833d015eaf7bde493749e68fba7b49b8701de1b91440740381d234e",
         "profile": "profiles/raster_persist_16x32_16views.md"},
     ("raster_fwd", "16x32", 0, 1): {
         "bytes": 3.00 * (1.313e9 + 0.365e9), "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
-        "sha256": "0de7b8b7e3681e0653fdab7d65c64a4120f2f0e71b194a5461a259b16bd85bd0",
+        "sha256": "bf867d3cc833d015eaf7bde493749e68fba7b49b8701de1b91440740381d234e",
         "profile": "profiles/raster_persist_16x32_16views.md"},
 }
 

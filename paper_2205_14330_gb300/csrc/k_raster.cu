@@ -719,8 +719,10 @@ __device__ __forceinline__ void fwd_pair_item(const PixelGeom &gA, const PixelGe
 // 14.8 ms with the reduction for 2 or more and 22 ms with atomics only).
 constexpr int BWD_DIRECT_MAX = 16;
 // The same for the two-pixels-per-lane backward, whose lanes add the terms
-// of both their pixels: fastest at 24 (11.1 ms; 11.4 ms at 16, 11.9 ms at
-// 8, 15.8 ms with atomics only) on the same workload.
+// of both their pixels: fastest at 20-24 (11.1 ms; 11.4 ms at 16, 11.9 ms
+// at 8, 15.8 ms with atomics only on the same workload; with the current
+// kernels 9.89 ms at 24, 9.89 at 20, 10.61 at 28 and 11.39 with the
+// reduction for every point).
 constexpr int BWD_PAIR_DIRECT_MAX = 24;
 // The persistent backward runs 8 x 8-pixel warps (two pixels per lane):
 // 8 x 16 (four pixels per lane) examined 41% more pairs through the coarser
@@ -1092,9 +1094,9 @@ __device__ __forceinline__ uint4 tile_desc(const Batch &b, const uint2 *ranges, 
 
 // STATS: count examined / composited pairs into stats (which must then be
 // non-null); without, the loops carry no counting.  The forward's 8 x 8
-// warps run five blocks per SM (48 registers): 5.84 ms on the 1M-point,
-// 64-view step against 6.05 at four and 6.10 at six.  The backward runs
-// best at its natural four blocks (five: 11.1 -> 11.9 ms).
+// warps run five blocks per SM (48 registers): 5.47 ms on the 1M-point,
+// 64-view step against 5.66 at four (six spill).  The backward runs best at
+// its natural four blocks (five: 11.1 -> 11.9 ms).
 template <int TW, int TH, bool STATS, bool STORE>
 __global__ void __launch_bounds__(PERSIST_THREADS, FWD_PERSIST_BLOCKS)
 raster_fwd_persist_kernel(Batch b, DevOpts o, const uint2 *__restrict__ ranges,
