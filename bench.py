@@ -49,11 +49,11 @@ FLOP_TEST, FLOP_FWD, FLOP_BWD = 6, 11, 31
 CAPTURED_TRAFFIC = {
     ("raster_bwd", "16x32", 0, 1): {
         "bytes": 3.00 * (2.244e9 + 0.247e9), "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
-        "sha256": "bf867d3cc833d015eaf7bde493749e68fba7b49b8701de1b91440740381d234e",
+        "sha256": "bcace96283d8ee03fc4922e54bb71897e1d4abd2fe8ee4205a525ca23a971ae9",
         "profile": "profiles/raster_persist_16x32_16views.md"},
     ("raster_fwd", "16x32", 0, 1): {
         "bytes": 3.00 * (1.313e9 + 0.365e9), "file": "paper_2205_14330_gb300/csrc/k_raster.cu",
-        "sha256": "bf867d3cc833d015eaf7bde493749e68fba7b49b8701de1b91440740381d234e",
+        "sha256": "bcace96283d8ee03fc4922e54bb71897e1d4abd2fe8ee4205a525ca23a971ae9",
         "profile": "profiles/raster_persist_16x32_16views.md"},
 }
 

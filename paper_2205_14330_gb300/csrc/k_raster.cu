@@ -720,9 +720,9 @@ __device__ __forceinline__ void fwd_pair_item(const PixelGeom &gA, const PixelGe
 constexpr int BWD_DIRECT_MAX = 16;
 // The same for the two-pixels-per-lane backward, whose lanes add the terms
 // of both their pixels: fastest at 20-24 (11.1 ms; 11.4 ms at 16, 11.9 ms
-// at 8, 15.8 ms with atomics only on the same workload; with the current
-// kernels 9.89 ms at 24, 9.89 at 20, 10.61 at 28 and 11.39 with the
-// reduction for every point).
+// at 8, 15.8 ms with atomics only on the same workload; re-measured on a
+// later version: 10.13 ms at 24, 10.14 at 20, 10.61 at 28 and 11.39 with
+// the reduction for every point).
 constexpr int BWD_PAIR_DIRECT_MAX = 24;
 // The persistent backward runs 8 x 8-pixel warps (two pixels per lane):
 // 8 x 16 (four pixels per lane) examined 41% more pairs through the coarser
