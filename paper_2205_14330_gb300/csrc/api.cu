@@ -378,13 +378,15 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
     TempBufs tmp(s);
     uint32_t *zbits = nullptr;
     uint4 *rect = nullptr;
+    uint8_t *nt8 = nullptr;
     PBR_TRY(tmp.alloc(&zbits, sizeof(uint32_t) * npv));
     PBR_TRY(tmp.alloc(&rect, sizeof(uint4) * npv));
+    PBR_TRY(tmp.alloc(&nt8, (size_t)npv));
     PBR_CUDA(cudaMemsetAsync(st->counters, 0, 128, s));
     PBR_CUDA(cudaMemsetAsync((char *)st->counters + 48, 0xff, 4, s)); // depth-bits minimum
     {
         StageScope t(c, STG_PREPROCESS_FWD, s);
-        launch_preprocess_fwd(b, o, st->rec, zbits, st->ntiles, rect, st->counters, s);
+        launch_preprocess_fwd(b, o, st->rec, zbits, st->ntiles, nt8, rect, st->counters, s);
     }
     PBR_CUDA(cudaGetLastError());
     // size the lists (pinned read-back buffer per host thread: the serving
@@ -451,7 +453,7 @@ int pbr::forward_eager(pbr_ctx *c, pbr_state *st, float *out_rgb, cudaStream_t s
     uint32_t *tk = st->tile_keys, *tv = st->tile_vals;
     {
         StageScope t(c, STG_EMIT, s);
-        launch_emit_pairs(b, o, vv, n_vis_dev, (int64_t)n_vis, st->ntiles, rect, tk, tv,
+        launch_emit_pairs(b, o, vv, n_vis_dev, (int64_t)n_vis, st->ntiles, nt8, rect, tk, tv,
                           (int64_t)n_pairs, status, temp, s);
     }
     // 4. stable sort by tile id
@@ -516,7 +518,8 @@ size_t pbr::forward_bytes(const HostLayout &L, int64_t n_vis, int64_t n_pairs,
     size_t b = al(sizeof(DevView) * L.views.size()) + al(sizeof(DevScene) * L.scenes.size()) +
                al(sizeof(int32_t) * L.view_list.size());
     b += al(32 * (size_t)npv) + al(4 * (size_t)npv) + 128;         // records, tile counts, counters
-    b += al(4 * (size_t)npv) + al(16 * (size_t)npv);              // depth bits, rectangles
+    b += al(4 * (size_t)npv) + al(16 * (size_t)npv) + al((size_t)npv); // depth bits, rectangles,
+                                                                         // one-byte counts
     b += (direct ? 0 : al(4 * (size_t)n_sort)) + 3 * al(4 * (size_t)n_sort); // depth sort
     b += 4 * al(4 * (size_t)n_pairs);                              // pair lists, sort buffers
     b += al(8 * (size_t)L.n_tiles) + 2 * al(4 * (size_t)L.n_pix);  // ranges, T_final, n_contrib
@@ -567,7 +570,8 @@ extern "C" int pbr_forward_workspace_size(pbr_ctx *c, const pbr_points *scenes, 
     b.n_tiles = L.n_tiles;
     b.n_pix = L.n_pix;
     b.n_point_blocks = L.n_point_blocks;
-    launch_preprocess_fwd(b, dev_opts(opts), nullptr, nullptr, nullptr, nullptr, counters, s);
+    launch_preprocess_fwd(b, dev_opts(opts), nullptr, nullptr, nullptr, nullptr, nullptr, counters,
+                          s);
     PBR_CUDA(cudaGetLastError());
     unsigned long long host[2] = {0, 0};
     PBR_CUDA(cudaMemcpyAsync(host, counters, sizeof host, cudaMemcpyDeviceToHost, s));

@@ -99,6 +99,7 @@ extern "C" int pbr_render_forward_noalloc(const pbr_points *scenes, int32_t n_sc
     uint32_t *ntiles = cv.take<uint32_t>(sizeof(uint32_t) * npv);
     uint32_t *zbits = cv.take<uint32_t>(sizeof(uint32_t) * npv);
     uint4 *rect = cv.take<uint4>(sizeof(uint4) * npv);
+    uint8_t *nt8 = cv.take<uint8_t>((size_t)npv);
     uint2 *ranges = cv.take<uint2>(sizeof(uint2) * L.n_tiles);
     float *T_final = cv.take<float>(sizeof(float) * L.n_pix);
     uint32_t *n_contrib = cv.take<uint32_t>(sizeof(uint32_t) * L.n_pix);
@@ -124,7 +125,7 @@ extern "C" int pbr_render_forward_noalloc(const pbr_points *scenes, int32_t n_sc
     b.n_pix = L.n_pix;
     b.n_point_blocks = L.n_point_blocks;
     PBR_CUDA(cudaMemsetAsync(counters, 0, 128, s));
-    launch_preprocess_fwd(b, o, rec, zbits, ntiles, rect, counters, s);
+    launch_preprocess_fwd(b, o, rec, zbits, ntiles, nt8, rect, counters, s);
     PBR_CUDA(cudaGetLastError());
     unsigned long long host_counts[2] = {0, 0};
     PBR_CUDA(cudaMemcpyAsync(host_counts, counters, sizeof host_counts, cudaMemcpyDeviceToHost, s));
@@ -151,7 +152,7 @@ extern "C" int pbr_render_forward_noalloc(const pbr_points *scenes, int32_t n_sc
     const uint32_t *n_pairs_dev = (const uint32_t *)(counters + 0);
     launch_compact_visible(ntiles, zbits, npv, vk, vv, nullptr, temp, s);
     radix_sort_pairs(vk, vv, vk2, vv2, n_vis_dev, (int64_t)n_vis, 32, temp, s);
-    launch_emit_pairs(b, o, vv, n_vis_dev, (int64_t)n_vis, ntiles, rect, tk, tv,
+    launch_emit_pairs(b, o, vv, n_vis_dev, (int64_t)n_vis, ntiles, nt8, rect, tk, tv,
                       (int64_t)n_pairs, status, temp, s);
     int key_bits = 1;
     while (key_bits < 32 && ((L.n_tiles - 1) >> key_bits)) ++key_bits;

@@ -91,6 +91,7 @@ struct pbr_graph {
     int32_t *d_view_list = nullptr;
     float4 *rec = nullptr, *g2d = nullptr;
     uint32_t *ntiles = nullptr, *zbits = nullptr;
+    uint8_t *nt8 = nullptr;
     uint4 *rect = nullptr;
     uint2 *ranges = nullptr;
     unsigned long long *counters = nullptr;
@@ -167,7 +168,7 @@ void enqueue_forward(pbr_graph *g, cudaStream_t s)
     const uint32_t *n_pairs_dev = (const uint32_t *)(g->counters + 0);
     cudaMemsetAsync(g->counters, 0, 128, s);
     cudaMemsetAsync((char *)g->counters + 48, 0xff, 4, s);
-    launch_preprocess_fwd(b, o, g->rec, g->zbits, g->ntiles, g->rect, g->counters, s);
+    launch_preprocess_fwd(b, o, g->rec, g->zbits, g->ntiles, g->nt8, g->rect, g->counters, s);
     // visible keys must lie below the marker (direct) or inside the bits
     const uint64_t span = g->direct_depth ? (uint64_t)g->depth_marker
                           : g->depth_bits >= 32 ? (1ull << 32) : (1ull << g->depth_bits);
@@ -184,7 +185,7 @@ void enqueue_forward(pbr_graph *g, cudaStream_t s)
                          g->depth_lo);
     }
     uint32_t *tk = g->tk, *tv = g->tv, *tk2 = g->tk2, *tv2 = g->tv2;
-    launch_emit_pairs(b, o, vv, n_vis_dev, g->cap_vis, g->ntiles, g->rect, tk, tv,
+    launch_emit_pairs(b, o, vv, n_vis_dev, g->cap_vis, g->ntiles, g->nt8, g->rect, tk, tv,
                       g->cap_pairs, status, g->temp, s);
     int key_bits = bit_width(L.n_tiles > 0 ? L.n_tiles - 1 : 0);
     if (key_bits < 1) key_bits = 1;
@@ -331,6 +332,7 @@ int plan_and_capture(pbr_graph *g, cudaStream_t user_stream)
     PBR_TRY(g->alloc(&g->ntiles, sizeof(uint32_t) * npv));
     PBR_TRY(g->alloc(&g->zbits, sizeof(uint32_t) * npv));
     PBR_TRY(g->alloc(&g->rect, sizeof(uint4) * npv));
+    PBR_TRY(g->alloc(&g->nt8, (size_t)npv));
     if (!g->direct_depth) PBR_TRY(g->alloc(&g->vk, 4 * (size_t)g->cap_vis));
     PBR_TRY(g->alloc(&g->vv, 4 * (size_t)g->cap_vis));
     PBR_TRY(g->alloc(&g->vk2, 4 * (size_t)g->cap_vis));

@@ -82,6 +82,7 @@ template <int DEG>
 __device__ void pre_fwd_point(const Batch &b, const DevOpts &o, const DevScene &sc, int64_t i,
                               const float *hs, float4 *__restrict__ rec,
                               uint32_t *__restrict__ zbits, uint32_t *__restrict__ ntiles,
+                              uint8_t *__restrict__ nt8,
                               uint4 *__restrict__ rect, uint32_t &vis_cnt, uint32_t &pair_cnt,
                               uint32_t &zlo, uint32_t &zhi)
 {
@@ -192,13 +193,15 @@ __device__ void pre_fwd_point(const Batch &b, const DevOpts &o, const DevScene &
         }
         if (!rec) continue; // counting only: nothing is written
         ntiles[pv] = nt;
+        nt8[pv] = (uint8_t)(nt < 255u ? nt : 255u);
         if (nt == 0) zbits[pv] = 0xffffffffu; // not visible: sorts behind every depth
     }
 }
 
 __global__ void __launch_bounds__(PRE_THREADS, 6)
 preprocess_fwd_kernel(Batch b, DevOpts o, float4 *__restrict__ rec, uint32_t *__restrict__ zbits,
-                      uint32_t *__restrict__ ntiles, uint4 *__restrict__ rect,
+                      uint32_t *__restrict__ ntiles, uint8_t *__restrict__ nt8,
+                      uint4 *__restrict__ rect,
                       unsigned long long *__restrict__ counters)
 {
     __shared__ float s_sh[48 * SH_STRIDE];
@@ -215,10 +218,10 @@ preprocess_fwd_kernel(Batch b, DevOpts o, float4 *__restrict__ rec, uint32_t *__
         const int64_t i = first + threadIdx.x;
         const float *hs = s_sh + threadIdx.x; // coefficient j at hs[j * SH_STRIDE]
         switch (sc.deg) {
-        case 0: pre_fwd_point<0>(b, o, sc, i, hs, rec, zbits, ntiles, rect, vis, pairs, zlo, zhi); break;
-        case 1: pre_fwd_point<1>(b, o, sc, i, hs, rec, zbits, ntiles, rect, vis, pairs, zlo, zhi); break;
-        case 2: pre_fwd_point<2>(b, o, sc, i, hs, rec, zbits, ntiles, rect, vis, pairs, zlo, zhi); break;
-        default: pre_fwd_point<3>(b, o, sc, i, hs, rec, zbits, ntiles, rect, vis, pairs, zlo, zhi); break;
+        case 0: pre_fwd_point<0>(b, o, sc, i, hs, rec, zbits, ntiles, nt8, rect, vis, pairs, zlo, zhi); break;
+        case 1: pre_fwd_point<1>(b, o, sc, i, hs, rec, zbits, ntiles, nt8, rect, vis, pairs, zlo, zhi); break;
+        case 2: pre_fwd_point<2>(b, o, sc, i, hs, rec, zbits, ntiles, nt8, rect, vis, pairs, zlo, zhi); break;
+        default: pre_fwd_point<3>(b, o, sc, i, hs, rec, zbits, ntiles, nt8, rect, vis, pairs, zlo, zhi); break;
         }
     }
     // per-warp totals, one atomic per warp: counters[0] pairs, [1] visible,
@@ -421,12 +424,12 @@ preprocess_bwd_kernel(Batch b, DevOpts o, const float4 *__restrict__ g2d,
 } // namespace
 
 void launch_preprocess_fwd(const Batch &b, const DevOpts &o, float4 *rec, uint32_t *zbits,
-                           uint32_t *ntiles, uint4 *rect, unsigned long long *counters,
-                           cudaStream_t s)
+                           uint32_t *ntiles, uint8_t *nt8, uint4 *rect,
+                           unsigned long long *counters, cudaStream_t s)
 {
     if (b.n_point_blocks <= 0) return;
     preprocess_fwd_kernel<<<(unsigned)b.n_point_blocks, PRE_THREADS, 0, s>>>(
-        b, o, rec, zbits, ntiles, rect, counters);
+        b, o, rec, zbits, ntiles, nt8, rect, counters);
     count_launches(1);
 }
 

@@ -432,13 +432,19 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__res
 // ------------------------------------------------------------ emission
 // Tile counts in depth order (the scan that places each point-view's run of
 // pairs reads them).
+// The random gather reads the one-byte copy (a fourth of the bytes, which
+// stay in L2) and the full count only for the rare counts above 254.
 __global__ void gather_counts_kernel(const uint32_t *__restrict__ sorted_pv,
-                                     const uint32_t *__restrict__ ntiles, const uint32_t *n_dev,
+                                     const uint32_t *__restrict__ ntiles,
+                                     const uint8_t *__restrict__ nt8, const uint32_t *n_dev,
                                      int64_t cap, uint32_t *__restrict__ nt_sorted)
 {
     const int64_t n = dev_count(n_dev, cap);
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n) nt_sorted[j] = ntiles[sorted_pv[j]];
+    if (j >= n) return;
+    const uint32_t pv = sorted_pv[j];
+    const uint32_t c = nt8[pv];
+    nt_sorted[j] = c < 255u ? c : ntiles[pv];
 }
 
 // Position of the (t+1)-th set bit of m (t < popc(m)), by halving.
@@ -717,7 +723,8 @@ size_t emit_temp_bytes(int64_t cap_vis)
 
 void launch_emit_pairs(const Batch &b, const DevOpts &o, const uint32_t *sorted_pv,
                        const uint32_t *n_vis, int64_t cap_vis, const uint32_t *ntiles,
-                       const uint4 *rect, uint32_t *keys, uint32_t *vals, int64_t cap_pairs,
+                       const uint8_t *nt8, const uint4 *rect, uint32_t *keys, uint32_t *vals,
+                       int64_t cap_pairs,
                        uint32_t *status, void *temp, cudaStream_t s)
 {
     if (cap_vis <= 0) return;
@@ -725,7 +732,7 @@ void launch_emit_pairs(const Batch &b, const DevOpts &o, const uint32_t *sorted_
     uint32_t *offs = nt_sorted + cap_vis;
     void *scan_tmp = offs + cap_vis;
     const unsigned nb = (unsigned)((cap_vis + 255) / 256);
-    gather_counts_kernel<<<nb, 256, 0, s>>>(sorted_pv, ntiles, n_vis, cap_vis, nt_sorted);
+    gather_counts_kernel<<<nb, 256, 0, s>>>(sorted_pv, ntiles, nt8, n_vis, cap_vis, nt_sorted);
     run_scan(LoadU32{nt_sorted}, ActStore{offs}, n_vis, cap_vis, scan_tmp, nullptr, status, s);
     auto emit = emit_pairs_kernel<16, 16>;
     if (o.tile_w == 8 && o.tile_h == 8) emit = emit_pairs_kernel<8, 8>;

@@ -187,14 +187,16 @@ __device__ __forceinline__ bool pixel_box(float px, float py, float rc, int W, i
 // point-views (word 12 must start at 0xffffffff, word 13 at 0).
 // zbits[pv] = fp32 bits of the depth, 0xffffffff for a point-view listing no
 // tile (every finite depth's bits are smaller).
+// nt8[pv] = min(tile count, 255): a one-byte copy of the counts, small
+// enough to stay in L2 while the emission's count gather reads it.
 // rect[pv] = {px, py, rc (fp32 bits), w}: the splat centre and cutoff
 // radius (the pixel box follows from them by pixel_box), w = the mask of
 // the listed tiles of the box (bit (ty - ty0) * wx + (tx - tx0)) when the
 // box spans at most 32 tiles, else the number of listed tiles.
 // rec == nullptr: counting only (the counters; nothing else is written).
 void launch_preprocess_fwd(const Batch &b, const DevOpts &o, float4 *rec, uint32_t *zbits,
-                           uint32_t *ntiles, uint4 *rect, unsigned long long *counters,
-                           cudaStream_t s);
+                           uint32_t *ntiles, uint8_t *nt8, uint4 *rect,
+                           unsigned long long *counters, cudaStream_t s);
 void launch_preprocess_bwd(const Batch &b, const DevOpts &o, const float4 *g2d, float *grad_pos,
                            float *grad_sh, float *grad_opacity, cudaStream_t s);
 
@@ -229,6 +231,7 @@ size_t emit_temp_bytes(int64_t cap_vis);
 // Keys are tile << block_bits(tile size) | block mask.
 void launch_emit_pairs(const Batch &b, const DevOpts &o, const uint32_t *sorted_pv,
                        const uint32_t *n_vis, int64_t cap_vis, const uint32_t *ntiles,
+                       const uint8_t *nt8,
                        const uint4 *rect, uint32_t *keys, uint32_t *vals, int64_t cap_pairs,
                        uint32_t *status, void *temp, cudaStream_t s);
 // Ranges of the tiles key >> shift of the sorted keys.
