@@ -89,6 +89,13 @@ def test_graph_frames_match_oracle(env, sched):
     assert G.check()[0]
     out = G.out.cpu().numpy()
     err = max(float(np.abs(out[f * npx:(f + 1) * npx] - refs[f]).max()) for f in range(nf))
+    # the eager forward of the same batch and schedule: tells a wrong replay
+    # from a wrong reference when the comparison below fails
+    eager, st = R.forward(sc, views, pbr.default_opts(**sched), scene_of_view=sov)
+    st.close()
+    e_eager = max(float(np.abs(eager.cpu().numpy()[f * npx:(f + 1) * npx] - refs[f]).max())
+                  for f in range(nf))
+    same = bool(torch.equal(G.out, eager))
     # STEP: dL/dI = 2 (I - target) per frame, adjoint per frame
     G.launch(pbr.Graph.STEP)
     assert G.check()[0]
@@ -118,8 +125,10 @@ def test_graph_frames_match_oracle(env, sched):
         e_train.append((_rel_np((sc[f].pos - p0[f]).cpu().numpy(), -lr_pos * dpos),
                         _rel_np((sc[f].sh - h0[f]).cpu().numpy().reshape(dsh.shape),
                                 -lr_sh * dsh)))
-    print(f"graph frames {sched}: image max abs err {err:.3e}; step grad rel L2 (worst frame) "
+    print(f"graph frames {sched}: image max abs err {err:.3e} (eager {e_eager:.3e}, replay "
+          f"bitwise equal to eager: {same}); step grad rel L2 (worst frame) "
           f"{np.max(e_step, 0)}; train update rel L2 {np.max(e_train, 0)}")
+    assert same
     assert err <= IMG_TOL
     assert np.max(e_step) <= GRAD_TOL
     assert np.max(e_train) <= GRAD_TOL
