@@ -297,6 +297,20 @@ int pbr_autotune(pbr_ctx *ctx, const pbr_points *scenes, int32_t n_scenes,
                  const int32_t *scene_of_view, const pbr_camera *cams, int32_t n_cams,
                  pbr_render_opts *opts, int32_t mode, int32_t reps, double *ms_out,
                  int32_t *n_candidates, pbr_stream_t stream);
+/* The autotuner's cache on disk (host only, no device work).
+ * pbr_autotune_save writes every cached shape class and its schedule to
+ * `path` (UTF-8 JSON: {"format": "pbr-autotune-1", "classes": [{"views",
+ * "log2_pixels", "log2_point_views", "degrees", "mode", "tile_w", "tile_h",
+ * "batch_depth", "persistent"}, ...]}, integers), through a temporary file
+ * renamed over `path`.  pbr_autotune_load merges such a file into the
+ * context's cache (its entries replace cached ones of the same class) and
+ * reports the number of entries in *n_loaded (nullable).  The file is read
+ * whole and checked before the cache changes: PBR_ERR_NOT_FOUND if it
+ * cannot be opened, PBR_ERR_INVALID_ARG if it is not such a file or holds
+ * a schedule pbr_render_forward would reject; the cache is then unchanged.
+ * Not thread-safe against a concurrent pbr_autotune on the same context. */
+int pbr_autotune_save(const pbr_ctx *ctx, const char *path);
+int pbr_autotune_load(pbr_ctx *ctx, const char *path, int32_t *n_loaded);
 
 /* ---------------------------------------------------------- training step */
 /* Optimiser settings of the training step (Sec. 3.3: per-group learning

@@ -13,8 +13,10 @@
 // pbr_graph_replan re-plans and re-captures.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <map>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -645,5 +647,130 @@ extern "C" int pbr_autotune(pbr_ctx *c, const pbr_points *scenes, int32_t n_scen
     *opts = best_o;
     c->tuned[key] = {best_o.tile_w, best_o.tile_h, best_o.batch_depth, best_o.persistent};
     if (n_candidates) *n_candidates = idx;
+    return PBR_OK;
+}
+
+// ------------------------------------------------- autotuner cache on disk
+// One JSON object: {"format": "pbr-autotune-1", "classes": [{...}, ...]},
+// one object per shape class with the integer fields of kTuneFields.
+namespace {
+
+const char *const kTuneFields[9] = {"views",  "log2_pixels", "log2_point_views",
+                                    "degrees", "mode",        "tile_w",
+                                    "tile_h",  "batch_depth", "persistent"};
+
+// Integer value of "name": inside [b, e); false if absent or malformed.
+bool json_int_field(const char *b, const char *e, const char *name, int64_t &out)
+{
+    const size_t n = std::strlen(name);
+    for (const char *p = b; p + n + 2 < e; ++p) {
+        if (p[0] != '"' || std::strncmp(p + 1, name, n) != 0 || p[n + 1] != '"') continue;
+        const char *q = p + n + 2;
+        while (q < e && (*q == ' ' || *q == '\t' || *q == '\n' || *q == '\r')) ++q;
+        if (q >= e || *q != ':') return false;
+        ++q;
+        while (q < e && (*q == ' ' || *q == '\t' || *q == '\n' || *q == '\r')) ++q;
+        bool neg = false;
+        if (q < e && *q == '-') {
+            neg = true;
+            ++q;
+        }
+        if (q >= e || *q < '0' || *q > '9') return false;
+        int64_t v = 0;
+        while (q < e && *q >= '0' && *q <= '9') {
+            if (v > (INT64_MAX - 9) / 10) return false;
+            v = v * 10 + (*q++ - '0');
+        }
+        out = neg ? -v : v;
+        return true;
+    }
+    return false;
+}
+
+} // namespace
+
+extern "C" int pbr_autotune_save(const pbr_ctx *c, const char *path)
+{
+    if (!c || !path) return set_error(PBR_ERR_INVALID_ARG, "pbr_autotune_save: NULL argument");
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = std::fopen(tmp.c_str(), "w");
+    if (!f) return set_error(PBR_ERR_INVALID_ARG, "cannot write %s", tmp.c_str());
+    std::fprintf(f, "{\"format\": \"pbr-autotune-1\", \"classes\": [");
+    bool first = true;
+    for (const auto &kv : c->tuned) {
+        const int64_t v[9] = {std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+                              std::get<3>(kv.first), std::get<4>(kv.first), kv.second[0],
+                              kv.second[1],          kv.second[2],          kv.second[3]};
+        std::fprintf(f, "%s\n  {", first ? "" : ",");
+        for (int k = 0; k < 9; ++k)
+            std::fprintf(f, "%s\"%s\": %lld", k ? ", " : "", kTuneFields[k], (long long)v[k]);
+        std::fprintf(f, "}");
+        first = false;
+    }
+    std::fprintf(f, "\n]}\n");
+    const bool ok = std::fflush(f) == 0 && !std::ferror(f);
+    std::fclose(f);
+    if (!ok || std::rename(tmp.c_str(), path) != 0) {
+        std::remove(tmp.c_str());
+        return set_error(PBR_ERR_INVALID_ARG, "cannot write %s", path);
+    }
+    return PBR_OK;
+}
+
+extern "C" int pbr_autotune_load(pbr_ctx *c, const char *path, int32_t *n_loaded)
+{
+    if (n_loaded) *n_loaded = 0;
+    if (!c || !path) return set_error(PBR_ERR_INVALID_ARG, "pbr_autotune_load: NULL argument");
+    FILE *f = std::fopen(path, "r");
+    if (!f) return set_error(PBR_ERR_NOT_FOUND, "cannot read %s", path);
+    std::string text;
+    char buf[4096];
+    size_t got;
+    while ((got = std::fread(buf, 1, sizeof buf, f)) > 0) {
+        text.append(buf, got);
+        if (text.size() > (64u << 20)) {
+            std::fclose(f);
+            return set_error(PBR_ERR_INVALID_ARG, "%s: larger than 64 MiB", path);
+        }
+    }
+    std::fclose(f);
+    if (text.find("\"pbr-autotune-1\"") == std::string::npos)
+        return set_error(PBR_ERR_INVALID_ARG, "%s: not an autotuner cache", path);
+    const size_t lst = text.find("\"classes\"");
+    if (lst == std::string::npos)
+        return set_error(PBR_ERR_INVALID_ARG, "%s: no \"classes\" list", path);
+    // parse every entry before changing the cache: a bad file changes nothing
+    std::vector<std::pair<std::tuple<int64_t, int64_t, int64_t, int64_t, int64_t>,
+                          std::array<int, 4>>> entries;
+    size_t pos = text.find('[', lst);
+    if (pos == std::string::npos)
+        return set_error(PBR_ERR_INVALID_ARG, "%s: no \"classes\" list", path);
+    for (;;) {
+        const size_t ob = text.find('{', pos), cl = text.find(']', pos);
+        if (ob == std::string::npos || (cl != std::string::npos && cl < ob)) break;
+        const size_t oe = text.find('}', ob);
+        if (oe == std::string::npos)
+            return set_error(PBR_ERR_INVALID_ARG, "%s: unterminated entry", path);
+        int64_t v[9];
+        for (int k = 0; k < 9; ++k)
+            if (!json_int_field(text.data() + ob, text.data() + oe, kTuneFields[k], v[k]))
+                return set_error(PBR_ERR_INVALID_ARG, "%s: entry %zu lacks an integer \"%s\"",
+                                 path, entries.size(), kTuneFields[k]);
+        pbr_render_opts o;
+        pbr_default_opts(&o);
+        o.tile_w = (int32_t)v[5];
+        o.tile_h = (int32_t)v[6];
+        o.batch_depth = (int32_t)v[7];
+        o.persistent = (int32_t)v[8];
+        if (v[5] != o.tile_w || v[6] != o.tile_h || v[7] != o.batch_depth ||
+            (v[8] != 0 && v[8] != 1) || (v[4] != 0 && v[4] != 1) || check_opts(&o) != PBR_OK)
+            return set_error(PBR_ERR_INVALID_ARG, "%s: entry %zu holds an invalid schedule", path,
+                             entries.size());
+        entries.push_back({std::make_tuple(v[0], v[1], v[2], v[3], v[4]),
+                           {(int)v[5], (int)v[6], (int)v[7], (int)v[8]}});
+        pos = oe + 1;
+    }
+    for (const auto &e : entries) c->tuned[e.first] = e.second;
+    if (n_loaded) *n_loaded = (int32_t)entries.size();
     return PBR_OK;
 }

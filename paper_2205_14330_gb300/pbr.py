@@ -22,6 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libpbr.so")
 
 PBR_OK = 0
+PBR_ERR_INVALID_ARG, PBR_ERR_NOT_FOUND = -1, -7
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "CAPACITY", -5: "TIMEOUT",
           -6: "DEVICE_STATUS", -7: "NOT_FOUND", -8: "BUSY"}
 
@@ -138,6 +139,8 @@ def lib():
             L.pbr_autotune.argtypes = [vp, C.POINTER(Points), i32, vp, C.POINTER(Camera), i32,
                                        C.POINTER(Opts), i32, i32, C.POINTER(C.c_double),
                                        C.POINTER(i32), vp]
+            L.pbr_autotune_save.argtypes = [vp, C.c_char_p]
+            L.pbr_autotune_load.argtypes = [vp, C.c_char_p, C.POINTER(i32)]
             L.pbr_serve_start.argtypes = [vp, C.POINTER(Opts), i32, i32]
             L.pbr_serve_stop.argtypes = [vp]
             L.pbr_serve_set_budget.argtypes = [vp, C.c_size_t]
@@ -335,6 +338,17 @@ class Renderer:
         calls = (C.c_longlong * len(STAGES))()
         check(lib().pbr_stage_times(self.ctx, ms, calls, len(STAGES)))
         return {name: (ms[i], calls[i]) for i, name in enumerate(STAGES)}
+
+    def save_tuning(self, path):
+        """Writes the autotuner's cached schedules to a JSON file."""
+        check(lib().pbr_autotune_save(self.ctx, os.fsencode(path)))
+
+    def load_tuning(self, path) -> int:
+        """Merges a file written by save_tuning into the autotuner's cache;
+        returns the number of shape classes it held."""
+        n = C.c_int32()
+        check(lib().pbr_autotune_load(self.ctx, os.fsencode(path), C.byref(n)))
+        return n.value
 
     def forward(self, scenes, cams, opts=None, scene_of_view=None, keep_state=True, out=None):
         """Renders every camera; returns (image [sum H W, 3] fp32 on device, State|None)."""
@@ -577,9 +591,11 @@ TUNE_CANDIDATES = [(t, d, p) for t in ((16, 16), (8, 8), (16, 32))
 
 
 def autotune(renderer, scenes, cams, opts=None, scene_of_view=None, backward=True, reps=2,
-             report=True):
+             report=True, info=None):
     """Times every schedule candidate on this batch and returns (best opts,
-    {(tile, batch_depth, persistent): ms})."""
+    {(tile, batch_depth, persistent): ms}).  Without `report` a shape class
+    already in the renderer's cache returns its schedule untimed; `info`
+    (a dict) receives the number of candidates timed as "n_timed"."""
     scenes = scenes if isinstance(scenes, (list, tuple)) else [scenes]
     opts = opts or default_opts()
     pts = (Points * len(scenes))(*[s.points() for s in scenes])
@@ -592,6 +608,8 @@ def autotune(renderer, scenes, cams, opts=None, scene_of_view=None, backward=Tru
                              C.byref(opts), 1 if backward else 0, int(reps), ms if report else None,
                              C.byref(n), _stream()))
     table = {TUNE_CANDIDATES[i]: ms[i] for i in range(n.value)} if report else {}
+    if info is not None:
+        info["n_timed"] = n.value
     return opts, table
 
 

@@ -5,6 +5,8 @@ gradients and one training update rel L2 1e-3) and reproduce the eager
 path of the same schedule: the forward bit for bit, gradients to the
 backward's atomic-order tolerance.  Different schedules composite the same
 points and agree to fp32 rounding (1e-6)."""
+import json
+
 import numpy as np
 import pytest
 
@@ -231,17 +233,46 @@ def test_graph_follows_in_place_updates_and_replans(env):
     G.close()
 
 
-def test_autotuner_picks_a_timed_candidate(env):
+def test_autotuner_picks_a_timed_candidate(env, tmp_path):
     pbr, R = env
     sc, cams, sov = _batch(pbr, seed=5)
     best, table = pbr.autotune(R, sc, cams, scene_of_view=sov, backward=True, reps=1)
     assert len(table) == pbr.N_TUNE_CANDIDATES
     key = ((best.tile_w, best.tile_h), best.batch_depth, best.persistent)
     assert key in table and table[key] == min(table.values())
+    sched = lambda o: (o.tile_w, o.tile_h, o.batch_depth, o.persistent)  # noqa: E731
     # cached: a second call returns the same choice without timing
-    again, t2 = pbr.autotune(R, sc, cams, scene_of_view=sov, backward=True, report=False)
-    assert (again.tile_w, again.tile_h, again.batch_depth, again.persistent) == \
-        (best.tile_w, best.tile_h, best.batch_depth, best.persistent) and t2 == {}
+    info = {}
+    again, t2 = pbr.autotune(R, sc, cams, scene_of_view=sov, backward=True, report=False,
+                             info=info)
+    assert sched(again) == sched(best) and t2 == {} and info["n_timed"] == 0
+    # the cache through its file: a fresh context that loads it times nothing
+    path = tmp_path / "tuning.json"
+    R.save_tuning(path)
+    data = json.loads(path.read_text())
+    assert data["format"] == "pbr-autotune-1" and len(data["classes"]) >= 1
+    R2 = pbr.Renderer(0)
+    assert R2.load_tuning(path) == len(data["classes"])
+    info = {}
+    loaded, _ = pbr.autotune(R2, sc, cams, scene_of_view=sov, backward=True, report=False,
+                             info=info)
+    assert sched(loaded) == sched(best) and info["n_timed"] == 0
+    # a missing file, a file of another kind and an invalid schedule are
+    # refused and leave the cache as it was
+    with pytest.raises(pbr.PBRError) as ei:
+        R2.load_tuning(tmp_path / "absent.json")
+    assert ei.value.code == pbr.PBR_ERR_NOT_FOUND
+    (tmp_path / "other.json").write_text('{"classes": []}')
+    bad = dict(data["classes"][0], tile_w=12, tile_h=12)
+    (tmp_path / "bad.json").write_text(json.dumps({"format": "pbr-autotune-1",
+                                                   "classes": [data["classes"][0], bad]}))
+    for name in ("other.json", "bad.json"):
+        with pytest.raises(pbr.PBRError) as ei:
+            R2.load_tuning(tmp_path / name)
+        assert ei.value.code == pbr.PBR_ERR_INVALID_ARG
+    R2.save_tuning(tmp_path / "again.json")
+    assert json.loads((tmp_path / "again.json").read_text()) == data
+    R2.close()
     # every candidate renders the same image (to fp32 rounding)
     ref, _ = R.forward(sc, cams, pbr.default_opts(), scene_of_view=sov, keep_state=False)
     img, _ = R.forward(sc, cams, best, scene_of_view=sov, keep_state=False)
