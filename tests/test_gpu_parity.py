@@ -316,6 +316,30 @@ def test_edge_cases(R, sched):
     ref, _, _ = O.render(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"], [cam])
     assert np.abs(img.cpu().numpy() - ref).max() <= IMG_TOL
     st.close()
+    # transparent points (opacity 0) are composited with alpha 0: the image
+    # is the background, T stays 1, the position and SH gradients are 0 and
+    # the opacity gradient is not (it carries the background term); and a
+    # scene of one point
+    bg = (0.2, 0.3, 0.4)
+    for n, op in ((60, 0.0), (1, 0.9)):
+        sc = _small_scene(12 + n, n=n, spread=0.3, r=(0.05, 0.1))
+        sc["opacity"][:] = np.float32(op)
+        img, st, _ = _gpu_render(R, sc, [cam], bg=bg, **sched)
+        ref, T, cnt = O.render(sc["pos"], sc["sh"], sc["opacity"], sc["radius"], sc["deg"],
+                               [cam], bg=bg)
+        assert cnt.sum() > 0
+        assert np.abs(img.cpu().numpy() - ref).max() <= IMG_TOL
+        g = np.random.default_rng(n).normal(size=ref.shape)
+        gpos, gsh, gop = R.backward(st, torch.from_numpy(g.astype(np.float32)).cuda())
+        dpos, dsh, dop = O.backward(sc["pos"], sc["sh"], sc["opacity"], sc["radius"],
+                                    sc["deg"], [cam], g, bg=bg)
+        if op == 0.0:
+            assert np.allclose(ref, bg) and np.all(T == 1.0)
+            assert not gpos.any() and not gsh.any() and np.linalg.norm(dop) > 0
+        for a, b in ((gpos, dpos), (gsh, dsh), (gop, dop)):
+            a = a.cpu().numpy().astype(np.float64).reshape(b.shape)
+            assert np.linalg.norm(a - b) <= GRAD_TOL * max(np.linalg.norm(b), 1e-12)
+        st.close()
     # invalid arguments are rejected, not run
     with pytest.raises(pbr.PBRError):
         _gpu_render(R, sc, [cam], tile=(32, 32))
