@@ -962,8 +962,9 @@ def main():
                 "stage_ms": res["stage_ms"], "roofline": res["roof"], "parity": parity,
                 "alu_peaks_measured": alu,
                 "cpu_baseline": cpu, "e2e": res["e2e"],
-                "gpu_launches": int(res["launches"] // max(1, res["steps"])),
-                "gpu_launches_timed_region": int(res["launches"]), "clocks": res["clk"],
+                "gpu_launches": int(res["launches"]),
+                "gpu_launches_per_step": int(res["launches"] // max(1, res["steps"])),
+                "clocks": res["clk"],
                 "pairs": res["pairs"], "sizes": res["sizes"],
                 "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src}
         print(json.dumps(line))
