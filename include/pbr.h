@@ -211,7 +211,8 @@ int pbr_forward_workspace_size(pbr_ctx *ctx, const pbr_points *scenes, int32_t n
 /* Backward pass (Sec. 3.3) for L with dL/dI = grad_rgb (device, packed like
  * out_rgb).  Gradients are OVERWRITTEN, packed over scenes in scene order:
  * grad_pos [sum_s n_s, 3], grad_sh [sum_s n_s K_s 3], grad_opacity [sum_s n_s]
- * (nullable).  Does not synchronise. */
+ * (nullable); the slices of scenes that no view sees are set to zero.  Does
+ * not synchronise. */
 int pbr_render_backward(pbr_ctx *ctx, pbr_state *state, const float *grad_rgb, float *grad_pos,
                         float *grad_sh, float *grad_opacity, pbr_stream_t stream);
 int pbr_state_free(pbr_ctx *ctx, pbr_state *state);

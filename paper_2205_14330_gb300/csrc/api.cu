@@ -610,6 +610,18 @@ extern "C" int pbr_render_forward(pbr_ctx *c, const pbr_points *scenes, int32_t 
     return PBR_OK;
 }
 
+void pbr::zero_unviewed_grads(const HostLayout &L, float *grad_pos, float *grad_sh,
+                              float *grad_opacity, cudaStream_t s)
+{
+    for (const DevScene &d : L.scenes) {
+        if (d.view_count > 0 || d.n == 0) continue;
+        cudaMemsetAsync(grad_pos + 3 * d.point_base, 0, sizeof(float) * 3 * (size_t)d.n, s);
+        cudaMemsetAsync(grad_sh + d.sh_base, 0, sizeof(float) * 3 * (size_t)d.K * d.n, s);
+        if (grad_opacity)
+            cudaMemsetAsync(grad_opacity + d.point_base, 0, sizeof(float) * (size_t)d.n, s);
+    }
+}
+
 extern "C" int pbr_render_backward(pbr_ctx *c, pbr_state *st, const float *grad_rgb,
                                    float *grad_pos, float *grad_sh, float *grad_opacity,
                                    pbr_stream_t stream)
@@ -636,6 +648,7 @@ extern "C" int pbr_render_backward(pbr_ctx *c, pbr_state *st, const float *grad_
     {
         StageScope t(c, STG_PREPROCESS_BWD, s);
         launch_preprocess_bwd(b, st->dopts, g2d, grad_pos, grad_sh, grad_opacity, s);
+        zero_unviewed_grads(L, grad_pos, grad_sh, grad_opacity, s);
     }
     cudaError_t e = cudaGetLastError();
     dfree(g2d, s);

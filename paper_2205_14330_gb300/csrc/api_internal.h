@@ -56,6 +56,10 @@ int build_layout(const pbr_points *scenes, int32_t n_scenes, const int32_t *scen
 // the stored transmittance list).
 size_t forward_bytes(const HostLayout &L, int64_t n_vis, int64_t n_pairs,
                      const pbr_render_opts *o, int32_t store_depth);
+// Zeroes the gradient slices of the scenes that no view of the layout sees
+// (the point backward runs over the points of viewed scenes only).
+void zero_unviewed_grads(const HostLayout &L, float *grad_pos, float *grad_sh,
+                         float *grad_opacity, cudaStream_t s);
 int dalloc(void **p, size_t bytes, cudaStream_t s);
 void dfree(void *p, cudaStream_t s);
 void serve_shutdown(pbr_ctx *c);

@@ -216,6 +216,7 @@ void enqueue_backward(pbr_graph *g, const float *grad_rgb, cudaStream_t s)
                       g->T_final, g->n_contrib, grad_rgb, g->g2d, nullptr, s,
                       persist ? g->order : nullptr, g->work);
     launch_preprocess_bwd(b, g->dopts, g->g2d, g->grad_pos, g->grad_sh, g->grad_opacity, s);
+    zero_unviewed_grads(L, g->grad_pos, g->grad_sh, g->grad_opacity, s);
 }
 
 // Optimiser update of every scene's parameters from the packed gradients.

@@ -383,15 +383,25 @@ class Renderer:
                                                C.byref(b), C.byref(sb), _stream()))
         return b.value, sb.value
 
-    def backward(self, state: State, grad_rgb, want_opacity=True):
-        """Gradients (packed over the state's scenes) for dL/dimage = grad_rgb."""
+    def backward(self, state: State, grad_rgb, want_opacity=True, out=None):
+        """Gradients (packed over the state's scenes) for dL/dimage = grad_rgb.
+        `out` = (grad_pos [n,3], grad_sh [n_sh], grad_opacity [n] or None):
+        preallocated fp32 device buffers to overwrite."""
         scenes = state.scenes
         dev = f"cuda:{self.device}"
         n_tot = sum(s.n for s in scenes)
         n_sh = sum(s.n * (s.deg + 1) ** 2 * 3 for s in scenes)
-        gpos = torch.empty((n_tot, 3), dtype=torch.float32, device=dev)
-        gsh = torch.empty((n_sh,), dtype=torch.float32, device=dev)
-        gop = torch.empty((n_tot,), dtype=torch.float32, device=dev) if want_opacity else None
+        if out is not None:
+            gpos, gsh, gop = out
+            assert gpos.shape == (n_tot, 3) and gsh.numel() == n_sh and gpos.is_contiguous() \
+                and gsh.is_contiguous() and gpos.dtype == gsh.dtype == torch.float32
+            assert gop is None or (gop.numel() == n_tot and gop.is_contiguous()
+                                   and gop.dtype == torch.float32)
+        else:
+            gpos = torch.empty((n_tot, 3), dtype=torch.float32, device=dev)
+            gsh = torch.empty((n_sh,), dtype=torch.float32, device=dev)
+            gop = (torch.empty((n_tot,), dtype=torch.float32, device=dev) if want_opacity
+                   else None)
         g = grad_rgb.to(dtype=torch.float32).contiguous()
         check(lib().pbr_render_backward(self.ctx, state.handle, _ptr(g), _ptr(gpos), _ptr(gsh),
                                         _ptr(gop) if gop is not None else None, _stream()))

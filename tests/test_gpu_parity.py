@@ -406,6 +406,71 @@ def test_multi_scene_multi_view(R):
     st.close()
 
 
+@pytest.mark.parametrize("sched", [dict(), dict(persistent=1, tile=(16, 32)),
+                                   dict(batch_depth=128)],
+                         ids=["streamed", "persistent-16x32", "staged"])
+def test_batch_with_empty_view_and_empty_scene(R, sched):
+    """A batch holding a view that sees nothing (the camera looks away from
+    its scene), a scene of no points, a view of that scene between views
+    that do see points, and a scene no view sees: every view's image and
+    every scene's gradients against the oracle (the empty parts give the
+    background and zero gradients, the unseen scene zero gradients written
+    over the NaN-filled buffers, and none shifts its neighbours' offsets)."""
+    import torch
+    pbr = _pbr()
+    a = _small_scene(21, n=300, deg=1)
+    b = _small_scene(22, n=200, deg=2)
+    e = dict(pos=np.zeros((0, 3), np.float32), sh=np.zeros((0, 4, 3), np.float32),
+             opacity=np.zeros(0, np.float32), radius=np.zeros(0, np.float32), deg=1)
+    cams = [scenes.camera((0.2, 0.1, 2.3), 48, 40),
+            scenes.camera((0.0, 0.0, 2.5), 40, 24, target=(0.0, 0.0, 6.0)),  # looks away
+            scenes.camera((0.3, 0.2, 2.0), 32, 32),
+            scenes.camera((-1.5, 0.3, 1.6), 41, 33)]
+    sov = [0, 0, 1, 2]
+    u = _small_scene(24, n=70, deg=3)  # no view sees it
+    groups = (a, e, b, u)
+    bg = (0.1, 0.2, 0.3)
+    sc = [pbr.Scene(x["pos"], x["sh"], x["opacity"], x["radius"], x["deg"]) for x in groups]
+    img, st = R.forward(sc, cams, pbr.default_opts(bg=bg, **sched), scene_of_view=sov)
+    got = img.cpu().numpy()
+    offs = np.cumsum([0] + [c["width"] * c["height"] for c in cams])
+    for v, c in enumerate(cams):
+        x = groups[sov[v]]
+        ref, _, cnt = O.render(x["pos"], x["sh"], x["opacity"], x["radius"], x["deg"], [c],
+                               bg=bg)
+        if v in (1, 2):
+            assert cnt.sum() == 0 and np.allclose(ref, bg)
+        err = np.abs(got[offs[v]:offs[v + 1]] - ref).max()
+        assert err <= IMG_TOL, (v, err)
+    g = np.random.default_rng(23).normal(size=got.shape).astype(np.float32)
+    n_tot = sum(len(x["pos"]) for x in groups)
+    n_sh = sum(len(x["pos"]) * (x["deg"] + 1) ** 2 * 3 for x in groups)
+    out = (torch.full((n_tot, 3), float("nan"), device="cuda"),
+           torch.full((n_sh,), float("nan"), device="cuda"),
+           torch.full((n_tot,), float("nan"), device="cuda"))
+    gpos, gsh, gop = R.backward(st, torch.from_numpy(g).cuda(), out=out)
+    gpos, gsh, gop = gpos.cpu().numpy(), gsh.cpu().numpy(), gop.cpu().numpy()
+    assert np.isfinite(gpos).all() and np.isfinite(gsh).all() and np.isfinite(gop).all()
+    pbase = shbase = 0
+    for si, x in enumerate(groups):
+        views = [v for v in range(len(cams)) if sov[v] == si]
+        n, K = len(x["pos"]), (x["deg"] + 1) ** 2
+        if n and not views:
+            assert not gpos[pbase:pbase + n].any() and not gop[pbase:pbase + n].any()
+            assert not gsh[shbase:shbase + n * K * 3].any()
+        elif n:
+            gsel = np.concatenate([g[offs[v]:offs[v + 1]] for v in views])
+            dpos, dsh, dop = O.backward(x["pos"], x["sh"], x["opacity"], x["radius"], x["deg"],
+                                        [cams[v] for v in views], gsel, bg=bg)
+            assert _rel(gpos[pbase:pbase + n], dpos) <= GRAD_TOL
+            assert _rel(gsh[shbase:shbase + n * K * 3].reshape(n, K, 3), dsh) <= GRAD_TOL
+            assert _rel(gop[pbase:pbase + n], dop) <= GRAD_TOL
+        pbase += n
+        shbase += n * K * 3
+    assert pbase == len(gpos) and shbase == len(gsh)
+    st.close()
+
+
 # ----------------------------------------------------------------- backward
 def test_tiny_config_gradients(R):
     """Config: L2 loss against the image of positions jittered by N(0, 0.01).
