@@ -468,6 +468,10 @@ def test_batch_with_empty_view_and_empty_scene(R, sched):
         pbase += n
         shbase += n * K * 3
     assert pbase == len(gpos) and shbase == len(gsh)
+    # without the opacity gradient (a NULL buffer): the same other gradients
+    gpos2, gsh2, gop2 = R.backward(st, torch.from_numpy(g).cuda(), want_opacity=False)
+    assert gop2 is None
+    assert _rel(gpos2.cpu().numpy(), gpos) <= 1e-5 and _rel(gsh2.cpu().numpy(), gsh) <= 1e-5
     st.close()
 
 
