@@ -609,7 +609,8 @@ int pbr_consistency_filter(pbr_ctx *ctx, const pbr_points *in, const pbr_camera 
  * Lea and Flood 2014: output i of stream s is the generator's finaliser of
  * s + (i + 1) 0x9E3779B97F4A7C15) times 2^-24.  With out_sh set, the kept
  * points' SH coefficients ([n, (sh_degree+1)^2, 3], flattened index c) are
- * standard normals by Box-Muller (fp64) on stream seed ^ 0x5DEECE66D,
+ * standard normals by Box-Muller (fp32 logf and sincospif: no decision
+ * depends on them) on stream seed ^ 0x5DEECE66D,
  * pair c / 2 from outputs c - c % 2 and c - c % 2 + 1 (even c: cosine,
  * odd: sine; u1 = (top 24 bits + 1) 2^-24).
  *   out_pos [n_target,3] (device, caller-owned); out_sh nullable.
