@@ -120,7 +120,7 @@ typedef struct {
                               not faster: writing and reading the list costs
                               more than the reciprocal and multiply per
                               composited point it saves (on the 1M-point,
-                              64-view step, 33.9 against 25.1 ms), so callers
+                              64-view step, 34.0 against 24.3 ms), so callers
                               after speed set 1. */
     int32_t store_depth;   /* composited points per pixel whose T is kept in store
                               mode (0 = default 32; at most 255) */
@@ -256,7 +256,8 @@ int pbr_state_stats(pbr_state *state, unsigned long long *out4);
  * when gradient buffers are given, the backward pass and a whole training
  * step (forward, image loss against `target`, backward) -- are captured.
  * Graph phases for pbr_graph_launch: 0 forward (writes out_rgb), 1 backward
- * (reads grad_rgb, needs grad_rgb non-NULL), 2 forward + loss + backward
+ * (reads grad_rgb; with grad_rgb NULL and a target, the dL/dI that the last
+ * phase 2 or 3 replay wrote), 2 forward + loss + backward
  * (needs target; writes the loss to loss_out when non-NULL and gradients to
  * grad_*), 3 full training iteration (after pbr_graph_set_optimizer).
  * The point arrays and output buffers are bound at capture: update their
